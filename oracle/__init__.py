@@ -1,0 +1,198 @@
+"""Oracle for the coupled LBM-MEM method (arXiv 2103.10882).
+
+TEST INFRASTRUCTURE ONLY.  A plain FP64 CPU restatement of the paper's
+method (C++ in this folder, loaded through ctypes) against which the CUDA
+library is checked.  It shares no code with the library.  Only tests/, the
+smoke check in __graft_entry__ and the CPU-baseline leg of bench.py may use it.
+
+Function-level citations are in uniform.cpp; every pin of this oracle is in
+tests/test_oracle_*.py.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("periodic", ctypes.c_int * 3),
+        ("tau", ctypes.c_double),
+        ("magic", ctypes.c_double),
+        ("body_force", ctypes.c_double * 3),
+        ("boundary", ctypes.c_int),
+        ("force_average", ctypes.c_int),
+        ("plain_mem", ctypes.c_int),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        L.orc_create.restype = vp
+        L.orc_create.argtypes = [ctypes.POINTER(OrcParams)]
+        L.orc_destroy.argtypes = [vp]
+        L.orc_add_sphere.restype = ip
+        L.orc_add_sphere.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ip]
+        L.orc_set_particle_velocity.argtypes = [vp, dp, dp]
+        L.orc_set_gravity.argtypes = [vp, dp]
+        L.orc_set_planes.restype = ip
+        L.orc_set_planes.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, dp, dp]
+        L.orc_init_equilibrium.argtypes = [vp, ctypes.c_double, dp, dp]
+        L.orc_set_populations.argtypes = [vp, dp]
+        L.orc_get_populations.argtypes = [vp, dp]
+        L.orc_get_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
+        L.orc_moments.argtypes = [vp, dp, dp]
+        L.orc_step.argtypes = [vp, ip]
+        L.orc_get_links.restype = ctypes.c_int64
+        L.orc_get_links.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), dp,
+                                    ctypes.c_int64]
+        L.orc_get_particle.argtypes = [vp, dp]
+        L.orc_get_history.restype = ctypes.c_int64
+        L.orc_get_history.argtypes = [vp, dp, ctypes.c_int64]
+        L.orc_get_plane_force.argtypes = [vp, dp]
+        L.orc_particle_only_step.argtypes = [vp, dp, dp]
+        L.orc_set_threads.restype = ip
+        L.orc_set_threads.argtypes = [ip]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def set_threads(n: int) -> int:
+    return lib().orc_set_threads(int(n))
+
+
+class UniformSim:
+    """One uniform-grid simulation held by the C++ oracle."""
+
+    def __init__(self, shape, tau, magic=3.0 / 16.0, periodic=(1, 1, 1), body_force=(0.0, 0.0, 0.0),
+                 boundary="cli", force_average=True, plain_mem=False):
+        L = lib()
+        p = OrcParams()
+        p.nx, p.ny, p.nz = (int(v) for v in shape)
+        p.periodic = (ctypes.c_int * 3)(*[int(v) for v in periodic])
+        p.tau = float(tau)
+        p.magic = float(magic)
+        p.body_force = (ctypes.c_double * 3)(*[float(v) for v in body_force])
+        p.boundary = {"cli": 0, "sbb": 1}[boundary]
+        p.force_average = int(bool(force_average))
+        p.plain_mem = int(bool(plain_mem))
+        self.shape = tuple(int(v) for v in shape)
+        self.ncells = self.shape[0] * self.shape[1] * self.shape[2]
+        self._h = L.orc_create(ctypes.byref(p))
+        if not self._h:
+            raise ValueError("oracle rejected the parameters")
+        self._L = L
+
+    def close(self):
+        if self._h:
+            self._L.orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_sphere(self, pos, diameter, density_ratio, cv=0.0, cv_omega=None, fixed=False):
+        if cv_omega is None:
+            cv_omega = cv
+        a, pa = _d(pos)
+        rc = self._L.orc_add_sphere(self._h, pa, float(diameter), float(density_ratio), float(cv),
+                                    float(cv_omega), int(bool(fixed)))
+        if rc != 0:
+            raise ValueError("add_sphere rejected")
+
+    def set_particle_velocity(self, u, w=(0.0, 0.0, 0.0)):
+        a, pa = _d(u)
+        b, pb = _d(w)
+        self._L.orc_set_particle_velocity(self._h, pa, pb)
+
+    def set_gravity(self, g):
+        a, pa = _d(g)
+        self._L.orc_set_gravity(self._h, pa)
+
+    def set_planes(self, axis, lo, hi, v_lo=(0, 0, 0), v_hi=(0, 0, 0)):
+        a, pa = _d(v_lo)
+        b, pb = _d(v_hi)
+        if self._L.orc_set_planes(self._h, int(axis), float(lo), float(hi), pa, pb) != 0:
+            raise ValueError("set_planes rejected")
+
+    def init_equilibrium(self, rho=1.0, u=(0.0, 0.0, 0.0), u_field=None):
+        a, pa = _d(u)
+        if u_field is not None:
+            f, pf = _d(np.asarray(u_field).reshape(3, -1))
+        else:
+            f, pf = None, None
+        self._L.orc_init_equilibrium(self._h, float(rho), pa, pf)
+
+    def set_populations(self, g):
+        a, pa = _d(np.asarray(g).reshape(19, -1))
+        assert a.shape[1] == self.ncells
+        self._L.orc_set_populations(self._h, pa)
+
+    def populations(self):
+        out = np.empty((19, self.ncells), dtype=np.float64)
+        self._L.orc_get_populations(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def flags(self):
+        out = np.empty(self.ncells, dtype=np.uint8)
+        self._L.orc_get_flags(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+        return out
+
+    def moments(self):
+        rho = np.empty(self.ncells)
+        u = np.empty((3, self.ncells))
+        self._L.orc_moments(self._h, rho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return rho, u
+
+    def step(self, n=1):
+        self._L.orc_step(self._h, int(n))
+
+    def links(self):
+        n = self._L.orc_get_links(self._h, None, None, None, 0)
+        cell = np.empty(n, dtype=np.int64)
+        q = np.empty(n, dtype=np.int32)
+        delta = np.empty(n, dtype=np.float64)
+        self._L.orc_get_links(self._h, cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              delta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return cell, q, delta
+
+    def particle(self):
+        out = np.empty(24)
+        self._L.orc_get_particle(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def history(self):
+        n = self._L.orc_get_history(self._h, None, 0)
+        out = np.empty((n, 15))
+        self._L.orc_get_history(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return out
+
+    def plane_force(self):
+        out = np.empty(3)
+        self._L.orc_get_plane_force(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def particle_only_step(self, F, T=(0.0, 0.0, 0.0)):
+        a, pa = _d(F)
+        b, pb = _d(T)
+        self._L.orc_particle_only_step(self._h, pa, pb)
