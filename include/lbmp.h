@@ -1,0 +1,173 @@
+/*
+ * lbmp.h -- C ABI of the GB300 library for the coupled lattice Boltzmann /
+ * momentum exchange method of Werner, Rettinger & Ruede, "Coupling fully
+ * resolved light particles with the Lattice Boltzmann method on adaptively
+ * refined grids" (arXiv 2103.10882).
+ *
+ * One handle holds one simulation on one GPU: a D3Q19 TRT fluid on a
+ * periodic/walled box (Sec. 2.1), one sphere coupled by the momentum exchange
+ * method with the CLI boundary (Sec. 2.3), and the virtual-mass rigid-body
+ * update (Sec. 3.3, Algorithm 1).  All work runs in CUDA kernels on the
+ * stream given in the configuration; nothing falls back to the CPU.
+ *
+ * General rules
+ *   - Every call returns an lbmp_status; nothing throws across the ABI.
+ *   - Units are lattice units of the finest level: dx = dt = rho_0 = 1
+ *     (Sec. 2.1).  Cell (i,j,k) has its centre at (i+1/2, j+1/2, k+1/2).
+ *   - Populations cross the ABI as FP64 deviations g_q = f_q - w_q in the
+ *     layout [q][z][y][x]; q = 0 rest, 1..6 faces (+x,-x,+y,-y,+z,-z),
+ *     7..18 edges (+x+y,-x-y,+x-y,-x+y,+x+z,-x-z,+x-z,-x+z,+y+z,-y-z,+y-z,-y+z).
+ *     The opposite of q >= 1 is q+1 for odd q and q-1 for even q.
+ *   - Host pointers passed in are read during the call only; output buffers
+ *     are owned by the caller.  "cap" arguments give the capacity of an
+ *     output buffer in elements; passing cap = 0 (and out = NULL) returns
+ *     the required size in *n where the call has one.
+ *   - A handle is not thread-safe.  All device work is ordered on
+ *     config.cuda_stream; calls that return host data synchronise it.
+ *   - After a failed call lbmp_last_error() describes the failure.
+ */
+#ifndef LBMP_H
+#define LBMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbmp_handle lbmp_handle;
+
+typedef enum {
+    LBMP_OK = 0,
+    LBMP_ERR_INVALID_ARG = 1,   /* bad size, pointer, parameter or state */
+    LBMP_ERR_OOM = 2,           /* device allocation failed */
+    LBMP_ERR_CUDA = 3,          /* a CUDA call failed (message in lbmp_last_error) */
+    LBMP_ERR_UNSTABLE = 4,      /* NaN/Inf or |u| > 0.3 in the fluid, or a particle moved > 0.5 cell in one step */
+    LBMP_ERR_PARTICLE_NOT_FINEST = 5,
+    LBMP_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    LBMP_ERR_UNSUPPORTED = 7    /* valid request this build does not implement */
+} lbmp_status;
+
+enum { LBMP_PERIODIC = 0, LBMP_NOSLIP = 1 };
+enum { LBMP_FP64 = 0, LBMP_FP32 = 1, LBMP_FP16 = 2 };
+enum { LBMP_CLI = 0, LBMP_SBB = 1 };
+
+/* Optional device allocator (e.g. a framework's caching allocator). Both
+ * NULL: cudaMalloc / cudaFree.  alloc returns NULL on failure. */
+typedef void* (*lbmp_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*lbmp_free_fn)(void* ptr, size_t bytes, void* ctx);
+
+typedef struct {
+    int nx, ny, nz;          /* cells along x, y, z (each >= 1) */
+    int levels;              /* grid levels; 1 = uniform grid */
+    int bc[3];               /* LBMP_PERIODIC or LBMP_NOSLIP per axis (no-slip: bounce-back walls half-way outside) */
+    int precision;           /* population storage: LBMP_FP64, LBMP_FP32 (deviations), LBMP_FP16 (scaled deviations, FP32 math) */
+    double tau;              /* relaxation time of the symmetric part, s+ = 1/tau, nu = (tau - 1/2)/3 (Sec. 2.1) */
+    double magic;            /* TRT magic parameter Lambda (Sec. 2.1); 3/16 by default */
+    int boundary;            /* LBMP_CLI (Sec. 2.3) or LBMP_SBB (delta = 1/2 on every link) */
+    int force_average;       /* 1: average F/T over two steps (Algorithm 1) */
+    int rescale_noneq;       /* refined grids: rescale non-equilibrium parts at level interfaces */
+    int regrid_interval;     /* refined grids: coarse steps between regrids, 0 = manual */
+    int history_capacity;    /* particle history records kept on the device (ring) */
+    int fp16_scale_log2;     /* LBMP_FP16: deviations are stored times 2^fp16_scale_log2 */
+    uintptr_t cuda_stream;   /* cudaStream_t to run on; 0 = legacy default stream */
+    lbmp_alloc_fn alloc;
+    lbmp_free_fn free;
+    void* alloc_ctx;
+} lbmp_config;
+
+/* Fills *cfg with defaults: 32^3 periodic, 1 level, FP32, tau 0.6,
+ * Lambda 3/16, CLI, force averaging on, history 4096, fp16 scale 2^11. */
+lbmp_status lbmp_config_default(lbmp_config* cfg);
+
+/* Creates a simulation: allocates its device memory and initialises the
+ * fluid at rest (rho = 1, u = 0).  On success *out owns everything. */
+lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out);
+/* Frees everything the handle owns. NULL is accepted. */
+lbmp_status lbmp_destroy(lbmp_handle* h);
+
+/* Adds the sphere (Sec. 2.2-2.3): centre pos (lattice units), diameter d_p,
+ * density ratio pi_p = rho_p / rho_f, virtual-mass coefficients C_v and
+ * C_v,omega (Sec. 3.3; 0 gives plain MEM).  Maps it into the grid (solid
+ * flags, boundary links) and zeroes the populations it covers.  One sphere
+ * per handle: a second call returns LBMP_ERR_UNSUPPORTED.  *id receives 0. */
+lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter, double density_ratio,
+                            double cv, double cv_omega, int* id);
+/* Translational and angular velocity of the sphere (the wall velocity the
+ * fluid sees in the next step). */
+lbmp_status lbmp_set_particle_velocity(lbmp_handle* h, int id, const double u[3], const double omega[3]);
+/* fixed != 0 keeps the sphere in place (forces are still computed). */
+lbmp_status lbmp_set_particle_fixed(lbmp_handle* h, int id, int fixed);
+
+/* Galileo number relation (Sec. 3.1, Eq. Ga): u_g = sqrt(|pi_p - 1| g d_p),
+ * Ga = u_g d_p / nu.  Pure host arithmetic: returns nu, |g| and tau. */
+lbmp_status lbmp_ga_parameters(double ga, double u_g, double diameter, double density_ratio,
+                               double* nu, double* g, double* tau);
+/* Applies lbmp_ga_parameters for the handle's sphere: sets tau and gravity
+ * |g| along the unit vector dir (normalised here). */
+lbmp_status lbmp_set_ga(lbmp_handle* h, double ga, double u_g, const double dir[3]);
+lbmp_status lbmp_set_tau(lbmp_handle* h, double tau);
+/* Gravitational acceleration acting on the sphere (F_g = (rho_p - rho_f) g V). */
+lbmp_status lbmp_set_gravity(lbmp_handle* h, const double g[3]);
+/* Body force density acting on the fluid (Guo-type source term). */
+lbmp_status lbmp_set_body_force(lbmp_handle* h, const double f[3]);
+
+/* Equilibrium initialisation of every fluid cell with density rho and
+ * velocity u, or the velocity field u_field ([3][nz][ny][nx] FP64) when
+ * non-NULL; u_field_on_device says whether it is a device or host pointer. */
+lbmp_status lbmp_init_fluid(lbmp_handle* h, double rho, const double u[3], const double* u_field,
+                            int u_field_on_device);
+/* Whole population field in/out as FP64 deviations (host memory, 19*cells). */
+lbmp_status lbmp_set_populations(lbmp_handle* h, const double* g, size_t cap);
+lbmp_status lbmp_get_populations(lbmp_handle* h, double* g, size_t cap);
+
+/* Gathers the populations of n cells (linear indices i + nx*(j + ny*k),
+ * host array) into out[n][19] (FP64 deviations, host memory). */
+lbmp_status lbmp_gather_populations(lbmp_handle* h, const int64_t* cells, size_t n, double* out);
+
+/* Advances n coupled steps (Algorithm 1): stream + collide with CLI and
+ * momentum-exchange forces, force averaging, gravity, virtual force and
+ * Velocity Verlet, then the remap with equilibrium refill.  Asynchronous on
+ * the handle's stream except for a status check every call. */
+lbmp_status lbmp_step(lbmp_handle* h, int n);
+/* Same as lbmp_step but does not read the device status word (fully
+ * asynchronous); lbmp_check_status reads it later. */
+lbmp_status lbmp_step_async(lbmp_handle* h, int n);
+lbmp_status lbmp_check_status(lbmp_handle* h);
+lbmp_status lbmp_synchronize(lbmp_handle* h);
+
+/* Particle record, 24 doubles: F_hyd of the last step [0:3], T_hyd [3:6],
+ * position [6:9], velocity u(t+1/2) [9:12], angular velocity [12:15],
+ * acceleration a_p [15:18], angular acceleration [18:21], total force F_p [21:24]. */
+lbmp_status lbmp_get_particle(lbmp_handle* h, int id, double out[24]);
+/* Per-step history, 15 doubles per step (F_hyd, T_hyd, x_p, u_p, omega_p),
+ * oldest first; at most max_steps records (the last ones kept in the ring). */
+lbmp_status lbmp_get_history(lbmp_handle* h, int id, double* out, int max_steps, int* n);
+
+/* Cell flags (0 fluid, 1 particle solid), one byte per cell. */
+lbmp_status lbmp_get_flags(lbmp_handle* h, uint8_t* out, size_t cap);
+/* Boundary links (x fluid, x + c_q solid) with their wall distance delta_q
+ * (Sec. 2.3); order unspecified.  *n receives the number of links. */
+lbmp_status lbmp_get_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n);
+
+/* Counters: [0] steps, [1] cell updates (MLUPS numerator), [2] kernel
+ * launches, [3] host-to-device bytes, [4] device-to-host bytes copied by
+ * the library since the handle was created. */
+lbmp_status lbmp_get_counters(lbmp_handle* h, int64_t out[5]);
+/* Per-phase timing with CUDA events recorded on the handle's stream
+ * (enable != 0 starts a new measurement, 0 stops recording).  While
+ * enabled every step records events around its stream-collide kernel. */
+lbmp_status lbmp_profile(lbmp_handle* h, int enable);
+/* Results since the last lbmp_profile(h, 1): [0] total ms in the
+ * stream-collide kernel, [1] its launches, [2] total ms of the whole steps,
+ * [3] steps.  Synchronises the stream. */
+lbmp_status lbmp_get_profile(lbmp_handle* h, double out[4]);
+/* Message of the last failure on this handle (or of the last failed create
+ * when h is NULL).  Never NULL. */
+const char* lbmp_last_error(const lbmp_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMP_H */

@@ -1,0 +1,359 @@
+"""GB300 library for the coupled lattice Boltzmann / momentum exchange method
+with virtual-mass correction for light particles (Werner, Rettinger & Ruede,
+arXiv 2103.10882).
+
+The compute path is the CUDA library liblbmp.so (C ABI in include/lbmp.h).
+This module only marshals arguments: the functions named lbmp_* mirror the C
+entry points one to one, and `Simulation` wraps a handle for convenience.
+PyTorch supplies device memory (its caching allocator) and the CUDA stream.
+There is no CPU fallback: without the library or a GPU every call raises.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import LbmpConfig
+
+__all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbmp_destroy", "lbmp_add_sphere",
+           "lbmp_set_particle_velocity", "lbmp_set_particle_fixed", "lbmp_ga_parameters", "lbmp_set_ga",
+           "lbmp_set_tau", "lbmp_set_gravity", "lbmp_set_body_force", "lbmp_init_fluid", "lbmp_set_populations",
+           "lbmp_get_populations", "lbmp_gather_populations", "lbmp_step", "lbmp_step_async", "lbmp_check_status", "lbmp_synchronize",
+           "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
+           "lbmp_profile", "lbmp_get_profile", "lbmp_last_error", "PRECISIONS"]
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
+BC = {"periodic": 0, "noslip": 1}
+BOUNDARY = {"cli": 0, "sbb": 1}
+STATUS = {0: "LBMP_OK", 1: "LBMP_ERR_INVALID_ARG", 2: "LBMP_ERR_OOM", 3: "LBMP_ERR_CUDA", 4: "LBMP_ERR_UNSTABLE",
+          5: "LBMP_ERR_PARTICLE_NOT_FINEST", 6: "LBMP_ERR_TIMEOUT", 7: "LBMP_ERR_UNSUPPORTED"}
+
+
+class LbmpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+
+
+def _lib():
+    return _native.load()
+
+
+def _dp(a):
+    return a.ctypes.data_as(_native.c_double_p)
+
+
+def _vec3(v):
+    return np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3))
+
+
+def _check(h, rc):
+    if rc != 0:
+        msg = _lib().lbmp_last_error(h)
+        raise LbmpError(rc, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------- C ABI mirror
+def lbmp_config_default():
+    cfg = LbmpConfig()
+    _check(None, _lib().lbmp_config_default(ctypes.byref(cfg)))
+    return cfg
+
+
+def lbmp_create(cfg):
+    h = ctypes.c_void_p()
+    _check(None, _lib().lbmp_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def lbmp_destroy(h):
+    _check(h, _lib().lbmp_destroy(h))
+
+
+def lbmp_add_sphere(h, pos, diameter, density_ratio, cv=0.0, cv_omega=None):
+    p = _vec3(pos)
+    pid = ctypes.c_int(-1)
+    cvw = cv if cv_omega is None else cv_omega
+    _check(h, _lib().lbmp_add_sphere(h, _dp(p), float(diameter), float(density_ratio), float(cv), float(cvw),
+                                     ctypes.byref(pid)))
+    return pid.value
+
+
+def lbmp_set_particle_velocity(h, pid, u, omega=(0.0, 0.0, 0.0)):
+    a, b = _vec3(u), _vec3(omega)
+    _check(h, _lib().lbmp_set_particle_velocity(h, int(pid), _dp(a), _dp(b)))
+
+
+def lbmp_set_particle_fixed(h, pid, fixed=True):
+    _check(h, _lib().lbmp_set_particle_fixed(h, int(pid), int(bool(fixed))))
+
+
+def lbmp_ga_parameters(ga, u_g, diameter, density_ratio):
+    nu, g, tau = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(None, _lib().lbmp_ga_parameters(float(ga), float(u_g), float(diameter), float(density_ratio),
+                                           ctypes.byref(nu), ctypes.byref(g), ctypes.byref(tau)))
+    return nu.value, g.value, tau.value
+
+
+def lbmp_set_ga(h, ga, u_g, direction):
+    d = _vec3(direction)
+    _check(h, _lib().lbmp_set_ga(h, float(ga), float(u_g), _dp(d)))
+
+
+def lbmp_set_tau(h, tau):
+    _check(h, _lib().lbmp_set_tau(h, float(tau)))
+
+
+def lbmp_set_gravity(h, g):
+    a = _vec3(g)
+    _check(h, _lib().lbmp_set_gravity(h, _dp(a)))
+
+
+def lbmp_set_body_force(h, f):
+    a = _vec3(f)
+    _check(h, _lib().lbmp_set_body_force(h, _dp(a)))
+
+
+def lbmp_init_fluid(h, rho=1.0, u=(0.0, 0.0, 0.0), u_field=None):
+    """u_field: None, a host array [3, nz, ny, nx] (FP64), or a CUDA tensor of that shape (float64)."""
+    a = _vec3(u)
+    if u_field is None:
+        _check(h, _lib().lbmp_init_fluid(h, float(rho), _dp(a), None, 0))
+    elif hasattr(u_field, "is_cuda") and u_field.is_cuda:
+        import torch
+        t = u_field.to(torch.float64).contiguous()
+        _check(h, _lib().lbmp_init_fluid(h, float(rho), _dp(a), ctypes.c_void_p(t.data_ptr()), 1))
+    else:
+        f = np.ascontiguousarray(np.asarray(u_field, dtype=np.float64))
+        _check(h, _lib().lbmp_init_fluid(h, float(rho), _dp(a), f.ctypes.data_as(ctypes.c_void_p), 0))
+
+
+def lbmp_set_populations(h, g):
+    a = np.ascontiguousarray(np.asarray(g, dtype=np.float64)).reshape(-1)
+    _check(h, _lib().lbmp_set_populations(h, _dp(a), a.size))
+
+
+def lbmp_get_populations(h, ncells):
+    out = np.empty(19 * int(ncells), dtype=np.float64)
+    _check(h, _lib().lbmp_get_populations(h, _dp(out), out.size))
+    return out.reshape(19, -1)
+
+
+def lbmp_gather_populations(h, cells):
+    c = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+    out = np.empty((c.size, 19), dtype=np.float64)
+    _check(h, _lib().lbmp_gather_populations(h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), c.size,
+                                             _dp(out)))
+    return out
+
+
+def lbmp_step(h, n=1):
+    _check(h, _lib().lbmp_step(h, int(n)))
+
+
+def lbmp_step_async(h, n=1):
+    _check(h, _lib().lbmp_step_async(h, int(n)))
+
+
+def lbmp_check_status(h):
+    _check(h, _lib().lbmp_check_status(h))
+
+
+def lbmp_synchronize(h):
+    _check(h, _lib().lbmp_synchronize(h))
+
+
+def lbmp_get_particle(h, pid=0):
+    out = np.empty(24, dtype=np.float64)
+    _check(h, _lib().lbmp_get_particle(h, int(pid), _dp(out)))
+    return out
+
+
+def lbmp_get_history(h, pid=0, max_steps=None):
+    n = ctypes.c_int(0)
+    _check(h, _lib().lbmp_get_history(h, int(pid), None, 0, ctypes.byref(n)))
+    m = n.value if max_steps is None else min(n.value, int(max_steps))
+    out = np.empty((max(m, 0), 15), dtype=np.float64)
+    if m > 0:
+        _check(h, _lib().lbmp_get_history(h, int(pid), _dp(out), m, ctypes.byref(n)))
+    return out[: n.value]
+
+
+def lbmp_get_flags(h, ncells):
+    out = np.empty(int(ncells), dtype=np.uint8)
+    _check(h, _lib().lbmp_get_flags(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), out.size))
+    return out
+
+
+def lbmp_get_links(h):
+    n = ctypes.c_size_t(0)
+    _check(h, _lib().lbmp_get_links(h, None, None, None, 0, ctypes.byref(n)))
+    m = n.value
+    cell = np.empty(m, dtype=np.int64)
+    q = np.empty(m, dtype=np.int32)
+    delta = np.empty(m, dtype=np.float64)
+    if m:
+        _check(h, _lib().lbmp_get_links(h, cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(delta), m,
+                                        ctypes.byref(n)))
+    return cell, q, delta
+
+
+def lbmp_get_counters(h):
+    out = (ctypes.c_int64 * 5)()
+    _check(h, _lib().lbmp_get_counters(h, out))
+    return tuple(out)
+
+
+def lbmp_profile(h, enable=True):
+    _check(h, _lib().lbmp_profile(h, int(bool(enable))))
+
+
+def lbmp_get_profile(h):
+    out = np.zeros(4, dtype=np.float64)
+    _check(h, _lib().lbmp_get_profile(h, _dp(out)))
+    return out
+
+
+def lbmp_last_error(h=None):
+    m = _lib().lbmp_last_error(h)
+    return m.decode() if m else ""
+
+
+# ------------------------------------------------------------ convenience
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device, stream):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _alloc(nbytes, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, ctx):
+            try:
+                torch.cuda.caching_allocator_delete(ptr)
+            except Exception:
+                pass
+
+        self.alloc = _native.ALLOC_FN(_alloc)
+        self.free = _native.FREE_FN(_free)
+
+
+class Simulation:
+    """One coupled LBM-MEM simulation on the current CUDA device."""
+
+    def __init__(self, shape, precision="fp32", tau=0.6, magic=3.0 / 16.0, bc=("periodic",) * 3, boundary="cli",
+                 force_average=True, history_capacity=4096, fp16_scale_log2=11, stream=None,
+                 torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise LbmpError(3, "no CUDA device: this library has no CPU path")
+        cfg = lbmp_config_default()
+        cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
+        cfg.levels = 1
+        cfg.bc = (ctypes.c_int * 3)(*[BC[b] for b in bc])
+        cfg.precision = PRECISIONS[precision]
+        cfg.tau = float(tau)
+        cfg.magic = float(magic)
+        cfg.boundary = BOUNDARY[boundary]
+        cfg.force_average = int(bool(force_average))
+        cfg.history_capacity = int(history_capacity)
+        cfg.fp16_scale_log2 = int(fp16_scale_log2)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self._allocator = None
+        if torch_allocator:
+            self._allocator = _TorchAllocator(torch.cuda.current_device(), self.stream)
+            cfg.alloc = self._allocator.alloc
+            cfg.free = self._allocator.free
+        self.shape = tuple(int(v) for v in shape)
+        self.ncells = self.shape[0] * self.shape[1] * self.shape[2]
+        self.precision = precision
+        self.h = lbmp_create(cfg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbmp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_sphere(self, pos, diameter, density_ratio, cv=0.0, cv_omega=None):
+        return lbmp_add_sphere(self.h, pos, diameter, density_ratio, cv, cv_omega)
+
+    def set_particle_velocity(self, u, omega=(0.0, 0.0, 0.0)):
+        lbmp_set_particle_velocity(self.h, 0, u, omega)
+
+    def set_fixed(self, fixed=True):
+        lbmp_set_particle_fixed(self.h, 0, fixed)
+
+    def set_ga(self, ga, u_g=0.01, direction=(0.0, 0.0, -1.0)):
+        lbmp_set_ga(self.h, ga, u_g, direction)
+
+    def set_tau(self, tau):
+        lbmp_set_tau(self.h, tau)
+
+    def set_gravity(self, g):
+        lbmp_set_gravity(self.h, g)
+
+    def set_body_force(self, f):
+        lbmp_set_body_force(self.h, f)
+
+    def init_fluid(self, rho=1.0, u=(0.0, 0.0, 0.0), u_field=None):
+        lbmp_init_fluid(self.h, rho, u, u_field)
+
+    def set_populations(self, g):
+        lbmp_set_populations(self.h, g)
+
+    def populations(self):
+        return lbmp_get_populations(self.h, self.ncells)
+
+    def gather(self, cells):
+        """Populations of the given cells, shape [len(cells), 19]."""
+        return lbmp_gather_populations(self.h, cells)
+
+    def step(self, n=1):
+        lbmp_step(self.h, n)
+
+    def step_async(self, n=1):
+        lbmp_step_async(self.h, n)
+
+    def check(self):
+        lbmp_check_status(self.h)
+
+    def synchronize(self):
+        lbmp_synchronize(self.h)
+
+    def particle(self):
+        return lbmp_get_particle(self.h, 0)
+
+    def history(self, max_steps=None):
+        return lbmp_get_history(self.h, 0, max_steps)
+
+    def flags(self):
+        return lbmp_get_flags(self.h, self.ncells)
+
+    def links(self):
+        return lbmp_get_links(self.h)
+
+    def counters(self):
+        """(steps, cell updates, kernel launches, h2d bytes, d2h bytes)."""
+        return lbmp_get_counters(self.h)
+
+    def profile(self, enable=True):
+        lbmp_profile(self.h, enable)
+
+    def profile_result(self):
+        """(stream-collide ms total, its launches, step ms total, steps)."""
+        return lbmp_get_profile(self.h)

@@ -1,0 +1,723 @@
+// Host side of the C ABI declared in include/lbmp.h: handle management,
+// parameter conversion and the per-step launch sequence of Algorithm 1.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace lbmp;
+
+struct lbmp_handle {
+    lbmp_config cfg;
+    GridDesc G;
+    cudaStream_t stream = nullptr;
+    void* pops[2] = {nullptr, nullptr};
+    int cur = 0;                         // pops[cur] holds the post-collision field
+    uint8_t* flags[2] = {nullptr, nullptr};
+    int fcur = 0;                        // flags[fcur] are the flags of pops[cur]
+    int* list = nullptr;                 // boundary cells
+    int* count = nullptr;
+    int list_cap = 0;
+    double* partials = nullptr;
+    int partial_blocks = 0;
+    ParticleState* d_ps = nullptr;
+    ParticleState h_ps;                  // host copy of the parameters
+    double* history = nullptr;
+    int* status = nullptr;
+    BoxDesc box;
+    bool has_particle = false;
+    double tau = 0.6, magic = 3.0 / 16.0;
+    double body_force[3] = {0, 0, 0};
+    long long steps = 0, updates = 0, launches = 0, h2d = 0, d2h = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;    // events of the current measurement, 3 per step
+    size_t ev_used = 0;
+    std::vector<std::pair<void*, size_t>> allocations;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+size_t elem_size(int prec) { return prec == LBMP_FP64 ? 8 : (prec == LBMP_FP32 ? 4 : 2); }
+
+lbmp_status fail(lbmp_handle* h, lbmp_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+lbmp_status cuda_fail(lbmp_handle* h, cudaError_t e, const char* where) {
+    return fail(h, LBMP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LBMP_CK(h, call)                                          \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);  \
+    } while (0)
+
+void* dev_alloc(lbmp_handle* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (h->cfg.alloc) {
+        p = h->cfg.alloc(bytes, h->cfg.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) h->allocations.emplace_back(p, bytes);
+    return p;
+}
+
+void dev_free(lbmp_handle* h, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->allocations.size(); ++i) {
+        if (h->allocations[i].first == p) {
+            if (h->cfg.free) h->cfg.free(p, h->allocations[i].second, h->cfg.alloc_ctx);
+            else cudaFree(p);
+            h->allocations.erase(h->allocations.begin() + (long)i);
+            return;
+        }
+    }
+}
+
+// s- from the magic parameter: Lambda = (1/s+ - 1/2)(1/s- - 1/2)  (Sec. 2.1)
+void relaxation_rates(double tau, double magic, double* sp, double* sm) {
+    *sp = 1.0 / tau;
+    *sm = 1.0 / (0.5 + magic / (tau - 0.5));
+}
+
+template <typename A>
+CollideParams<A> collide_params(const lbmp_handle* h) {
+    CollideParams<A> p;
+    double sp, sm;
+    relaxation_rates(h->tau, h->magic, &sp, &sm);
+    p.sp = (A)sp;
+    p.sm = (A)sm;
+    for (int a = 0; a < 3; ++a) p.F[a] = (A)h->body_force[a];
+    p.forced = (h->body_force[0] != 0.0 || h->body_force[1] != 0.0 || h->body_force[2] != 0.0) ? 1 : 0;
+    if (h->cfg.precision == LBMP_FP16) {
+        p.scale = (A)std::ldexp(1.0, h->cfg.fp16_scale_log2);
+        p.inv_scale = (A)std::ldexp(1.0, -h->cfg.fp16_scale_log2);
+    } else {
+        p.scale = (A)1;
+        p.inv_scale = (A)1;
+    }
+    return p;
+}
+
+double fp16_scale(const lbmp_handle* h, bool inverse) {
+    if (h->cfg.precision != LBMP_FP16) return 1.0;
+    return std::ldexp(1.0, inverse ? -h->cfg.fp16_scale_log2 : h->cfg.fp16_scale_log2);
+}
+
+// Dispatch on the storage type.
+template <typename F>
+void with_storage(int prec, F&& f) {
+    if (prec == LBMP_FP64) f((double*)nullptr);
+    else if (prec == LBMP_FP32) f((float*)nullptr);
+    else f((__half*)nullptr);
+}
+
+cudaEvent_t next_event(lbmp_handle* h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+void record(lbmp_handle* h) {
+    if (!h->profiling) return;
+    cudaEvent_t e = next_event(h);
+    if (e) cudaEventRecord(e, h->stream);
+}
+
+// One coupled step (Algorithm 1) on the handle's stream.
+void enqueue_step(lbmp_handle* h) {
+    const int prec = h->cfg.precision;
+    record(h);
+    with_storage(prec, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using A = typename Store<S>::A;
+        const S* src = (const S*)h->pops[h->cur];
+        S* dst = (S*)h->pops[1 - h->cur];
+        const CollideParams<A> p = collide_params<A>(h);
+        // 1. stream + collide every cell (LBM step)
+        launch_bulk<S>(src, dst, h->G, p, h->status, h->stream);
+        record(h);
+        h->launches += 1;
+        if (h->has_particle) {
+            // 2. cells next to the sphere: CLI links + momentum-exchange force partials
+            int nb = 0;
+            launch_boundary<S>(src, dst, h->flags[h->fcur], h->list, h->count, h->list_cap, h->G, p, h->d_ps,
+                               h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials, &nb, h->status, h->stream);
+            // 3. force average, gravity, virtual mass, Velocity Verlet
+            launch_particle_update(h->d_ps, h->partials, nb, h->G, h->history, h->cfg.history_capacity, h->status,
+                                   h->stream);
+            // 4. remap: new flags in the box, refill/zero, new boundary list
+            uint8_t* fnext = h->flags[1 - h->fcur];
+            launch_flags_box(fnext, h->G, h->box, h->d_ps, h->stream);
+            launch_refill<S>(dst, h->flags[h->fcur], fnext, h->G, h->box, h->d_ps, (A)fp16_scale(h, false),
+                             (A)fp16_scale(h, true), h->stream);
+            launch_build_links(fnext, h->G, h->box, h->d_ps, h->list, h->count, h->list_cap, h->status,
+                               h->stream);
+            h->fcur = 1 - h->fcur;
+            h->launches += 5;
+        }
+    });
+    record(h);
+    h->cur = 1 - h->cur;
+    h->steps += 1;
+    h->updates += h->G.n;
+}
+
+lbmp_status read_status(lbmp_handle* h) {
+    int st = 0;
+    LBMP_CK(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    h->d2h += sizeof(int);
+    if (st != 0) {
+        int zero = 0;
+        LBMP_CK(h, cudaMemcpyAsync(h->status, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        LBMP_CK(h, cudaStreamSynchronize(h->stream));
+        std::string m = "device status:";
+        if (st & STATUS_UNSTABLE_FLUID) m += " fluid velocity NaN/Inf or |u|^2 > 0.09;";
+        if (st & STATUS_PARTICLE_JUMP) m += " particle moved more than 0.5 cell in one step;";
+        if (st & STATUS_LINK_OVERFLOW) {
+            m += " boundary list overflow;";
+            return fail(h, LBMP_ERR_INVALID_ARG, m);
+        }
+        return fail(h, LBMP_ERR_UNSTABLE, m);
+    }
+    return LBMP_OK;
+}
+
+lbmp_status upload_particle(lbmp_handle* h) {
+    LBMP_CK(h, cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice, h->stream));
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    h->h2d += sizeof(ParticleState);
+    return LBMP_OK;
+}
+
+lbmp_status download_particle(lbmp_handle* h) {
+    LBMP_CK(h, cudaMemcpyAsync(&h->h_ps, h->d_ps, sizeof(ParticleState), cudaMemcpyDeviceToHost, h->stream));
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    h->d2h += sizeof(ParticleState);
+    return LBMP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbmp_status lbmp_config_default(lbmp_config* c) {
+    if (!c) return LBMP_ERR_INVALID_ARG;
+    std::memset(c, 0, sizeof(*c));
+    c->nx = c->ny = c->nz = 32;
+    c->levels = 1;
+    c->bc[0] = c->bc[1] = c->bc[2] = LBMP_PERIODIC;
+    c->precision = LBMP_FP32;
+    c->tau = 0.6;
+    c->magic = 3.0 / 16.0;
+    c->boundary = LBMP_CLI;
+    c->force_average = 1;
+    c->rescale_noneq = 1;
+    c->regrid_interval = 0;
+    c->history_capacity = 4096;
+    c->fp16_scale_log2 = 11;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
+    if (!cfg || !out) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: NULL argument");
+    *out = nullptr;
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1)
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: grid extents must be >= 1");
+    const long long n = (long long)cfg->nx * cfg->ny * cfg->nz;
+    if (n >= (1LL << 31)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: more than 2^31 - 1 cells");
+    if (cfg->nz > 65535) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: nz > 65535");
+    if (cfg->levels != 1)
+        return fail(nullptr, LBMP_ERR_UNSUPPORTED, "lbmp_create: refined hierarchies use lbmp_amr_create");
+    if (cfg->precision < LBMP_FP64 || cfg->precision > LBMP_FP16)
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown precision");
+    if (!(cfg->tau > 0.5)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: tau must exceed 1/2");
+    if (!(cfg->magic > 0.0)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: magic parameter must be > 0");
+    if (cfg->boundary != LBMP_CLI && cfg->boundary != LBMP_SBB)
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown boundary scheme");
+    for (int a = 0; a < 3; ++a)
+        if (cfg->bc[a] != LBMP_PERIODIC && cfg->bc[a] != LBMP_NOSLIP)
+            return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown boundary condition");
+    if (cfg->history_capacity < 0) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: history < 0");
+    if (cfg->precision == LBMP_FP16 && (cfg->fp16_scale_log2 < 0 || cfg->fp16_scale_log2 > 20))
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: fp16_scale_log2 outside [0, 20]");
+    if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: give both alloc and free, or neither");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(nullptr, LBMP_ERR_CUDA, "lbmp_create: no CUDA device");
+    }
+    lbmp_handle* h = new (std::nothrow) lbmp_handle();
+    if (!h) return fail(nullptr, LBMP_ERR_OOM, "lbmp_create: host allocation failed");
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)cfg->cuda_stream;
+    h->G.nx = cfg->nx;
+    h->G.ny = cfg->ny;
+    h->G.nz = cfg->nz;
+    for (int a = 0; a < 3; ++a) h->G.periodic[a] = cfg->bc[a] == LBMP_PERIODIC ? 1 : 0;
+    h->G.n = n;
+    h->tau = cfg->tau;
+    h->magic = cfg->magic;
+    std::memset(&h->h_ps, 0, sizeof(ParticleState));
+    h->h_ps.force_average = cfg->force_average ? 1 : 0;
+
+    const size_t pop_bytes = (size_t)19 * (size_t)n * elem_size(cfg->precision);
+    h->pops[0] = dev_alloc(h, pop_bytes);
+    h->pops[1] = dev_alloc(h, pop_bytes);
+    h->flags[0] = (uint8_t*)dev_alloc(h, (size_t)n);
+    h->flags[1] = (uint8_t*)dev_alloc(h, (size_t)n);
+    h->d_ps = (ParticleState*)dev_alloc(h, sizeof(ParticleState));
+    h->status = (int*)dev_alloc(h, sizeof(int));
+    h->count = (int*)dev_alloc(h, sizeof(int));
+    h->history = (double*)dev_alloc(h, sizeof(double) * 15 * (size_t)std::max(1, cfg->history_capacity));
+    if (!h->pops[0] || !h->pops[1] || !h->flags[0] || !h->flags[1] || !h->d_ps || !h->status || !h->count ||
+        !h->history) {
+        lbmp_destroy(h);
+        return fail(nullptr, LBMP_ERR_OOM, "lbmp_create: device allocation failed");
+    }
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pops[0], 0, pop_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pops[1], 0, pop_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags[0], 0, (size_t)n, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags[1], 0, (size_t)n, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice,
+                                              h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        std::string m = std::string("lbmp_create: ") + cudaGetErrorString(e);
+        lbmp_destroy(h);
+        return fail(nullptr, LBMP_ERR_CUDA, m);
+    }
+    *out = h;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_destroy(lbmp_handle* h) {
+    if (!h) return LBMP_OK;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+    while (!h->allocations.empty()) dev_free(h, h->allocations.back().first);
+    delete h;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter, double density_ratio, double cv,
+                            double cv_omega, int* id) {
+    if (!h || !pos) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_add_sphere: NULL argument");
+    if (h->has_particle) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_add_sphere: one sphere per handle");
+    if (!(diameter > 0.0) || !(density_ratio > 0.0) || cv < 0.0 || cv_omega < 0.0)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_add_sphere: diameter and density ratio must be > 0, C_v >= 0");
+    const int n3[3] = {h->G.nx, h->G.ny, h->G.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (!(pos[a] >= 0.0 && pos[a] <= (double)n3[a]))
+            return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_add_sphere: centre outside the domain");
+        if (diameter + 4.0 > (double)n3[a])
+            return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_add_sphere: sphere (plus 2 cells) does not fit the domain");
+    }
+    ParticleState& P = h->h_ps;
+    for (int a = 0; a < 3; ++a) P.x[a] = pos[a];
+    P.D = diameter;
+    P.r = 0.5 * diameter;
+    P.rho_p = density_ratio;
+    P.cv = cv;
+    P.cvw = cv_omega;
+    P.V = M_PI * diameter * diameter * diameter / 6.0;
+    P.present = 1;
+    P.force_average = h->cfg.force_average ? 1 : 0;
+    // box around the sphere: half width ceil(r) + 3 cells covers every cell
+    // whose flag or boundary status can change in one step (|dx| < 1/2)
+    BoxDesc& B = h->box;
+    B.R = (int)std::ceil(P.r) + 3;
+    B.cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        B.E[a] = 2 * B.R + 2;
+        if (h->G.periodic[a] && B.E[a] >= n3[a]) B.E[a] = n3[a];
+        B.cells *= B.E[a];
+    }
+    h->list_cap = (int)B.cells;
+    h->list = (int*)dev_alloc(h, sizeof(int) * (size_t)h->list_cap);
+    const int max_blocks = (h->list_cap + 127) / 128;
+    h->partials = (double*)dev_alloc(h, sizeof(double) * 6 * (size_t)max_blocks);
+    if (!h->list || !h->partials) return fail(h, LBMP_ERR_OOM, "lbmp_add_sphere: device allocation failed");
+    lbmp_status s = upload_particle(h);
+    if (s != LBMP_OK) return s;
+    launch_flags_full(h->flags[h->fcur], h->G, h->d_ps, h->stream);
+    launch_flags_full(h->flags[1 - h->fcur], h->G, h->d_ps, h->stream);
+    with_storage(h->cfg.precision, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        launch_zero_solid<S>((S*)h->pops[h->cur], h->flags[h->fcur], h->G, h->stream);
+    });
+    launch_build_links(h->flags[h->fcur], h->G, h->box, h->d_ps, h->list, h->count, h->list_cap, h->status,
+                       h->stream);
+    LBMP_CK(h, cudaGetLastError());
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    h->has_particle = true;
+    if (id) *id = 0;
+    return read_status(h);
+}
+
+lbmp_status lbmp_set_particle_velocity(lbmp_handle* h, int id, const double u[3], const double w[3]) {
+    if (!h || !u || !w) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_velocity: NULL argument");
+    if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_velocity: no such sphere");
+    lbmp_status s = download_particle(h);
+    if (s != LBMP_OK) return s;
+    for (int a = 0; a < 3; ++a) {
+        h->h_ps.u[a] = u[a];
+        h->h_ps.w[a] = w[a];
+    }
+    return upload_particle(h);
+}
+
+lbmp_status lbmp_set_particle_fixed(lbmp_handle* h, int id, int fixed) {
+    if (!h) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_fixed: NULL handle");
+    if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_fixed: no such sphere");
+    lbmp_status s = download_particle(h);
+    if (s != LBMP_OK) return s;
+    h->h_ps.fixed = fixed ? 1 : 0;
+    return upload_particle(h);
+}
+
+lbmp_status lbmp_ga_parameters(double ga, double u_g, double diameter, double density_ratio, double* nu, double* g,
+                               double* tau) {
+    if (!(ga > 0.0) || !(u_g > 0.0) || !(diameter > 0.0) || !(density_ratio > 0.0) || density_ratio == 1.0)
+        return LBMP_ERR_INVALID_ARG;
+    // Ga = u_g d_p / nu, u_g = sqrt(|pi_p - 1| g d_p)   (Sec. 3.1)
+    const double v = u_g * diameter / ga;
+    const double gg = u_g * u_g / (std::fabs(density_ratio - 1.0) * diameter);
+    if (nu) *nu = v;
+    if (g) *g = gg;
+    if (tau) *tau = 3.0 * v + 0.5;   // nu = c_s^2 (tau - 1/2)
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_set_ga(lbmp_handle* h, double ga, double u_g, const double dir[3]) {
+    if (!h || !dir) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_ga: NULL argument");
+    if (!h->has_particle) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_ga: add the sphere first");
+    double nu, g, tau;
+    if (lbmp_ga_parameters(ga, u_g, h->h_ps.D, h->h_ps.rho_p, &nu, &g, &tau) != LBMP_OK)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_ga: invalid Ga, u_g or density ratio == 1");
+    const double norm = std::sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(norm > 0.0)) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_ga: zero direction");
+    const double gv[3] = {g * dir[0] / norm, g * dir[1] / norm, g * dir[2] / norm};
+    lbmp_status s = lbmp_set_tau(h, tau);
+    if (s != LBMP_OK) return s;
+    return lbmp_set_gravity(h, gv);
+}
+
+lbmp_status lbmp_set_tau(lbmp_handle* h, double tau) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (!(tau > 0.5)) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_tau: tau must exceed 1/2");
+    h->tau = tau;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_set_gravity(lbmp_handle* h, const double g[3]) {
+    if (!h || !g) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_gravity: NULL argument");
+    lbmp_status s = download_particle(h);
+    if (s != LBMP_OK) return s;
+    for (int a = 0; a < 3; ++a) h->h_ps.g[a] = g[a];
+    return upload_particle(h);
+}
+
+lbmp_status lbmp_set_body_force(lbmp_handle* h, const double f[3]) {
+    if (!h || !f) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_body_force: NULL argument");
+    for (int a = 0; a < 3; ++a) h->body_force[a] = f[a];
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_init_fluid(lbmp_handle* h, double rho, const double u[3], const double* u_field,
+                            int u_field_on_device) {
+    if (!h || !u) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_init_fluid: NULL argument");
+    const double* dfield = nullptr;
+    double* tmp = nullptr;
+    if (u_field && !u_field_on_device) {
+        tmp = (double*)dev_alloc(h, sizeof(double) * 3 * (size_t)h->G.n);
+        if (!tmp) return fail(h, LBMP_ERR_OOM, "lbmp_init_fluid: staging allocation failed");
+        LBMP_CK(h, cudaMemcpyAsync(tmp, u_field, sizeof(double) * 3 * (size_t)h->G.n, cudaMemcpyHostToDevice,
+                                   h->stream));
+        dfield = tmp;
+    } else if (u_field) {
+        dfield = u_field;
+    }
+    with_storage(h->cfg.precision, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using A = typename Store<S>::A;
+        launch_init_equilibrium<S>((S*)h->pops[h->cur], h->flags[h->fcur], h->G, rho, u, dfield,
+                                   (A)fp16_scale(h, false), h->stream);
+    });
+    LBMP_CK(h, cudaGetLastError());
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    dev_free(h, tmp);
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_set_populations(lbmp_handle* h, const double* g, size_t cap) {
+    if (!h || !g) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_populations: NULL argument");
+    const long long total = 19LL * h->G.n;
+    if ((long long)cap < total) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_populations: cap < 19*cells");
+    const long long chunk = std::min<long long>(total, 1LL << 25);
+    double* tmp = (double*)dev_alloc(h, sizeof(double) * (size_t)chunk);
+    if (!tmp) return fail(h, LBMP_ERR_OOM, "lbmp_set_populations: staging allocation failed");
+    lbmp_status st = LBMP_OK;
+    for (long long off = 0; off < total && st == LBMP_OK; off += chunk) {
+        const long long m = std::min(chunk, total - off);
+        cudaError_t e = cudaMemcpyAsync(tmp, g + off, sizeof(double) * (size_t)m, cudaMemcpyHostToDevice, h->stream);
+        h->h2d += (long long)sizeof(double) * m;
+        if (e != cudaSuccess) {
+            st = cuda_fail(h, e, "lbmp_set_populations");
+            break;
+        }
+        with_storage(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            using A = typename Store<S>::A;
+            launch_from_f64<S>(tmp, (S*)h->pops[h->cur] + off, m, (A)fp16_scale(h, false), h->stream);
+        });
+        e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "lbmp_set_populations");
+    }
+    dev_free(h, tmp);
+    return st;
+}
+
+lbmp_status lbmp_get_populations(lbmp_handle* h, double* g, size_t cap) {
+    if (!h || !g) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_populations: NULL argument");
+    const long long total = 19LL * h->G.n;
+    if ((long long)cap < total) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_populations: cap < 19*cells");
+    const long long chunk = std::min<long long>(total, 1LL << 25);
+    double* tmp = (double*)dev_alloc(h, sizeof(double) * (size_t)chunk);
+    if (!tmp) return fail(h, LBMP_ERR_OOM, "lbmp_get_populations: staging allocation failed");
+    lbmp_status st = LBMP_OK;
+    for (long long off = 0; off < total && st == LBMP_OK; off += chunk) {
+        const long long m = std::min(chunk, total - off);
+        with_storage(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            using A = typename Store<S>::A;
+            launch_to_f64<S>((const S*)h->pops[h->cur] + off, tmp, m, (A)fp16_scale(h, true), h->stream);
+        });
+        cudaError_t e = cudaMemcpyAsync(g + off, tmp, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, h->stream);
+        h->d2h += (long long)sizeof(double) * m;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) st = cuda_fail(h, e, "lbmp_get_populations");
+    }
+    dev_free(h, tmp);
+    return st;
+}
+
+lbmp_status lbmp_gather_populations(lbmp_handle* h, const int64_t* cells, size_t n, double* out) {
+    if (!h || (n > 0 && (!cells || !out))) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_gather_populations: NULL argument");
+    if (n == 0) return LBMP_OK;
+    for (size_t i = 0; i < n; ++i)
+        if (cells[i] < 0 || cells[i] >= h->G.n)
+            return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_gather_populations: cell index out of range");
+    int64_t* dc = (int64_t*)dev_alloc(h, sizeof(int64_t) * n);
+    double* dout = (double*)dev_alloc(h, sizeof(double) * 19 * n);
+    if (!dc || !dout) {
+        dev_free(h, dc);
+        dev_free(h, dout);
+        return fail(h, LBMP_ERR_OOM, "lbmp_gather_populations: staging allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(dc, cells, sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) {
+        with_storage(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            using A = typename Store<S>::A;
+            launch_gather<S>((const S*)h->pops[h->cur], h->G.n, dc, (long long)n, dout, (A)fp16_scale(h, true),
+                             h->stream);
+        });
+        e = cudaMemcpyAsync(out, dout, sizeof(double) * 19 * n, cudaMemcpyDeviceToHost, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, dc);
+    dev_free(h, dout);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmp_gather_populations");
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_step_async(lbmp_handle* h, int n) {
+    if (!h || n < 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_step: bad argument");
+    for (int i = 0; i < n; ++i) enqueue_step(h);
+    LBMP_CK(h, cudaGetLastError());
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_step(lbmp_handle* h, int n) {
+    lbmp_status s = lbmp_step_async(h, n);
+    if (s != LBMP_OK) return s;
+    return read_status(h);
+}
+
+lbmp_status lbmp_check_status(lbmp_handle* h) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    return read_status(h);
+}
+
+lbmp_status lbmp_synchronize(lbmp_handle* h) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_get_particle(lbmp_handle* h, int id, double out[24]) {
+    if (!h || !out) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: NULL argument");
+    if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: no such sphere");
+    lbmp_status s = download_particle(h);
+    if (s != LBMP_OK) return s;
+    const ParticleState& P = h->h_ps;
+    for (int a = 0; a < 3; ++a) {
+        out[a] = P.Fh[a];
+        out[3 + a] = P.Th[a];
+        out[6 + a] = P.x[a];
+        out[9 + a] = P.u[a];
+        out[12 + a] = P.w[a];
+        out[15 + a] = P.a[a];
+        out[18 + a] = P.b[a];
+        out[21 + a] = P.Fp[a];
+    }
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_get_history(lbmp_handle* h, int id, double* out, int max_steps, int* n) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_history: no such sphere");
+    lbmp_status s = download_particle(h);
+    if (s != LBMP_OK) return s;
+    const long long steps = h->h_ps.steps;
+    const int cap = h->cfg.history_capacity;
+    const long long avail = std::min<long long>(steps, cap);
+    if (n) *n = (int)avail;
+    if (!out || max_steps <= 0 || avail == 0) return LBMP_OK;
+    std::vector<double> ring((size_t)cap * 15);
+    LBMP_CK(h, cudaMemcpyAsync(ring.data(), h->history, sizeof(double) * 15 * (size_t)cap, cudaMemcpyDeviceToHost,
+                               h->stream));
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    const long long m = std::min<long long>(avail, max_steps);
+    const long long first = steps - m;   // oldest step returned
+    for (long long i = 0; i < m; ++i) {
+        const long long st = first + i;
+        std::memcpy(out + i * 15, ring.data() + (size_t)(st % cap) * 15, sizeof(double) * 15);
+    }
+    if (n) *n = (int)m;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_get_flags(lbmp_handle* h, uint8_t* out, size_t cap) {
+    if (!h || !out) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_flags: NULL argument");
+    if ((long long)cap < h->G.n) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_flags: cap < cells");
+    LBMP_CK(h, cudaMemcpyAsync(out, h->flags[h->fcur], (size_t)h->G.n, cudaMemcpyDeviceToHost, h->stream));
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_get_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n) {
+    if (!h || !n) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_links: NULL argument");
+    *n = 0;
+    if (!h->has_particle) return LBMP_OK;
+    int cnt = 0;
+    LBMP_CK(h, cudaMemcpyAsync(&cnt, h->count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    if (cnt == 0) return LBMP_OK;
+    int32_t* dq = (int32_t*)dev_alloc(h, sizeof(int32_t) * 18 * (size_t)cnt);
+    double* dd = (double*)dev_alloc(h, sizeof(double) * 18 * (size_t)cnt);
+    if (!dq || !dd) {
+        dev_free(h, dq);
+        dev_free(h, dd);
+        return fail(h, LBMP_ERR_OOM, "lbmp_get_links: staging allocation failed");
+    }
+    launch_export_links(h->flags[h->fcur], h->list, h->count, cnt, h->G, h->d_ps, 1, dq, dd, h->stream);
+    std::vector<int32_t> hq((size_t)cnt * 18);
+    std::vector<double> hd((size_t)cnt * 18);
+    std::vector<int> hl((size_t)cnt);
+    cudaError_t e = cudaMemcpyAsync(hq.data(), dq, sizeof(int32_t) * hq.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), dd, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hl.data(), h->list, sizeof(int) * hl.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_free(h, dq);
+    dev_free(h, dd);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmp_get_links");
+    size_t m = 0;
+    for (int i = 0; i < cnt; ++i)
+        for (int s = 0; s < 18; ++s) {
+            const size_t slot = (size_t)i * 18 + s;
+            if (hq[slot] < 0) continue;
+            if (m < cap) {
+                if (cell) cell[m] = hl[i];
+                if (q) q[m] = hq[slot];
+                if (delta) delta[m] = hd[slot];
+            }
+            ++m;
+        }
+    *n = m;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_get_counters(lbmp_handle* h, int64_t out[5]) {
+    if (!h || !out) return LBMP_ERR_INVALID_ARG;
+    out[0] = h->steps;
+    out[1] = h->updates;
+    out[2] = h->launches;
+    out[3] = h->h2d;
+    out[4] = h->d2h;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_profile(lbmp_handle* h, int enable) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (enable) {
+        LBMP_CK(h, cudaStreamSynchronize(h->stream));
+        h->ev_used = 0;
+    }
+    h->profiling = enable != 0;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_get_profile(lbmp_handle* h, double out[4]) {
+    if (!h || !out) return LBMP_ERR_INVALID_ARG;
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    double bulk = 0.0, total = 0.0;
+    const size_t steps = h->ev_used / 3;
+    for (size_t s = 0; s < steps; ++s) {
+        float a = 0.f, b = 0.f;
+        LBMP_CK(h, cudaEventElapsedTime(&a, h->ev_pool[3 * s], h->ev_pool[3 * s + 1]));
+        LBMP_CK(h, cudaEventElapsedTime(&b, h->ev_pool[3 * s], h->ev_pool[3 * s + 2]));
+        bulk += a;
+        total += b;
+    }
+    out[0] = bulk;
+    out[1] = (double)steps;
+    out[2] = total;
+    out[3] = (double)steps;
+    return LBMP_OK;
+}
+
+const char* lbmp_last_error(const lbmp_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

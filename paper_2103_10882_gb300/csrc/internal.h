@@ -1,0 +1,74 @@
+// Internal declarations shared by the host API and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbmp.h"
+#include "lattice.cuh"
+
+namespace lbmp {
+
+struct GridDesc {
+    int nx, ny, nz;
+    int periodic[3];
+    long long n;   // nx * ny * nz
+};
+
+// Collision parameters in the arithmetic precision A of the storage type.
+template <typename A>
+struct CollideParams {
+    A sp, sm;          // s+ = 1/tau, s- from the magic parameter
+    A F[3];            // fluid body force
+    int forced;
+    A scale, inv_scale;   // FP16 storage scaling (1 otherwise)
+};
+
+// Axis-aligned box of cells around the sphere, fixed extent, origin read
+// from the particle state on the device.
+struct BoxDesc {
+    int R;        // half width in cells
+    int E[3];     // extent per axis (clamped to the domain for periodic axes)
+    long long cells;
+};
+
+// Launchers (uniform.cu).  All are asynchronous on `stream`.
+template <typename S>
+void launch_bulk(const S* src, S* dst, const GridDesc& g, const CollideParams<typename Store<S>::A>& p,
+                 int* status, cudaStream_t stream);
+template <typename S>
+void launch_boundary(const S* src, S* dst, const uint8_t* flags, const int* list, const int* count, int max_cells,
+                     const GridDesc& g, const CollideParams<typename Store<S>::A>& p, const ParticleState* ps,
+                     int cli, double* partials, int* nblocks_out, int* status, cudaStream_t stream);
+void launch_particle_update(ParticleState* ps, const double* partials, int nblocks, const GridDesc& g,
+                            double* history, int hist_cap, int* status, cudaStream_t stream);
+void launch_flags_full(uint8_t* flags, const GridDesc& g, const ParticleState* ps, cudaStream_t stream);
+void launch_flags_box(uint8_t* flags_next, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
+                      cudaStream_t stream);
+template <typename S>
+void launch_refill(S* pops, const uint8_t* flags_cur, const uint8_t* flags_next, const GridDesc& g,
+                   const BoxDesc& b, const ParticleState* ps, typename Store<S>::A scale,
+                   typename Store<S>::A inv_scale, cudaStream_t stream);
+void launch_build_links(const uint8_t* flags, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
+                        int* list, int* count, int capacity, int* status, cudaStream_t stream);
+void launch_export_links(const uint8_t* flags, const int* list, const int* count, int max_cells,
+                         const GridDesc& g, const ParticleState* ps, int cli, int32_t* q_out, double* delta_out,
+                         cudaStream_t stream);
+template <typename S>
+void launch_init_equilibrium(S* pops, const uint8_t* flags, const GridDesc& g, double rho, const double u[3],
+                             const double* u_field, typename Store<S>::A scale, cudaStream_t stream);
+template <typename S>
+void launch_to_f64(const S* pops, double* out, long long count, typename Store<S>::A inv_scale,
+                   cudaStream_t stream);
+template <typename S>
+void launch_from_f64(const double* in, S* pops, long long count, typename Store<S>::A scale, cudaStream_t stream);
+template <typename S>
+void launch_gather(const S* pops, long long ncells, const int64_t* cells, long long n, double* out,
+                   typename Store<S>::A inv_scale, cudaStream_t stream);
+template <typename S>
+void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStream_t stream);
+
+}  // namespace lbmp

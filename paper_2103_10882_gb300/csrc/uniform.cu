@@ -1,0 +1,697 @@
+// Uniform-grid kernels of the coupled step (Algorithm 1):
+//   k_bulk       stream (pull) + TRT collide of every cell         Sec. 2.1, Eq. LBE
+//   k_boundary   re-does the cells next to the sphere with CLI links and
+//                sums the momentum-exchange force/torque in FP64     Sec. 2.3
+//   k_particle   force averaging, gravity, virtual mass, Velocity Verlet   Sec. 2.2, 3.3
+//   k_flags_box, k_refill, k_build_links   remap after the sphere moved    Sec. 2.3
+// Populations are stored as deviations g = f - w in SoA layout [q][z][y][x].
+#include <cuda_fp16.h>
+
+#include "internal.h"
+
+namespace lbmp {
+namespace {
+
+constexpr int BULK_THREADS = 256;
+constexpr int BND_THREADS = 128;
+
+// Source coordinate x - c along one axis; -1 when it leaves through a wall.
+__device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
+    int s = x - c;
+    if (s < 0) return periodic ? s + n : -1;
+    if (s >= n) return periodic ? s - n : -1;
+    return s;
+}
+
+// Minimum-image difference for periodic axes.
+__device__ __forceinline__ double wrap_diff(double d, int n, int periodic) {
+    if (!periodic) return d;
+    double L = (double)n;
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
+// Cell centre inside the closed ball.  Explicit round-to-nearest products and
+// sums (no contraction) so the predicate is evaluated exactly as written.
+__device__ __forceinline__ bool inside_ball(int i, int j, int k, const GridDesc& G, const ParticleState& P) {
+    double dx = wrap_diff(__dsub_rn((double)i + 0.5, P.x[0]), G.nx, G.periodic[0]);
+    double dy = wrap_diff(__dsub_rn((double)j + 0.5, P.x[1]), G.ny, G.periodic[1]);
+    double dz = wrap_diff(__dsub_rn((double)k + 0.5, P.x[2]), G.nz, G.periodic[2]);
+    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 <= __dmul_rn(P.r, P.r);
+}
+
+// Wall distance fraction along c_q from the fluid cell centre (Sec. 2.3):
+// smallest root in (0,1] of |d + s c|^2 = r^2.
+__device__ __forceinline__ double link_delta(const double d[3], int q, double r) {
+    double c0 = cx(q), c1 = cy(q), c2 = cz(q);
+    double cc = c0 * c0 + c1 * c1 + c2 * c2;
+    double dc = d[0] * c0 + d[1] * c1 + d[2] * c2;
+    double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double disc = dc * dc - cc * (dd - r * r);
+    disc = disc < 0.0 ? 0.0 : disc;
+    double s = (-dc - sqrt(disc)) / cc;
+    return s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+}
+
+// TRT collision on deviations (Sec. 2.1, Lambda_b = 1): the symmetric part of
+// each pair relaxes with s+, the antisymmetric part with s-; incompressible
+// equilibrium with rho_0 = 1; optional Guo-type source split the same way.
+template <typename A>
+__device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& P, int* status) {
+    A drho = A(0), jx = A(0), jy = A(0), jz = A(0);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        drho += g[q];
+        if (cx(q) == 1) jx += g[q];
+        if (cx(q) == -1) jx -= g[q];
+        if (cy(q) == 1) jy += g[q];
+        if (cy(q) == -1) jy -= g[q];
+        if (cz(q) == 1) jz += g[q];
+        if (cz(q) == -1) jz -= g[q];
+    }
+    A ux = jx, uy = jy, uz = jz;
+    if (P.forced) {
+        ux += A(0.5) * P.F[0];
+        uy += A(0.5) * P.F[1];
+        uz += A(0.5) * P.F[2];
+    }
+    const A uu = ux * ux + uy * uy + uz * uz;
+    if (!(uu <= A(0.09))) atomicOr(status, STATUS_UNSTABLE_FLUID);
+    const A sp = P.sp, sm = P.sm;
+    {
+        const A e0 = wgt<A>(0) * (drho - A(1.5) * uu);
+        A o = g[0] - sp * (g[0] - e0);
+        if (P.forced) {
+            const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
+            o += (A(1) - A(0.5) * sp) * wgt<A>(0) * (A(-3) * uF);
+        }
+        g[0] = o;
+    }
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {
+        const A cu = A(cx(q)) * ux + A(cy(q)) * uy + A(cz(q)) * uz;
+        const A w = wgt<A>(q);
+        const A ep = w * (drho + A(4.5) * cu * cu - A(1.5) * uu);
+        const A em = w * (A(3) * cu);
+        const A gp = A(0.5) * (g[q] + g[q + 1]);
+        const A gm = A(0.5) * (g[q] - g[q + 1]);
+        const A dp = sp * (gp - ep);
+        const A dm = sm * (gm - em);
+        A a = g[q] - dp - dm;
+        A b = g[q + 1] - dp + dm;
+        if (P.forced) {
+            const A cF = A(cx(q)) * P.F[0] + A(cy(q)) * P.F[1] + A(cz(q)) * P.F[2];
+            const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
+            const A Sp = (A(1) - A(0.5) * sp) * w * (A(9) * cu * cF - A(3) * uF);
+            const A Sm = (A(1) - A(0.5) * sm) * w * (A(3) * cF);
+            a += Sp + Sm;
+            b += Sp - Sm;
+        }
+        g[q] = a;
+        g[q + 1] = b;
+    }
+}
+
+// ------------------------------------------------------------------ bulk
+template <typename S>
+__global__ void __launch_bounds__(BULK_THREADS)
+    k_bulk(const S* __restrict__ src, S* __restrict__ dst, GridDesc G,
+           CollideParams<typename Store<S>::A> P, int* __restrict__ status) {
+    using A = typename Store<S>::A;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= G.nx || y >= G.ny) return;
+    const size_t n = (size_t)G.n;
+    const size_t nx = (size_t)G.nx, nxy = (size_t)G.nx * (size_t)G.ny;
+    const size_t cell = (size_t)x + nx * (size_t)y + nxy * (size_t)z;
+    // source coordinates x - c for c = -1, 0, +1
+    const int xs[3] = {src_coord(x, -1, G.nx, G.periodic[0]), x, src_coord(x, 1, G.nx, G.periodic[0])};
+    const int ys[3] = {src_coord(y, -1, G.ny, G.periodic[1]), y, src_coord(y, 1, G.ny, G.periodic[1])};
+    const int zs[3] = {src_coord(z, -1, G.nz, G.periodic[2]), z, src_coord(z, 1, G.nz, G.periodic[2])};
+    A g[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int sx = xs[cx(q) + 1], sy = ys[cy(q) + 1], sz = zs[cz(q) + 1];
+        if (sx < 0 || sy < 0 || sz < 0)   // stationary no-slip domain wall: bounce-back
+            g[q] = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
+        else
+            g[q] = Store<S>::load(src + (size_t)q * n + (size_t)sx + nx * (size_t)sy + nxy * (size_t)sz,
+                                  P.inv_scale);
+    }
+    trt_collide<A>(g, P, status);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) Store<S>::store(dst + (size_t)q * n + cell, g[q], P.scale);
+}
+
+// -------------------------------------------------------------- boundary
+// One thread per fluid cell that has a solid neighbour.  Recomputes the
+// whole cell update, replacing pulls from solid cells by the CLI rule of
+// Sec. 2.3 and summing the link forces (Galilean-invariant form) in FP64.
+template <typename S>
+__global__ void __launch_bounds__(BND_THREADS)
+    k_boundary(const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ flags,
+               const int* __restrict__ list, const int* __restrict__ count, GridDesc G,
+               CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
+               double* __restrict__ partials, int* __restrict__ status) {
+    using A = typename Store<S>::A;
+    __shared__ double red[6][BND_THREADS / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    if (i < *count) {
+        const int cell = list[i];
+        const size_t n = (size_t)G.n;
+        const size_t nx = (size_t)G.nx, nxy = (size_t)G.nx * (size_t)G.ny;
+        const int x = cell % G.nx;
+        const int y = (cell / G.nx) % G.ny;
+        const int z = cell / (G.nx * G.ny);
+        const int xs[3] = {src_coord(x, -1, G.nx, G.periodic[0]), x, src_coord(x, 1, G.nx, G.periodic[0])};
+        const int ys[3] = {src_coord(y, -1, G.ny, G.periodic[1]), y, src_coord(y, 1, G.ny, G.periodic[1])};
+        const int zs[3] = {src_coord(z, -1, G.nz, G.periodic[2]), z, src_coord(z, 1, G.nz, G.periodic[2])};
+        const ParticleState& Pp = *ps;
+        const double d[3] = {wrap_diff((x + 0.5) - Pp.x[0], G.nx, G.periodic[0]),
+                             wrap_diff((y + 0.5) - Pp.x[1], G.ny, G.periodic[1]),
+                             wrap_diff((z + 0.5) - Pp.x[2], G.nz, G.periodic[2])};
+        A g[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const int sx = xs[cx(q) + 1], sy = ys[cy(q) + 1], sz = zs[cz(q) + 1];
+            if (sx < 0 || sy < 0 || sz < 0) {
+                g[q] = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
+                continue;
+            }
+            const size_t s = (size_t)sx + nx * (size_t)sy + nxy * (size_t)sz;
+            if (q == 0 || flags[s] == 0) {
+                g[q] = Store<S>::load(src + (size_t)q * n + s, P.inv_scale);
+                continue;
+            }
+            // Link: k = opp(q) points from x into the solid; the unknown is
+            // f_q(x, t+1).  The CLI needs the cell x - c_k = x + c_q.
+            const int k = opp(q);
+            const int fx = xs[cx(k) + 1], fy = ys[cy(k) + 1], fz = zs[cz(k) + 1];
+            bool far_ok = fx >= 0 && fy >= 0 && fz >= 0;
+            size_t far = 0;
+            if (far_ok) {
+                far = (size_t)fx + nx * (size_t)fy + nxy * (size_t)fz;
+                far_ok = flags[far] == 0;
+            }
+            double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+            const double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
+            const double alpha = 4.0 / (1.0 + 2.0 * delta);
+            const double arm[3] = {d[0] + delta * cx(k), d[1] + delta * cy(k), d[2] + delta * cz(k)};
+            const double vb[3] = {Pp.u[0] + (Pp.w[1] * arm[2] - Pp.w[2] * arm[1]),
+                                  Pp.u[1] + (Pp.w[2] * arm[0] - Pp.w[0] * arm[2]),
+                                  Pp.u[2] + (Pp.w[0] * arm[1] - Pp.w[1] * arm[0])};
+            const double vc = vb[0] * cx(k) + vb[1] * cy(k) + vb[2] * cz(k);
+            const A gt_k = Store<S>::load(src + (size_t)k * n + cell, P.inv_scale);
+            const A gt_q = Store<S>::load(src + (size_t)q * n + cell, P.inv_scale);
+            const A gt_far = far_ok ? Store<S>::load(src + (size_t)k * n + far, P.inv_scale) : A(0);
+            // CLI on deviations (the w_q parts cancel since w_q = w_qbar):
+            // g_q = gt_k + kappa0 gt_k(x - c_k) - kappa0 gt_q - alpha w_k / c_s^2 (v . c_k)
+            const A gnew = gt_k + A(kappa0) * gt_far - A(kappa0) * gt_q -
+                           A(alpha * 3.0 * wgt<double>(k) * vc);
+            g[q] = gnew;
+            // link force on full populations, FP64: (c_k - v) ft_k - (c_q - v) f_q(t+1)
+            const double ftk = wgt<double>(k) + (double)gt_k;
+            const double fnew = wgt<double>(q) + (double)gnew;
+            const double Fl[3] = {(cx(k) - vb[0]) * ftk - (cx(q) - vb[0]) * fnew,
+                                  (cy(k) - vb[1]) * ftk - (cy(q) - vb[1]) * fnew,
+                                  (cz(k) - vb[2]) * ftk - (cz(q) - vb[2]) * fnew};
+            F[0] += Fl[0];
+            F[1] += Fl[1];
+            F[2] += Fl[2];
+            T[0] += arm[1] * Fl[2] - arm[2] * Fl[1];
+            T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
+            T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
+        }
+        trt_collide<A>(g, P, status);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) Store<S>::store(dst + (size_t)q * n + cell, g[q], P.scale);
+    }
+    // deterministic block reduction of the six sums
+    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) red[c][warp] = v[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int w = 0; w < BND_THREADS / 32; ++w) s += red[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+    }
+}
+
+// -------------------------------------------------------------- particle
+// Sums the per-block partial forces in a fixed order, then Algorithm 1:
+// average over two steps, gravity/buoyancy F_g = (rho_p - rho_f) g V,
+// virtual force/torque from the previous accelerations, and Velocity
+// Verlet (kick-drift-kick) with m = (rho_p + C_v) V, I = 2/5 (rho_p + C_vw) V r^2.
+constexpr int PART_THREADS = 256;
+__global__ void __launch_bounds__(PART_THREADS)
+    k_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials, int nblocks, GridDesc G,
+               double* __restrict__ history, int hist_cap, int* __restrict__ status) {
+    __shared__ double red[6][PART_THREADS];
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += PART_THREADS)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] += partials[(size_t)b * 6 + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) red[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int s = PART_THREADS / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int c = 0; c < 6; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    ParticleState& P = *ps;
+    const double Fh[3] = {red[0][0], red[1][0], red[2][0]};
+    const double Th[3] = {red[3][0], red[4][0], red[5][0]};
+    const double V = P.V, r = P.r;
+    const double m = (P.rho_p + P.cv) * V;
+    const double I = 0.4 * (P.rho_p + P.cvw) * V * r * r;
+    const bool avg = P.force_average && P.steps > 0;
+    double xold[3];
+    for (int a = 0; a < 3; ++a) {
+        const double Fbar = avg ? 0.5 * (Fh[a] + P.Fh_old[a]) : Fh[a];
+        const double Tbar = avg ? 0.5 * (Th[a] + P.Th_old[a]) : Th[a];
+        P.Fh[a] = Fh[a];
+        P.Th[a] = Th[a];
+        P.Fh_old[a] = Fh[a];
+        P.Th_old[a] = Th[a];
+        const double Fg = (P.rho_p - 1.0) * P.g[a] * V;
+        const double Fv = P.cv * V * P.a[a];
+        const double Tv = 0.4 * P.cvw * V * r * r * P.b[a];
+        const double Fp = Fbar + Fg + Fv;
+        const double Tp = Tbar + Tv;
+        P.Fp[a] = Fp;
+        xold[a] = P.x[a];
+        if (!P.fixed) {
+            if (P.steps > 0) {
+                P.u[a] += Fp / (2.0 * m);
+                P.w[a] += Tp / (2.0 * I);
+            }
+            P.a[a] = Fp / m;
+            P.b[a] = Tp / I;
+            P.u[a] += Fp / (2.0 * m);
+            P.w[a] += Tp / (2.0 * I);
+            P.x[a] += P.u[a];
+        } else {
+            P.a[a] = Fp / m;
+            P.b[a] = Tp / I;
+        }
+    }
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (fabs(P.x[a] - xold[a]) > 0.5 || !(fabs(P.u[a]) < 0.5)) atomicOr(status, STATUS_PARTICLE_JUMP);
+        if (G.periodic[a]) {   // keep the centre inside the periodic box
+            const double L = (double)n3[a];
+            if (P.x[a] >= L) P.x[a] -= L;
+            else if (P.x[a] < 0.0) P.x[a] += L;
+        }
+    }
+    if (hist_cap > 0) {
+        double* h = history + (size_t)(P.steps % hist_cap) * 15;
+        for (int a = 0; a < 3; ++a) {
+            h[a] = Fh[a];
+            h[3 + a] = Th[a];
+            h[6 + a] = P.x[a];
+            h[9 + a] = P.u[a];
+            h[12 + a] = P.w[a];
+        }
+    }
+    P.steps += 1;
+}
+
+// ------------------------------------------------------------------ remap
+// Box of cells around the sphere: cell (o + t) for t in [0, E), o from the
+// current centre.  Returns false for cells outside a walled domain.
+__device__ __forceinline__ bool box_cell(long long t, const GridDesc& G, const BoxDesc& B, const ParticleState& P,
+                                         int* ci, int* cj, int* ck) {
+    const int ti = (int)(t % B.E[0]);
+    const int tj = (int)((t / B.E[0]) % B.E[1]);
+    const int tk = (int)(t / ((long long)B.E[0] * B.E[1]));
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    const int tt[3] = {ti, tj, tk};
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+        int o = (B.E[a] >= n3[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
+        int v = o + tt[a];
+        if (v < 0 || v >= n3[a]) {
+            if (!G.periodic[a]) return false;
+            v = ((v % n3[a]) + n3[a]) % n3[a];
+        }
+        c[a] = v;
+    }
+    *ci = c[0];
+    *cj = c[1];
+    *ck = c[2];
+    return true;
+}
+
+__global__ void k_flags_full(uint8_t* __restrict__ flags, GridDesc G, const ParticleState* __restrict__ ps) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= G.n) return;
+    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
+    flags[c] = (ps->present && inside_ball(i, j, k, G, *ps)) ? 1 : 0;
+}
+
+__global__ void k_flags_box(uint8_t* __restrict__ flags_next, GridDesc G, BoxDesc B,
+                            const ParticleState* __restrict__ ps) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.cells) return;
+    const ParticleState P = *ps;
+    int i, j, k;
+    if (!box_cell(t, G, B, P, &i, &j, &k)) return;
+    const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+    flags_next[c] = inside_ball(i, j, k, G, P) ? 1 : 0;
+}
+
+// Cells now solid are zeroed; cells the sphere uncovered are refilled with
+// the equilibrium at the mean density of neighbours fluid before and after,
+// and the rigid-body velocity u_p + omega_p x (x - x_p).
+template <typename S>
+__global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur, const uint8_t* __restrict__ fnext,
+                         GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
+                         typename Store<S>::A scale, typename Store<S>::A inv_scale) {
+    using A = typename Store<S>::A;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.cells) return;
+    const ParticleState P = *ps;
+    int i, j, k;
+    if (!box_cell(t, G, B, P, &i, &j, &k)) return;
+    const size_t n = (size_t)G.n;
+    const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+    if (fnext[c] != 0) {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) Store<S>::store(pops + (size_t)q * n + c, A(0), scale);
+        return;
+    }
+    if (fcur[c] == 0) return;
+    // uncovered cell
+    A rsum = A(0);
+    int cnt = 0;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    for (int q = 1; q < 19; ++q) {
+        int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            if (v[a] < 0 || v[a] >= n3[a]) {
+                if (!G.periodic[a]) ok = false;
+                v[a] = (v[a] + n3[a]) % n3[a];
+            }
+        }
+        if (!ok) continue;
+        const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+        if (fcur[y] != 0 || fnext[y] != 0) continue;
+        A r = A(1);
+        for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + (size_t)p * n + y, inv_scale);
+        rsum += r;
+        cnt += 1;
+    }
+    const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
+    const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, G.periodic[0]),
+                         wrap_diff((j + 0.5) - P.x[1], G.ny, G.periodic[1]),
+                         wrap_diff((k + 0.5) - P.x[2], G.nz, G.periodic[2])};
+    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
+        const A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+        Store<S>::store(pops + (size_t)q * n + c, e, scale);
+    }
+}
+
+// Ordered compaction of the fluid cells with a solid neighbour inside the
+// box (one block; the order is the box traversal order, so it is the same
+// in every run).
+constexpr int LINK_THREADS = 1024;
+__global__ void __launch_bounds__(LINK_THREADS)
+    k_build_links(const uint8_t* __restrict__ flags, GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
+                  int* __restrict__ list, int* __restrict__ count, int capacity, int* __restrict__ status) {
+    __shared__ int warp_sum[LINK_THREADS / 32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const ParticleState P = *ps;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    for (long long t0 = 0; t0 < B.cells; t0 += LINK_THREADS) {
+        const long long t = t0 + threadIdx.x;
+        int is_b = 0;
+        size_t c = 0;
+        int i, j, k;
+        if (t < B.cells && box_cell(t, G, B, P, &i, &j, &k)) {
+            c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+            if (flags[c] == 0) {
+                for (int q = 1; q < 19 && !is_b; ++q) {
+                    int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
+                    bool ok = true;
+                    for (int a = 0; a < 3; ++a) {
+                        if (v[a] < 0 || v[a] >= n3[a]) {
+                            if (!G.periodic[a]) ok = false;
+                            v[a] = (v[a] + n3[a]) % n3[a];
+                        }
+                    }
+                    if (!ok) continue;
+                    const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+                    if (flags[y] != 0) is_b = 1;
+                }
+            }
+        }
+        const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
+        if (lane == 0) warp_sum[warp] = __popc(ballot);
+        __syncthreads();
+        if (threadIdx.x == 0) {   // exclusive prefix over the warps, in place
+            int s = 0;
+            for (int w = 0; w < LINK_THREADS / 32; ++w) {
+                const int v = warp_sum[w];
+                warp_sum[w] = s;
+                s += v;
+            }
+        }
+        __syncthreads();
+        if (is_b) {
+            const int pos = base + warp_sum[warp] + __popc(ballot & ((1u << lane) - 1u));
+            if (pos < capacity) list[pos] = (int)c;
+            else atomicOr(status, STATUS_LINK_OVERFLOW);
+        }
+        __syncthreads();
+        if (threadIdx.x == LINK_THREADS - 1) base += warp_sum[warp] + __popc(ballot);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = base < capacity ? base : capacity;
+}
+
+// Link export for inspection: slot (i*18 + q-1) of the i-th boundary cell
+// holds q and delta_q when x + c_q is solid, q = -1 otherwise.
+__global__ void k_export_links(const uint8_t* __restrict__ flags, const int* __restrict__ list,
+                               const int* __restrict__ count, GridDesc G, const ParticleState* __restrict__ ps,
+                               int32_t* __restrict__ q_out, double* __restrict__ delta_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *count) return;
+    const int cell = list[i];
+    const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
+    const ParticleState& P = *ps;
+    const double d[3] = {wrap_diff((x + 0.5) - P.x[0], G.nx, G.periodic[0]),
+                         wrap_diff((y + 0.5) - P.x[1], G.ny, G.periodic[1]),
+                         wrap_diff((z + 0.5) - P.x[2], G.nz, G.periodic[2])};
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    for (int q = 1; q < 19; ++q) {
+        int v[3] = {x + cx(q), y + cy(q), z + cz(q)};
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+            if (v[a] < 0 || v[a] >= n3[a]) {
+                if (!G.periodic[a]) ok = false;
+                v[a] = (v[a] + n3[a]) % n3[a];
+            }
+        }
+        const size_t slot = (size_t)i * 18 + (q - 1);
+        const size_t yy = ok ? (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]) : 0;
+        if (ok && flags[yy] != 0) {
+            q_out[slot] = q;
+            delta_out[slot] = link_delta(d, q, P.r);
+        } else {
+            q_out[slot] = -1;
+            delta_out[slot] = 0.0;
+        }
+    }
+}
+
+template <typename S>
+__global__ void k_init_eq(S* __restrict__ pops, const uint8_t* __restrict__ flags, GridDesc G, double rho,
+                          double u0, double u1, double u2, const double* __restrict__ ufield,
+                          typename Store<S>::A scale) {
+    using A = typename Store<S>::A;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= G.n) return;
+    const size_t n = (size_t)G.n;
+    const bool fluid = flags == nullptr || flags[c] == 0;
+    double u[3] = {u0, u1, u2};
+    if (ufield) {
+        u[0] = ufield[c];
+        u[1] = ufield[n + c];
+        u[2] = ufield[2 * n + c];
+    }
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int q = 0; q < 19; ++q) {
+        const double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+        const double e = wgt<double>(q) * ((rho - 1.0) + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        Store<S>::store(pops + (size_t)q * n + c, fluid ? A(e) : A(0), scale);
+    }
+}
+
+template <typename S>
+__global__ void k_to_f64(const S* __restrict__ pops, double* __restrict__ out, long long count,
+                         typename Store<S>::A inv_scale) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = (double)Store<S>::load(pops + i, inv_scale);
+}
+
+template <typename S>
+__global__ void k_from_f64(const double* __restrict__ in, S* __restrict__ pops, long long count,
+                           typename Store<S>::A scale) {
+    using A = typename Store<S>::A;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) Store<S>::store(pops + i, (A)in[i], scale);
+}
+
+template <typename S>
+__global__ void k_gather(const S* __restrict__ pops, long long ncells, const int64_t* __restrict__ cells,
+                         long long n, double* __restrict__ out, typename Store<S>::A inv_scale) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * 19) return;
+    const long long i = t / 19;
+    const int q = (int)(t % 19);
+    const long long c = cells[i];
+    out[t] = (c >= 0 && c < ncells) ? (double)Store<S>::load(pops + (size_t)q * ncells + c, inv_scale) : 0.0;
+}
+
+template <typename S>
+__global__ void k_zero_solid(S* __restrict__ pops, const uint8_t* __restrict__ flags, GridDesc G) {
+    using A = typename Store<S>::A;
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= G.n || flags[c] == 0) return;
+    for (int q = 0; q < 19; ++q) Store<S>::store(pops + (size_t)q * G.n + c, A(0), A(1));
+}
+
+inline unsigned blocks_for(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+template <typename S>
+void launch_bulk(const S* src, S* dst, const GridDesc& g, const CollideParams<typename Store<S>::A>& p,
+                 int* status, cudaStream_t stream) {
+    int bx = 32;
+    while (bx < g.nx && bx < 128) bx *= 2;
+    const int by = BULK_THREADS / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
+    k_bulk<S><<<grid, block, 0, stream>>>(src, dst, g, p, status);
+}
+
+template <typename S>
+void launch_boundary(const S* src, S* dst, const uint8_t* flags, const int* list, const int* count, int max_cells,
+                     const GridDesc& g, const CollideParams<typename Store<S>::A>& p, const ParticleState* ps,
+                     int cli, double* partials, int* nblocks_out, int* status, cudaStream_t stream) {
+    const int nb = max_cells > 0 ? (int)blocks_for(max_cells, BND_THREADS) : 1;
+    *nblocks_out = nb;
+    k_boundary<S><<<nb, BND_THREADS, 0, stream>>>(src, dst, flags, list, count, g, p, ps, cli, partials, status);
+}
+
+void launch_particle_update(ParticleState* ps, const double* partials, int nblocks, const GridDesc& g,
+                            double* history, int hist_cap, int* status, cudaStream_t stream) {
+    k_particle<<<1, PART_THREADS, 0, stream>>>(ps, partials, nblocks, g, history, hist_cap, status);
+}
+
+void launch_flags_full(uint8_t* flags, const GridDesc& g, const ParticleState* ps, cudaStream_t stream) {
+    k_flags_full<<<blocks_for(g.n, 256), 256, 0, stream>>>(flags, g, ps);
+}
+
+void launch_flags_box(uint8_t* flags_next, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
+                      cudaStream_t stream) {
+    k_flags_box<<<blocks_for(b.cells, 256), 256, 0, stream>>>(flags_next, g, b, ps);
+}
+
+template <typename S>
+void launch_refill(S* pops, const uint8_t* flags_cur, const uint8_t* flags_next, const GridDesc& g,
+                   const BoxDesc& b, const ParticleState* ps, typename Store<S>::A scale,
+                   typename Store<S>::A inv_scale, cudaStream_t stream) {
+    k_refill<S><<<blocks_for(b.cells, 128), 128, 0, stream>>>(pops, flags_cur, flags_next, g, b, ps, scale,
+                                                               inv_scale);
+}
+
+void launch_build_links(const uint8_t* flags, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
+                        int* list, int* count, int capacity, int* status, cudaStream_t stream) {
+    k_build_links<<<1, LINK_THREADS, 0, stream>>>(flags, g, b, ps, list, count, capacity, status);
+}
+
+void launch_export_links(const uint8_t* flags, const int* list, const int* count, int max_cells, const GridDesc& g,
+                         const ParticleState* ps, int cli, int32_t* q_out, double* delta_out, cudaStream_t stream) {
+    (void)cli;
+    if (max_cells <= 0) return;
+    k_export_links<<<blocks_for(max_cells, 128), 128, 0, stream>>>(flags, list, count, g, ps, q_out, delta_out);
+}
+
+template <typename S>
+void launch_init_equilibrium(S* pops, const uint8_t* flags, const GridDesc& g, double rho, const double u[3],
+                             const double* u_field, typename Store<S>::A scale, cudaStream_t stream) {
+    k_init_eq<S><<<blocks_for(g.n, 256), 256, 0, stream>>>(pops, flags, g, rho, u[0], u[1], u[2], u_field, scale);
+}
+
+template <typename S>
+void launch_to_f64(const S* pops, double* out, long long count, typename Store<S>::A inv_scale,
+                   cudaStream_t stream) {
+    k_to_f64<S><<<blocks_for(count, 256), 256, 0, stream>>>(pops, out, count, inv_scale);
+}
+
+template <typename S>
+void launch_from_f64(const double* in, S* pops, long long count, typename Store<S>::A scale, cudaStream_t stream) {
+    k_from_f64<S><<<blocks_for(count, 256), 256, 0, stream>>>(in, pops, count, scale);
+}
+
+template <typename S>
+void launch_gather(const S* pops, long long ncells, const int64_t* cells, long long n, double* out,
+                   typename Store<S>::A inv_scale, cudaStream_t stream) {
+    if (n <= 0) return;
+    k_gather<S><<<blocks_for(n * 19, 256), 256, 0, stream>>>(pops, ncells, cells, n, out, inv_scale);
+}
+
+template <typename S>
+void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStream_t stream) {
+    k_zero_solid<S><<<blocks_for(g.n, 256), 256, 0, stream>>>(pops, flags, g);
+}
+
+#define LBMP_INSTANTIATE(S)                                                                                        \
+    template void launch_bulk<S>(const S*, S*, const GridDesc&, const CollideParams<Store<S>::A>&, int*,           \
+                                 cudaStream_t);                                                                    \
+    template void launch_boundary<S>(const S*, S*, const uint8_t*, const int*, const int*, int, const GridDesc&,   \
+                                     const CollideParams<Store<S>::A>&, const ParticleState*, int, double*, int*,  \
+                                     int*, cudaStream_t);                                                          \
+    template void launch_refill<S>(S*, const uint8_t*, const uint8_t*, const GridDesc&, const BoxDesc&,            \
+                                   const ParticleState*, Store<S>::A, Store<S>::A, cudaStream_t);                  \
+    template void launch_init_equilibrium<S>(S*, const uint8_t*, const GridDesc&, double, const double*,           \
+                                             const double*, Store<S>::A, cudaStream_t);                            \
+    template void launch_to_f64<S>(const S*, double*, long long, Store<S>::A, cudaStream_t);                       \
+    template void launch_from_f64<S>(const double*, S*, long long, Store<S>::A, cudaStream_t);                      \
+    template void launch_zero_solid<S>(S*, const uint8_t*, const GridDesc&, cudaStream_t);                       \
+    template void launch_gather<S>(const S*, long long, const int64_t*, long long, double*, Store<S>::A,           \
+                                   cudaStream_t);
+
+LBMP_INSTANTIATE(double)
+LBMP_INSTANTIATE(float)
+LBMP_INSTANTIATE(__half)
+
+}  // namespace lbmp
