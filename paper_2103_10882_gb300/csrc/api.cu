@@ -26,6 +26,8 @@ struct lbmp_handle {
     int* list = nullptr;                 // boundary cells
     int* count = nullptr;
     int list_cap = 0;
+    uint8_t* link_mask = nullptr;        // scratch of the link compaction (one byte per box cell)
+    int* link_blocks = nullptr;          // scratch: per-block counts
     double* partials = nullptr;
     int partial_blocks = 0;
     ParticleState* d_ps = nullptr;
@@ -171,10 +173,10 @@ void enqueue_step(lbmp_handle* h) {
             launch_flags_box(fnext, h->G, h->box, h->d_ps, h->stream);
             launch_refill<S>(dst, h->flags[h->fcur], fnext, h->G, h->box, h->d_ps, (A)fp16_scale(h, false),
                              (A)fp16_scale(h, true), h->stream);
-            launch_build_links(fnext, h->G, h->box, h->d_ps, h->list, h->count, h->list_cap, h->status,
-                               h->stream);
+            launch_build_links(fnext, h->G, h->box, h->d_ps, h->link_mask, h->link_blocks, h->list, h->count,
+                               h->list_cap, h->status, h->stream);
             h->fcur = 1 - h->fcur;
-            h->launches += 5;
+            h->launches += 6;
         }
     });
     record(h);
@@ -360,11 +362,20 @@ lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter
         if (h->G.periodic[a] && B.E[a] >= n3[a]) B.E[a] = n3[a];
         B.cells *= B.E[a];
     }
-    h->list_cap = (int)B.cells;
+    // Boundary cells lie in the shell r < |x - x_p| <= r + sqrt(2); cell
+    // centres in it are bounded by the volume of the shell widened by the
+    // half-diagonal sqrt(3)/2 of a cell on both sides.
+    const double h3 = 0.5 * std::sqrt(3.0);
+    const double ro = P.r + std::sqrt(2.0) + h3, ri = std::max(0.0, P.r - h3);
+    const double shell = 4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri);
+    h->list_cap = (int)std::min<double>((double)B.cells, std::ceil(shell) + 64.0);
     h->list = (int*)dev_alloc(h, sizeof(int) * (size_t)h->list_cap);
     const int max_blocks = (h->list_cap + 127) / 128;
     h->partials = (double*)dev_alloc(h, sizeof(double) * 6 * (size_t)max_blocks);
-    if (!h->list || !h->partials) return fail(h, LBMP_ERR_OOM, "lbmp_add_sphere: device allocation failed");
+    h->link_mask = (uint8_t*)dev_alloc(h, (size_t)B.cells);
+    h->link_blocks = (int*)dev_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));
+    if (!h->list || !h->partials || !h->link_mask || !h->link_blocks)
+        return fail(h, LBMP_ERR_OOM, "lbmp_add_sphere: device allocation failed");
     lbmp_status s = upload_particle(h);
     if (s != LBMP_OK) return s;
     launch_flags_full(h->flags[h->fcur], h->G, h->d_ps, h->stream);
@@ -373,8 +384,8 @@ lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter
         using S = std::remove_pointer_t<decltype(tag)>;
         launch_zero_solid<S>((S*)h->pops[h->cur], h->flags[h->fcur], h->G, h->stream);
     });
-    launch_build_links(h->flags[h->fcur], h->G, h->box, h->d_ps, h->list, h->count, h->list_cap, h->status,
-                       h->stream);
+    launch_build_links(h->flags[h->fcur], h->G, h->box, h->d_ps, h->link_mask, h->link_blocks, h->list, h->count,
+                       h->list_cap, h->status, h->stream);
     LBMP_CK(h, cudaGetLastError());
     LBMP_CK(h, cudaStreamSynchronize(h->stream));
     h->has_particle = true;

@@ -52,8 +52,11 @@ template <typename S>
 void launch_refill(S* pops, const uint8_t* flags_cur, const uint8_t* flags_next, const GridDesc& g,
                    const BoxDesc& b, const ParticleState* ps, typename Store<S>::A scale,
                    typename Store<S>::A inv_scale, cudaStream_t stream);
+// Boundary-cell list of the box; mask (b.cells bytes) and block_count
+// (ceil(b.cells / 256) ints) are scratch.
 void launch_build_links(const uint8_t* flags, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
-                        int* list, int* count, int capacity, int* status, cudaStream_t stream);
+                        uint8_t* mask, int* block_count, int* list, int* count, int capacity, int* status,
+                        cudaStream_t stream);
 void launch_export_links(const uint8_t* flags, const int* list, const int* count, int max_cells,
                          const GridDesc& g, const ParticleState* ps, int cli, int32_t* q_out, double* delta_out,
                          cudaStream_t stream);

@@ -58,7 +58,7 @@ __device__ __forceinline__ double link_delta(const double d[3], int q, double r)
 // TRT collision on deviations (Sec. 2.1, Lambda_b = 1): the symmetric part of
 // each pair relaxes with s+, the antisymmetric part with s-; incompressible
 // equilibrium with rho_0 = 1; optional Guo-type source split the same way.
-template <typename A>
+template <typename A, bool FORCED>
 __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& P, int* status) {
     A drho = A(0), jx = A(0), jy = A(0), jz = A(0);
 #pragma unroll
@@ -72,7 +72,7 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
         if (cz(q) == -1) jz -= g[q];
     }
     A ux = jx, uy = jy, uz = jz;
-    if (P.forced) {
+    if (FORCED) {
         ux += A(0.5) * P.F[0];
         uy += A(0.5) * P.F[1];
         uz += A(0.5) * P.F[2];
@@ -83,7 +83,7 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
     {
         const A e0 = wgt<A>(0) * (drho - A(1.5) * uu);
         A o = g[0] - sp * (g[0] - e0);
-        if (P.forced) {
+        if (FORCED) {
             const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
             o += (A(1) - A(0.5) * sp) * wgt<A>(0) * (A(-3) * uF);
         }
@@ -101,7 +101,7 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
         const A dm = sm * (gm - em);
         A a = g[q] - dp - dm;
         A b = g[q + 1] - dp + dm;
-        if (P.forced) {
+        if (FORCED) {
             const A cF = A(cx(q)) * P.F[0] + A(cy(q)) * P.F[1] + A(cz(q)) * P.F[2];
             const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
             const A Sp = (A(1) - A(0.5) * sp) * w * (A(9) * cu * cF - A(3) * uF);
@@ -115,33 +115,47 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
 }
 
 // ------------------------------------------------------------------ bulk
-template <typename S>
+// One thread per cell, pull form: g_q(x, t+1) = g~_q(x - c_q, t), then TRT.
+// WALLS: some axis has no-slip walls (bounce-back at the domain edge);
+// FORCED: fluid body force present.  Both are compile-time so the common
+// periodic, unforced case carries no per-population branches.  Spatial
+// offsets are 32-bit (cells < 2^31); each population array is addressed
+// from its own base pointer.
+template <typename S, bool WALLS, bool FORCED>
 __global__ void __launch_bounds__(BULK_THREADS)
-    k_bulk(const S* __restrict__ src, S* __restrict__ dst, GridDesc G,
-           CollideParams<typename Store<S>::A> P, int* __restrict__ status) {
+    k_bulk(const S* __restrict__ src, S* __restrict__ dst, GridDesc G, CollideParams<typename Store<S>::A> P,
+           int* __restrict__ status) {
     using A = typename Store<S>::A;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (x >= G.nx || y >= G.ny) return;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    if (x >= nx || y >= ny) return;
     const size_t n = (size_t)G.n;
-    const size_t nx = (size_t)G.nx, nxy = (size_t)G.nx * (size_t)G.ny;
-    const size_t cell = (size_t)x + nx * (size_t)y + nxy * (size_t)z;
-    // source coordinates x - c for c = -1, 0, +1
-    const int xs[3] = {src_coord(x, -1, G.nx, G.periodic[0]), x, src_coord(x, 1, G.nx, G.periodic[0])};
-    const int ys[3] = {src_coord(y, -1, G.ny, G.periodic[1]), y, src_coord(y, 1, G.ny, G.periodic[1])};
-    const int zs[3] = {src_coord(z, -1, G.nz, G.periodic[2]), z, src_coord(z, 1, G.nz, G.periodic[2])};
+    const int cell = x + nx * (y + ny * z);
+    // source coordinate x - c for c = -1, 0, +1 (-1 marks a wall)
+    int xs[3], ys[3], zs[3];
+    xs[1] = x;
+    ys[1] = y;
+    zs[1] = z;
+    xs[0] = x + 1 < nx ? x + 1 : (WALLS && !G.periodic[0] ? -1 : 0);
+    xs[2] = x > 0 ? x - 1 : (WALLS && !G.periodic[0] ? -1 : nx - 1);
+    ys[0] = y + 1 < ny ? y + 1 : (WALLS && !G.periodic[1] ? -1 : 0);
+    ys[2] = y > 0 ? y - 1 : (WALLS && !G.periodic[1] ? -1 : ny - 1);
+    zs[0] = z + 1 < nz ? z + 1 : (WALLS && !G.periodic[2] ? -1 : 0);
+    zs[2] = z > 0 ? z - 1 : (WALLS && !G.periodic[2] ? -1 : nz - 1);
     A g[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const int sx = xs[cx(q) + 1], sy = ys[cy(q) + 1], sz = zs[cz(q) + 1];
-        if (sx < 0 || sy < 0 || sz < 0)   // stationary no-slip domain wall: bounce-back
+        if (WALLS && (sx < 0 || sy < 0 || sz < 0)) {   // stationary no-slip wall: bounce-back
             g[q] = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
-        else
-            g[q] = Store<S>::load(src + (size_t)q * n + (size_t)sx + nx * (size_t)sy + nxy * (size_t)sz,
-                                  P.inv_scale);
+        } else {
+            const int off = sx + nx * (sy + ny * sz);
+            g[q] = Store<S>::load(src + (size_t)q * n + off, P.inv_scale);
+        }
     }
-    trt_collide<A>(g, P, status);
+    trt_collide<A, FORCED>(g, P, status);
 #pragma unroll
     for (int q = 0; q < 19; ++q) Store<S>::store(dst + (size_t)q * n + cell, g[q], P.scale);
 }
@@ -226,7 +240,8 @@ __global__ void __launch_bounds__(BND_THREADS)
             T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
             T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
         }
-        trt_collide<A>(g, P, status);
+        if (P.forced) trt_collide<A, true>(g, P, status);
+        else trt_collide<A, false>(g, P, status);
 #pragma unroll
         for (int q = 0; q < 19; ++q) Store<S>::store(dst + (size_t)q * n + cell, g[q], P.scale);
     }
@@ -335,20 +350,23 @@ __global__ void __launch_bounds__(PART_THREADS)
 // ------------------------------------------------------------------ remap
 // Box of cells around the sphere: cell (o + t) for t in [0, E), o from the
 // current centre.  Returns false for cells outside a walled domain.
-__device__ __forceinline__ bool box_cell(long long t, const GridDesc& G, const BoxDesc& B, const ParticleState& P,
+__device__ __forceinline__ bool box_cell(int t, const GridDesc& G, const BoxDesc& B, const ParticleState& P,
                                          int* ci, int* cj, int* ck) {
-    const int ti = (int)(t % B.E[0]);
-    const int tj = (int)((t / B.E[0]) % B.E[1]);
-    const int tk = (int)(t / ((long long)B.E[0] * B.E[1]));
+    const int e0 = B.E[0], e1 = B.E[1];
+    const int tk = t / (e0 * e1);
+    const int r = t - tk * e0 * e1;
+    const int tj = r / e0;
+    const int ti = r - tj * e0;
     const int n3[3] = {G.nx, G.ny, G.nz};
     const int tt[3] = {ti, tj, tk};
     int c[3];
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int o = (B.E[a] >= n3[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
+        const int o = (B.E[a] >= n3[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
         int v = o + tt[a];
         if (v < 0 || v >= n3[a]) {
             if (!G.periodic[a]) return false;
-            v = ((v % n3[a]) + n3[a]) % n3[a];
+            v = v < 0 ? v + n3[a] : v - n3[a];   // |v| stays within one period: the box is narrower than the domain
         }
         c[a] = v;
     }
@@ -359,15 +377,16 @@ __device__ __forceinline__ bool box_cell(long long t, const GridDesc& G, const B
 }
 
 __global__ void k_flags_full(uint8_t* __restrict__ flags, GridDesc G, const ParticleState* __restrict__ ps) {
-    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= G.n) return;
-    const int i = (int)(c % G.nx), j = (int)((c / G.nx) % G.ny), k = (int)(c / ((long long)G.nx * G.ny));
+    const int ij = c % (G.nx * G.ny);
+    const int i = ij % G.nx, j = ij / G.nx, k = c / (G.nx * G.ny);
     flags[c] = (ps->present && inside_ball(i, j, k, G, *ps)) ? 1 : 0;
 }
 
 __global__ void k_flags_box(uint8_t* __restrict__ flags_next, GridDesc G, BoxDesc B,
                             const ParticleState* __restrict__ ps) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.cells) return;
     const ParticleState P = *ps;
     int i, j, k;
@@ -384,7 +403,7 @@ __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
                          GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
                          typename Store<S>::A scale, typename Store<S>::A inv_scale) {
     using A = typename Store<S>::A;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.cells) return;
     const ParticleState P = *ps;
     int i, j, k;
@@ -434,64 +453,85 @@ __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
 }
 
 // Ordered compaction of the fluid cells with a solid neighbour inside the
-// box (one block; the order is the box traversal order, so it is the same
-// in every run).
-constexpr int LINK_THREADS = 1024;
+// box, in two passes over the box: k_links_mark flags each box cell and
+// counts per block; k_links_emit gives every block its offset (sum of the
+// counts of the blocks before it) and writes its cells in traversal order.
+// The order is the box traversal order, identical in every run.
+constexpr int LINK_THREADS = 256;
+
+__device__ __forceinline__ int wrap_idx(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
 __global__ void __launch_bounds__(LINK_THREADS)
-    k_build_links(const uint8_t* __restrict__ flags, GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
-                  int* __restrict__ list, int* __restrict__ count, int capacity, int* __restrict__ status) {
-    __shared__ int warp_sum[LINK_THREADS / 32];
-    __shared__ int base;
-    if (threadIdx.x == 0) base = 0;
-    __syncthreads();
-    const ParticleState P = *ps;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n3[3] = {G.nx, G.ny, G.nz};
-    for (long long t0 = 0; t0 < B.cells; t0 += LINK_THREADS) {
-        const long long t = t0 + threadIdx.x;
-        int is_b = 0;
-        size_t c = 0;
+    k_links_mark(const uint8_t* __restrict__ flags, GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
+                 uint8_t* __restrict__ mask, int* __restrict__ block_count) {
+    const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
+    int is_b = 0;
+    if (t < B.cells) {
         int i, j, k;
-        if (t < B.cells && box_cell(t, G, B, P, &i, &j, &k)) {
-            c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+        if (box_cell(t, G, B, *ps, &i, &j, &k)) {
+            const int nx = G.nx, ny = G.ny;
+            const int c = i + nx * (j + ny * k);
             if (flags[c] == 0) {
-                for (int q = 1; q < 19 && !is_b; ++q) {
-                    int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
-                    bool ok = true;
-                    for (int a = 0; a < 3; ++a) {
-                        if (v[a] < 0 || v[a] >= n3[a]) {
-                            if (!G.periodic[a]) ok = false;
-                            v[a] = (v[a] + n3[a]) % n3[a];
-                        }
-                    }
-                    if (!ok) continue;
-                    const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
-                    if (flags[y] != 0) is_b = 1;
+#pragma unroll
+                for (int q = 1; q < 19; ++q) {
+                    const int a = i + cx(q), b = j + cy(q), d = k + cz(q);
+                    if ((!G.periodic[0] && (a < 0 || a >= nx)) || (!G.periodic[1] && (b < 0 || b >= ny)) ||
+                        (!G.periodic[2] && (d < 0 || d >= G.nz)))
+                        continue;
+                    const int y = wrap_idx(a, nx) + nx * (wrap_idx(b, ny) + ny * wrap_idx(d, G.nz));
+                    is_b |= flags[y] != 0;
                 }
             }
         }
-        const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
-        if (lane == 0) warp_sum[warp] = __popc(ballot);
-        __syncthreads();
-        if (threadIdx.x == 0) {   // exclusive prefix over the warps, in place
-            int s = 0;
-            for (int w = 0; w < LINK_THREADS / 32; ++w) {
-                const int v = warp_sum[w];
-                warp_sum[w] = s;
-                s += v;
-            }
-        }
-        __syncthreads();
-        if (is_b) {
-            const int pos = base + warp_sum[warp] + __popc(ballot & ((1u << lane) - 1u));
-            if (pos < capacity) list[pos] = (int)c;
-            else atomicOr(status, STATUS_LINK_OVERFLOW);
-        }
-        __syncthreads();
-        if (threadIdx.x == LINK_THREADS - 1) base += warp_sum[warp] + __popc(ballot);
+        mask[t] = (uint8_t)is_b;
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
+    __shared__ int wsum[LINK_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < LINK_THREADS / 32; ++w) s += wsum[w];
+        block_count[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(LINK_THREADS)
+    k_links_emit(const uint8_t* __restrict__ mask, const int* __restrict__ block_count, GridDesc G, BoxDesc B,
+                 const ParticleState* __restrict__ ps, int* __restrict__ list, int* __restrict__ count, int capacity,
+                 int* __restrict__ status) {
+    __shared__ int red[LINK_THREADS];
+    __shared__ int wsum[LINK_THREADS / 32];
+    // offset of this block: sum of the counts of all earlier blocks
+    int s = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += LINK_THREADS) s += block_count[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = LINK_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *count = base < capacity ? base : capacity;
+    const int base = red[0];
+    const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
+    const int is_b = (t < B.cells) ? mask[t] : 0;
+    const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wsum[warp] = __popc(ballot);
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += wsum[w];
+    if (is_b) {
+        int i, j, k;
+        box_cell(t, G, B, *ps, &i, &j, &k);
+        const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
+        if (pos < capacity) list[pos] = i + G.nx * (j + G.ny * k);
+        else atomicOr(status, STATUS_LINK_OVERFLOW);
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        int tot = base;
+        for (int w = 0; w < LINK_THREADS / 32; ++w) tot += wsum[w];
+        *count = tot < capacity ? tot : capacity;
+    }
 }
 
 // Link export for inspection: slot (i*18 + q-1) of the i-th boundary cell
@@ -599,7 +639,14 @@ void launch_bulk(const S* src, S* dst, const GridDesc& g, const CollideParams<ty
     const int by = BULK_THREADS / bx;
     dim3 block(bx, by, 1);
     dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
-    k_bulk<S><<<grid, block, 0, stream>>>(src, dst, g, p, status);
+    const bool walls = !(g.periodic[0] && g.periodic[1] && g.periodic[2]);
+    if (walls) {
+        if (p.forced) k_bulk<S, true, true><<<grid, block, 0, stream>>>(src, dst, g, p, status);
+        else k_bulk<S, true, false><<<grid, block, 0, stream>>>(src, dst, g, p, status);
+    } else {
+        if (p.forced) k_bulk<S, false, true><<<grid, block, 0, stream>>>(src, dst, g, p, status);
+        else k_bulk<S, false, false><<<grid, block, 0, stream>>>(src, dst, g, p, status);
+    }
 }
 
 template <typename S>
@@ -634,8 +681,11 @@ void launch_refill(S* pops, const uint8_t* flags_cur, const uint8_t* flags_next,
 }
 
 void launch_build_links(const uint8_t* flags, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
-                        int* list, int* count, int capacity, int* status, cudaStream_t stream) {
-    k_build_links<<<1, LINK_THREADS, 0, stream>>>(flags, g, b, ps, list, count, capacity, status);
+                        uint8_t* mask, int* block_count, int* list, int* count, int capacity, int* status,
+                        cudaStream_t stream) {
+    const unsigned nb = blocks_for(b.cells, LINK_THREADS);
+    k_links_mark<<<nb, LINK_THREADS, 0, stream>>>(flags, g, b, ps, mask, block_count);
+    k_links_emit<<<nb, LINK_THREADS, 0, stream>>>(mask, block_count, g, b, ps, list, count, capacity, status);
 }
 
 void launch_export_links(const uint8_t* flags, const int* list, const int* count, int max_cells, const GridDesc& g,
