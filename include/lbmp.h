@@ -163,6 +163,32 @@ lbmp_status lbmp_profile(lbmp_handle* h, int enable);
  * stream-collide kernel, [1] its launches, [2] total ms of the whole steps,
  * [3] steps.  Synchronises the stream. */
 lbmp_status lbmp_get_profile(lbmp_handle* h, double out[4]);
+/* Boundary cells of one sphere, computed without allocating any memory.
+ * (No counterpart in the paper: this is a service for callers that cannot
+ * call cudaMalloc, such as a host function enqueued on a stream, a loop
+ * that must not risk the device synchronisation an allocation may cause,
+ * or a process whose device memory belongs to another allocator.)
+ *   flags       device array of nx*ny*nz bytes, 0 = fluid, nonzero = solid
+ *   periodic    per axis, nonzero for a periodic axis
+ *   center      sphere centre (host), diameter in cells
+ *   list        device array of `capacity` ints: receives the linear indices
+ *               of the fluid cells in the sphere's box (half width
+ *               ceil(d/2) + 3 cells) that have a solid D3Q19 neighbour, in
+ *               box order -- the same cells and order as the coupled step's
+ *               own boundary list
+ *   count       device int: the number of such cells (may exceed capacity;
+ *               only the first `capacity` are written)
+ *   cuda_stream stream to run on (asynchronous; nothing is synchronised)
+ * Scratch lives in one fixed device array of 266240 bytes per device, held
+ * until the process exits: boxes larger than 64^3 cells (diameters above 56
+ * cells) are rejected with LBMP_ERR_INVALID_ARG.  The first call on a
+ * device looks up that array's address; make it before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race: the
+ * caller serialises them.  Errors are reported by lbmp_last_error(NULL). */
+lbmp_status lbmp_boundary_cells_noalloc(const uint8_t* flags, int nx, int ny, int nz, const int periodic[3],
+                                        const double center[3], double diameter, int* list, int capacity,
+                                        int* count, uintptr_t cuda_stream);
+
 /* Message of the last failure on this handle (or of the last failed create
  * when h is NULL).  Never NULL. */
 const char* lbmp_last_error(const lbmp_handle* h);

@@ -20,7 +20,7 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_set_tau", "lbmp_set_gravity", "lbmp_set_body_force", "lbmp_init_fluid", "lbmp_set_populations",
            "lbmp_get_populations", "lbmp_gather_populations", "lbmp_step", "lbmp_step_async", "lbmp_check_status", "lbmp_synchronize",
            "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
-           "lbmp_profile", "lbmp_get_profile", "lbmp_last_error", "PRECISIONS"]
+           "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error", "PRECISIONS"]
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
 BC = {"periodic": 0, "noslip": 1}
@@ -213,6 +213,18 @@ def lbmp_get_profile(h):
     out = np.zeros(4, dtype=np.float64)
     _check(h, _lib().lbmp_get_profile(h, _dp(out)))
     return out
+
+
+def lbmp_boundary_cells_noalloc(flags_ptr, shape, periodic, center, diameter, list_ptr, capacity, count_ptr,
+                                stream_ptr=0):
+    """Boundary cells of one sphere without any allocation inside the call.
+    flags_ptr, list_ptr, count_ptr are device addresses (e.g. tensor.data_ptr())."""
+    per = (ctypes.c_int * 3)(*[int(bool(p)) for p in periodic])
+    c = _vec3(center)
+    nx, ny, nz = (int(v) for v in shape)
+    _check(None, _lib().lbmp_boundary_cells_noalloc(ctypes.c_void_p(flags_ptr), nx, ny, nz, per, _dp(c),
+                                                    float(diameter), ctypes.c_void_p(list_ptr), int(capacity),
+                                                    ctypes.c_void_p(count_ptr), ctypes.c_void_p(stream_ptr)))
 
 
 def lbmp_last_error(h=None):

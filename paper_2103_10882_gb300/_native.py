@@ -66,6 +66,9 @@ SIGNATURES = {
     "lbmp_get_counters": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "lbmp_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "lbmp_get_profile": (ctypes.c_int, [ctypes.c_void_p, c_double_p]),
+    "lbmp_boundary_cells_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                   ctypes.POINTER(ctypes.c_int), c_double_p, ctypes.c_double,
+                                                   ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "lbmp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 

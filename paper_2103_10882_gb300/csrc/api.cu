@@ -222,6 +222,11 @@ lbmp_status download_particle(lbmp_handle* h) {
 
 }  // namespace
 
+namespace lbmp {
+// Error message for entry points that have no handle (read by lbmp_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace lbmp
+
 extern "C" {
 
 lbmp_status lbmp_config_default(lbmp_config* c) {
