@@ -66,6 +66,29 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def profiled_traffic(args):
+    """DRAM bytes per k_bulk launch from the committed ncu summary (captured
+    at 256^3 and scaled by the cells processed); None when the summary does
+    not exist or the kernel source changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_bulk_%s_uniform256.md" % args.precision)
+    if args.edge != 512 or not os.path.exists(path):
+        return None
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.strip().split(":")[0] in ("source_sha256_16", "traffic_bytes_per_launch_512"):
+            k, v = line.strip().split(":", 1)
+            fields[k] = v.strip()
+    src = os.path.join(ROOT, "paper_2103_10882_gb300", "csrc", "uniform.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if fields.get("source_sha256_16") != sha:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch_512"])
+    except (KeyError, ValueError):
+        return None
+
+
 class ClockSampler:
     """Samples SM clocks and throttle reasons with nvidia-smi while running."""
 
@@ -249,13 +272,7 @@ def main():
     bulk_avg_s = bulk_ms / max(bulk_n, 1) * 1e-3
     achieved = alg_bytes / bulk_avg_s / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic_%s_%d.json" % (args.precision, args.edge))
-    if os.path.exists(tp):
-        try:
-            traffic = json.load(open(tp)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = profiled_traffic(args)
 
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
