@@ -31,6 +31,20 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+class OrcAmrParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("levels", ctypes.c_int),
+        ("periodic", ctypes.c_int * 3),
+        ("tau", ctypes.c_double),
+        ("magic", ctypes.c_double),
+        ("boundary", ctypes.c_int),
+        ("force_average", ctypes.c_int),
+        ("plain_mem", ctypes.c_int),
+        ("rescale", ctypes.c_int),
+    ]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -63,6 +77,32 @@ def lib():
         L.orc_particle_only_step.argtypes = [vp, dp, dp]
         L.orc_set_threads.restype = ip
         L.orc_set_threads.argtypes = [ip]
+        L.orc_amr_create.restype = vp
+        L.orc_amr_create.argtypes = [ctypes.POINTER(OrcAmrParams)]
+        L.orc_amr_destroy.argtypes = [vp]
+        L.orc_amr_refine_box.restype = ip
+        L.orc_amr_refine_box.argtypes = [vp, dp, dp]
+        L.orc_amr_add_sphere.restype = ip
+        L.orc_amr_add_sphere.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ip]
+        L.orc_amr_set_gravity.argtypes = [vp, dp]
+        L.orc_amr_set_particle_velocity.argtypes = [vp, dp, dp]
+        L.orc_amr_regrid.restype = ip
+        L.orc_amr_regrid.argtypes = [vp]
+        L.orc_amr_init_equilibrium.argtypes = [vp, ctypes.c_double, dp, ctypes.c_double, ip, ip]
+        L.orc_amr_step.restype = ip
+        L.orc_amr_step.argtypes = [vp, ip]
+        L.orc_amr_error.restype = ip
+        L.orc_amr_error.argtypes = [vp]
+        L.orc_amr_level_shape.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
+        L.orc_amr_block_map.restype = ctypes.c_int64
+        L.orc_amr_block_map.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64]
+        L.orc_amr_level_populations.argtypes = [vp, ip, dp]
+        L.orc_amr_mass.argtypes = [vp, dp]
+        L.orc_amr_real_cells.restype = ctypes.c_int64
+        L.orc_amr_real_cells.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int32), dp, ctypes.c_int64]
+        L.orc_amr_get_particle.argtypes = [vp, dp]
+        L.orc_amr_get_history.restype = ctypes.c_int64
+        L.orc_amr_get_history.argtypes = [vp, dp, ctypes.c_int64]
         _lib = L
     return _lib
 
@@ -196,3 +236,114 @@ class UniformSim:
         a, pa = _d(F)
         b, pb = _d(T)
         self._L.orc_particle_only_step(self._h, pa, pb)
+
+
+class RefinedSim:
+    """Block-structured refined simulation held by the C++ oracle (refined.cpp)."""
+
+    def __init__(self, shape, levels, tau, magic=3.0 / 16.0, periodic=(1, 1, 1), boundary="cli",
+                 force_average=True, plain_mem=False, rescale=False):
+        L = lib()
+        p = OrcAmrParams()
+        p.nx, p.ny, p.nz = (int(v) for v in shape)
+        p.levels = int(levels)
+        p.periodic = (ctypes.c_int * 3)(*[int(v) for v in periodic])
+        p.tau = float(tau)
+        p.magic = float(magic)
+        p.boundary = {"cli": 0, "sbb": 1}[boundary]
+        p.force_average = int(bool(force_average))
+        p.plain_mem = int(bool(plain_mem))
+        p.rescale = int(bool(rescale))
+        self._L = L
+        self.levels = int(levels)
+        self._h = L.orc_amr_create(ctypes.byref(p))
+        if not self._h:
+            raise ValueError("oracle rejected the parameters")
+
+    def close(self):
+        if self._h:
+            self._L.orc_amr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rc(self, rc):
+        if rc != 0:
+            raise RuntimeError("refined oracle error %d" % rc)
+
+    def refine_box(self, lo, hi):
+        a, pa = _d(lo)
+        b, pb = _d(hi)
+        self._rc(self._L.orc_amr_refine_box(self._h, pa, pb))
+
+    def add_sphere(self, pos, diameter, density_ratio, cv=0.0, cv_omega=None, fixed=False):
+        if cv_omega is None:
+            cv_omega = cv
+        a, pa = _d(pos)
+        self._rc(self._L.orc_amr_add_sphere(self._h, pa, float(diameter), float(density_ratio), float(cv),
+                                            float(cv_omega), int(bool(fixed))))
+
+    def set_gravity(self, g):
+        a, pa = _d(g)
+        self._L.orc_amr_set_gravity(self._h, pa)
+
+    def set_particle_velocity(self, u, w=(0.0, 0.0, 0.0)):
+        a, pa = _d(u)
+        b, pb = _d(w)
+        self._L.orc_amr_set_particle_velocity(self._h, pa, pb)
+
+    def regrid(self):
+        self._rc(self._L.orc_amr_regrid(self._h))
+
+    def init_equilibrium(self, rho=1.0, u=(0.0, 0.0, 0.0), shear=0.0, shear_dir=0, shear_axis=2):
+        a, pa = _d(u)
+        self._L.orc_amr_init_equilibrium(self._h, float(rho), pa, float(shear), int(shear_dir), int(shear_axis))
+
+    def step(self, n=1):
+        self._rc(self._L.orc_amr_step(self._h, int(n)))
+
+    def level_shape(self, level):
+        out = (ctypes.c_int * 3)()
+        self._L.orc_amr_level_shape(self._h, int(level), out)
+        return tuple(out)
+
+    def block_map(self, level):
+        n = self._L.orc_amr_block_map(self._h, int(level), None, 0)
+        out = np.empty(n, dtype=np.int32)
+        self._L.orc_amr_block_map(self._h, int(level), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n)
+        return out
+
+    def level_populations(self, level):
+        nx, ny, nz = self.level_shape(level)
+        out = np.empty((19, nx * ny * nz))
+        self._L.orc_amr_level_populations(self._h, int(level), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def real_cells(self, level):
+        """(coords [n,3] int32, deviations [n,19]) of the real cells of a level."""
+        n = self._L.orc_amr_real_cells(self._h, int(level), None, None, 0)
+        xyz = np.empty((n, 3), dtype=np.int32)
+        g = np.empty((n, 19))
+        self._L.orc_amr_real_cells(self._h, int(level), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return xyz, g
+
+    def mass(self):
+        out = np.empty(4)
+        self._L.orc_amr_mass(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def particle(self):
+        out = np.empty(24)
+        self._L.orc_amr_get_particle(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return out
+
+    def history(self):
+        n = self._L.orc_amr_get_history(self._h, None, 0)
+        out = np.empty((n, 15))
+        self._L.orc_amr_get_history(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return out

@@ -10,12 +10,12 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
-SOURCES = ["uniform.cpp"]
+SOURCES = ["uniform.cpp", "refined.cpp"]
 
 
 def build(force: bool = False) -> str:
     srcs = [os.path.join(HERE, s) for s in SOURCES]
-    deps = srcs + [os.path.join(HERE, "lbm_oracle.h")]
+    deps = srcs + [os.path.join(HERE, h) for h in ("lbm_oracle.h", "common.h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):

@@ -79,6 +79,50 @@ void orc_particle_only_step(orc_sim* s, const double F_hyd[3], const double T_hy
 /* Threads for the per-cell loops (results do not depend on it). Returns the count in use. */
 int orc_set_threads(int n);
 
+/* ------------------------------------------------------------------------
+ * Refined (block-structured) grid, refined.cpp.  Levels 0..levels-1, blocks
+ * of 16^3 cells, nx, ny, nz = level-0 cells (multiples of 16), positions and
+ * diameters in finest-level lattice units, tau of the finest level.
+ */
+typedef struct {
+    int nx, ny, nz;
+    int levels;
+    int periodic[3];
+    double tau;
+    double magic;
+    int boundary;
+    int force_average;
+    int plain_mem;
+    int rescale;          /* 1: rescale non-equilibrium parts at level interfaces */
+} orc_amr_params;
+typedef struct orc_amr orc_amr;
+orc_amr* orc_amr_create(const orc_amr_params* p);
+void orc_amr_destroy(orc_amr* a);
+/* Refines the finest-level blocks intersecting [lo, hi) (and regrids). */
+int orc_amr_refine_box(orc_amr* a, const double lo[3], const double hi[3]);
+int orc_amr_add_sphere(orc_amr* a, const double pos[3], double diameter, double density_ratio, double cv,
+                       double cv_omega, int fixed);
+void orc_amr_set_gravity(orc_amr* a, const double g[3]);
+void orc_amr_set_particle_velocity(orc_amr* a, const double u[3], const double w[3]);
+int orc_amr_regrid(orc_amr* a);
+/* Equilibrium everywhere with velocity u + amp sin(2 pi x_axis / L_axis) e_dir. */
+void orc_amr_init_equilibrium(orc_amr* a, double rho, const double u[3], double amp, int dir, int axis);
+/* n coarse (level-0) steps; returns 0 or an error code (1: missing source, 2: sphere not on the finest level). */
+int orc_amr_step(orc_amr* a, int n);
+int orc_amr_error(const orc_amr* a);
+void orc_amr_level_shape(const orc_amr* a, int level, int out[3]);
+/* Block-position map of a level: >= 0 real block (position order), -2 ghost block, -1 none. */
+int64_t orc_amr_block_map(const orc_amr* a, int level, int32_t* out, int64_t cap);
+/* Dense [19][cells of the level] deviations, NaN where the level has no real cell. */
+void orc_amr_level_populations(const orc_amr* a, int level, double* out);
+/* Real cells of a level in block-position order then local (x fastest)
+ * order: coordinates [n][3] and deviations [n][19].  Returns n. */
+int64_t orc_amr_real_cells(const orc_amr* a, int level, int32_t* xyz, double* g, int64_t cap);
+/* sum over real cells of (rho, rho u) times the cell volume in finest units. */
+void orc_amr_mass(const orc_amr* a, double out[4]);
+void orc_amr_get_particle(const orc_amr* a, double out[24]);
+int64_t orc_amr_get_history(const orc_amr* a, double* out, int64_t cap_steps);
+
 #ifdef __cplusplus
 }
 #endif

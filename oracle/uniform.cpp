@@ -8,6 +8,7 @@
  * stay serial, so a threaded build gives bit-identical results.
  */
 #include "lbm_oracle.h"
+#include "common.h"
 
 #include <cmath>
 #include <cstdlib>
@@ -17,40 +18,9 @@
 #include <omp.h>
 #endif
 
+using namespace orc;
+
 namespace {
-
-// ---------------------------------------------------------------- lattice
-// D3Q19 velocity set (Sec. 2.1 names D3Q19; the set and weights are the
-// standard ones: w0 = 1/3, faces 1/18, edges 1/36, c_s^2 = 1/3).
-const int C[19][3] = {
-    {0, 0, 0},
-    {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},   {0, 0, -1},
-    {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1},
-    {1, 0, -1}, {-1, 0, 1},  {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-const double W[19] = {1.0 / 3.0,
-                      1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0, 1.0 / 18.0,
-                      1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0,
-                      1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
-const double CS2 = 1.0 / 3.0;
-
-int opposite(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
-
-enum : uint8_t { FLUID = 0, SOLID_PARTICLE = 1, SOLID_PLANE = 2 };
-
-struct Particle {
-    bool present = false;
-    bool fixed = false;
-    double x[3] = {0, 0, 0};
-    double u[3] = {0, 0, 0};   // wall velocity seen by the fluid (u at t + 1/2)
-    double w[3] = {0, 0, 0};
-    double a[3] = {0, 0, 0};   // acceleration of the previous step (a_{p,t-1})
-    double b[3] = {0, 0, 0};   // angular acceleration of the previous step
-    double Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0};        // hydrodynamic, this step
-    double Fh_old[3] = {0, 0, 0}, Th_old[3] = {0, 0, 0};  // previous step
-    double Fp[3] = {0, 0, 0};
-    double D = 0, r = 0, rho_p = 1, cv = 0, cvw = 0, V = 0;
-    long steps = 0;
-};
 
 struct Planes {
     bool present = false;
@@ -154,14 +124,6 @@ double plane_delta(const orc_sim* s, int i, int j, int k, int q) {
     return C[q][a] > 0 ? (s->planes.hi - xc) : (xc - s->planes.lo);
 }
 
-// Incompressible equilibrium deviation (He & Luo form cited in Sec. 2.1,
-// rho_0 = 1): f_eq - w = w (drho + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u).
-double geq(int q, double drho, const double u[3]) {
-    double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
-    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    return W[q] * (drho + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-}
-
 // Moments, Eq. (rho_f, rho_0 u_f), with half the body force added to the
 // velocity for the forced case.
 void cell_moments(const orc_sim* s, const std::vector<double>& g, long x, double* drho, double u[3]) {
@@ -215,12 +177,6 @@ void collide_cell(orc_sim* s, long x) {
         }
     }
     for (int q = 0; q < 19; ++q) g[(size_t)q * s->n + x] = out[q];
-}
-
-void cross(const double a[3], const double b[3], double out[3]) {
-    out[0] = a[1] * b[2] - a[2] * b[1];
-    out[1] = a[2] * b[0] - a[0] * b[2];
-    out[2] = a[0] * b[1] - a[1] * b[0];
 }
 
 // Stream (Eq. LBE, pull form) with domain walls, and the CLI boundary of
@@ -331,88 +287,11 @@ void collide_all(orc_sim* s) {
         if (s->flag[x] == FLUID) collide_cell(s, x);
 }
 
-// Sec. 2.2 and Sec. 3.3 (Algorithm 1): average the hydrodynamic force and
-// torque over two steps, add gravity/buoyancy and the virtual force/torque
-// (built from the previous accelerations), and advance with Velocity Verlet
-// using the virtually increased mass and moment of inertia.  The paper's
-// position and velocity updates are taken in kick-drift-kick order: the
-// first step has no preceding half kick.
+// Particle update of Algorithm 1 (see common.h).
 void particle_update(orc_sim* s, const double Fh[3], const double Th[3]) {
-    Particle& P = s->part;
-    double Fbar[3], Tbar[3];
-    for (int a = 0; a < 3; ++a) {
-        if (s->p.force_average && P.steps > 0) {
-            Fbar[a] = 0.5 * (Fh[a] + P.Fh_old[a]);
-            Tbar[a] = 0.5 * (Th[a] + P.Th_old[a]);
-        } else {
-            Fbar[a] = Fh[a];
-            Tbar[a] = Th[a];
-        }
-        P.Fh[a] = Fh[a];
-        P.Th[a] = Th[a];
-        P.Fh_old[a] = Fh[a];
-        P.Th_old[a] = Th[a];
-    }
-    const double V = P.V, r = P.r;
-    double Fp[3], Tp[3], m, I;
-    if (s->p.plain_mem) {
-        // Sec. 2.2: F_p = F_g + F_hyd, T_p = T_hyd, m = rho_p V, I = 2/5 m r^2
-        m = P.rho_p * V;
-        I = 0.4 * P.rho_p * V * r * r;
-        for (int a = 0; a < 3; ++a) {
-            double Fg = (P.rho_p - 1.0) * s->gravity[a] * V;
-            Fp[a] = Fbar[a] + Fg;
-            Tp[a] = Tbar[a];
-        }
-    } else {
-        // Sec. 3.3: F_v = C_v rho_f V a_{t-1}, T_v = 2/5 C_vw rho_f V r^2 beta_{t-1},
-        // m = (rho_p + C_v rho_f) V, I = 2/5 (rho_p + C_vw rho_f) V r^2, rho_f = 1
-        m = (P.rho_p + P.cv) * V;
-        I = 0.4 * (P.rho_p + P.cvw) * V * r * r;
-        for (int a = 0; a < 3; ++a) {
-            double Fg = (P.rho_p - 1.0) * s->gravity[a] * V;
-            double Fv = P.cv * V * P.a[a];
-            double Tv = 0.4 * P.cvw * V * r * r * P.b[a];
-            Fp[a] = Fbar[a] + Fg + Fv;
-            Tp[a] = Tbar[a] + Tv;
-        }
-    }
-    for (int a = 0; a < 3; ++a) P.Fp[a] = Fp[a];
-    if (!P.fixed) {
-        for (int a = 0; a < 3; ++a) {
-            // second half kick of the previous step completes u(t)
-            if (P.steps > 0) {
-                P.u[a] += Fp[a] / (2.0 * m);
-                P.w[a] += Tp[a] / (2.0 * I);
-            }
-            P.a[a] = Fp[a] / m;
-            P.b[a] = Tp[a] / I;
-            // first half kick, then drift with u(t + 1/2)
-            P.u[a] += Fp[a] / (2.0 * m);
-            P.w[a] += Tp[a] / (2.0 * I);
-            P.x[a] += P.u[a];
-            if (s->p.periodic[a]) {
-                double L = (double)extent(s, a);
-                if (P.x[a] >= L) P.x[a] -= L;
-                else if (P.x[a] < 0.0) P.x[a] += L;
-            }
-        }
-    } else {
-        for (int a = 0; a < 3; ++a) {
-            P.a[a] = Fp[a] / m;
-            P.b[a] = Tp[a] / I;
-        }
-    }
-    P.steps += 1;
-    double rec[15];
-    for (int a = 0; a < 3; ++a) {
-        rec[a] = Fh[a];
-        rec[3 + a] = Th[a];
-        rec[6 + a] = P.x[a];
-        rec[9 + a] = P.u[a];
-        rec[12 + a] = P.w[a];
-    }
-    s->history.insert(s->history.end(), rec, rec + 15);
+    const double ext[3] = {(double)s->p.nx, (double)s->p.ny, (double)s->p.nz};
+    particle_advance(s->part, Fh, Th, s->gravity, s->p.force_average != 0, s->p.plain_mem != 0, s->p.periodic, ext,
+                     s->history);
 }
 
 // Sec. 2.3: new solid flags after the particle moved; cells the sphere

@@ -1,0 +1,239 @@
+"""Pins of the refined-grid oracle (Sec. 4.1, 4.2.1) against what the method fixes.
+
+- one level reduces to the uniform oracle;
+- a uniform flow is an exact fixed point across level interfaces (explosion
+  and coalescence of equilibria, non-equilibrium rescaling inert);
+- with rescaling off the interface transfer moves populations by copies,
+  volume averages and rigid translations only, so total mass and momentum
+  are conserved to rounding, also at edges and corners of the refined
+  region and across a regrid;
+- the viscosity per level follows acoustic scaling: a shear wave crossing a
+  refined slab decays at the rate of the finest-level viscosity;
+- the block forest is 2:1 balanced, complete (all eight children) and keeps
+  the sphere's block and its neighbours on the finest level;
+- before the disturbance of a sphere reaches the interface, the refined run
+  near the sphere is the uniform fine run.
+"""
+import numpy as np
+import pytest
+
+from lattice_ref import C, W
+
+
+def totals(sim, levels):
+    """Exactly rounded sums (math.fsum) of delta-rho V and rho u V over the
+    real cells of all levels (V in finest cells), and of |rho u| V."""
+    import math
+    m, p, scale = [], [[], [], []], []
+    for l in range(levels):
+        _, g = sim.real_cells(l)
+        vol = 8.0 ** (levels - 1 - l)
+        m.extend((g.sum(axis=1) * vol).tolist())
+        for k in range(3):
+            mk = (g @ C[:, k].astype(float)) * vol
+            p[k].extend(mk.tolist())
+            scale.extend(np.abs(mk).tolist())
+    return math.fsum(m), np.array([math.fsum(v) for v in p]), math.fsum(scale)
+
+
+def eq_dev(u, rho=1.0):
+    u = np.asarray(u, dtype=float)
+    cu = C @ u
+    return W * ((rho - 1) + 3 * cu + 4.5 * cu ** 2 - 1.5 * u @ u)
+
+
+def test_single_level_equals_uniform_oracle(orc):
+    shape, tau, D, pi, g = (32, 32, 32), 0.6, 8.0, 0.5, -2.5e-5
+    pos = (16.3, 15.8, 16.4)
+    u = orc.UniformSim(shape, tau=tau)
+    u.add_sphere(pos, D, pi, cv=0.5)
+    u.set_gravity((0, 0, g))
+    u.init_equilibrium()
+    r = orc.RefinedSim(shape, 1, tau=tau)
+    r.add_sphere(pos, D, pi, cv=0.5)
+    r.set_gravity((0, 0, g))
+    r.init_equilibrium()
+    u.step(40)
+    r.step(40)
+    gu = u.populations()
+    xyz, gr = r.real_cells(0)
+    lin = xyz[:, 0] + 32 * (xyz[:, 1] + 32 * xyz[:, 2])
+    assert np.abs(gu[:, lin].T - gr).max() < 1e-13
+    hu, hr = u.history(), r.history()
+    assert np.abs(hu - hr).max() < 1e-13
+
+
+@pytest.mark.parametrize("levels,rescale", [(2, True), (2, False), (3, True)])
+def test_uniform_flow_exact_across_levels(orc, levels, rescale):
+    shape = (48, 48, 64) if levels == 3 else (32, 32, 48)
+    s = orc.RefinedSim(shape, levels, tau=0.7, rescale=rescale)
+    f = 1 << (levels - 1)
+    s.refine_box((10 * f, 12 * f, 14 * f), (22 * f, 20 * f, 30 * f))
+    u = (0.02, -0.01, 0.005)
+    s.init_equilibrium(u=u)
+    s.step(2)
+    e = eq_dev(u)
+    for l in range(levels):
+        _, g = s.real_cells(l)
+        assert len(g) > 0
+        assert np.abs(g - e[None, :]).max() < 2e-16
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_mass_momentum_conserved_rescale_off(orc, levels):
+    """Box refinement with edges and corners, a shear wave plus a uniform
+    drift, periodic domain: total mass and momentum over the hierarchy are
+    conserved to rounding with the plain (unscaled) transfer."""
+    shape = (48, 48, 64) if levels == 3 else (32, 32, 48)
+    s = orc.RefinedSim(shape, levels, tau=0.8, rescale=False)
+    f = 1 << (levels - 1)
+    s.refine_box((9 * f, 13 * f, 15 * f), (21 * f, 19 * f, 29 * f))
+    s.init_equilibrium(u=(0.01, 0.004, -0.007), shear=0.01, shear_dir=0, shear_axis=2)
+    m0, p0, scale = totals(s, levels)
+    s.step(4 if levels == 3 else 6)
+    m1, p1, _ = totals(s, levels)
+    assert all(len(s.real_cells(l)[0]) > 0 for l in range(levels))
+    # rounding of the cell updates only (the sums themselves are exact)
+    assert abs(m1 - m0) < 1e-14 * scale
+    assert np.abs(p1 - p0).max() < 1e-14 * scale
+
+
+def test_shear_wave_decay_across_refined_slab(orc):
+    """u_x = A sin(2 pi z / L) with the middle third of z refined (planar
+    interfaces): the mode decays with the finest-level viscosity
+    nu = (tau_f - 1/2)/3 (finest units), since each level's tau follows
+    acoustic scaling.  A wrong per-level tau makes the coarse region decay at
+    a different rate and the mode amplitude is off by far more than 1%."""
+    shape = (16, 16, 96)
+    tau_f = 0.8
+    s = orc.RefinedSim(shape, 2, tau=tau_f, rescale=False)
+    s.refine_box((0, 0, 64), (32, 32, 128))
+    A = 1e-3
+    s.init_equilibrium(shear=A, shear_dir=0, shear_axis=2)
+    T = 150   # coarse steps = 300 finest steps
+    s.step(T)
+    nu = (tau_f - 0.5) / 3
+    Lz = 96 * 2
+    k = 2 * np.pi / Lz
+    expect = np.exp(-nu * k * k * 2 * T)
+    # volume-weighted projection on sin(k z) over both levels
+    num = den = 0.0
+    for l in range(2):
+        xyz, g = s.real_cells(l)
+        h = 2 ** (1 - l)
+        ux = g @ C[:, 0].astype(float)
+        z = (xyz[:, 2] + 0.5) * h
+        num += np.sum(ux * np.sin(k * z)) * h ** 3
+        den += np.sum(np.sin(k * z) ** 2) * h ** 3
+    assert abs(num / den / A / expect - 1) < 1e-3
+
+
+def _neighbours(nb, p, periodic=(1, 1, 1)):
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if dx == dy == dz == 0:
+                    continue
+                c = [p[0] + dx, p[1] + dy, p[2] + dz]
+                ok = True
+                for k in range(3):
+                    if c[k] < 0 or c[k] >= nb[k]:
+                        if periodic[k]:
+                            c[k] %= nb[k]
+                        else:
+                            ok = False
+                if ok:
+                    yield tuple(c)
+
+
+def test_block_forest_balanced_and_complete(orc):
+    shape = (32, 32, 64)
+    s = orc.RefinedSim(shape, 3, tau=0.55)
+    pos = (60.3, 70.7, 130.2)   # finest units (x4)
+    s.add_sphere(pos, 20.0, 0.5, cv=0.5)
+    # finest-level level map: for each finest block position, the level of the block covering it
+    nbs = [tuple(v // 16 for v in s.level_shape(l)) for l in range(3)]
+    maps = [s.block_map(l).reshape(nbs[l][2], nbs[l][1], nbs[l][0]) for l in range(3)]
+    nbf = nbs[2]
+    level = -np.ones((nbf[2], nbf[1], nbf[0]), dtype=int)
+    for l in range(3):
+        f = 1 << (2 - l)
+        real = maps[l] >= 0
+        up = np.repeat(np.repeat(np.repeat(real, f, 0), f, 1), f, 2)
+        assert not np.any(level[up] >= 0)    # no overlap between levels
+        level[up] = l
+    assert np.all(level >= 0)                # every position covered once
+    # 2:1 balance between any two touching blocks (checked at finest granularity)
+    for z in range(nbf[2]):
+        for y in range(nbf[1]):
+            for x in range(nbf[0]):
+                for c in _neighbours(nbf, (x, y, z)):
+                    assert abs(level[z, y, x] - level[c[2], c[1], c[0]]) <= 1
+    # completeness: the eight children of a block are covered at the finer
+    # level (real there or refined further) together or not at all
+    for l in (1, 2):
+        f = 1 << (2 - l)
+        cov = (level >= l).reshape(nbs[l][2], f, nbs[l][1], f, nbs[l][0], f).all(axis=(1, 3, 5))
+        oct_ = cov.reshape(nbs[l][2] // 2, 2, nbs[l][1] // 2, 2, nbs[l][0] // 2, 2).sum(axis=(1, 3, 5))
+        assert np.all((oct_ == 0) | (oct_ == 8))
+    # the sphere's blocks and their neighbours are on the finest level
+    r = 10.0
+    lo = [int(np.floor((pos[k] - r - 1) / 16)) for k in range(3)]
+    hi = [int(np.floor((pos[k] + r + 1) / 16)) for k in range(3)]
+    for z in range(lo[2] - 1, hi[2] + 2):
+        for y in range(lo[1] - 1, hi[1] + 2):
+            for x in range(lo[0] - 1, hi[0] + 2):
+                assert level[z % nbf[2], y % nbf[1], x % nbf[0]] == 2
+
+
+def test_refined_sphere_matches_uniform_fine_before_interface(orc):
+    """Fluid at rest, sphere released: information moves one cell per step,
+    and the nearest coarse cell is more than 16 finest cells from the sphere,
+    so for the first 8 finest steps (2 coarse steps of a 3-level grid) the
+    refined run reproduces the uniform finest-resolution run near the sphere."""
+    shape_c = (16, 16, 16)
+    D, pi, gz = 10.0, 0.3, -2e-4
+    pos = (30.7, 33.2, 31.6)
+    r = orc.RefinedSim(shape_c, 3, tau=0.7)
+    r.add_sphere(pos, D, pi, cv=0.5)
+    r.set_gravity((0, 0, gz))
+    r.init_equilibrium()
+    u = orc.UniformSim((64, 64, 64), tau=0.7)
+    u.add_sphere(pos, D, pi, cv=0.5)
+    u.set_gravity((0, 0, gz))
+    u.init_equilibrium()
+    r.step(2)
+    u.step(8)
+    hr, hu = r.history(), u.history()
+    assert hr.shape == hu.shape == (8, 15)
+    assert np.abs(hr - hu).max() < 1e-13
+    assert np.abs(hu[:, 0:3]).max() > 1e-6   # the sphere does feel a force
+
+
+def test_regrid_keeps_uniform_flow_and_mass(orc):
+    """Moving the refined region (regrid with refinement and coarsening)
+    copies, explodes or averages populations only: a uniform flow stays
+    exact, and with rescaling off the mass of a shear wave is unchanged."""
+    shape = (48, 48, 48)
+    for rescale in (True, False):
+        s = orc.RefinedSim(shape, 2, tau=0.7, rescale=rescale)
+        s.refine_box((8, 8, 8), (24, 40, 24))
+        s.init_equilibrium(u=(0.01, 0.0, -0.02), shear=0.0 if rescale else 0.01)
+        s.step(2)
+        m0, p0, scale = totals(s, 2)
+        before = [s.block_map(l).copy() for l in range(2)]
+        s.refine_box((50, 40, 52), (70, 64, 84))
+        m1, p1, _ = totals(s, 2)
+        after = [s.block_map(l) for l in range(2)]
+        # blocks were both refined and coarsened, and both levels keep cells
+        assert np.any((before[1] >= 0) & (after[1] < 0)) and np.any((before[1] < 0) & (after[1] >= 0))
+        assert all(len(s.real_cells(l)[0]) > 0 for l in range(2))
+        s.step(2)
+        if rescale:
+            e = eq_dev((0.01, 0.0, -0.02))
+            for l in range(2):
+                _, g = s.real_cells(l)
+                assert np.abs(g - e[None, :]).max() < 2e-16
+        else:
+            assert abs(m1 - m0) < 1e-14 * scale
+            assert np.abs(p1 - p0).max() < 1e-14 * scale
