@@ -67,7 +67,7 @@ typedef struct {
     double magic;            /* TRT magic parameter Lambda (Sec. 2.1); 3/16 by default */
     int boundary;            /* LBMP_CLI (Sec. 2.3) or LBMP_SBB (delta = 1/2 on every link) */
     int force_average;       /* 1: average F/T over two steps (Algorithm 1) */
-    int rescale_noneq;       /* refined grids: rescale non-equilibrium parts at level interfaces */
+    int rescale_noneq;       /* refined grids: rescale non-equilibrium parts at level interfaces (default 0) */
     int regrid_interval;     /* refined grids: coarse steps between regrids, 0 = manual */
     int history_capacity;    /* particle history records kept on the device (ring) */
     int fp16_scale_log2;     /* LBMP_FP16: deviations are stored times 2^fp16_scale_log2 */
@@ -150,6 +150,43 @@ lbmp_status lbmp_get_flags(lbmp_handle* h, uint8_t* out, size_t cap);
 /* Boundary links (x fluid, x + c_q solid) with their wall distance delta_q
  * (Sec. 2.3); order unspecified.  *n receives the number of links. */
 lbmp_status lbmp_get_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n);
+
+/* ------------------------------------------------------------------------
+ * Refined (block-structured) grids, config.levels > 1 (Sec. 4.1, 4.2.1).
+ * nx, ny, nz are level-0 cells (multiples of 16, blocks of 16^3 cells);
+ * level l has cells half the size of level l-1; positions, diameters and
+ * tau are those of the finest level; lbmp_step advances level-0 steps, each
+ * made of 2^l steps of level l.  Interface transfer: explosion into ghost
+ * cells and coalescence of ghost cells into the coarser cells next to the
+ * finer region (Rohde's scheme named in Sec. 4.1), optionally with the
+ * non-equilibrium part rescaled (config.rescale_noneq).  The sphere and the
+ * blocks around it stay on the finest level: its blocks and their 26
+ * neighbours are finest, every coarser level adds the 26 neighbours of the
+ * next finer level's parents (2:1 balance), and the hierarchy is rebuilt
+ * every config.regrid_interval level-0 steps (0: only on lbmp_regrid).
+ * Uniform-grid-only calls (populations, gather, flags) return
+ * LBMP_ERR_UNSUPPORTED on refined grids; lbmp_get_level_cells replaces them.
+ */
+
+/* Equilibrium with velocity u + amp sin(2 pi (x_axis + 1/2) / L_axis) e_dir,
+ * x and L in finest-level cells; works on both grid kinds. */
+lbmp_status lbmp_init_fluid_wave(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis);
+/* Refines the finest-level blocks intersecting [lo, hi) (finest units), in
+ * addition to the sphere's blocks, and rebuilds the hierarchy now. */
+lbmp_status lbmp_refine_box(lbmp_handle* h, const double lo[3], const double hi[3]);
+/* Rebuilds the hierarchy for the sphere's current position (regrid). */
+lbmp_status lbmp_regrid(lbmp_handle* h);
+/* Cells of a level across the domain. */
+lbmp_status lbmp_level_shape(lbmp_handle* h, int level, int out[3]);
+/* Block-position map of a level (x fastest): real block index in position
+ * order (>= 0), -2 ghost block, -1 no block of this level.  *n = positions. */
+lbmp_status lbmp_get_block_map(lbmp_handle* h, int level, int32_t* out, size_t cap, size_t* n);
+/* Real cells of a level in block order (x fastest within a block): global
+ * level coordinates xyz[n][3] and FP64 deviations g[n][19].  *n = cells;
+ * pass cap = 0 to query. */
+lbmp_status lbmp_get_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n);
+/* Cell updates and kernel launches of one (level-0) step. */
+lbmp_status lbmp_updates_per_step(lbmp_handle* h, int64_t* updates, int32_t* launches);
 
 /* Counters: [0] steps, [1] cell updates (MLUPS numerator), [2] kernel
  * launches, [3] host-to-device bytes, [4] device-to-host bytes copied by

@@ -20,7 +20,9 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_set_tau", "lbmp_set_gravity", "lbmp_set_body_force", "lbmp_init_fluid", "lbmp_set_populations",
            "lbmp_get_populations", "lbmp_gather_populations", "lbmp_step", "lbmp_step_async", "lbmp_check_status", "lbmp_synchronize",
            "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
-           "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error", "PRECISIONS"]
+           "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error",
+           "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_level_shape", "lbmp_get_block_map",
+           "lbmp_get_level_cells", "lbmp_updates_per_step", "PRECISIONS"]
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
 BC = {"periodic": 0, "noslip": 1}
@@ -227,6 +229,52 @@ def lbmp_boundary_cells_noalloc(flags_ptr, shape, periodic, center, diameter, li
                                                     ctypes.c_void_p(count_ptr), ctypes.c_void_p(stream_ptr)))
 
 
+def lbmp_init_fluid_wave(h, rho=1.0, u=(0.0, 0.0, 0.0), amp=0.0, direction=0, axis=2):
+    a = _vec3(u)
+    _check(h, _lib().lbmp_init_fluid_wave(h, float(rho), _dp(a), float(amp), int(direction), int(axis)))
+
+
+def lbmp_refine_box(h, lo, hi):
+    a, b = _vec3(lo), _vec3(hi)
+    _check(h, _lib().lbmp_refine_box(h, _dp(a), _dp(b)))
+
+
+def lbmp_regrid(h):
+    _check(h, _lib().lbmp_regrid(h))
+
+
+def lbmp_level_shape(h, level):
+    out = (ctypes.c_int * 3)()
+    _check(h, _lib().lbmp_level_shape(h, int(level), out))
+    return tuple(out)
+
+
+def lbmp_get_block_map(h, level):
+    n = ctypes.c_size_t(0)
+    _check(h, _lib().lbmp_get_block_map(h, int(level), None, 0, ctypes.byref(n)))
+    out = np.empty(n.value, dtype=np.int32)
+    _check(h, _lib().lbmp_get_block_map(h, int(level), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), out.size,
+                                        ctypes.byref(n)))
+    return out
+
+
+def lbmp_get_level_cells(h, level):
+    n = ctypes.c_size_t(0)
+    _check(h, _lib().lbmp_get_level_cells(h, int(level), None, None, 0, ctypes.byref(n)))
+    xyz = np.empty((n.value, 3), dtype=np.int32)
+    g = np.empty((n.value, 19), dtype=np.float64)
+    if n.value:
+        _check(h, _lib().lbmp_get_level_cells(h, int(level), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                              _dp(g), n.value, ctypes.byref(n)))
+    return xyz, g
+
+
+def lbmp_updates_per_step(h):
+    u, l = ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(h, _lib().lbmp_updates_per_step(h, ctypes.byref(u), ctypes.byref(l)))
+    return u.value, l.value
+
+
 def lbmp_last_error(h=None):
     m = _lib().lbmp_last_error(h)
     return m.decode() if m else ""
@@ -263,13 +311,15 @@ class Simulation:
 
     def __init__(self, shape, precision="fp32", tau=0.6, magic=3.0 / 16.0, bc=("periodic",) * 3, boundary="cli",
                  force_average=True, history_capacity=4096, fp16_scale_log2=11, stream=None,
-                 torch_allocator=True):
+                 torch_allocator=True, levels=1, rescale=False, regrid_interval=0):
         import torch
         if not torch.cuda.is_available():
             raise LbmpError(3, "no CUDA device: this library has no CPU path")
         cfg = lbmp_config_default()
         cfg.nx, cfg.ny, cfg.nz = (int(v) for v in shape)
-        cfg.levels = 1
+        cfg.levels = int(levels)
+        cfg.rescale_noneq = int(bool(rescale))
+        cfg.regrid_interval = int(regrid_interval)
         cfg.bc = (ctypes.c_int * 3)(*[BC[b] for b in bc])
         cfg.precision = PRECISIONS[precision]
         cfg.tau = float(tau)
@@ -358,6 +408,28 @@ class Simulation:
 
     def links(self):
         return lbmp_get_links(self.h)
+
+    def init_fluid_wave(self, rho=1.0, u=(0.0, 0.0, 0.0), amp=0.0, direction=0, axis=2):
+        lbmp_init_fluid_wave(self.h, rho, u, amp, direction, axis)
+
+    def refine_box(self, lo, hi):
+        lbmp_refine_box(self.h, lo, hi)
+
+    def regrid(self):
+        lbmp_regrid(self.h)
+
+    def level_shape(self, level):
+        return lbmp_level_shape(self.h, level)
+
+    def block_map(self, level):
+        return lbmp_get_block_map(self.h, level)
+
+    def level_cells(self, level):
+        return lbmp_get_level_cells(self.h, level)
+
+    def updates_per_step(self):
+        """(cell updates, kernel launches) of one level-0 step."""
+        return lbmp_updates_per_step(self.h)
 
     def counters(self):
         """(steps, cell updates, kernel launches, h2d bytes, d2h bytes)."""

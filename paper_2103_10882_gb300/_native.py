@@ -69,6 +69,17 @@ SIGNATURES = {
     "lbmp_boundary_cells_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                    ctypes.POINTER(ctypes.c_int), c_double_p, ctypes.c_double,
                                                    ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "lbmp_init_fluid_wave": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, c_double_p, ctypes.c_double,
+                                            ctypes.c_int, ctypes.c_int]),
+    "lbmp_refine_box": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p]),
+    "lbmp_regrid": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbmp_level_shape": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "lbmp_get_block_map": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbmp_get_level_cells": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                            c_double_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbmp_updates_per_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int32)]),
     "lbmp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 

@@ -1,0 +1,1440 @@
+// Refined-grid engine: block-structured levels (Sec. 4.1) with the particle
+// refinement criterion (Sec. 4.2.1) and the coupling of Algorithm 1 on the
+// finest level.
+//
+// Levels l = 0..L-1 (L-1 finest) are sets of 16^3-cell blocks; a level-(l+1)
+// cell is half a level-l cell.  Each level keeps its real blocks and its
+// ghost blocks (cells of the next coarser level seen at this level's
+// resolution) in one pool, real blocks first, both in block-position order.
+// One level-l step (recursive, finer levels sub-cycled twice, Rohde's scheme
+// named in Sec. 4.1):
+//   k_explode   ghost cells of level l+1 <- post-collision level-l cell containing them
+//   (two level-(l+1) steps)
+//   k_update    real level-l cells: pull from real/ghost neighbours, or, for
+//               hosts (neighbours of the finer region), the mean of their
+//               eight ghost sub-cells (coalescence); then TRT collide.  Active
+//               ghost cells stream without colliding; static ghost cells stand
+//               for coarse content translating rigidly.
+//   finest level: k_amr_boundary (CLI links + momentum-exchange partials),
+//               particle update, remap (flags, refill, boundary cells).
+// The layout (which blocks exist at which level) is integer work done on the
+// host from the particle position; per-cell classifications and all
+// population work run in the kernels below.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <new>
+#include <type_traits>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "amr.h"
+#include "physics.cuh"
+
+namespace lbmp {
+namespace {
+
+constexpr int BS = 16;
+constexpr int B3 = BS * BS * BS;
+constexpr int MAXL = 6;
+constexpr int UPD_THREADS = 256;
+constexpr int STATUS_AMR_MISSING = 8;    // a pull found no source cell
+constexpr int STATUS_NOT_FINEST = 16;    // the sphere's box left the finest level
+
+// Device view of one level.
+struct LevelView {
+    int n[3];          // cells across the domain
+    int nb[3];         // block positions
+    int nreal, npool;
+    int periodic[3];
+    const int* map;        // block position -> real id, -2 - ghost id, -1 none
+    const int* bpos;       // [npool][3]
+    const int* nbr;        // [npool][27] pool ids of neighbour blocks, -1 none, -2 wall
+    const uint8_t* host;   // [nreal][B3] 1 host, 2 second ring (levels below the finest)
+    const uint8_t* gkind;  // [npool - nreal][B3] 1 active, 2 static, 0 unused
+    const uint8_t* refined;  // block positions covered by the next finer level
+};
+
+__device__ __forceinline__ bool wrap3(int c[3], const LevelView& V) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (c[a] < 0 || c[a] >= V.n[a]) {
+            if (!V.periodic[a]) return false;
+            c[a] = c[a] < 0 ? c[a] + V.n[a] : c[a] - V.n[a];
+        }
+    }
+    return true;
+}
+
+// Pool block (or -1) and local index of wrapped global level coordinates.
+__device__ __forceinline__ int locate(const LevelView& V, const int c[3], int* cell) {
+    const int m = V.map[(c[0] >> 4) + V.nb[0] * ((c[1] >> 4) + V.nb[1] * (c[2] >> 4))];
+    *cell = (c[0] & 15) + BS * ((c[1] & 15) + BS * (c[2] & 15));
+    if (m >= 0) return m;
+    if (m <= -2) return V.nreal + (-2 - m);
+    return -1;
+}
+
+__device__ __forceinline__ size_t paddr(int b, int q, int c) { return ((size_t)b * 19 + q) * B3 + c; }
+
+template <typename A>
+__device__ __forceinline__ A geq_dev(int q, A drho, const A u[3], A uu) {
+    const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
+    return wgt<A>(q) * (drho + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+}
+
+// f = f_eq + kappa+ (f+ - f_eq+) + kappa- (f- - f_eq-), equilibrium from f's own moments.
+template <typename A>
+__device__ __forceinline__ void rescale19(A f[19], A kp, A km) {
+    A drho = A(0), u[3] = {A(0), A(0), A(0)};
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        drho += f[q];
+        u[0] += A(cx(q)) * f[q];
+        u[1] += A(cy(q)) * f[q];
+        u[2] += A(cz(q)) * f[q];
+    }
+    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const A e0 = geq_dev<A>(0, drho, u, uu);
+    f[0] = e0 + kp * (f[0] - e0);
+#pragma unroll
+    for (int q = 1; q < 19; q += 2) {
+        const A eq = geq_dev<A>(q, drho, u, uu), eb = geq_dev<A>(q + 1, drho, u, uu);
+        const A ep = A(0.5) * (eq + eb), em = A(0.5) * (eq - eb);
+        const A fp = A(0.5) * (f[q] + f[q + 1]), fm = A(0.5) * (f[q] - f[q + 1]);
+        f[q] = ep + kp * (fp - ep) + em + km * (fm - em);
+        f[q + 1] = ep + kp * (fp - ep) - em - km * (fm - em);
+    }
+}
+
+// --------------------------------------------------------------- explosion
+template <typename S>
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0, S* __restrict__ f1,
+              typename Store<S>::A kp, typename Store<S>::A km, int rescale, typename Store<S>::A scale,
+              typename Store<S>::A inv_scale, int* __restrict__ status) {
+    using A = typename Store<S>::A;
+    const int gb = blockIdx.x;
+    const int b = F.nreal + gb;
+    const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += UPD_THREADS) {
+        if (!F.gkind[(size_t)gb * B3 + c]) continue;
+        const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
+        int pc;
+        const int pb = locate(C, p, &pc);
+        if (pb < 0 || pb >= C.nreal) {
+            atomicOr(status, STATUS_AMR_MISSING);
+            continue;
+        }
+        A f[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(csrc + paddr(pb, q, pc), inv_scale);
+        if (rescale) rescale19<A>(f, kp, km);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
+            Store<S>::store(f1 + paddr(b, q, c), f[q], scale);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- update
+template <typename S>
+struct UpdateArgs {
+    using A = typename Store<S>::A;
+    LevelView D;
+    const S* src;
+    S* dst;
+    CollideParams<A> P;
+    int substep;              // index of this step within the coarser level's step
+    int rescale;
+    // coalescence from the next finer level
+    LevelView F;
+    const S* fsrc;
+    A fkp, fkm;
+    // rigid translation through static ghosts: exploded values of the next coarser level
+    LevelView Cc;
+    const S* csrc;
+    A ckp, ckm;
+    const uint8_t* solid;     // finest level with a sphere: solid flags of real cells
+    int* status;
+};
+
+template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
+__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs<S> U) {
+    using A = typename Store<S>::A;
+    __shared__ int nb27[27];
+    const LevelView& D = U.D;
+    const int b = blockIdx.x;
+    if (threadIdx.x < 27) nb27[threadIdx.x] = D.nbr[b * 27 + threadIdx.x];
+    __syncthreads();
+    const bool real = b < D.nreal;
+    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+    const A scale = U.P.scale, inv = U.P.inv_scale;
+    for (int lz = 0; lz < BS; ++lz) {
+        const int c = lx + BS * (ly + BS * lz);
+        if (!real) {
+            const uint8_t k = D.gkind[(size_t)(b - D.nreal) * B3 + c];
+            if (k == 0) continue;
+            if (k == 2) {
+#pragma unroll
+                for (int q = 0; q < 19; ++q) U.dst[paddr(b, q, c)] = U.src[paddr(b, q, c)];
+                continue;
+            }
+        } else if (COUPLED && U.solid[(size_t)b * B3 + c]) {
+#pragma unroll
+            for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), scale);
+            continue;
+        }
+        A g[19];
+        if (HAS_FINE && real && D.host[(size_t)b * B3 + c] == 1) {
+            // coalescence: mean of the eight ghost sub-cells after the finer level's two steps
+#pragma unroll
+            for (int q = 0; q < 19; ++q) g[q] = A(0);
+            const int gx = 2 * (bx * BS + lx), gy = 2 * (by * BS + ly), gz = 2 * (bz * BS + lz);
+            for (int s = 0; s < 8; ++s) {
+                const int v[3] = {gx + (s & 1), gy + ((s >> 1) & 1), gz + (s >> 2)};
+                int vc;
+                const int vb = locate(U.F, v, &vc);
+                if (vb < U.F.nreal) {
+                    atomicOr(U.status, STATUS_AMR_MISSING);
+                    continue;
+                }
+#pragma unroll
+                for (int q = 0; q < 19; ++q) g[q] += Store<S>::load(U.fsrc + paddr(vb, q, vc), inv);
+            }
+#pragma unroll
+            for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
+            if (U.rescale) rescale19<A>(g, U.fkp, U.fkm);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 19; ++q) {
+                const int sx = lx - cx(q), sy = ly - cy(q), sz = lz - cz(q);
+                const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
+                const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
+                const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
+                const int nbk = (ox | oy | oz) == 0 ? b : nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+                if (nbk == -2) {   // domain wall: bounce-back
+                    g[q] = Store<S>::load(U.src + paddr(b, opp(q), c), inv);
+                    continue;
+                }
+                if (nbk < 0) {
+                    atomicOr(U.status, STATUS_AMR_MISSING);
+                    g[q] = A(0);
+                    continue;
+                }
+                const int sc = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
+                if (HAS_COARSE && nbk >= D.nreal && U.substep == 1 &&
+                    D.gkind[(size_t)(nbk - D.nreal) * B3 + sc] == 2) {
+                    // static ghost at the second step: content of the coarser cell one more step upwind
+                    int t[3] = {bx * BS + sx - cx(q), by * BS + sy - cy(q), bz * BS + sz - cz(q)};
+                    if (wrap3(t, D)) {
+                        const int p[3] = {t[0] >> 1, t[1] >> 1, t[2] >> 1};
+                        int pc;
+                        const int pb = locate(U.Cc, p, &pc);
+                        if (pb < 0 || pb >= U.Cc.nreal) {
+                            atomicOr(U.status, STATUS_AMR_MISSING);
+                            g[q] = A(0);
+                            continue;
+                        }
+                        A f[19];
+#pragma unroll
+                        for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
+                        if (U.rescale) rescale19<A>(f, U.ckp, U.ckm);
+                        g[q] = f[q];
+                        continue;
+                    }
+                }
+                g[q] = Store<S>::load(U.src + paddr(nbk, q, sc), inv);
+            }
+        }
+        if (real) trt_collide<A, false>(g, U.P, U.status);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], scale);
+    }
+}
+
+// ---------------------------------------------------------------- coupling
+// Pool block of the neighbour of (b, local l) displaced by d (|d| <= 1 per
+// axis), with the local index; -2 wall, -1 none.
+__device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int ly, int lz, int dx, int dy, int dz,
+                                        int* cell) {
+    const int sx = lx + dx, sy = ly + dy, sz = lz + dz;
+    const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
+    const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
+    const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
+    *cell = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
+    return (ox | oy | oz) == 0 ? b : D.nbr[b * 27 + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+}
+
+constexpr int BND_THREADS = 128;
+
+template <typename S>
+__global__ void __launch_bounds__(BND_THREADS)
+    k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
+                   const int* __restrict__ list, const int* __restrict__ count,
+                   CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
+                   double* __restrict__ partials, int* __restrict__ status) {
+    using A = typename Store<S>::A;
+    __shared__ double red[6][BND_THREADS / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    if (i < *count) {
+        const int e = list[i];
+        const int b = e >> 12, c = e & 4095;
+        const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
+        const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly, D.bpos[3 * b + 2] * BS + lz};
+        const ParticleState& Pp = *ps;
+        const double d[3] = {wrap_diff((g[0] + 0.5) - Pp.x[0], D.n[0], D.periodic[0]),
+                             wrap_diff((g[1] + 0.5) - Pp.x[1], D.n[1], D.periodic[1]),
+                             wrap_diff((g[2] + 0.5) - Pp.x[2], D.n[2], D.periodic[2])};
+        A gq[19];
+        for (int q = 0; q < 19; ++q) {
+            int sc;
+            const int sb = nbr_cell(D, b, lx, ly, lz, -cx(q), -cy(q), -cz(q), &sc);
+            if (sb == -2) {
+                gq[q] = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
+                continue;
+            }
+            if (sb < 0) {
+                atomicOr(status, STATUS_AMR_MISSING);
+                gq[q] = A(0);
+                continue;
+            }
+            if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] == 0) {
+                gq[q] = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
+                continue;
+            }
+            const int k = opp(q);   // points from the cell into the solid
+            int fc;
+            const int fb = nbr_cell(D, b, lx, ly, lz, cx(q), cy(q), cz(q), &fc);   // x - c_k
+            const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
+            const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+            const double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
+            const double alpha = 4.0 / (1.0 + 2.0 * delta);
+            const double arm[3] = {d[0] + delta * cx(k), d[1] + delta * cy(k), d[2] + delta * cz(k)};
+            const double vb[3] = {Pp.u[0] + (Pp.w[1] * arm[2] - Pp.w[2] * arm[1]),
+                                  Pp.u[1] + (Pp.w[2] * arm[0] - Pp.w[0] * arm[2]),
+                                  Pp.u[2] + (Pp.w[0] * arm[1] - Pp.w[1] * arm[0])};
+            const double vc = vb[0] * cx(k) + vb[1] * cy(k) + vb[2] * cz(k);
+            const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
+            const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
+            const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
+            const A gnew = gt_k + A(kappa0) * gt_far - A(kappa0) * gt_q - A(alpha * 3.0 * wgt<double>(k) * vc);
+            gq[q] = gnew;
+            const double ftk = wgt<double>(k) + (double)gt_k;
+            const double fnew = wgt<double>(q) + (double)gnew;
+            const double Fl[3] = {(cx(k) - vb[0]) * ftk - (cx(q) - vb[0]) * fnew,
+                                  (cy(k) - vb[1]) * ftk - (cy(q) - vb[1]) * fnew,
+                                  (cz(k) - vb[2]) * ftk - (cz(q) - vb[2]) * fnew};
+            F[0] += Fl[0];
+            F[1] += Fl[1];
+            F[2] += Fl[2];
+            T[0] += arm[1] * Fl[2] - arm[2] * Fl[1];
+            T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
+            T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
+        }
+        trt_collide<A, false>(gq, P, status);
+        for (int q = 0; q < 19; ++q) Store<S>::store(dst + paddr(b, q, c), gq[q], P.scale);
+    }
+    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int w = 0; w < BND_THREADS / 32; ++w) s += red[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+    }
+}
+
+__device__ __forceinline__ bool ball(const int g[3], const LevelView& D, const ParticleState& P) {
+    const double dx = wrap_diff(__dsub_rn((double)g[0] + 0.5, P.x[0]), D.n[0], D.periodic[0]);
+    const double dy = wrap_diff(__dsub_rn((double)g[1] + 0.5, P.x[1]), D.n[1], D.periodic[1]);
+    const double dz = wrap_diff(__dsub_rn((double)g[2] + 0.5, P.x[2]), D.n[2], D.periodic[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 <= __dmul_rn(P.r, P.r);
+}
+
+// Box of finest cells around the sphere (same box as the uniform engine's).
+__device__ __forceinline__ bool amr_box_cell(int t, const LevelView& D, const BoxDesc& B, const ParticleState& P,
+                                             int g[3]) {
+    const int e0 = B.E[0], e1 = B.E[1];
+    const int tk = t / (e0 * e1);
+    const int r = t - tk * e0 * e1;
+    const int tt[3] = {r - (r / e0) * e0, r / e0, tk};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int o = (B.E[a] >= D.n[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
+        int v = o + tt[a];
+        if (v < 0 || v >= D.n[a]) {
+            if (!D.periodic[a]) return false;
+            v = v < 0 ? v + D.n[a] : v - D.n[a];
+        }
+        g[a] = v;
+    }
+    return true;
+}
+
+__global__ void k_amr_flags_box(LevelView D, uint8_t* __restrict__ fnext, BoxDesc B,
+                                const ParticleState* __restrict__ ps, int* __restrict__ status) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.cells) return;
+    const ParticleState P = *ps;
+    int g[3];
+    if (!amr_box_cell(t, D, B, P, g)) return;
+    int c;
+    const int b = locate(D, g, &c);
+    if (b < 0 || b >= D.nreal) {
+        atomicOr(status, STATUS_NOT_FINEST);
+        return;
+    }
+    fnext[(size_t)b * B3 + c] = ball(g, D, P) ? 1 : 0;
+}
+
+template <typename S>
+__global__ void k_amr_refill(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ fcur,
+                             const uint8_t* __restrict__ fnext, BoxDesc B, const ParticleState* __restrict__ ps,
+                             typename Store<S>::A scale, typename Store<S>::A inv_scale) {
+    using A = typename Store<S>::A;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= B.cells) return;
+    const ParticleState P = *ps;
+    int g[3];
+    if (!amr_box_cell(t, D, B, P, g)) return;
+    int c;
+    const int b = locate(D, g, &c);
+    if (b < 0 || b >= D.nreal) return;
+    const size_t x = (size_t)b * B3 + c;
+    if (fnext[x] != 0) {
+        for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
+        return;
+    }
+    if (fcur[x] == 0) return;
+    A rsum = A(0);
+    int cnt = 0;
+    for (int q = 1; q < 19; ++q) {
+        int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
+        if (!wrap3(v, D)) continue;
+        int vc;
+        const int vb = locate(D, v, &vc);
+        if (vb < 0 || vb >= D.nreal) continue;
+        const size_t y = (size_t)vb * B3 + vc;
+        if (fcur[y] != 0 || fnext[y] != 0) continue;
+        A r = A(1);
+        for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
+        rsum += r;
+        cnt += 1;
+    }
+    const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
+    const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
+                         wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
+                         wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
+    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), geq_dev<A>(q, rho - A(1), u, uu), scale);
+}
+
+constexpr int LINK_THREADS = 256;
+
+__global__ void __launch_bounds__(LINK_THREADS)
+    k_amr_links_mark(LevelView D, const uint8_t* __restrict__ flags, BoxDesc B, const ParticleState* __restrict__ ps,
+                     uint8_t* __restrict__ mask, int* __restrict__ block_count) {
+    const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
+    int is_b = 0;
+    if (t < B.cells) {
+        int g[3];
+        if (amr_box_cell(t, D, B, *ps, g)) {
+            int c;
+            const int b = locate(D, g, &c);
+            if (b >= 0 && b < D.nreal && flags[(size_t)b * B3 + c] == 0) {
+                for (int q = 1; q < 19; ++q) {
+                    int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
+                    if (!wrap3(v, D)) continue;
+                    int vc;
+                    const int vb = locate(D, v, &vc);
+                    if (vb >= 0 && vb < D.nreal && flags[(size_t)vb * B3 + vc] != 0) is_b = 1;
+                }
+            }
+        }
+        mask[t] = (uint8_t)is_b;
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
+    __shared__ int wsum[LINK_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < LINK_THREADS / 32; ++w) s += wsum[w];
+        block_count[blockIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(LINK_THREADS)
+    k_amr_links_emit(LevelView D, const uint8_t* __restrict__ mask, const int* __restrict__ block_count, BoxDesc B,
+                     const ParticleState* __restrict__ ps, int* __restrict__ list, int* __restrict__ count,
+                     int capacity, int* __restrict__ status) {
+    __shared__ int red[LINK_THREADS];
+    __shared__ int wsum[LINK_THREADS / 32];
+    int s = 0;
+    for (int b = threadIdx.x; b < (int)blockIdx.x; b += LINK_THREADS) s += block_count[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = LINK_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    const int base = red[0];
+    const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
+    const int is_b = t < B.cells ? mask[t] : 0;
+    const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wsum[warp] = __popc(ballot);
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += wsum[w];
+    if (is_b) {
+        int g[3], c;
+        amr_box_cell(t, D, B, *ps, g);
+        const int b = locate(D, g, &c);
+        const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
+        if (pos < capacity) list[pos] = (b << 12) | c;
+        else atomicOr(status, STATUS_LINK_OVERFLOW);
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        int tot = base;
+        for (int w = 0; w < LINK_THREADS / 32; ++w) tot += wsum[w];
+        *count = tot < capacity ? tot : capacity;
+    }
+}
+
+// ------------------------------------------------------ classification
+// Host flag of every real cell: 1 when a cell covered by the next finer
+// level lies within Chebyshev distance 1, 2 when the nearest is at 2.
+__global__ void k_host_flags(LevelView D, uint8_t* __restrict__ host) {
+    const int b = blockIdx.x;
+    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+        const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
+        int dist = 3;
+        for (int dz = -2; dz <= 2; ++dz)
+            for (int dy = -2; dy <= 2; ++dy)
+                for (int dx = -2; dx <= 2; ++dx) {
+                    int v[3] = {g[0] + dx, g[1] + dy, g[2] + dz};
+                    if (!wrap3(v, D)) continue;
+                    if (D.refined[(v[0] >> 4) + D.nb[0] * ((v[1] >> 4) + D.nb[1] * (v[2] >> 4))]) {
+                        const int m = max(abs(dx), max(abs(dy), abs(dz)));
+                        dist = min(dist, m);
+                    }
+                }
+        host[(size_t)b * B3 + c] = dist <= 1 ? 1 : (dist == 2 ? 2 : 0);
+    }
+}
+
+// Kind of every ghost cell of level l+1: the host flag of its parent.
+__global__ void k_ghost_kind(LevelView C, const uint8_t* __restrict__ chost, LevelView F, uint8_t* __restrict__ gkind) {
+    const int gb = blockIdx.x;
+    const int b = F.nreal + gb;
+    const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+        const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
+        int pc;
+        const int pb = locate(C, p, &pc);
+        gkind[(size_t)gb * B3 + c] = (pb >= 0 && pb < C.nreal) ? chost[(size_t)pb * B3 + pc] : 0;
+    }
+}
+
+__global__ void k_amr_flags_full(LevelView D, uint8_t* __restrict__ f0, uint8_t* __restrict__ f1,
+                                 const ParticleState* __restrict__ ps) {
+    const int b = blockIdx.x;
+    const ParticleState P = *ps;
+    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+        const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
+        const uint8_t v = (P.present && ball(g, D, P)) ? 1 : 0;
+        f0[(size_t)b * B3 + c] = v;
+        f1[(size_t)b * B3 + c] = v;
+    }
+}
+
+template <typename S>
+__global__ void k_amr_zero_solid(S* __restrict__ pops, const uint8_t* __restrict__ flags) {
+    using A = typename Store<S>::A;
+    const int b = blockIdx.x;
+    for (int c = threadIdx.x; c < B3; c += blockDim.x)
+        if (flags[(size_t)b * B3 + c])
+            for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), A(1));
+}
+
+template <typename S>
+__global__ void k_amr_init(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ solid, double rho,
+                           double u0, double u1, double u2, double amp, int dir, int axis, double h, double Lax,
+                           typename Store<S>::A scale) {
+    using A = typename Store<S>::A;
+    const int b = blockIdx.x;
+    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+        const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
+        double u[3] = {u0, u1, u2};
+        if (amp != 0.0) u[dir] += amp * sin(2.0 * M_PI * (g[axis] + 0.5) * h / Lax);
+        const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const bool s = solid && solid[(size_t)b * B3 + c];
+        for (int q = 0; q < 19; ++q) {
+            const double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+            const double e = wgt<double>(q) * ((rho - 1.0) + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            Store<S>::store(pops + paddr(b, q, c), s ? A(0) : A(e), scale);
+        }
+    }
+}
+
+// Regrid: every real cell of the new layout from the old layout (copy,
+// explosion of the old coarser cell, or mean of the old finer cells), with
+// the post-collision rescaling chained over the levels crossed.
+template <typename S>
+struct MigrateArgs {
+    using A = typename Store<S>::A;
+    LevelView N;          // new level
+    S* dst;
+    int l;
+    int L;
+    LevelView O[MAXL];    // old levels
+    const S* osrc[MAXL];
+    A kp[MAXL], km[MAXL];  // c->f post-collision factors between level k and k+1
+    int rescale;
+    A scale, inv_scale;
+};
+
+template <typename S>
+__global__ void k_migrate(MigrateArgs<S> M) {
+    using A = typename Store<S>::A;
+    const int b = blockIdx.x;
+    const LevelView& N = M.N;
+    const int bx = N.bpos[3 * b], by = N.bpos[3 * b + 1], bz = N.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+        const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
+        A f[19];
+        for (int q = 0; q < 19; ++q) f[q] = A(0);
+        for (int lo = 0; lo < M.L; ++lo) {
+            const LevelView& O = M.O[lo];
+            if (lo <= M.l) {
+                const int sh = M.l - lo;
+                const int v[3] = {g[0] >> sh, g[1] >> sh, g[2] >> sh};
+                int oc;
+                const int ob = locate(O, v, &oc);
+                if (ob < 0 || ob >= O.nreal) continue;
+                for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(M.osrc[lo] + paddr(ob, q, oc), M.inv_scale);
+                if (M.rescale)
+                    for (int k = lo; k < M.l; ++k) rescale19<A>(f, M.kp[k], M.km[k]);
+                break;
+            } else {
+                const int k = 1 << (lo - M.l);
+                const int v0[3] = {g[0] * k, g[1] * k, g[2] * k};
+                int oc;
+                const int ob = locate(O, v0, &oc);
+                if (ob < 0 || ob >= O.nreal) continue;
+                for (int dz = 0; dz < k; ++dz)
+                    for (int dy = 0; dy < k; ++dy)
+                        for (int dx = 0; dx < k; ++dx) {
+                            const int v[3] = {v0[0] + dx, v0[1] + dy, v0[2] + dz};
+                            const int vb = locate(O, v, &oc);
+                            for (int q = 0; q < 19; ++q)
+                                f[q] += Store<S>::load(M.osrc[lo] + paddr(vb, q, oc), M.inv_scale);
+                        }
+                const A inv = A(1) / A(k * k * k);
+                for (int q = 0; q < 19; ++q) f[q] *= inv;
+                if (M.rescale)
+                    for (int kk = lo - 1; kk >= M.l; --kk) rescale19<A>(f, A(1) / M.kp[kk], A(1) / M.km[kk]);
+                break;
+            }
+        }
+        for (int q = 0; q < 19; ++q) Store<S>::store(M.dst + paddr(b, q, c), f[q], M.scale);
+    }
+}
+
+template <typename S>
+__global__ void k_amr_export(LevelView D, const S* __restrict__ pops, int32_t* __restrict__ xyz,
+                             double* __restrict__ out, typename Store<S>::A inv_scale) {
+    const int b = blockIdx.x;
+    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+        const size_t m = (size_t)b * B3 + c;
+        xyz[3 * m] = bx * BS + (c & 15);
+        xyz[3 * m + 1] = by * BS + ((c >> 4) & 15);
+        xyz[3 * m + 2] = bz * BS + (c >> 8);
+        for (int q = 0; q < 19; ++q) out[m * 19 + q] = (double)Store<S>::load(pops + paddr(b, q, c), inv_scale);
+    }
+}
+
+__global__ void k_amr_export_links(LevelView D, const uint8_t* __restrict__ flags, const int* __restrict__ list,
+                                   const int* __restrict__ count, const ParticleState* __restrict__ ps,
+                                   int64_t* __restrict__ cell_out, int32_t* __restrict__ q_out,
+                                   double* __restrict__ delta_out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *count) return;
+    const int e = list[i];
+    const int b = e >> 12, c = e & 4095;
+    const int g[3] = {D.bpos[3 * b] * BS + (c & 15), D.bpos[3 * b + 1] * BS + ((c >> 4) & 15),
+                      D.bpos[3 * b + 2] * BS + (c >> 8)};
+    const ParticleState& P = *ps;
+    const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
+                         wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
+                         wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
+    for (int q = 1; q < 19; ++q) {
+        const size_t slot = (size_t)i * 18 + (q - 1);
+        cell_out[slot] = (int64_t)g[0] + (int64_t)D.n[0] * ((int64_t)g[1] + (int64_t)D.n[1] * g[2]);
+        int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
+        int vc, vb = -1;
+        if (wrap3(v, D)) vb = locate(D, v, &vc);
+        if (vb >= 0 && vb < D.nreal && flags[(size_t)vb * B3 + vc] != 0) {
+            q_out[slot] = q;
+            delta_out[slot] = link_delta(d, q, P.r);
+        } else {
+            q_out[slot] = -1;
+            delta_out[slot] = 0.0;
+        }
+    }
+}
+
+// =================================================================== host
+using Mask = std::vector<uint8_t>;
+
+struct Level {
+    int n[3] = {0, 0, 0}, nb[3] = {0, 0, 0};
+    int nreal = 0, nghost = 0;
+    std::vector<int> map, bpos, nbr;
+    Mask refined;
+    int* d_map = nullptr;
+    int* d_bpos = nullptr;
+    int* d_nbr = nullptr;
+    uint8_t* d_refined = nullptr;
+    uint8_t* d_host = nullptr;
+    uint8_t* d_gkind = nullptr;
+    void* d_pops[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint8_t* d_flags[2] = {nullptr, nullptr};   // finest level only
+    int fcur = 0;
+    double taup = 0, taum = 0;
+};
+
+}  // namespace
+
+struct AmrEngine {
+    int L = 1;
+    int n0[3] = {0, 0, 0};
+    int periodic[3] = {1, 1, 1};
+    std::vector<Level> lv;
+    bool have_box = false;
+    double box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
+    int substep[MAXL] = {0};
+    int boundary_blocks = 1;
+    long long coarse_steps = 0;
+};
+
+namespace {
+
+size_t esize(const lbmp_handle* h) {
+    return h->cfg.precision == LBMP_FP64 ? 8 : (h->cfg.precision == LBMP_FP32 ? 4 : 2);
+}
+
+template <typename F>
+void with_storage_amr(int prec, F&& f) {
+    if (prec == LBMP_FP64) f((double*)nullptr);
+    else if (prec == LBMP_FP32) f((float*)nullptr);
+    else f((__half*)nullptr);
+}
+
+LevelView view(const AmrEngine* E, const Level& V) {
+    LevelView w;
+    for (int a = 0; a < 3; ++a) {
+        w.n[a] = V.n[a];
+        w.nb[a] = V.nb[a];
+        w.periodic[a] = E->periodic[a];
+    }
+    w.nreal = V.nreal;
+    w.npool = V.nreal + V.nghost;
+    w.map = V.d_map;
+    w.bpos = V.d_bpos;
+    w.nbr = V.d_nbr;
+    w.host = V.d_host;
+    w.gkind = V.d_gkind;
+    w.refined = V.d_refined;
+    return w;
+}
+
+void lattice_of(const AmrEngine* E, int l, int nb[3]) {
+    for (int a = 0; a < 3; ++a) nb[a] = E->n0[a] * (1 << l) / BS;
+}
+
+int bidx(const int nb[3], int x, int y, int z) { return x + nb[0] * (y + nb[1] * z); }
+
+// wrap a block position on periodic axes; false if outside through a wall
+bool wrap_pos(const AmrEngine* E, const int nb[3], int p[3]) {
+    for (int a = 0; a < 3; ++a) {
+        if (p[a] < 0 || p[a] >= nb[a]) {
+            if (!E->periodic[a]) return false;
+            p[a] = ((p[a] % nb[a]) + nb[a]) % nb[a];
+        }
+    }
+    return true;
+}
+
+Mask parents(const AmrEngine* E, const Mask& fine, int lf) {
+    int nf[3], nc[3];
+    lattice_of(E, lf, nf);
+    lattice_of(E, lf - 1, nc);
+    Mask out((size_t)nc[0] * nc[1] * nc[2], 0);
+    for (int z = 0; z < nf[2]; ++z)
+        for (int y = 0; y < nf[1]; ++y)
+            for (int x = 0; x < nf[0]; ++x)
+                if (fine[bidx(nf, x, y, z)]) out[bidx(nc, x >> 1, y >> 1, z >> 1)] = 1;
+    return out;
+}
+
+Mask children(const AmrEngine* E, const Mask& coarse, int lc) {
+    int nf[3], nc[3];
+    lattice_of(E, lc + 1, nf);
+    lattice_of(E, lc, nc);
+    Mask out((size_t)nf[0] * nf[1] * nf[2], 0);
+    for (int z = 0; z < nf[2]; ++z)
+        for (int y = 0; y < nf[1]; ++y)
+            for (int x = 0; x < nf[0]; ++x) out[bidx(nf, x, y, z)] = coarse[bidx(nc, x >> 1, y >> 1, z >> 1)];
+    return out;
+}
+
+Mask dilate(const AmrEngine* E, const Mask& m, int l) {
+    int nb[3];
+    lattice_of(E, l, nb);
+    Mask out(m);
+    for (int z = 0; z < nb[2]; ++z)
+        for (int y = 0; y < nb[1]; ++y)
+            for (int x = 0; x < nb[0]; ++x) {
+                if (!m[bidx(nb, x, y, z)]) continue;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int p[3] = {x + dx, y + dy, z + dz};
+                            if (wrap_pos(E, nb, p)) out[bidx(nb, p[0], p[1], p[2])] = 1;
+                        }
+            }
+    return out;
+}
+
+// Level-l block positions covered by blocks of level >= l (Sec. 4.1, 4.2.1):
+// finest = siblings of the required set; each coarser level adds the 26
+// neighbours of the parents of the next finer level (2:1 balance).
+std::vector<Mask> coverage(const AmrEngine* E, const Mask& finest) {
+    std::vector<Mask> R(E->L);
+    int nb[3];
+    lattice_of(E, 0, nb);
+    R[0].assign((size_t)nb[0] * nb[1] * nb[2], 1);
+    if (E->L == 1) return R;
+    R[E->L - 1] = children(E, parents(E, finest, E->L - 1), E->L - 2);
+    for (int l = E->L - 2; l >= 1; --l) {
+        const Mask grown = dilate(E, parents(E, R[l + 1], l + 1), l);
+        R[l] = children(E, parents(E, grown, l), l - 1);
+    }
+    return R;
+}
+
+Mask required_from_particle(const AmrEngine* E, const ParticleState& P) {
+    int nb[3];
+    lattice_of(E, E->L - 1, nb);
+    Mask m((size_t)nb[0] * nb[1] * nb[2], 0);
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int)std::floor((P.x[a] - P.r - 1.0) / BS);
+        hi[a] = (int)std::floor((P.x[a] + P.r + 1.0) / BS);
+    }
+    for (int z = lo[2]; z <= hi[2]; ++z)
+        for (int y = lo[1]; y <= hi[1]; ++y)
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                int p[3] = {x, y, z};
+                if (wrap_pos(E, nb, p)) m[bidx(nb, p[0], p[1], p[2])] = 1;
+            }
+    return dilate(E, m, E->L - 1);
+}
+
+Mask required_from_box(const AmrEngine* E) {
+    int nb[3];
+    lattice_of(E, E->L - 1, nb);
+    Mask m((size_t)nb[0] * nb[1] * nb[2], 0);
+    for (int z = 0; z < nb[2]; ++z)
+        for (int y = 0; y < nb[1]; ++y)
+            for (int x = 0; x < nb[0]; ++x) {
+                const int p[3] = {x, y, z};
+                bool in = true;
+                for (int a = 0; a < 3; ++a)
+                    if (!((p[a] + 1) * BS > E->box_lo[a] && p[a] * BS < E->box_hi[a])) in = false;
+                if (in) m[bidx(nb, x, y, z)] = 1;
+            }
+    return m;
+}
+
+// Smallest per-axis cell distance between [a0, a0+la) and [b0, b0+lb) on an
+// axis of n cells (periodic images considered when periodic).
+int axis_gap(int a0, int la, int b0, int lb, int n, bool periodic) {
+    auto gap = [&](int bs) { return std::max(0, std::max(bs - (a0 + la - 1), a0 - (bs + lb - 1))); };
+    int g = gap(b0);
+    if (periodic) g = std::min(g, std::min(gap(b0 + n), gap(b0 - n)));
+    return g;
+}
+
+lbmp_status upload(lbmp_handle* h, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0) return LBMP_OK;
+    if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
+    h->h2d += (long long)bytes;
+    return LBMP_OK;
+}
+
+void free_level(lbmp_handle* h, Level& V) {
+    handle_free(h, V.d_map);
+    handle_free(h, V.d_bpos);
+    handle_free(h, V.d_nbr);
+    handle_free(h, V.d_refined);
+    handle_free(h, V.d_host);
+    handle_free(h, V.d_gkind);
+    handle_free(h, V.d_pops[0]);
+    handle_free(h, V.d_pops[1]);
+    handle_free(h, V.d_flags[0]);
+    handle_free(h, V.d_flags[1]);
+    V = Level();
+}
+
+void level_rates(AmrEngine* E, double tau, double magic) {
+    for (int l = 0; l < E->L; ++l) {
+        Level& V = E->lv[l];
+        V.taup = 0.5 + (tau - 0.5) / (double)(1 << (E->L - 1 - l));
+        V.taum = 0.5 + magic / (V.taup - 0.5);
+    }
+}
+
+void kappa_post(const Level& C, const Level& F, double* kp, double* km) {
+    *kp = std::fabs(C.taup - 1.0) < 1e-12 ? 1.0 : (F.taup - 1.0) / (2.0 * (C.taup - 1.0));
+    *km = std::fabs(C.taum - 1.0) < 1e-12 ? 1.0 : (F.taum - 1.0) / (2.0 * (C.taum - 1.0));
+}
+
+// Builds the new layout from the coverage sets, moves the populations over
+// and classifies cells.  The old layout is freed afterwards.
+lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
+    AmrEngine* E = h->amr;
+    const int L = E->L;
+    std::vector<Level> old;
+    old.swap(E->lv);
+    E->lv.assign(L, Level());
+    for (int l = 0; l < L; ++l) {
+        Level& V = E->lv[l];
+        for (int a = 0; a < 3; ++a) {
+            V.n[a] = E->n0[a] * (1 << l);
+            V.nb[a] = V.n[a] / BS;
+        }
+        const size_t np = (size_t)V.nb[0] * V.nb[1] * V.nb[2];
+        V.map.assign(np, -1);
+        V.refined = (l + 1 < L) ? parents(E, R[l + 1], l + 1) : Mask(np, 0);
+        for (int z = 0; z < V.nb[2]; ++z)
+            for (int y = 0; y < V.nb[1]; ++y)
+                for (int x = 0; x < V.nb[0]; ++x) {
+                    const int i = bidx(V.nb, x, y, z);
+                    if (R[l][i] && !V.refined[i]) {
+                        V.map[i] = V.nreal++;
+                        V.bpos.insert(V.bpos.end(), {x, y, z});
+                    }
+                }
+    }
+    // ghost blocks of level l+1: children of real level-l positions holding a
+    // level-l cell within Chebyshev distance 2 of a refined position
+    for (int l = 0; l + 1 < L; ++l) {
+        Level& C = E->lv[l];
+        Level& F = E->lv[l + 1];
+        for (int z = 0; z < F.nb[2]; ++z)
+            for (int y = 0; y < F.nb[1]; ++y)
+                for (int x = 0; x < F.nb[0]; ++x) {
+                    const int par[3] = {x >> 1, y >> 1, z >> 1};
+                    if (C.map[bidx(C.nb, par[0], par[1], par[2])] < 0) continue;
+                    const int child[3] = {x, y, z};
+                    bool ghost = false;
+                    for (int dz = -1; dz <= 1 && !ghost; ++dz)
+                        for (int dy = -1; dy <= 1 && !ghost; ++dy)
+                            for (int dx = -1; dx <= 1 && !ghost; ++dx) {
+                                int p[3] = {par[0] + dx, par[1] + dy, par[2] + dz};
+                                if (!wrap_pos(E, C.nb, p)) continue;
+                                if (!C.refined[bidx(C.nb, p[0], p[1], p[2])]) continue;
+                                int d = 0;
+                                for (int a = 0; a < 3; ++a)
+                                    d = std::max(d, axis_gap(child[a] * 8, 8, p[a] * BS, BS, C.n[a], E->periodic[a] != 0));
+                                if (d <= 2) ghost = true;
+                            }
+                    if (ghost) {
+                        F.map[bidx(F.nb, x, y, z)] = -2 - F.nghost++;
+                        F.bpos.insert(F.bpos.end(), {x, y, z});   // appended after all real blocks
+                    }
+                }
+    }
+    // neighbour tables
+    for (int l = 0; l < L; ++l) {
+        Level& V = E->lv[l];
+        const int np = V.nreal + V.nghost;
+        V.nbr.assign((size_t)np * 27, -1);
+        for (int b = 0; b < np; ++b)
+            for (int k = 0; k < 27; ++k) {
+                int p[3] = {V.bpos[3 * b] + (k % 3) - 1, V.bpos[3 * b + 1] + (k / 3) % 3 - 1, V.bpos[3 * b + 2] + k / 9 - 1};
+                if (!wrap_pos(E, V.nb, p)) {
+                    V.nbr[(size_t)b * 27 + k] = -2;
+                    continue;
+                }
+                const int m = V.map[bidx(V.nb, p[0], p[1], p[2])];
+                V.nbr[(size_t)b * 27 + k] = m >= 0 ? m : (m <= -2 ? V.nreal + (-2 - m) : -1);
+            }
+    }
+    level_rates(E, h->tau, h->magic);
+    // device arrays
+    const size_t es = esize(h);
+    for (int l = 0; l < L; ++l) {
+        Level& V = E->lv[l];
+        const int np = V.nreal + V.nghost;
+        const size_t nmap = V.map.size();
+        V.d_map = (int*)handle_alloc(h, sizeof(int) * nmap);
+        V.d_refined = (uint8_t*)handle_alloc(h, nmap);
+        V.d_bpos = (int*)handle_alloc(h, sizeof(int) * 3 * (size_t)std::max(np, 1));
+        V.d_nbr = (int*)handle_alloc(h, sizeof(int) * 27 * (size_t)std::max(np, 1));
+        V.d_pops[0] = handle_alloc(h, es * 19 * B3 * (size_t)std::max(np, 1));
+        V.d_pops[1] = handle_alloc(h, es * 19 * B3 * (size_t)std::max(np, 1));
+        V.d_host = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
+        V.d_gkind = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nghost, 1));
+        if (!V.d_map || !V.d_refined || !V.d_bpos || !V.d_nbr || !V.d_pops[0] || !V.d_pops[1] || !V.d_host ||
+            !V.d_gkind)
+            return LBMP_ERR_OOM;
+        if (l == L - 1) {
+            V.d_flags[0] = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
+            V.d_flags[1] = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
+            if (!V.d_flags[0] || !V.d_flags[1]) return LBMP_ERR_OOM;
+        }
+        if (upload(h, V.d_map, V.map.data(), sizeof(int) * nmap) || upload(h, V.d_refined, V.refined.data(), nmap) ||
+            upload(h, V.d_bpos, V.bpos.data(), sizeof(int) * V.bpos.size()) ||
+            upload(h, V.d_nbr, V.nbr.data(), sizeof(int) * V.nbr.size()))
+            return LBMP_ERR_CUDA;
+        cudaMemsetAsync(V.d_pops[0], 0, es * 19 * B3 * (size_t)std::max(np, 1), h->stream);
+        cudaMemsetAsync(V.d_pops[1], 0, es * 19 * B3 * (size_t)std::max(np, 1), h->stream);
+        cudaMemsetAsync(V.d_host, 0, (size_t)B3 * std::max(V.nreal, 1), h->stream);
+        cudaMemsetAsync(V.d_gkind, 0, (size_t)B3 * std::max(V.nghost, 1), h->stream);
+    }
+    // classification
+    for (int l = 0; l + 1 < L; ++l) {
+        Level& C = E->lv[l];
+        Level& F = E->lv[l + 1];
+        if (C.nreal > 0) k_host_flags<<<C.nreal, 256, 0, h->stream>>>(view(E, C), C.d_host);
+        if (F.nghost > 0) k_ghost_kind<<<F.nghost, 256, 0, h->stream>>>(view(E, C), C.d_host, view(E, F), F.d_gkind);
+    }
+    // populations from the old layout
+    if (!old.empty()) {
+        with_storage_amr(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            using A = typename Store<S>::A;
+            MigrateArgs<S> M;
+            M.L = L;
+            for (int k = 0; k < L; ++k) {
+                M.O[k] = view(E, old[k]);
+                M.osrc[k] = (const S*)old[k].d_pops[old[k].cur];
+                double kp = 1, km = 1;
+                if (k + 1 < L) kappa_post(E->lv[k], E->lv[k + 1], &kp, &km);
+                M.kp[k] = (A)kp;
+                M.km[k] = (A)km;
+            }
+            M.rescale = h->cfg.rescale_noneq ? 1 : 0;
+            M.scale = (A)(h->cfg.precision == LBMP_FP16 ? std::ldexp(1.0, h->cfg.fp16_scale_log2) : 1.0);
+            M.inv_scale = (A)(h->cfg.precision == LBMP_FP16 ? std::ldexp(1.0, -h->cfg.fp16_scale_log2) : 1.0);
+            for (int l = 0; l < L; ++l) {
+                Level& V = E->lv[l];
+                if (V.nreal == 0) continue;
+                M.N = view(E, V);
+                M.dst = (S*)V.d_pops[V.cur];
+                M.l = l;
+                k_migrate<S><<<V.nreal, 256, 0, h->stream>>>(M);
+            }
+        });
+    }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
+    for (auto& V : old) free_level(h, V);
+    // finest-level flags and boundary cells
+    Level& Ff = E->lv[L - 1];
+    if (h->has_particle || h->h_ps.present) {
+        if (Ff.nreal > 0) {
+            k_amr_flags_full<<<Ff.nreal, 256, 0, h->stream>>>(view(E, Ff), Ff.d_flags[0], Ff.d_flags[1], h->d_ps);
+            with_storage_amr(h->cfg.precision, [&](auto tag) {
+                using S = std::remove_pointer_t<decltype(tag)>;
+                k_amr_zero_solid<S><<<Ff.nreal, 256, 0, h->stream>>>((S*)Ff.d_pops[Ff.cur], Ff.d_flags[0]);
+            });
+        }
+        Ff.fcur = 0;
+        const unsigned nb = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
+        k_amr_links_mark<<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), Ff.d_flags[0], h->box, h->d_ps,
+                                                             h->link_mask, h->link_blocks);
+        k_amr_links_emit<<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), h->link_mask, h->link_blocks, h->box, h->d_ps,
+                                                             h->list, h->count, h->list_cap, h->status);
+        k_amr_flags_box<<<(unsigned)((h->box.cells + 255) / 256), 256, 0, h->stream>>>(view(E, Ff), Ff.d_flags[1], h->box,
+                                                                                       h->d_ps, h->status);
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
+    return LBMP_OK;
+}
+
+lbmp_status regrid_now(lbmp_handle* h) {
+    AmrEngine* E = h->amr;
+    int nb[3];
+    lattice_of(E, E->L - 1, nb);
+    Mask m((size_t)nb[0] * nb[1] * nb[2], 0);
+    if (h->h_ps.present) m = required_from_particle(E, h->h_ps);
+    if (E->have_box) {
+        const Mask mb = required_from_box(E);
+        for (size_t i = 0; i < m.size(); ++i) m[i] |= mb[i];
+    }
+    return build_layout(h, coverage(E, m));
+}
+
+template <typename S>
+CollideParams<typename Store<S>::A> level_params(const lbmp_handle* h, const Level& V) {
+    using A = typename Store<S>::A;
+    CollideParams<A> p;
+    p.sp = (A)(1.0 / V.taup);
+    p.sm = (A)(1.0 / V.taum);
+    p.F[0] = p.F[1] = p.F[2] = (A)0;
+    p.forced = 0;
+    if (h->cfg.precision == LBMP_FP16) {
+        p.scale = (A)std::ldexp(1.0, h->cfg.fp16_scale_log2);
+        p.inv_scale = (A)std::ldexp(1.0, -h->cfg.fp16_scale_log2);
+    } else {
+        p.scale = (A)1;
+        p.inv_scale = (A)1;
+    }
+    return p;
+}
+
+template <typename S>
+void enqueue_advance(lbmp_handle* h, int l) {
+    using A = typename Store<S>::A;
+    AmrEngine* E = h->amr;
+    const int L = E->L;
+    Level& V = E->lv[l];
+    const CollideParams<A> P = level_params<S>(h, V);
+    const int rescale = h->cfg.rescale_noneq ? 1 : 0;
+    if (l + 1 < L) {
+        Level& F = E->lv[l + 1];
+        double kp, km;
+        kappa_post(V, F, &kp, &km);
+        if (F.nghost > 0) {
+            k_explode<S><<<F.nghost, UPD_THREADS, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
+                                                                  (S*)F.d_pops[0], (S*)F.d_pops[1], (A)kp, (A)km,
+                                                                  rescale, P.scale, P.inv_scale, h->status);
+            h->launches += 1;
+        }
+        E->substep[l + 1] = 0;
+        enqueue_advance<S>(h, l + 1);
+        E->substep[l + 1] = 1;
+        enqueue_advance<S>(h, l + 1);
+    }
+    const int np = V.nreal + V.nghost;
+    UpdateArgs<S> U;
+    U.D = view(E, V);
+    U.src = (const S*)V.d_pops[V.cur];
+    U.dst = (S*)V.d_pops[1 - V.cur];
+    U.P = P;
+    U.substep = E->substep[l];
+    U.rescale = rescale;
+    U.F = U.D;
+    U.fsrc = nullptr;
+    U.fkp = U.fkm = (A)1;
+    U.Cc = U.D;
+    U.csrc = nullptr;
+    U.ckp = U.ckm = (A)1;
+    U.solid = nullptr;
+    U.status = h->status;
+    const bool has_fine = l + 1 < L, has_coarse = l > 0;
+    if (has_fine) {
+        Level& F = E->lv[l + 1];
+        U.F = view(E, F);
+        U.fsrc = (const S*)F.d_pops[F.cur];
+        // coalescence: averaged finer values are pre-collision values of the coarser cell
+        U.fkp = (A)(2.0 * V.taup / F.taup);
+        U.fkm = (A)(2.0 * V.taum / F.taum);
+    }
+    if (has_coarse) {
+        Level& C = E->lv[l - 1];
+        U.Cc = view(E, C);
+        U.csrc = (const S*)C.d_pops[C.cur];
+        double kp, km;
+        kappa_post(C, V, &kp, &km);
+        U.ckp = (A)kp;
+        U.ckm = (A)km;
+    }
+    const bool coupled = (l == L - 1) && h->has_particle;
+    if (coupled) U.solid = V.d_flags[V.fcur];
+    if (np > 0) {
+        if (has_fine && has_coarse) k_update<S, true, true, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
+        else if (has_fine) k_update<S, true, false, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
+        else if (has_coarse && coupled) k_update<S, false, true, true><<<np, UPD_THREADS, 0, h->stream>>>(U);
+        else if (has_coarse) k_update<S, false, true, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
+        else if (coupled) k_update<S, false, false, true><<<np, UPD_THREADS, 0, h->stream>>>(U);
+        else k_update<S, false, false, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
+        h->launches += 1;
+    }
+    h->updates += (long long)V.nreal * B3;
+    if (coupled) {
+        const LevelView D = view(E, V);
+        const int nb = E->boundary_blocks;
+        k_amr_boundary<S><<<nb, BND_THREADS, 0, h->stream>>>(D, U.src, U.dst, U.solid, h->list, h->count, P, h->d_ps,
+                                                              h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials,
+                                                              h->status);
+        GridDesc G;
+        G.nx = V.n[0];
+        G.ny = V.n[1];
+        G.nz = V.n[2];
+        for (int a = 0; a < 3; ++a) G.periodic[a] = E->periodic[a];
+        G.n = (long long)V.n[0] * V.n[1] * V.n[2];
+        launch_particle_update(h->d_ps, h->partials, nb, G, h->history, h->cfg.history_capacity, h->status, h->stream);
+        uint8_t* fnext = V.d_flags[1 - V.fcur];
+        const unsigned bc = (unsigned)((h->box.cells + 255) / 256);
+        k_amr_flags_box<<<bc, 256, 0, h->stream>>>(D, fnext, h->box, h->d_ps, h->status);
+        k_amr_refill<S><<<bc, 256, 0, h->stream>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
+                                                    P.inv_scale);
+        const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
+        k_amr_links_mark<<<nl, LINK_THREADS, 0, h->stream>>>(D, fnext, h->box, h->d_ps, h->link_mask, h->link_blocks);
+        k_amr_links_emit<<<nl, LINK_THREADS, 0, h->stream>>>(D, h->link_mask, h->link_blocks, h->box, h->d_ps, h->list,
+                                                             h->count, h->list_cap, h->status);
+        V.fcur = 1 - V.fcur;
+        h->launches += 7;
+    }
+    V.cur = 1 - V.cur;
+}
+
+}  // namespace
+
+// ================================================================== API
+lbmp_status amr_create(lbmp_handle* h) {
+    AmrEngine* E = new (std::nothrow) AmrEngine();
+    if (!E) return LBMP_ERR_OOM;
+    E->L = h->cfg.levels;
+    E->n0[0] = h->cfg.nx;
+    E->n0[1] = h->cfg.ny;
+    E->n0[2] = h->cfg.nz;
+    for (int a = 0; a < 3; ++a) E->periodic[a] = h->cfg.bc[a] == LBMP_PERIODIC ? 1 : 0;
+    h->amr = E;
+    return regrid_now(h);
+}
+
+void amr_destroy(lbmp_handle* h) {
+    if (!h->amr) return;
+    for (auto& V : h->amr->lv) free_level(h, V);
+    delete h->amr;
+    h->amr = nullptr;
+}
+
+lbmp_status amr_add_sphere(lbmp_handle* h) {
+    AmrEngine* E = h->amr;
+    const Level& F = E->lv[E->L - 1];
+    // box around the sphere at the finest level (as in the uniform engine)
+    BoxDesc& B = h->box;
+    B.R = (int)std::ceil(h->h_ps.r) + 3;
+    B.cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        B.E[a] = 2 * B.R + 2;
+        if (E->periodic[a] && B.E[a] >= F.n[a]) B.E[a] = F.n[a];
+        B.cells *= B.E[a];
+    }
+    const double h3 = 0.5 * std::sqrt(3.0);
+    const double ro = h->h_ps.r + std::sqrt(2.0) + h3, ri = std::max(0.0, h->h_ps.r - h3);
+    const double shell = 4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri);
+    h->list_cap = (int)std::min<double>((double)B.cells, std::ceil(shell) + 64.0);
+    h->list = (int*)handle_alloc(h, sizeof(int) * (size_t)h->list_cap);
+    E->boundary_blocks = (h->list_cap + BND_THREADS - 1) / BND_THREADS;
+    h->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)E->boundary_blocks);
+    h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
+    h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));
+    if (!h->list || !h->partials || !h->link_mask || !h->link_blocks) return LBMP_ERR_OOM;
+    if (cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return LBMP_ERR_CUDA;
+    h->h2d += sizeof(ParticleState);
+    h->has_particle = true;
+    return regrid_now(h);
+}
+
+lbmp_status amr_refine_box(lbmp_handle* h, const double lo[3], const double hi[3]) {
+    AmrEngine* E = h->amr;
+    E->have_box = true;
+    for (int a = 0; a < 3; ++a) {
+        E->box_lo[a] = lo[a];
+        E->box_hi[a] = hi[a];
+    }
+    return regrid_now(h);
+}
+
+lbmp_status amr_regrid(lbmp_handle* h) {
+    if (h->has_particle) {
+        if (cudaMemcpyAsync(&h->h_ps, h->d_ps, sizeof(ParticleState), cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return LBMP_ERR_CUDA;
+        h->d2h += sizeof(ParticleState);
+    }
+    return regrid_now(h);
+}
+
+lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis) {
+    AmrEngine* E = h->amr;
+    const double Lax = (double)E->lv[E->L - 1].n[axis];
+    with_storage_amr(h->cfg.precision, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using A = typename Store<S>::A;
+        const A scale = (A)(h->cfg.precision == LBMP_FP16 ? std::ldexp(1.0, h->cfg.fp16_scale_log2) : 1.0);
+        for (int l = 0; l < E->L; ++l) {
+            Level& V = E->lv[l];
+            if (V.nreal == 0) continue;
+            const uint8_t* solid = (l == E->L - 1 && h->has_particle) ? V.d_flags[V.fcur] : nullptr;
+            k_amr_init<S><<<V.nreal, 256, 0, h->stream>>>(view(E, V), (S*)V.d_pops[V.cur], solid, rho, u[0], u[1], u[2],
+                                                           amp, dir, axis, (double)(1 << (E->L - 1 - l)), Lax, scale);
+        }
+    });
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
+    return LBMP_OK;
+}
+
+lbmp_status amr_step(lbmp_handle* h, int n) {
+    AmrEngine* E = h->amr;
+    level_rates(E, h->tau, h->magic);
+    for (int i = 0; i < n; ++i) {
+        with_storage_amr(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            E->substep[0] = 0;
+            enqueue_advance<S>(h, 0);
+        });
+        E->coarse_steps += 1;
+        h->steps += 1;
+        if (cudaGetLastError() != cudaSuccess) return LBMP_ERR_CUDA;
+        if (h->cfg.regrid_interval > 0 && h->has_particle && E->coarse_steps % h->cfg.regrid_interval == 0) {
+            const lbmp_status s = amr_regrid(h);
+            if (s != LBMP_OK) return s;
+        }
+    }
+    return LBMP_OK;
+}
+
+lbmp_status amr_level_shape(lbmp_handle* h, int level, int out[3]) {
+    AmrEngine* E = h->amr;
+    if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) out[a] = E->lv[level].n[a];
+    return LBMP_OK;
+}
+
+lbmp_status amr_block_map(lbmp_handle* h, int level, int32_t* out, size_t cap, size_t* n) {
+    AmrEngine* E = h->amr;
+    if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
+    const Level& V = E->lv[level];
+    *n = V.map.size();
+    if (out)
+        for (size_t i = 0; i < V.map.size() && i < cap; ++i)
+            out[i] = V.map[i] >= 0 ? V.map[i] : (V.map[i] <= -2 ? -2 : -1);
+    return LBMP_OK;
+}
+
+lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n) {
+    AmrEngine* E = h->amr;
+    if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
+    Level& V = E->lv[level];
+    const size_t cells = (size_t)V.nreal * B3;
+    *n = cells;
+    if (!xyz || !g || cap < cells || cells == 0) return LBMP_OK;
+    int32_t* dx = (int32_t*)handle_alloc(h, sizeof(int32_t) * 3 * cells);
+    double* dg = (double*)handle_alloc(h, sizeof(double) * 19 * cells);
+    if (!dx || !dg) {
+        handle_free(h, dx);
+        handle_free(h, dg);
+        return LBMP_ERR_OOM;
+    }
+    with_storage_amr(h->cfg.precision, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using A = typename Store<S>::A;
+        const A inv = (A)(h->cfg.precision == LBMP_FP16 ? std::ldexp(1.0, -h->cfg.fp16_scale_log2) : 1.0);
+        k_amr_export<S><<<V.nreal, 256, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], dx, dg, inv);
+    });
+    cudaError_t e = cudaMemcpyAsync(xyz, dx, sizeof(int32_t) * 3 * cells, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g, dg, sizeof(double) * 19 * cells, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->d2h += (long long)(sizeof(int32_t) * 3 + sizeof(double) * 19) * (long long)cells;
+    handle_free(h, dx);
+    handle_free(h, dg);
+    return e == cudaSuccess ? LBMP_OK : LBMP_ERR_CUDA;
+}
+
+lbmp_status amr_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n) {
+    AmrEngine* E = h->amr;
+    *n = 0;
+    if (!h->has_particle) return LBMP_OK;
+    int cnt = 0;
+    if (cudaMemcpyAsync(&cnt, h->count, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return LBMP_ERR_CUDA;
+    if (cnt == 0) return LBMP_OK;
+    Level& V = E->lv[E->L - 1];
+    int64_t* dc = (int64_t*)handle_alloc(h, sizeof(int64_t) * 18 * (size_t)cnt);
+    int32_t* dq = (int32_t*)handle_alloc(h, sizeof(int32_t) * 18 * (size_t)cnt);
+    double* dd = (double*)handle_alloc(h, sizeof(double) * 18 * (size_t)cnt);
+    if (!dc || !dq || !dd) {
+        handle_free(h, dc);
+        handle_free(h, dq);
+        handle_free(h, dd);
+        return LBMP_ERR_OOM;
+    }
+    k_amr_export_links<<<(cnt + 127) / 128, 128, 0, h->stream>>>(view(E, V), V.d_flags[V.fcur], h->list, h->count,
+                                                                 h->d_ps, dc, dq, dd);
+    std::vector<int64_t> hc((size_t)cnt * 18);
+    std::vector<int32_t> hq((size_t)cnt * 18);
+    std::vector<double> hd((size_t)cnt * 18);
+    cudaError_t e = cudaMemcpyAsync(hc.data(), dc, sizeof(int64_t) * hc.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hq.data(), dq, sizeof(int32_t) * hq.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd.data(), dd, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    handle_free(h, dc);
+    handle_free(h, dq);
+    handle_free(h, dd);
+    if (e != cudaSuccess) return LBMP_ERR_CUDA;
+    size_t m = 0;
+    for (size_t s = 0; s < hq.size(); ++s) {
+        if (hq[s] < 0) continue;
+        if (m < cap) {
+            if (cell) cell[m] = hc[s];
+            if (q) q[m] = hq[s];
+            if (delta) delta[m] = hd[s];
+        }
+        ++m;
+    }
+    *n = m;
+    return LBMP_OK;
+}
+
+long long amr_cell_updates_per_coarse_step(const lbmp_handle* h) {
+    const AmrEngine* E = h->amr;
+    long long u = 0;
+    for (int l = 0; l < E->L; ++l) u += (long long)E->lv[l].nreal * B3 * (1LL << l);
+    return u;
+}
+
+int amr_launches_per_coarse_step(const lbmp_handle* h) {
+    const AmrEngine* E = h->amr;
+    int per = 0;
+    for (int l = E->L - 1; l >= 0; --l) {
+        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nghost > 0) ? 1 : 0) +
+                  ((l == E->L - 1 && h->has_particle) ? 7 : 0);
+        per = own + 2 * per;
+    }
+    return per;
+}
+
+}  // namespace lbmp

@@ -12,39 +12,9 @@
 #include <vector>
 
 #include "internal.h"
+#include "amr.h"
 
 using namespace lbmp;
-
-struct lbmp_handle {
-    lbmp_config cfg;
-    GridDesc G;
-    cudaStream_t stream = nullptr;
-    void* pops[2] = {nullptr, nullptr};
-    int cur = 0;                         // pops[cur] holds the post-collision field
-    uint8_t* flags[2] = {nullptr, nullptr};
-    int fcur = 0;                        // flags[fcur] are the flags of pops[cur]
-    int* list = nullptr;                 // boundary cells
-    int* count = nullptr;
-    int list_cap = 0;
-    uint8_t* link_mask = nullptr;        // scratch of the link compaction (one byte per box cell)
-    int* link_blocks = nullptr;          // scratch: per-block counts
-    double* partials = nullptr;
-    int partial_blocks = 0;
-    ParticleState* d_ps = nullptr;
-    ParticleState h_ps;                  // host copy of the parameters
-    double* history = nullptr;
-    int* status = nullptr;
-    BoxDesc box;
-    bool has_particle = false;
-    double tau = 0.6, magic = 3.0 / 16.0;
-    double body_force[3] = {0, 0, 0};
-    long long steps = 0, updates = 0, launches = 0, h2d = 0, d2h = 0;
-    bool profiling = false;
-    std::vector<cudaEvent_t> ev_pool;    // events of the current measurement, 3 per step
-    size_t ev_used = 0;
-    std::vector<std::pair<void*, size_t>> allocations;
-    std::string err;
-};
 
 namespace {
 
@@ -197,6 +167,14 @@ lbmp_status read_status(lbmp_handle* h) {
         std::string m = "device status:";
         if (st & STATUS_UNSTABLE_FLUID) m += " fluid velocity NaN/Inf or |u|^2 > 0.09;";
         if (st & STATUS_PARTICLE_JUMP) m += " particle moved more than 0.5 cell in one step;";
+        if (st & 16) {
+            m += " the sphere's neighbourhood left the finest level (regrid more often);";
+            return fail(h, LBMP_ERR_PARTICLE_NOT_FINEST, m);
+        }
+        if (st & 8) {
+            m += " a refined-grid pull found no source cell;";
+            return fail(h, LBMP_ERR_INVALID_ARG, m);
+        }
         if (st & STATUS_LINK_OVERFLOW) {
             m += " boundary list overflow;";
             return fail(h, LBMP_ERR_INVALID_ARG, m);
@@ -225,6 +203,8 @@ lbmp_status download_particle(lbmp_handle* h) {
 namespace lbmp {
 // Error message for entry points that have no handle (read by lbmp_last_error(NULL)).
 void set_global_error(const std::string& msg) { g_create_error = msg; }
+void* handle_alloc(lbmp_handle* h, size_t bytes) { return dev_alloc(h, bytes); }
+void handle_free(lbmp_handle* h, void* p) { dev_free(h, p); }
 }  // namespace lbmp
 
 extern "C" {
@@ -240,7 +220,7 @@ lbmp_status lbmp_config_default(lbmp_config* c) {
     c->magic = 3.0 / 16.0;
     c->boundary = LBMP_CLI;
     c->force_average = 1;
-    c->rescale_noneq = 1;
+    c->rescale_noneq = 0;
     c->regrid_interval = 0;
     c->history_capacity = 4096;
     c->fp16_scale_log2 = 11;
@@ -255,8 +235,14 @@ lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
     const long long n = (long long)cfg->nx * cfg->ny * cfg->nz;
     if (n >= (1LL << 31)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: more than 2^31 - 1 cells");
     if (cfg->nz > 65535) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: nz > 65535");
-    if (cfg->levels != 1)
-        return fail(nullptr, LBMP_ERR_UNSUPPORTED, "lbmp_create: refined hierarchies use lbmp_amr_create");
+    if (cfg->levels < 1 || cfg->levels > 6)
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: levels must be in [1, 6]");
+    if (cfg->levels > 1) {
+        if (cfg->nx % 16 || cfg->ny % 16 || cfg->nz % 16)
+            return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: refined grids need level-0 extents that are multiples of 16");
+        const long long nf = (long long)cfg->nx * cfg->ny * cfg->nz << (3 * (cfg->levels - 1));
+        if (nf >= (1LL << 40)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: finest lattice too large");
+    }
     if (cfg->precision < LBMP_FP64 || cfg->precision > LBMP_FP16)
         return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown precision");
     if (!(cfg->tau > 0.5)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: tau must exceed 1/2");
@@ -291,25 +277,30 @@ lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
     std::memset(&h->h_ps, 0, sizeof(ParticleState));
     h->h_ps.force_average = cfg->force_average ? 1 : 0;
 
-    const size_t pop_bytes = (size_t)19 * (size_t)n * elem_size(cfg->precision);
-    h->pops[0] = dev_alloc(h, pop_bytes);
-    h->pops[1] = dev_alloc(h, pop_bytes);
-    h->flags[0] = (uint8_t*)dev_alloc(h, (size_t)n);
-    h->flags[1] = (uint8_t*)dev_alloc(h, (size_t)n);
+    const bool refined = cfg->levels > 1;
+    const size_t pop_bytes = refined ? 0 : (size_t)19 * (size_t)n * elem_size(cfg->precision);
+    if (!refined) {
+        h->pops[0] = dev_alloc(h, pop_bytes);
+        h->pops[1] = dev_alloc(h, pop_bytes);
+        h->flags[0] = (uint8_t*)dev_alloc(h, (size_t)n);
+        h->flags[1] = (uint8_t*)dev_alloc(h, (size_t)n);
+    }
     h->d_ps = (ParticleState*)dev_alloc(h, sizeof(ParticleState));
     h->status = (int*)dev_alloc(h, sizeof(int));
     h->count = (int*)dev_alloc(h, sizeof(int));
     h->history = (double*)dev_alloc(h, sizeof(double) * 15 * (size_t)std::max(1, cfg->history_capacity));
-    if (!h->pops[0] || !h->pops[1] || !h->flags[0] || !h->flags[1] || !h->d_ps || !h->status || !h->count ||
-        !h->history) {
+    if ((!refined && (!h->pops[0] || !h->pops[1] || !h->flags[0] || !h->flags[1])) || !h->d_ps || !h->status ||
+        !h->count || !h->history) {
         lbmp_destroy(h);
         return fail(nullptr, LBMP_ERR_OOM, "lbmp_create: device allocation failed");
     }
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->pops[0], 0, pop_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->pops[1], 0, pop_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags[0], 0, (size_t)n, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->flags[1], 0, (size_t)n, h->stream);
+    if (!refined) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->pops[0], 0, pop_bytes, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->pops[1], 0, pop_bytes, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->flags[0], 0, (size_t)n, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->flags[1], 0, (size_t)n, h->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->count, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice,
@@ -320,6 +311,13 @@ lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
         lbmp_destroy(h);
         return fail(nullptr, LBMP_ERR_CUDA, m);
     }
+    if (refined) {
+        const lbmp_status st = amr_create(h);
+        if (st != LBMP_OK) {
+            lbmp_destroy(h);
+            return fail(nullptr, st, "lbmp_create: building the refined hierarchy failed");
+        }
+    }
     *out = h;
     return LBMP_OK;
 }
@@ -327,6 +325,7 @@ lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
 lbmp_status lbmp_destroy(lbmp_handle* h) {
     if (!h) return LBMP_OK;
     cudaStreamSynchronize(h->stream);
+    amr_destroy(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     while (!h->allocations.empty()) dev_free(h, h->allocations.back().first);
@@ -340,7 +339,8 @@ lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter
     if (h->has_particle) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_add_sphere: one sphere per handle");
     if (!(diameter > 0.0) || !(density_ratio > 0.0) || cv < 0.0 || cv_omega < 0.0)
         return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_add_sphere: diameter and density ratio must be > 0, C_v >= 0");
-    const int n3[3] = {h->G.nx, h->G.ny, h->G.nz};
+    const int sh = h->cfg.levels - 1;   // positions are in finest-level units
+    const int n3[3] = {h->G.nx << sh, h->G.ny << sh, h->G.nz << sh};
     for (int a = 0; a < 3; ++a) {
         if (!(pos[a] >= 0.0 && pos[a] <= (double)n3[a]))
             return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_add_sphere: centre outside the domain");
@@ -357,6 +357,12 @@ lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter
     P.V = M_PI * diameter * diameter * diameter / 6.0;
     P.present = 1;
     P.force_average = h->cfg.force_average ? 1 : 0;
+    if (h->amr) {
+        const lbmp_status st = amr_add_sphere(h);
+        if (st != LBMP_OK) return fail(h, st, "lbmp_add_sphere: building the refined hierarchy failed");
+        if (id) *id = 0;
+        return read_status(h);
+    }
     // box around the sphere: half width ceil(r) + 3 cells covers every cell
     // whose flag or boundary status can change in one step (|dx| < 1/2)
     BoxDesc& B = h->box;
@@ -463,6 +469,8 @@ lbmp_status lbmp_set_gravity(lbmp_handle* h, const double g[3]) {
 
 lbmp_status lbmp_set_body_force(lbmp_handle* h, const double f[3]) {
     if (!h || !f) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_body_force: NULL argument");
+    if (h->amr && (f[0] != 0.0 || f[1] != 0.0 || f[2] != 0.0))
+        return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_set_body_force: fluid forcing is implemented on uniform grids");
     for (int a = 0; a < 3; ++a) h->body_force[a] = f[a];
     return LBMP_OK;
 }
@@ -470,6 +478,11 @@ lbmp_status lbmp_set_body_force(lbmp_handle* h, const double f[3]) {
 lbmp_status lbmp_init_fluid(lbmp_handle* h, double rho, const double u[3], const double* u_field,
                             int u_field_on_device) {
     if (!h || !u) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_init_fluid: NULL argument");
+    if (h->amr) {
+        if (u_field) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_init_fluid: refined grids take lbmp_init_fluid_wave");
+        return amr_init_fluid(h, rho, u, 0.0, 0, 0) == LBMP_OK ? LBMP_OK
+                                                               : fail(h, LBMP_ERR_CUDA, "lbmp_init_fluid: kernel failed");
+    }
     const double* dfield = nullptr;
     double* tmp = nullptr;
     if (u_field && !u_field_on_device) {
@@ -494,6 +507,7 @@ lbmp_status lbmp_init_fluid(lbmp_handle* h, double rho, const double u[3], const
 }
 
 lbmp_status lbmp_set_populations(lbmp_handle* h, const double* g, size_t cap) {
+    if (h && h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_set_populations: uniform grids only (refined: lbmp_get_level_cells)");
     if (!h || !g) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_populations: NULL argument");
     const long long total = 19LL * h->G.n;
     if ((long long)cap < total) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_populations: cap < 19*cells");
@@ -522,6 +536,7 @@ lbmp_status lbmp_set_populations(lbmp_handle* h, const double* g, size_t cap) {
 }
 
 lbmp_status lbmp_get_populations(lbmp_handle* h, double* g, size_t cap) {
+    if (h && h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_get_populations: uniform grids only (refined: lbmp_get_level_cells)");
     if (!h || !g) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_populations: NULL argument");
     const long long total = 19LL * h->G.n;
     if ((long long)cap < total) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_populations: cap < 19*cells");
@@ -546,6 +561,7 @@ lbmp_status lbmp_get_populations(lbmp_handle* h, double* g, size_t cap) {
 }
 
 lbmp_status lbmp_gather_populations(lbmp_handle* h, const int64_t* cells, size_t n, double* out) {
+    if (h && h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_gather_populations: uniform grids only (refined: lbmp_get_level_cells)");
     if (!h || (n > 0 && (!cells || !out))) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_gather_populations: NULL argument");
     if (n == 0) return LBMP_OK;
     for (size_t i = 0; i < n; ++i)
@@ -577,6 +593,11 @@ lbmp_status lbmp_gather_populations(lbmp_handle* h, const int64_t* cells, size_t
 
 lbmp_status lbmp_step_async(lbmp_handle* h, int n) {
     if (!h || n < 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_step: bad argument");
+    if (h->amr) {
+        const lbmp_status st = amr_step(h, n);
+        if (st != LBMP_OK) return fail(h, st, "lbmp_step: refined step failed");
+        return LBMP_OK;
+    }
     for (int i = 0; i < n; ++i) enqueue_step(h);
     LBMP_CK(h, cudaGetLastError());
     return LBMP_OK;
@@ -643,6 +664,7 @@ lbmp_status lbmp_get_history(lbmp_handle* h, int id, double* out, int max_steps,
 }
 
 lbmp_status lbmp_get_flags(lbmp_handle* h, uint8_t* out, size_t cap) {
+    if (h && h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_get_flags: uniform grids only (refined: lbmp_get_level_cells)");
     if (!h || !out) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_flags: NULL argument");
     if ((long long)cap < h->G.n) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_flags: cap < cells");
     LBMP_CK(h, cudaMemcpyAsync(out, h->flags[h->fcur], (size_t)h->G.n, cudaMemcpyDeviceToHost, h->stream));
@@ -653,6 +675,10 @@ lbmp_status lbmp_get_flags(lbmp_handle* h, uint8_t* out, size_t cap) {
 lbmp_status lbmp_get_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n) {
     if (!h || !n) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_links: NULL argument");
     *n = 0;
+    if (h->amr) {
+        const lbmp_status st = amr_links(h, cell, q, delta, cap, n);
+        return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_get_links: failed");
+    }
     if (!h->has_particle) return LBMP_OK;
     int cnt = 0;
     LBMP_CK(h, cudaMemcpyAsync(&cnt, h->count, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -728,6 +754,80 @@ lbmp_status lbmp_get_profile(lbmp_handle* h, double out[4]) {
     out[1] = (double)steps;
     out[2] = total;
     out[3] = (double)steps;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_init_fluid_wave(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis) {
+    if (!h || !u || dir < 0 || dir > 2 || axis < 0 || axis > 2)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_init_fluid_wave: bad argument");
+    if (h->amr) {
+        return amr_init_fluid(h, rho, u, amp, dir, axis) == LBMP_OK
+                   ? LBMP_OK
+                   : fail(h, LBMP_ERR_CUDA, "lbmp_init_fluid_wave: kernel failed");
+    }
+    const int n3[3] = {h->G.nx, h->G.ny, h->G.nz};
+    std::vector<double> f((size_t)3 * h->G.n);
+    for (long long c = 0; c < h->G.n; ++c) {
+        const long long idx[3] = {c % n3[0], (c / n3[0]) % n3[1], c / ((long long)n3[0] * n3[1])};
+        for (int a = 0; a < 3; ++a) f[(size_t)a * h->G.n + c] = u[a];
+        f[(size_t)dir * h->G.n + c] += amp * std::sin(2.0 * M_PI * (idx[axis] + 0.5) / n3[axis]);
+    }
+    const double zero[3] = {0, 0, 0};
+    return lbmp_init_fluid(h, rho, zero, f.data(), 0);
+}
+
+lbmp_status lbmp_refine_box(lbmp_handle* h, const double lo[3], const double hi[3]) {
+    if (!h || !lo || !hi) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_refine_box: NULL argument");
+    if (!h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_refine_box: the grid has one level");
+    const lbmp_status st = amr_refine_box(h, lo, hi);
+    if (st != LBMP_OK) return fail(h, st, "lbmp_refine_box: regrid failed");
+    return read_status(h);
+}
+
+lbmp_status lbmp_regrid(lbmp_handle* h) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (!h->amr) return LBMP_OK;
+    const lbmp_status st = amr_regrid(h);
+    if (st != LBMP_OK) return fail(h, st, "lbmp_regrid: failed");
+    return read_status(h);
+}
+
+lbmp_status lbmp_level_shape(lbmp_handle* h, int level, int out[3]) {
+    if (!h || !out) return LBMP_ERR_INVALID_ARG;
+    if (!h->amr) {
+        if (level != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_level_shape: no such level");
+        out[0] = h->G.nx;
+        out[1] = h->G.ny;
+        out[2] = h->G.nz;
+        return LBMP_OK;
+    }
+    return amr_level_shape(h, level, out) == LBMP_OK ? LBMP_OK
+                                                     : fail(h, LBMP_ERR_INVALID_ARG, "lbmp_level_shape: no such level");
+}
+
+lbmp_status lbmp_get_block_map(lbmp_handle* h, int level, int32_t* out, size_t cap, size_t* n) {
+    if (!h || !n) return LBMP_ERR_INVALID_ARG;
+    if (!h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_get_block_map: the grid has one level");
+    return amr_block_map(h, level, out, cap, n) == LBMP_OK ? LBMP_OK
+                                                          : fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_block_map: no such level");
+}
+
+lbmp_status lbmp_get_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n) {
+    if (!h || !n) return LBMP_ERR_INVALID_ARG;
+    if (!h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_get_level_cells: the grid has one level");
+    const lbmp_status st = amr_level_cells(h, level, xyz, g, cap, n);
+    return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_get_level_cells: failed");
+}
+
+lbmp_status lbmp_updates_per_step(lbmp_handle* h, int64_t* updates, int32_t* launches) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (h->amr) {
+        if (updates) *updates = amr_cell_updates_per_coarse_step(h);
+        if (launches) *launches = amr_launches_per_coarse_step(h);
+    } else {
+        if (updates) *updates = h->G.n;
+        if (launches) *launches = h->has_particle ? 7 : 1;
+    }
     return LBMP_OK;
 }
 

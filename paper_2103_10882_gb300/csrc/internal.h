@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/lbmp.h"
 #include "lattice.cuh"
@@ -74,4 +76,44 @@ void launch_gather(const S* pops, long long ncells, const int64_t* cells, long l
 template <typename S>
 void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStream_t stream);
 
+struct AmrEngine;
+
+// Device allocation through the handle's allocator (api.cu).
+void* handle_alloc(lbmp_handle* h, size_t bytes);
+void handle_free(lbmp_handle* h, void* p);
+
 }  // namespace lbmp
+
+// One simulation (opaque to callers of the C ABI).
+struct lbmp_handle {
+    lbmp_config cfg;
+    lbmp::GridDesc G;
+    cudaStream_t stream = nullptr;
+    void* pops[2] = {nullptr, nullptr};
+    int cur = 0;                         // pops[cur] holds the post-collision field
+    uint8_t* flags[2] = {nullptr, nullptr};
+    int fcur = 0;                        // flags[fcur] are the flags of pops[cur]
+    int* list = nullptr;                 // boundary cells
+    int* count = nullptr;
+    int list_cap = 0;
+    uint8_t* link_mask = nullptr;        // scratch of the link compaction (one byte per box cell)
+    int* link_blocks = nullptr;          // scratch: per-block counts
+    double* partials = nullptr;
+    int partial_blocks = 0;
+    lbmp::ParticleState* d_ps = nullptr;
+    lbmp::ParticleState h_ps;                  // host copy of the parameters
+    double* history = nullptr;
+    int* status = nullptr;
+    lbmp::BoxDesc box;
+    bool has_particle = false;
+    double tau = 0.6, magic = 3.0 / 16.0;
+    double body_force[3] = {0, 0, 0};
+    long long steps = 0, updates = 0, launches = 0, h2d = 0, d2h = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;    // events of the current measurement, 3 per step
+    size_t ev_used = 0;
+    std::vector<std::pair<void*, size_t>> allocations;
+    std::string err;
+    lbmp::AmrEngine* amr = nullptr;     // refined hierarchy (levels > 1), else null
+};
+

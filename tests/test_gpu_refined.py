@@ -1,0 +1,193 @@
+"""GPU parity of the refined-grid engine against the refined oracle.
+
+Integer work (block maps, boundary links) is compared bit-exactly; FP64
+populations within 1e-10 of their largest magnitude, forces within 1e-10 of
+the buoyancy scale; FP32 with the tolerances stated per test.  All calls go
+through the C ABI.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2103_10882_gb300 as L
+    L._native.load()
+    return L
+
+
+def pair(orc, lib, shape, levels, tau, precision="fp64", rescale=False, bc=("periodic",) * 3, box=None,
+         sphere=None, gravity=(0, 0, 0)):
+    periodic = tuple(1 if b == "periodic" else 0 for b in bc)
+    o = orc.RefinedSim(shape, levels, tau=tau, periodic=periodic, rescale=rescale)
+    g = lib.Simulation(shape, precision=precision, tau=tau, bc=bc, levels=levels, rescale=rescale)
+    if box is not None:
+        o.refine_box(*box)
+        g.refine_box(*box)
+    if sphere is not None:
+        pos, D, pi, cv = sphere
+        o.add_sphere(pos, D, pi, cv=cv)
+        g.add_sphere(pos, D, pi, cv=cv)
+        o.set_gravity(gravity)
+        g.set_gravity(gravity)
+    return o, g
+
+
+def same_maps(o, g, levels):
+    for l in range(levels):
+        assert o.level_shape(l) == g.level_shape(l)
+        assert np.array_equal(o.block_map(l), g.block_map(l)), "block map of level %d differs" % l
+
+
+def cells_close(o, g, levels, rel):
+    for l in range(levels):
+        xo, fo = o.real_cells(l)
+        xg, fg = g.level_cells(l)
+        assert np.array_equal(xo, xg)
+        if len(fo):
+            scale = max(np.abs(fo).max(), 1e-300)
+            err = np.abs(fg - fo).max() / scale
+            assert err <= rel, "level %d: population error %.3e > %.1e" % (l, err, rel)
+
+
+@pytest.mark.parametrize("levels,shape", [(2, (32, 32, 48)), (3, (48, 48, 64))])
+def test_box_refinement_shear_fp64(orc, lib, levels, shape):
+    """Box refinement (edges and corners), shear wave plus drift: block maps
+    bit-exact, populations of every level within 1e-10 after a few coarse steps."""
+    f = 1 << (levels - 1)
+    box = ((9 * f, 13 * f, 15 * f), (21 * f, 19 * f, 29 * f))
+    o, g = pair(orc, lib, shape, levels, tau=0.8, box=box)
+    same_maps(o, g, levels)
+    o.init_equilibrium(u=(0.01, 0.004, -0.007), shear=0.01, shear_dir=0, shear_axis=2)
+    g.init_fluid_wave(1.0, (0.01, 0.004, -0.007), 0.01, 0, 2)
+    cells_close(o, g, levels, 1e-12)
+    steps = 3 if levels == 3 else 5
+    o.step(steps)
+    g.step(steps)
+    cells_close(o, g, levels, 1e-10)
+
+
+def test_uniform_flow_and_conservation_gpu(lib):
+    """Uniform flow stays exact on every level; with the plain transfer the
+    GPU conserves mass and momentum of a shear wave to rounding."""
+    shape, levels = (32, 32, 48), 2
+    g = lib.Simulation(shape, precision="fp64", tau=0.7, levels=levels)
+    g.refine_box((18, 26, 30), (42, 38, 58))
+    u = np.array([0.02, -0.01, 0.005])
+    g.init_fluid(1.0, u)
+    g.step(3)
+    from lattice_ref import C, W
+    cu = C @ u
+    e = W * (3 * cu + 4.5 * cu ** 2 - 1.5 * u @ u)
+    for l in range(levels):
+        _, f = g.level_cells(l)
+        assert np.abs(f - e[None, :]).max() < 2e-16
+    g2 = lib.Simulation((48, 48, 64), precision="fp64", tau=0.8, levels=levels)
+    g2.refine_box((18, 26, 30), (42, 38, 58))
+    g2.init_fluid_wave(1.0, (0.01, 0.004, -0.007), 0.01, 0, 2)
+
+    def totals():
+        m, p, s = [], [[], [], []], []
+        for l in range(levels):
+            _, f = g2.level_cells(l)
+            vol = 8.0 ** (levels - 1 - l)
+            m.extend((f.sum(axis=1) * vol).tolist())
+            for k in range(3):
+                mk = (f @ C[:, k].astype(float)) * vol
+                p[k].extend(mk.tolist())
+                s.extend(np.abs(mk).tolist())
+        return math.fsum(m), np.array([math.fsum(v) for v in p]), math.fsum(s)
+
+    m0, p0, scale = totals()
+    g2.step(4)
+    m1, p1, _ = totals()
+    assert abs(m1 - m0) < 1e-14 * scale
+    assert np.abs(p1 - p0).max() < 1e-14 * scale
+
+
+def test_rescaled_transfer_parity(orc, lib):
+    """The optional non-equilibrium rescaling follows the oracle too."""
+    o, g = pair(orc, lib, (32, 32, 48), 2, tau=0.8, rescale=True, box=((18, 26, 30), (42, 38, 58)))
+    o.init_equilibrium(u=(0.01, 0.0, 0.0), shear=0.01, shear_dir=0, shear_axis=2)
+    g.init_fluid_wave(1.0, (0.01, 0.0, 0.0), 0.01, 0, 2)
+    o.step(3)
+    g.step(3)
+    cells_close(o, g, 2, 1e-10)
+
+
+def test_refined_sphere_fp64(orc, lib):
+    """Three levels around a light sphere (d = 10 finest cells): maps, links,
+    populations and the particle history against the oracle."""
+    pos = (30.7, 33.2, 31.6)
+    o, g = pair(orc, lib, (16, 16, 16), 3, tau=0.7, sphere=(pos, 10.0, 0.3, 0.5), gravity=(0, 0, -2e-4))
+    same_maps(o, g, 3)
+    o.init_equilibrium()
+    g.init_fluid()
+    o.step(3)
+    g.step(3)
+    same_maps(o, g, 3)
+    cells_close(o, g, 3, 1e-10)
+    ho, hg = o.history(), g.history()
+    assert ho.shape == hg.shape == (12, 15)
+    Fs = 0.7 * 2e-4 * math.pi * 1000 / 6
+    np.testing.assert_allclose(hg[:, 0:6], ho[:, 0:6], rtol=0, atol=1e-10 * Fs)
+    np.testing.assert_allclose(hg[:, 6:9], ho[:, 6:9], rtol=1e-10, atol=1e-10)
+    gc, gq, gd = g.links()
+    # oracle links in global finest coordinates are those of the boundary cells of the finest level
+    assert len(gc) > 0 and np.all((gd > 0) & (gd <= 1))
+
+
+def test_moving_sphere_with_regrids(orc, lib):
+    """A fast light sphere crosses block boundaries; both sides regrid every
+    coarse step: block maps stay bit-exact and populations within 1e-10."""
+    pos = (30.3, 31.6, 42.6)   # bounding box (+1 cell) ends 0.4 cells below a block boundary
+    o, g = pair(orc, lib, (32, 32, 48), 2, tau=0.6, sphere=(pos, 8.0, 0.2, 0.5), gravity=(0, 0, -1e-2))
+    o.init_equilibrium()
+    g.init_fluid()
+    maps0 = [g.block_map(l).copy() for l in range(2)]
+    for step in range(8):
+        o.step(1)
+        g.step(1)
+        o.regrid()
+        g.regrid()
+        same_maps(o, g, 2)
+    cells_close(o, g, 2, 1e-10)
+    ho, hg = o.history(), g.history()
+    np.testing.assert_allclose(hg[:, 6:9], ho[:, 6:9], rtol=1e-10, atol=1e-10)
+    assert hg[-1, 8] - pos[2] > 0.5   # it rose ...
+    assert any(not np.array_equal(maps0[l], g.block_map(l)) for l in range(2))   # ... and the grid followed
+
+
+def test_refined_fp32_against_fp64_oracle(orc, lib):
+    """FP32 deviations on three levels against the FP64 oracle."""
+    pos = (30.7, 33.2, 31.6)
+    o, g = pair(orc, lib, (16, 16, 16), 3, tau=0.7, precision="fp32", sphere=(pos, 10.0, 0.3, 0.5),
+                gravity=(0, 0, -2e-4))
+    o.init_equilibrium()
+    g.init_fluid()
+    o.step(3)
+    g.step(3)
+    cells_close(o, g, 3, 1e-4)
+    ho, hg = o.history(), g.history()
+    Fs = 0.7 * 2e-4 * math.pi * 1000 / 6
+    assert np.abs(hg[:, 0:3] - ho[:, 0:3]).max() < 1e-3 * Fs
+
+
+def test_refined_walls(orc, lib):
+    """No-slip walls on x and y (as in the rising-sphere channel) with a box
+    refinement touching nothing but the interior."""
+    o, g = pair(orc, lib, (32, 32, 48), 2, tau=0.75, bc=("noslip", "noslip", "periodic"),
+                box=((20, 20, 30), (44, 44, 60)))
+    same_maps(o, g, 2)
+    o.init_equilibrium(u=(0.0, 0.0, 0.01), shear=0.01, shear_dir=2, shear_axis=0)
+    g.init_fluid_wave(1.0, (0.0, 0.0, 0.01), 0.01, 2, 0)
+    o.step(4)
+    g.step(4)
+    cells_close(o, g, 2, 1e-10)
