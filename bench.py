@@ -1,9 +1,16 @@
-"""Benchmark of the coupled LBM-MEM step (MLUPS and fraction of the HBM roofline).
+"""Benchmark of the coupled LBM-MEM step: MLUPS and fraction of the HBM roofline.
 
-Default workload: a periodic 512^3 D3Q19 TRT box with one light sphere
-(d = 40 cells, pi_p = 0.5, Ga = 200 at u_g = 0.01, C_v = 0.5), FP32
-deviation storage, the full coupled step of Algorithm 1 per timed step.
-The field (20.4 GB in FP32) is far larger than L2, so no flush is needed.
+Default workload (the single rising light sphere on a refined grid): level-0
+box of 64 x 64 x 256 cells in 16^3 blocks, 3 levels (finest 256 x 256 x
+1024), sphere of 20 finest cells, density ratio 0.5, Ga = 200 at u_g = 0.01,
+C_v = 0.5, no-slip walls on x and y, periodic z, regrid every 50 level-0
+steps, FP32 deviation storage.  A timed step is one level-0 step of the full
+coupled method (Algorithm 1 on the finest level, sub-cycling, explosion and
+coalescence, regrids when due).  MLUPS counts real cell updates of all levels.
+
+Also reported (key "uniform512"): a periodic 512^3 box with a sphere of 40
+cells, the bandwidth case of the stream-collide kernel.  Both fields are far
+larger than L2 (no flush needed).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16|fp64]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
@@ -13,6 +20,7 @@ independent replica on its own GPU (weak scaling, no collective on the data
 path); the time is the max over ranks.
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -29,62 +37,64 @@ METRIC = "MLUPS of coupled LBM-MEM step (FP32/FP16 vs FP64) and % of HBM rooflin
 BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math"}
 
+REFINED = dict(shape=(64, 64, 256), levels=3, diameter=20.0, density_ratio=0.5, ga=200.0, u_g=0.01, cv=0.5,
+               bc=("noslip", "noslip", "periodic"), regrid=50)
+UNIFORM = dict(shape=(512, 512, 512), diameter=40.0, density_ratio=0.5, ga=200.0, u_g=0.01, cv=0.5)
+
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100, help="timed level-0 steps of the refined workload")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "fp64"])
-    ap.add_argument("--edge", type=int, default=512)
+    ap.add_argument("--workload", default="refined", choices=["refined", "uniform"])
+    ap.add_argument("--edge", type=int, default=512, help="edge of the uniform bandwidth case")
+    ap.add_argument("--uniform-steps", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uniform", action="store_true")
     return ap.parse_args()
 
 
-def workload(args):
-    from paper_2103_10882_gb300 import workloads
-    w = dict(workloads.ROOFLINE_512)
-    e = args.edge
-    w["shape"] = (e, e, e)
-    return w
+def refined_name(prec):
+    return ("refined rising sphere: level-0 64x64x256 (16^3 blocks), 3 levels, d=20 finest, pi_p=0.5, Ga=200, "
+            "C_v=0.5, walls x/y, periodic z, regrid every 50 level-0 steps, %s" % prec)
 
 
-def workload_name(args):
-    e = args.edge
-    return "uniform %d^3 periodic D3Q19 TRT, 1 sphere d=40 pi_p=0.5 Ga=200 C_v=0.5, coupled step" % e
+def uniform_name(edge, prec):
+    return "uniform %d^3 periodic, 1 sphere d=40 pi_p=0.5 Ga=200 C_v=0.5, %s" % (edge, prec)
 
 
-def measured_peaks():
+def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+            return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
 
 
-def profiled_traffic(args):
-    """DRAM bytes per k_bulk launch from the committed ncu summary (captured
-    at 256^3 and scaled by the cells processed); None when the summary does
-    not exist or the kernel source changed since the capture."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_bulk_%s_uniform256.md" % args.precision)
-    if args.edge != 512 or not os.path.exists(path):
+def profiled_traffic(name, scale_cells):
+    """DRAM bytes per launch of a kernel from a committed ncu summary
+    (fields traffic_bytes_per_launch_* and source_sha256_16 of its source
+    file); None if absent or the source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
         return None
     fields = {}
     for line in open(path):
-        if ":" in line and line.strip().split(":")[0] in ("source_sha256_16", "traffic_bytes_per_launch_512"):
+        if ":" in line:
             k, v = line.strip().split(":", 1)
-            fields[k] = v.strip()
-    src = os.path.join(ROOT, "paper_2103_10882_gb300", "csrc", "uniform.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if fields.get("source_sha256_16") != sha:
+            fields[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2103_10882_gb300", "csrc", fields.get("source_file", "uniform.cu"))
+    if not os.path.exists(src):
+        return None
+    if fields.get("source_sha256_16") != hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]:
         return None
     try:
-        return int(fields["traffic_bytes_per_launch_512"])
+        return int(fields[scale_cells])
     except (KeyError, ValueError):
         return None
 
@@ -104,10 +114,11 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
@@ -142,28 +153,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(args, w, seconds):
-    """The FP64 oracle on the host cores, on a bounded sample of the same
-    workload: a periodic slab of the same box (full x-y extent, 48 layers)
-    through the sphere, same tau, sphere and gravity."""
-    import numpy as np
+def ga_tau_g(ga, u_g, d, pi):
+    nu = u_g * d / ga
+    return 3 * nu + 0.5, u_g ** 2 / (abs(pi - 1) * d)
 
-    import oracle
+
+def refined_start(shape, levels, d):
+    f = 1 << (levels - 1)
     from paper_2103_10882_gb300 import workloads
-    threads = os.cpu_count() or 1
-    oracle.set_threads(threads)
-    e = w["shape"][0]
-    shape = (e, e, 48)
-    D, pi = w["diameter"], w["density_ratio"]
-    nu = w["u_g"] * D / w["ga"]
-    tau = 3 * nu + 0.5
-    gm = w["u_g"] ** 2 / (abs(pi - 1) * D)
-    o = oracle.UniformSim(shape, tau=tau)
-    pos = np.array([e / 2, e / 2, 24.0]) + workloads.sub_cell_offset(0)
-    o.add_sphere(pos, D, pi, cv=w["cv"])
+    off = workloads.sub_cell_offset(0)
+    # lateral centre, 0.6 d above the bottom (finest units)
+    return (shape[0] * f / 2 + off[0], shape[1] * f / 2 + off[1], 0.6 * d + off[2])
+
+
+def cpu_baseline(seconds):
+    """The FP64 refined oracle on the host cores, on a bounded sample of the
+    same workload: the same hierarchy and sphere for as many level-0 steps as
+    fit in `seconds` (at least one)."""
+    import oracle
+    w = REFINED
+    tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    o = oracle.RefinedSim(w["shape"], w["levels"], tau=tau, periodic=(0, 0, 1))
+    o.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+                 cv=w["cv"])
     o.set_gravity((0, 0, -gm))
     o.init_equilibrium()
-    ncells = shape[0] * shape[1] * shape[2]
+    upd = sum((o.block_map(l) >= 0).sum() * 4096 * (1 << l) for l in range(w["levels"]))
     t0 = time.perf_counter()
     steps = 0
     while True:
@@ -173,24 +188,68 @@ def cpu_baseline(args, w, seconds):
         if dt >= seconds:
             break
     o.close()
-    return {"value": ncells * steps / dt / 1e6, "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": "%dx%dx%d periodic slab through the sphere, %d steps, %.1f s" % (shape + (steps, dt))}
+    return {"value": upd * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "refined workload (same hierarchy and sphere), %d level-0 steps in %.1f s, single thread"
+                      % (steps, dt)}
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    w = workload(args)
-    per = max(args.cpu_seconds / max(args.steps, 1), 1.0)
-    cb = cpu_baseline(args, w, per * max(args.steps, 1))
+    cb = cpu_baseline(max(args.cpu_seconds, 1.0))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(args), "precision": "fp64 oracle"},
-            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
+            "data": "synthetic", "config": {"workload": refined_name("fp64 oracle")}, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def timed(sim, steps, stream, torch):
+    c0 = sim.counters()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    sim.profile(True)
+    start.record(stream)
+    sim.step_async(steps)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    sim.check()
+    ms = start.elapsed_time(stop)
+    prof = sim.profile_result()
+    sim.profile(False)
+    c1 = sim.counters()
+    return ms, prof, c0, c1
+
+
+def e2e(sim, steps, g_host):
+    """Same metric end to end through the C ABI with host buffers: each step
+    uploads the gravity vector from a host array, advances one level-0 step
+    (reading the status word back) and reads the particle record into a host
+    array."""
+    import numpy as np
+    e0 = sim.counters()
+    t0 = time.perf_counter()
+    rec = None
+    for _ in range(steps):
+        sim.set_gravity(g_host)
+        sim.step(1)
+        rec = sim.particle()
+    t1 = time.perf_counter()
+    e1 = sim.counters()
+    assert np.all(np.isfinite(rec))
+    return {"value": (e1[1] - e0[1]) / (t1 - t0) / 1e6, "unit": "MLUPS",
+            "h2d_bytes_per_step": (e1[3] - e0[3]) / steps, "d2h_bytes_per_step": (e1[4] - e0[4]) / steps,
+            "steps": steps}
+
+
+def roofline(prof, kernel, traffic):
+    kms, launches, _, _, bytes_, _ = prof
+    peak, kind = measured_peak()
+    achieved = bytes_ / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": kernel, "peak_kind": kind, "launches": int(launches),
+            "kernel_ms_total": kms}
 
 
 def main():
@@ -211,88 +270,75 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    prec = args.precision
+    bpp = BYTES_PER_POP[prec]
+    line = {}
 
-    w = workload(args)
-    shape, D, pi = w["shape"], w["diameter"], w["density_ratio"]
-    sim = L.Simulation(shape, precision=args.precision)
-    pos = np.array(shape, dtype=float) / 2 + workloads.sub_cell_offset(rank)
-    pos[2] = 0.25 * shape[2] + workloads.sub_cell_offset(rank)[2]
-    sim.add_sphere(pos, D, pi, cv=w["cv"])
+    # ------------------------------------------------- refined (headline)
+    w = REFINED
+    tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    sim = L.Simulation(w["shape"], precision=prec, tau=tau, bc=w["bc"], levels=w["levels"],
+                       regrid_interval=w["regrid"], history_capacity=1 << 16)
+    sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+                   cv=w["cv"])
     sim.set_ga(w["ga"], w["u_g"], (0.0, 0.0, -1.0))
     sim.init_fluid()
-    ncells = sim.ncells
-
-    # warm-up
+    upd_step, launches_step = sim.updates_per_step()
     sim.step(args.warmup)
-    torch.cuda.synchronize()
-    stream = sim.stream
-    c0 = sim.counters()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        sim.profile(True)
-        start.record(stream)
-        sim.step_async(args.steps)
-        stop.record(stream)
-        torch.cuda.synchronize()
-    sim.check()
-    ms = start.elapsed_time(stop)
-    bulk_ms, bulk_n, _, _ = sim.profile_result()
-    sim.profile(False)
-    c1 = sim.counters()
-    launches = int(c1[2] - c0[2])
+        ms, prof, c0, c1 = timed(sim, args.steps, sim.stream, torch)
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = world * ncells * args.steps / (ms_max * 1e-3) / 1e6
-
-    # end to end through the public API with host buffers: each step uploads
-    # the gravity vector (host array), advances one step (status read back)
-    # and reads the particle record into a host array
-    g_host = np.array([0.0, 0.0, -(w["u_g"] ** 2) / (abs(pi - 1) * D)])
-    e0 = sim.counters()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        sim.set_gravity(g_host)
-        sim.step(1)
-        rec = sim.particle()
-    t1 = time.perf_counter()
-    e1 = sim.counters()
-    e2e_value = ncells * args.e2e_steps / (t1 - t0) / 1e6
-    h2d = (e1[3] - e0[3]) / args.e2e_steps
-    d2h = (e1[4] - e0[4]) / args.e2e_steps
-    assert np.all(np.isfinite(rec))
-
-    bpp = BYTES_PER_POP[args.precision]
-    alg_bytes = 2 * 19 * bpp * ncells
-    bulk_avg_s = bulk_ms / max(bulk_n, 1) * 1e-3
-    achieved = alg_bytes / bulk_avg_s / 1e9
-    peak, peak_kind = measured_peaks()
-    traffic = profiled_traffic(args)
-
-    line = {
-        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.precision], "data": "synthetic",
-        "config": {"workload": workload_name(args), "cells": ncells, "precision": args.precision,
-                   "l2": "inputs larger than L2 (%.1f GB field)" % (2 * alg_bytes / 2 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_bulk (stream + TRT collide, %s)" % args.precision,
-                     "peak_kind": peak_kind, "bytes_per_cell_update": 2 * 19 * bpp},
-        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": args.e2e_steps},
-        "gpu_launches": launches,
-        "clocks": clk.summary(),
-        "step_ms_breakdown": {"bulk_ms_avg": bulk_ms / max(bulk_n, 1), "step_ms_avg": ms_max / args.steps},
-    }
+    updates = c1[1] - c0[1]
+    value = world * updates / (ms_max * 1e-3) / 1e6
+    e2e_line = e2e(sim, args.e2e_steps, np.array([0.0, 0.0, -gm]))
+    part = sim.particle()
     sim.close()
+    line.update({
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "config": {"workload": refined_name(prec), "cell_updates_per_step": updates / args.steps,
+                   "launches_per_step": launches_step, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline(prof, "k_update (refined stream + collide / coalescence, %s)" % prec,
+                             profiled_traffic("k_update_%s_refined.md" % prec, "traffic_bytes_per_launch")),
+        "e2e": e2e_line,
+        "gpu_launches": int(c1[2] - c0[2]),
+        "clocks": clk.summary(),
+        "particle_after": {"z": part[8], "u_z": part[11]},
+    })
+    line["roofline"]["bytes_per_cell_update"] = 38 * bpp
+
+    # --------------------------------------------- uniform bandwidth case
+    if not args.no_uniform:
+        e = args.edge
+        uw = UNIFORM
+        tau_u, gm_u = ga_tau_g(uw["ga"], uw["u_g"], uw["diameter"], uw["density_ratio"])
+        us = L.Simulation((e, e, e), precision=prec, tau=tau_u)
+        pos = np.array([e / 2, e / 2, e / 4]) + workloads.sub_cell_offset(rank)
+        us.add_sphere(pos, uw["diameter"], uw["density_ratio"], cv=uw["cv"])
+        us.set_gravity((0.0, 0.0, -gm_u))
+        us.init_fluid()
+        us.step(3)
+        with ClockSampler(local) as clk_u:
+            ums, uprof, u0, u1 = timed(us, args.uniform_steps, us.stream, torch)
+        us.close()
+        line["uniform512"] = {
+            "workload": uniform_name(e, prec), "value": (u1[1] - u0[1]) / (ums * 1e-3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ums / args.uniform_steps,
+            "roofline": roofline(uprof, "k_bulk (stream + TRT collide, %s)" % prec,
+                                 profiled_traffic("k_bulk_%s_uniform256.md" % prec, "traffic_bytes_per_launch_512")
+                                 if e == 512 else None),
+            "roofline_mlups": measured_peak()[0] * 1e9 / (38 * bpp) / 1e6,
+            "clocks": clk_u.summary(),
+        }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, w, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if dist:
         dist.barrier()
         dist.destroy_process_group()

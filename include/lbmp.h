@@ -197,9 +197,11 @@ lbmp_status lbmp_get_counters(lbmp_handle* h, int64_t out[5]);
  * enabled every step records events around its stream-collide kernel. */
 lbmp_status lbmp_profile(lbmp_handle* h, int enable);
 /* Results since the last lbmp_profile(h, 1): [0] total ms in the
- * stream-collide kernel, [1] its launches, [2] total ms of the whole steps,
- * [3] steps.  Synchronises the stream. */
-lbmp_status lbmp_get_profile(lbmp_handle* h, double out[4]);
+ * stream-collide kernels, [1] their launches, [2] total ms of the whole
+ * steps, [3] steps, [4] algorithmic bytes of those launches (19 reads and
+ * 19 writes of a stored population per real cell updated), [5] cell
+ * updates of those launches.  Synchronises the stream. */
+lbmp_status lbmp_get_profile(lbmp_handle* h, double out[6]);
 /* Boundary cells of one sphere, computed without allocating any memory.
  * (No counterpart in the paper: this is a service for callers that cannot
  * call cudaMalloc, such as a host function enqueued on a stream, a loop

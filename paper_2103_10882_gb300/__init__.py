@@ -212,7 +212,7 @@ def lbmp_profile(h, enable=True):
 
 
 def lbmp_get_profile(h):
-    out = np.zeros(4, dtype=np.float64)
+    out = np.zeros(6, dtype=np.float64)
     _check(h, _lib().lbmp_get_profile(h, _dp(out)))
     return out
 
@@ -439,5 +439,5 @@ class Simulation:
         lbmp_profile(self.h, enable)
 
     def profile_result(self):
-        """(stream-collide ms total, its launches, step ms total, steps)."""
+        """(stream-collide ms, its launches, step ms, steps, algorithmic bytes, cell updates)."""
         return lbmp_get_profile(self.h)

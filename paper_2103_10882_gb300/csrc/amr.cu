@@ -1177,6 +1177,7 @@ void enqueue_advance(lbmp_handle* h, int l) {
     }
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) U.solid = V.d_flags[V.fcur];
+    const long long ev0 = profile_mark(h);
     if (np > 0) {
         if (has_fine && has_coarse) k_update<S, true, true, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
         else if (has_fine) k_update<S, true, false, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
@@ -1186,6 +1187,7 @@ void enqueue_advance(lbmp_handle* h, int l) {
         else k_update<S, false, false, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
         h->launches += 1;
     }
+    profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
     h->updates += (long long)V.nreal * B3;
     if (coupled) {
         const LevelView D = view(E, V);
@@ -1310,11 +1312,13 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
     AmrEngine* E = h->amr;
     level_rates(E, h->tau, h->magic);
     for (int i = 0; i < n; ++i) {
+        const long long ev_step = profile_mark(h);
         with_storage_amr(h->cfg.precision, [&](auto tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
             E->substep[0] = 0;
             enqueue_advance<S>(h, 0);
         });
+        profile_step(h, ev_step, profile_mark(h));
         E->coarse_steps += 1;
         h->steps += 1;
         if (cudaGetLastError() != cudaSuccess) return LBMP_ERR_CUDA;

@@ -101,25 +101,10 @@ void with_storage(int prec, F&& f) {
     else f((__half*)nullptr);
 }
 
-cudaEvent_t next_event(lbmp_handle* h) {
-    if (h->ev_used == h->ev_pool.size()) {
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-        h->ev_pool.push_back(e);
-    }
-    return h->ev_pool[h->ev_used++];
-}
-
-void record(lbmp_handle* h) {
-    if (!h->profiling) return;
-    cudaEvent_t e = next_event(h);
-    if (e) cudaEventRecord(e, h->stream);
-}
-
 // One coupled step (Algorithm 1) on the handle's stream.
 void enqueue_step(lbmp_handle* h) {
     const int prec = h->cfg.precision;
-    record(h);
+    const long long ev_step = profile_mark(h);
     with_storage(prec, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         using A = typename Store<S>::A;
@@ -127,8 +112,9 @@ void enqueue_step(lbmp_handle* h) {
         S* dst = (S*)h->pops[1 - h->cur];
         const CollideParams<A> p = collide_params<A>(h);
         // 1. stream + collide every cell (LBM step)
+        const long long ev_bulk = profile_mark(h);
         launch_bulk<S>(src, dst, h->G, p, h->status, h->stream);
-        record(h);
+        profile_kernel(h, ev_bulk, profile_mark(h), 38.0 * sizeof(S) * (double)h->G.n, (double)h->G.n);
         h->launches += 1;
         if (h->has_particle) {
             // 2. cells next to the sphere: CLI links + momentum-exchange force partials
@@ -149,7 +135,7 @@ void enqueue_step(lbmp_handle* h) {
             h->launches += 6;
         }
     });
-    record(h);
+    profile_step(h, ev_step, profile_mark(h));
     h->cur = 1 - h->cur;
     h->steps += 1;
     h->updates += h->G.n;
@@ -201,6 +187,29 @@ lbmp_status download_particle(lbmp_handle* h) {
 }  // namespace
 
 namespace lbmp {
+long long profile_mark(lbmp_handle* h) {
+    if (!h->profiling) return -1;
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        h->ev_pool.push_back(e);
+    }
+    cudaEventRecord(h->ev_pool[h->ev_used], h->stream);
+    return (long long)h->ev_used++;
+}
+
+void profile_kernel(lbmp_handle* h, long long start, long long end, double bytes, double updates) {
+    if (start < 0 || end < 0) return;
+    h->prof_kernel.emplace_back((size_t)start, (size_t)end);
+    h->prof_bytes.push_back(bytes);
+    h->prof_updates.push_back(updates);
+}
+
+void profile_step(lbmp_handle* h, long long start, long long end) {
+    if (start < 0 || end < 0) return;
+    h->prof_step.emplace_back((size_t)start, (size_t)end);
+}
+
 // Error message for entry points that have no handle (read by lbmp_last_error(NULL)).
 void set_global_error(const std::string& msg) { g_create_error = msg; }
 void* handle_alloc(lbmp_handle* h, size_t bytes) { return dev_alloc(h, bytes); }
@@ -733,27 +742,37 @@ lbmp_status lbmp_profile(lbmp_handle* h, int enable) {
     if (enable) {
         LBMP_CK(h, cudaStreamSynchronize(h->stream));
         h->ev_used = 0;
+        h->prof_kernel.clear();
+        h->prof_bytes.clear();
+        h->prof_updates.clear();
+        h->prof_step.clear();
     }
     h->profiling = enable != 0;
     return LBMP_OK;
 }
 
-lbmp_status lbmp_get_profile(lbmp_handle* h, double out[4]) {
+lbmp_status lbmp_get_profile(lbmp_handle* h, double out[6]) {
     if (!h || !out) return LBMP_ERR_INVALID_ARG;
     LBMP_CK(h, cudaStreamSynchronize(h->stream));
-    double bulk = 0.0, total = 0.0;
-    const size_t steps = h->ev_used / 3;
-    for (size_t s = 0; s < steps; ++s) {
-        float a = 0.f, b = 0.f;
-        LBMP_CK(h, cudaEventElapsedTime(&a, h->ev_pool[3 * s], h->ev_pool[3 * s + 1]));
-        LBMP_CK(h, cudaEventElapsedTime(&b, h->ev_pool[3 * s], h->ev_pool[3 * s + 2]));
-        bulk += a;
-        total += b;
+    double kms = 0.0, sms = 0.0, bytes = 0.0, upd = 0.0;
+    for (size_t i = 0; i < h->prof_kernel.size(); ++i) {
+        float a = 0.f;
+        LBMP_CK(h, cudaEventElapsedTime(&a, h->ev_pool[h->prof_kernel[i].first], h->ev_pool[h->prof_kernel[i].second]));
+        kms += a;
+        bytes += h->prof_bytes[i];
+        upd += h->prof_updates[i];
     }
-    out[0] = bulk;
-    out[1] = (double)steps;
-    out[2] = total;
-    out[3] = (double)steps;
+    for (auto& p : h->prof_step) {
+        float a = 0.f;
+        LBMP_CK(h, cudaEventElapsedTime(&a, h->ev_pool[p.first], h->ev_pool[p.second]));
+        sms += a;
+    }
+    out[0] = kms;
+    out[1] = (double)h->prof_kernel.size();
+    out[2] = sms;
+    out[3] = (double)h->prof_step.size();
+    out[4] = bytes;
+    out[5] = upd;
     return LBMP_OK;
 }
 

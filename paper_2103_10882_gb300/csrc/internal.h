@@ -78,6 +78,11 @@ void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStr
 
 struct AmrEngine;
 
+// Profiling events on the handle's stream (api.cu); -1 when profiling is off.
+long long profile_mark(lbmp_handle* h);
+void profile_kernel(lbmp_handle* h, long long start, long long end, double bytes, double updates);
+void profile_step(lbmp_handle* h, long long start, long long end);
+
 // Device allocation through the handle's allocator (api.cu).
 void* handle_alloc(lbmp_handle* h, size_t bytes);
 void handle_free(lbmp_handle* h, void* p);
@@ -110,8 +115,12 @@ struct lbmp_handle {
     double body_force[3] = {0, 0, 0};
     long long steps = 0, updates = 0, launches = 0, h2d = 0, d2h = 0;
     bool profiling = false;
-    std::vector<cudaEvent_t> ev_pool;    // events of the current measurement, 3 per step
+    std::vector<cudaEvent_t> ev_pool;    // events of the current measurement
     size_t ev_used = 0;
+    // (start, end) event indices of stream-collide launches with their algorithmic bytes and cell updates
+    std::vector<std::pair<size_t, size_t>> prof_kernel;
+    std::vector<double> prof_bytes, prof_updates;
+    std::vector<std::pair<size_t, size_t>> prof_step;
     std::vector<std::pair<void*, size_t>> allocations;
     std::string err;
     lbmp::AmrEngine* amr = nullptr;     // refined hierarchy (levels > 1), else null
