@@ -117,17 +117,18 @@ __global__ void __launch_bounds__(UPD_THREADS)
               typename Store<S>::A kp, typename Store<S>::A km, int rescale, typename Store<S>::A scale,
               typename Store<S>::A inv_scale, int* __restrict__ status) {
     using A = typename Store<S>::A;
-    const int gb = blockIdx.x;
+    const int gb = blockIdx.x >> 4;
     const int b = F.nreal + gb;
     const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += UPD_THREADS) {
-        if (!F.gkind[(size_t)gb * B3 + c]) continue;
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
+        if (!F.gkind[(size_t)gb * B3 + c]) return;
         const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
         int pc;
         const int pb = locate(C, p, &pc);
         if (pb < 0 || pb >= C.nreal) {
             atomicOr(status, STATUS_AMR_MISSING);
-            continue;
+            return;
         }
         A f[19];
 #pragma unroll
@@ -163,99 +164,111 @@ struct UpdateArgs {
     int* status;
 };
 
+// Update of one cell of pool block b: real cells pull (or, for hosts,
+// coalesce) and collide; active ghost cells pull only.  nb27 lists the pool
+// ids of block b's 26 neighbours (and itself at index 13).
+template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL>
+__device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27) {
+    using A = typename Store<S>::A;
+    const LevelView& D = U.D;
+    const A scale = U.P.scale, inv = U.P.inv_scale;
+    const bool real = REAL;
+    const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
+    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    A g[19];
+    if (HAS_FINE && real && D.host[(size_t)b * B3 + c] == 1) {
+        // coalescence: mean of the eight ghost sub-cells after the finer level's two steps
+#pragma unroll
+        for (int q = 0; q < 19; ++q) g[q] = A(0);
+        const int gx = 2 * (bx * BS + lx), gy = 2 * (by * BS + ly), gz = 2 * (bz * BS + lz);
+        for (int s = 0; s < 8; ++s) {
+            const int v[3] = {gx + (s & 1), gy + ((s >> 1) & 1), gz + (s >> 2)};
+            int vc;
+            const int vb = locate(U.F, v, &vc);
+            if (vb < U.F.nreal) {
+                atomicOr(U.status, STATUS_AMR_MISSING);
+                continue;
+            }
+#pragma unroll
+            for (int q = 0; q < 19; ++q) g[q] += Store<S>::load(U.fsrc + paddr(vb, q, vc), inv);
+        }
+#pragma unroll
+        for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
+        if (U.rescale) rescale19<A>(g, U.fkp, U.fkm);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const int sx = lx - cx(q), sy = ly - cy(q), sz = lz - cz(q);
+            const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
+            const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
+            const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
+            const int nbk = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];   // entry 13 is b itself
+            if (nbk == -2) {   // domain wall: bounce-back
+                g[q] = Store<S>::load(U.src + paddr(b, opp(q), c), inv);
+                continue;
+            }
+            if (nbk < 0) {
+                atomicOr(U.status, STATUS_AMR_MISSING);
+                g[q] = A(0);
+                continue;
+            }
+            const int sc = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
+            if (HAS_COARSE && nbk >= D.nreal && U.substep == 1 &&
+                D.gkind[(size_t)(nbk - D.nreal) * B3 + sc] == 2) {
+                // static ghost at the second step: content of the coarser cell one more step upwind
+                int t[3] = {bx * BS + sx - cx(q), by * BS + sy - cy(q), bz * BS + sz - cz(q)};
+                if (wrap3(t, D)) {
+                    const int p[3] = {t[0] >> 1, t[1] >> 1, t[2] >> 1};
+                    int pc;
+                    const int pb = locate(U.Cc, p, &pc);
+                    if (pb < 0 || pb >= U.Cc.nreal) {
+                        atomicOr(U.status, STATUS_AMR_MISSING);
+                        g[q] = A(0);
+                        continue;
+                    }
+                    A f[19];
+#pragma unroll
+                    for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
+                    if (U.rescale) rescale19<A>(f, U.ckp, U.ckm);
+                    g[q] = f[q];
+                    continue;
+                }
+            }
+            g[q] = Store<S>::load(U.src + (unsigned)((nbk * 19 + q) * B3 + sc), inv);   // pools hold < 2^31 elements
+        }
+    }
+    if (REAL) trt_collide<A, false>(g, U.P, U.status);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], scale);
+}
+
+// Real blocks: one CTA per z-slice of a block (256 cells, full warps).
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
 __global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs<S> U) {
     using A = typename Store<S>::A;
     __shared__ int nb27[27];
-    const LevelView& D = U.D;
-    const int b = blockIdx.x;
-    if (threadIdx.x < 27) nb27[threadIdx.x] = D.nbr[b * 27 + threadIdx.x];
+    const int b = blockIdx.x >> 4;
+    if (threadIdx.x < 27) nb27[threadIdx.x] = U.D.nbr[b * 27 + threadIdx.x];
     __syncthreads();
-    const bool real = b < D.nreal;
-    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-    const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
-    const A scale = U.P.scale, inv = U.P.inv_scale;
-    for (int lz = 0; lz < BS; ++lz) {
-        const int c = lx + BS * (ly + BS * lz);
-        if (!real) {
-            const uint8_t k = D.gkind[(size_t)(b - D.nreal) * B3 + c];
-            if (k == 0) continue;
-            if (k == 2) {
+    const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
+    if (COUPLED && U.solid[(size_t)b * B3 + c]) {
 #pragma unroll
-                for (int q = 0; q < 19; ++q) U.dst[paddr(b, q, c)] = U.src[paddr(b, q, c)];
-                continue;
-            }
-        } else if (COUPLED && U.solid[(size_t)b * B3 + c]) {
-#pragma unroll
-            for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), scale);
-            continue;
-        }
-        A g[19];
-        if (HAS_FINE && real && D.host[(size_t)b * B3 + c] == 1) {
-            // coalescence: mean of the eight ghost sub-cells after the finer level's two steps
-#pragma unroll
-            for (int q = 0; q < 19; ++q) g[q] = A(0);
-            const int gx = 2 * (bx * BS + lx), gy = 2 * (by * BS + ly), gz = 2 * (bz * BS + lz);
-            for (int s = 0; s < 8; ++s) {
-                const int v[3] = {gx + (s & 1), gy + ((s >> 1) & 1), gz + (s >> 2)};
-                int vc;
-                const int vb = locate(U.F, v, &vc);
-                if (vb < U.F.nreal) {
-                    atomicOr(U.status, STATUS_AMR_MISSING);
-                    continue;
-                }
-#pragma unroll
-                for (int q = 0; q < 19; ++q) g[q] += Store<S>::load(U.fsrc + paddr(vb, q, vc), inv);
-            }
-#pragma unroll
-            for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
-            if (U.rescale) rescale19<A>(g, U.fkp, U.fkm);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 19; ++q) {
-                const int sx = lx - cx(q), sy = ly - cy(q), sz = lz - cz(q);
-                const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
-                const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
-                const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
-                const int nbk = (ox | oy | oz) == 0 ? b : nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
-                if (nbk == -2) {   // domain wall: bounce-back
-                    g[q] = Store<S>::load(U.src + paddr(b, opp(q), c), inv);
-                    continue;
-                }
-                if (nbk < 0) {
-                    atomicOr(U.status, STATUS_AMR_MISSING);
-                    g[q] = A(0);
-                    continue;
-                }
-                const int sc = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
-                if (HAS_COARSE && nbk >= D.nreal && U.substep == 1 &&
-                    D.gkind[(size_t)(nbk - D.nreal) * B3 + sc] == 2) {
-                    // static ghost at the second step: content of the coarser cell one more step upwind
-                    int t[3] = {bx * BS + sx - cx(q), by * BS + sy - cy(q), bz * BS + sz - cz(q)};
-                    if (wrap3(t, D)) {
-                        const int p[3] = {t[0] >> 1, t[1] >> 1, t[2] >> 1};
-                        int pc;
-                        const int pb = locate(U.Cc, p, &pc);
-                        if (pb < 0 || pb >= U.Cc.nreal) {
-                            atomicOr(U.status, STATUS_AMR_MISSING);
-                            g[q] = A(0);
-                            continue;
-                        }
-                        A f[19];
-#pragma unroll
-                        for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
-                        if (U.rescale) rescale19<A>(f, U.ckp, U.ckm);
-                        g[q] = f[q];
-                        continue;
-                    }
-                }
-                g[q] = Store<S>::load(U.src + paddr(nbk, q, sc), inv);
-            }
-        }
-        if (real) trt_collide<A, false>(g, U.P, U.status);
-#pragma unroll
-        for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], scale);
+        for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), U.P.scale);
+        return;
     }
+    update_cell<S, HAS_FINE, HAS_COARSE, true>(U, b, c, nb27);
+}
+
+// Active ghost cells (sub-cells of the coarser level's hosts), from a list of
+// (pool block << 12 | cell): stream without collision.  Static ghost cells
+// keep the values the explosion wrote into both buffers.
+template <typename S>
+__global__ void __launch_bounds__(UPD_THREADS) k_ghost_stream(UpdateArgs<S> U, const int* __restrict__ list, int n) {
+    const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
+    if (i >= n) return;
+    const int e = list[i];
+    const int b = e >> 12, c = e & 4095;
+    update_cell<S, false, true, false>(U, b, c, U.D.nbr + (size_t)b * 27);
 }
 
 // ---------------------------------------------------------------- coupling
@@ -271,89 +284,71 @@ __device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int l
     return (ox | oy | oz) == 0 ? b : D.nbr[b * 27 + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
 }
 
-constexpr int BND_THREADS = 128;
+constexpr int BNDW_THREADS = 256;
 
+// One warp per boundary cell of the finest level, lane q handling population
+// q (CLI links of Sec. 2.3, FP64 force partials), cooperative collision.
 template <typename S>
-__global__ void __launch_bounds__(BND_THREADS)
+__global__ void __launch_bounds__(BNDW_THREADS)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
                    const int* __restrict__ list, const int* __restrict__ count,
                    CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
                    double* __restrict__ partials, int* __restrict__ status) {
     using A = typename Store<S>::A;
-    __shared__ double red[6][BND_THREADS / 32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double red[6][BNDW_THREADS / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (BNDW_THREADS / 32);
+    const int cnt = *count;
+    const ParticleState& Pp = *ps;
     double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
-    if (i < *count) {
-        const int e = list[i];
+    for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
+        const int e = list[w];
         const int b = e >> 12, c = e & 4095;
         const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
-        const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly, D.bpos[3 * b + 2] * BS + lz};
-        const ParticleState& Pp = *ps;
-        const double d[3] = {wrap_diff((g[0] + 0.5) - Pp.x[0], D.n[0], D.periodic[0]),
-                             wrap_diff((g[1] + 0.5) - Pp.x[1], D.n[1], D.periodic[1]),
-                             wrap_diff((g[2] + 0.5) - Pp.x[2], D.n[2], D.periodic[2])};
-        A gq[19];
-        for (int q = 0; q < 19; ++q) {
+        A gq = A(0);
+        if (lane < 19) {
+            const int q = lane;
+            const int cq[3] = {lane_c(q, 0), lane_c(q, 1), lane_c(q, 2)};
             int sc;
-            const int sb = nbr_cell(D, b, lx, ly, lz, -cx(q), -cy(q), -cz(q), &sc);
+            const int sb = nbr_cell(D, b, lx, ly, lz, -cq[0], -cq[1], -cq[2], &sc);
             if (sb == -2) {
-                gq[q] = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
-                continue;
-            }
-            if (sb < 0) {
+                gq = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
+            } else if (sb < 0) {
                 atomicOr(status, STATUS_AMR_MISSING);
-                gq[q] = A(0);
-                continue;
+            } else if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] == 0) {
+                gq = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
+            } else {
+                const int k = opp(q);
+                int fc;
+                const int fb = nbr_cell(D, b, lx, ly, lz, cq[0], cq[1], cq[2], &fc);   // x - c_k
+                const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
+                const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly, D.bpos[3 * b + 2] * BS + lz};
+                const double d[3] = {wrap_diff((g[0] + 0.5) - Pp.x[0], D.n[0], D.periodic[0]),
+                                     wrap_diff((g[1] + 0.5) - Pp.x[1], D.n[1], D.periodic[1]),
+                                     wrap_diff((g[2] + 0.5) - Pp.x[2], D.n[2], D.periodic[2])};
+                const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+                const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
+                const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
+                const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
+                gq = cli_link<A>(q, d, Pp.r, delta, gt_k, gt_q, gt_far, Pp, F, T);
             }
-            if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] == 0) {
-                gq[q] = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
-                continue;
-            }
-            const int k = opp(q);   // points from the cell into the solid
-            int fc;
-            const int fb = nbr_cell(D, b, lx, ly, lz, cx(q), cy(q), cz(q), &fc);   // x - c_k
-            const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
-            const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
-            const double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
-            const double alpha = 4.0 / (1.0 + 2.0 * delta);
-            const double arm[3] = {d[0] + delta * cx(k), d[1] + delta * cy(k), d[2] + delta * cz(k)};
-            const double vb[3] = {Pp.u[0] + (Pp.w[1] * arm[2] - Pp.w[2] * arm[1]),
-                                  Pp.u[1] + (Pp.w[2] * arm[0] - Pp.w[0] * arm[2]),
-                                  Pp.u[2] + (Pp.w[0] * arm[1] - Pp.w[1] * arm[0])};
-            const double vc = vb[0] * cx(k) + vb[1] * cy(k) + vb[2] * cz(k);
-            const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
-            const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
-            const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
-            const A gnew = gt_k + A(kappa0) * gt_far - A(kappa0) * gt_q - A(alpha * 3.0 * wgt<double>(k) * vc);
-            gq[q] = gnew;
-            const double ftk = wgt<double>(k) + (double)gt_k;
-            const double fnew = wgt<double>(q) + (double)gnew;
-            const double Fl[3] = {(cx(k) - vb[0]) * ftk - (cx(q) - vb[0]) * fnew,
-                                  (cy(k) - vb[1]) * ftk - (cy(q) - vb[1]) * fnew,
-                                  (cz(k) - vb[2]) * ftk - (cz(q) - vb[2]) * fnew};
-            F[0] += Fl[0];
-            F[1] += Fl[1];
-            F[2] += Fl[2];
-            T[0] += arm[1] * Fl[2] - arm[2] * Fl[1];
-            T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
-            T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
         }
-        trt_collide<A, false>(gq, P, status);
-        for (int q = 0; q < 19; ++q) Store<S>::store(dst + paddr(b, q, c), gq[q], P.scale);
+        gq = warp_trt_collide<A, false>(gq, lane, P, status);
+        if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
     }
     double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
 #pragma unroll
     for (int k = 0; k < 6; ++k)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
-        for (int k = 0; k < 6; ++k) red[k][warp] = v[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) red[k][wib] = v[k];
     __syncthreads();
     if (threadIdx.x < 6) {
-        double s = 0.0;
-        for (int w = 0; w < BND_THREADS / 32; ++w) s += red[threadIdx.x][w];
-        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+        double sum = 0.0;
+        for (int k = 0; k < BNDW_THREADS / 32; ++k) sum += red[threadIdx.x][k];
+        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = sum;
     }
 }
 
@@ -522,9 +517,10 @@ __global__ void __launch_bounds__(LINK_THREADS)
 // Host flag of every real cell: 1 when a cell covered by the next finer
 // level lies within Chebyshev distance 1, 2 when the nearest is at 2.
 __global__ void k_host_flags(LevelView D, uint8_t* __restrict__ host) {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x >> 4;
     const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
         int dist = 3;
         for (int dz = -2; dz <= 2; ++dz)
@@ -543,10 +539,11 @@ __global__ void k_host_flags(LevelView D, uint8_t* __restrict__ host) {
 
 // Kind of every ghost cell of level l+1: the host flag of its parent.
 __global__ void k_ghost_kind(LevelView C, const uint8_t* __restrict__ chost, LevelView F, uint8_t* __restrict__ gkind) {
-    const int gb = blockIdx.x;
+    const int gb = blockIdx.x >> 4;
     const int b = F.nreal + gb;
     const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
         int pc;
         const int pb = locate(C, p, &pc);
@@ -556,10 +553,11 @@ __global__ void k_ghost_kind(LevelView C, const uint8_t* __restrict__ chost, Lev
 
 __global__ void k_amr_flags_full(LevelView D, uint8_t* __restrict__ f0, uint8_t* __restrict__ f1,
                                  const ParticleState* __restrict__ ps) {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x >> 4;
     const ParticleState P = *ps;
     const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
         const uint8_t v = (P.present && ball(g, D, P)) ? 1 : 0;
         f0[(size_t)b * B3 + c] = v;
@@ -570,10 +568,10 @@ __global__ void k_amr_flags_full(LevelView D, uint8_t* __restrict__ f0, uint8_t*
 template <typename S>
 __global__ void k_amr_zero_solid(S* __restrict__ pops, const uint8_t* __restrict__ flags) {
     using A = typename Store<S>::A;
-    const int b = blockIdx.x;
-    for (int c = threadIdx.x; c < B3; c += blockDim.x)
-        if (flags[(size_t)b * B3 + c])
-            for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), A(1));
+    const int b = blockIdx.x >> 4;
+    const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
+    if (flags[(size_t)b * B3 + c])
+        for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), A(1));
 }
 
 template <typename S>
@@ -581,9 +579,10 @@ __global__ void k_amr_init(LevelView D, S* __restrict__ pops, const uint8_t* __r
                            double u0, double u1, double u2, double amp, int dir, int axis, double h, double Lax,
                            typename Store<S>::A scale) {
     using A = typename Store<S>::A;
-    const int b = blockIdx.x;
+    const int b = blockIdx.x >> 4;
     const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
         double u[3] = {u0, u1, u2};
         if (amp != 0.0) u[dir] += amp * sin(2.0 * M_PI * (g[axis] + 0.5) * h / Lax);
@@ -617,10 +616,11 @@ struct MigrateArgs {
 template <typename S>
 __global__ void k_migrate(MigrateArgs<S> M) {
     using A = typename Store<S>::A;
-    const int b = blockIdx.x;
+    const int b = blockIdx.x >> 4;
     const LevelView& N = M.N;
     const int bx = N.bpos[3 * b], by = N.bpos[3 * b + 1], bz = N.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
         A f[19];
         for (int q = 0; q < 19; ++q) f[q] = A(0);
@@ -664,9 +664,10 @@ __global__ void k_migrate(MigrateArgs<S> M) {
 template <typename S>
 __global__ void k_amr_export(LevelView D, const S* __restrict__ pops, int32_t* __restrict__ xyz,
                              double* __restrict__ out, typename Store<S>::A inv_scale) {
-    const int b = blockIdx.x;
+    const int b = blockIdx.x >> 4;
     const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-    for (int c = threadIdx.x; c < B3; c += blockDim.x) {
+    {
+        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const size_t m = (size_t)b * B3 + c;
         xyz[3 * m] = bx * BS + (c & 15);
         xyz[3 * m + 1] = by * BS + ((c >> 4) & 15);
@@ -719,6 +720,8 @@ struct Level {
     uint8_t* d_refined = nullptr;
     uint8_t* d_host = nullptr;
     uint8_t* d_gkind = nullptr;
+    int* d_glist = nullptr;      // active ghost cells: pool block << 12 | cell
+    int nglist = 0;
     void* d_pops[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t* d_flags[2] = {nullptr, nullptr};   // finest level only
@@ -738,7 +741,21 @@ struct AmrEngine {
     int substep[MAXL] = {0};
     int boundary_blocks = 1;
     long long coarse_steps = 0;
+    // one captured level-0 step per parity of the level-0 buffers; dropped
+    // whenever the layout or a kernel parameter changes
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    long long graph_launches = 0, graph_updates = 0;
+    double graph_tau = 0.0;
+    cudaStream_t capture_stream = nullptr;   // private stream used only for capturing
 };
+
+void amr_drop_graphs(AmrEngine* E) {
+    for (int p = 0; p < 2; ++p)
+        if (E->graph[p]) {
+            cudaGraphExecDestroy(E->graph[p]);
+            E->graph[p] = nullptr;
+        }
+}
 
 namespace {
 
@@ -903,6 +920,7 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_refined);
     handle_free(h, V.d_host);
     handle_free(h, V.d_gkind);
+    handle_free(h, V.d_glist);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
     handle_free(h, V.d_flags[0]);
@@ -928,6 +946,7 @@ void kappa_post(const Level& C, const Level& F, double* kp, double* km) {
 lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
     AmrEngine* E = h->amr;
     const int L = E->L;
+    amr_drop_graphs(E);
     std::vector<Level> old;
     old.swap(E->lv);
     E->lv.assign(L, Level());
@@ -996,6 +1015,8 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             }
     }
     level_rates(E, h->tau, h->magic);
+    for (int l = 0; l < L; ++l)   // kernels address a level pool with 32-bit element offsets
+        if ((long long)(E->lv[l].nreal + E->lv[l].nghost) * 19 * B3 >= (1LL << 31)) return LBMP_ERR_UNSUPPORTED;
     // device arrays
     const size_t es = esize(h);
     for (int l = 0; l < L; ++l) {
@@ -1031,8 +1052,26 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
     for (int l = 0; l + 1 < L; ++l) {
         Level& C = E->lv[l];
         Level& F = E->lv[l + 1];
-        if (C.nreal > 0) k_host_flags<<<C.nreal, 256, 0, h->stream>>>(view(E, C), C.d_host);
-        if (F.nghost > 0) k_ghost_kind<<<F.nghost, 256, 0, h->stream>>>(view(E, C), C.d_host, view(E, F), F.d_gkind);
+        if (C.nreal > 0) k_host_flags<<<(unsigned)C.nreal * 16, 256, 0, h->stream>>>(view(E, C), C.d_host);
+        if (F.nghost > 0) k_ghost_kind<<<(unsigned)F.nghost * 16, 256, 0, h->stream>>>(view(E, C), C.d_host, view(E, F), F.d_gkind);
+    }
+    // compact lists of the active ghost cells of every level
+    for (int l = 1; l < L; ++l) {
+        Level& F = E->lv[l];
+        if (F.nghost == 0) continue;
+        std::vector<uint8_t> kinds((size_t)F.nghost * B3);
+        if (cudaMemcpyAsync(kinds.data(), F.d_gkind, kinds.size(), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return LBMP_ERR_CUDA;
+        h->d2h += (long long)kinds.size();
+        std::vector<int> list;
+        for (int gb = 0; gb < F.nghost; ++gb)
+            for (int c = 0; c < B3; ++c)
+                if (kinds[(size_t)gb * B3 + c] == 1) list.push_back(((F.nreal + gb) << 12) | c);
+        F.nglist = (int)list.size();
+        F.d_glist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>(list.size(), 1));
+        if (!F.d_glist) return LBMP_ERR_OOM;
+        if (upload(h, F.d_glist, list.data(), sizeof(int) * list.size())) return LBMP_ERR_CUDA;
     }
     // populations from the old layout
     if (!old.empty()) {
@@ -1058,7 +1097,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
                 M.N = view(E, V);
                 M.dst = (S*)V.d_pops[V.cur];
                 M.l = l;
-                k_migrate<S><<<V.nreal, 256, 0, h->stream>>>(M);
+                k_migrate<S><<<(unsigned)V.nreal * 16, 256, 0, h->stream>>>(M);
             }
         });
     }
@@ -1068,10 +1107,10 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
     Level& Ff = E->lv[L - 1];
     if (h->has_particle || h->h_ps.present) {
         if (Ff.nreal > 0) {
-            k_amr_flags_full<<<Ff.nreal, 256, 0, h->stream>>>(view(E, Ff), Ff.d_flags[0], Ff.d_flags[1], h->d_ps);
+            k_amr_flags_full<<<(unsigned)Ff.nreal * 16, 256, 0, h->stream>>>(view(E, Ff), Ff.d_flags[0], Ff.d_flags[1], h->d_ps);
             with_storage_amr(h->cfg.precision, [&](auto tag) {
                 using S = std::remove_pointer_t<decltype(tag)>;
-                k_amr_zero_solid<S><<<Ff.nreal, 256, 0, h->stream>>>((S*)Ff.d_pops[Ff.cur], Ff.d_flags[0]);
+                k_amr_zero_solid<S><<<(unsigned)Ff.nreal * 16, 256, 0, h->stream>>>((S*)Ff.d_pops[Ff.cur], Ff.d_flags[0]);
             });
         }
         Ff.fcur = 0;
@@ -1131,7 +1170,7 @@ void enqueue_advance(lbmp_handle* h, int l) {
         double kp, km;
         kappa_post(V, F, &kp, &km);
         if (F.nghost > 0) {
-            k_explode<S><<<F.nghost, UPD_THREADS, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
+            k_explode<S><<<(unsigned)F.nghost * 16, UPD_THREADS, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
                                                                   (S*)F.d_pops[0], (S*)F.d_pops[1], (A)kp, (A)km,
                                                                   rescale, P.scale, P.inv_scale, h->status);
             h->launches += 1;
@@ -1178,13 +1217,19 @@ void enqueue_advance(lbmp_handle* h, int l) {
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) U.solid = V.d_flags[V.fcur];
     const long long ev0 = profile_mark(h);
-    if (np > 0) {
-        if (has_fine && has_coarse) k_update<S, true, true, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
-        else if (has_fine) k_update<S, true, false, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
-        else if (has_coarse && coupled) k_update<S, false, true, true><<<np, UPD_THREADS, 0, h->stream>>>(U);
-        else if (has_coarse) k_update<S, false, true, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
-        else if (coupled) k_update<S, false, false, true><<<np, UPD_THREADS, 0, h->stream>>>(U);
-        else k_update<S, false, false, false><<<np, UPD_THREADS, 0, h->stream>>>(U);
+    if (V.nreal > 0) {
+        const unsigned grid = (unsigned)V.nreal * 16;
+        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
+        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
+        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, h->stream>>>(U);
+        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
+        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, h->stream>>>(U);
+        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
+        h->launches += 1;
+    }
+    if (V.nglist > 0 && has_coarse) {
+        k_ghost_stream<S><<<(unsigned)((V.nglist + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, h->stream>>>(
+            U, V.d_glist, V.nglist);
         h->launches += 1;
     }
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
@@ -1192,7 +1237,7 @@ void enqueue_advance(lbmp_handle* h, int l) {
     if (coupled) {
         const LevelView D = view(E, V);
         const int nb = E->boundary_blocks;
-        k_amr_boundary<S><<<nb, BND_THREADS, 0, h->stream>>>(D, U.src, U.dst, U.solid, h->list, h->count, P, h->d_ps,
+        k_amr_boundary<S><<<nb, BNDW_THREADS, 0, h->stream>>>(D, U.src, U.dst, U.solid, h->list, h->count, P, h->d_ps,
                                                               h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials,
                                                               h->status);
         GridDesc G;
@@ -1220,6 +1265,12 @@ void enqueue_advance(lbmp_handle* h, int l) {
 }  // namespace
 
 // ================================================================== API
+lbmp_status amr_cuda_error(lbmp_handle* h, const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    h->err = std::string("refined step: ") + where + ": " + cudaGetErrorString(e);
+    return LBMP_ERR_CUDA;
+}
+
 lbmp_status amr_create(lbmp_handle* h) {
     AmrEngine* E = new (std::nothrow) AmrEngine();
     if (!E) return LBMP_ERR_OOM;
@@ -1234,6 +1285,8 @@ lbmp_status amr_create(lbmp_handle* h) {
 
 void amr_destroy(lbmp_handle* h) {
     if (!h->amr) return;
+    amr_drop_graphs(h->amr);
+    if (h->amr->capture_stream) cudaStreamDestroy(h->amr->capture_stream);
     for (auto& V : h->amr->lv) free_level(h, V);
     delete h->amr;
     h->amr = nullptr;
@@ -1256,7 +1309,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
     const double shell = 4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri);
     h->list_cap = (int)std::min<double>((double)B.cells, std::ceil(shell) + 64.0);
     h->list = (int*)handle_alloc(h, sizeof(int) * (size_t)h->list_cap);
-    E->boundary_blocks = (h->list_cap + BND_THREADS - 1) / BND_THREADS;
+    E->boundary_blocks = boundary_grid(h->list_cap);
     h->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)E->boundary_blocks);
     h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
     h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));
@@ -1300,7 +1353,7 @@ lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double
             Level& V = E->lv[l];
             if (V.nreal == 0) continue;
             const uint8_t* solid = (l == E->L - 1 && h->has_particle) ? V.d_flags[V.fcur] : nullptr;
-            k_amr_init<S><<<V.nreal, 256, 0, h->stream>>>(view(E, V), (S*)V.d_pops[V.cur], solid, rho, u[0], u[1], u[2],
+            k_amr_init<S><<<(unsigned)V.nreal * 16, 256, 0, h->stream>>>(view(E, V), (S*)V.d_pops[V.cur], solid, rho, u[0], u[1], u[2],
                                                            amp, dir, axis, (double)(1 << (E->L - 1 - l)), Lax, scale);
         }
     });
@@ -1311,17 +1364,66 @@ lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double
 lbmp_status amr_step(lbmp_handle* h, int n) {
     AmrEngine* E = h->amr;
     level_rates(E, h->tau, h->magic);
-    for (int i = 0; i < n; ++i) {
-        const long long ev_step = profile_mark(h);
+    if (E->graph_tau != h->tau) {
+        amr_drop_graphs(E);
+        E->graph_tau = h->tau;
+    }
+    auto enqueue = [&]() {
         with_storage_amr(h->cfg.precision, [&](auto tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
             E->substep[0] = 0;
             enqueue_advance<S>(h, 0);
         });
-        profile_step(h, ev_step, profile_mark(h));
+    };
+    for (int i = 0; i < n; ++i) {
+        if (h->profiling) {   // per-kernel events: plain launches
+            const long long ev_step = profile_mark(h);
+            enqueue();
+            profile_step(h, ev_step, profile_mark(h));
+        } else {
+            const int par = E->lv[0].cur;
+            if (!E->graph[par]) {
+                // capture one level-0 step on a private stream (the caller's
+                // stream may be the legacy default stream, which cannot be
+                // captured); enqueue() advances the host-side buffer indices
+                // exactly as the replayed graph will
+                if (!E->capture_stream &&
+                    cudaStreamCreateWithFlags(&E->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    return amr_cuda_error(h, "cudaStreamCreate");
+                const long long l0 = h->launches, u0 = h->updates;
+                cudaStream_t user = h->stream;
+                h->stream = E->capture_stream;
+                cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
+                if (e != cudaSuccess) {
+                    h->stream = user;
+                    return amr_cuda_error(h, "cudaStreamBeginCapture");
+                }
+                enqueue();
+                cudaGraph_t g = nullptr;
+                e = cudaStreamEndCapture(h->stream, &g);
+                h->stream = user;
+                if (e != cudaSuccess) return amr_cuda_error(h, "cudaStreamEndCapture");
+                cudaGraphExec_t ge = nullptr;
+                e = cudaGraphInstantiate(&ge, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return amr_cuda_error(h, "cudaGraphInstantiate");
+                E->graph[par] = ge;
+                E->graph_launches = h->launches - l0;
+                E->graph_updates = h->updates - u0;
+                if (cudaGraphLaunch(ge, h->stream) != cudaSuccess) return amr_cuda_error(h, "cudaGraphLaunch");
+            } else {
+                if (cudaGraphLaunch(E->graph[par], h->stream) != cudaSuccess)
+                    return amr_cuda_error(h, "cudaGraphLaunch");
+                // the same buffer flips as the captured enqueue
+                for (int l = 0; l < E->L; ++l)
+                    if ((1LL << l) & 1) E->lv[l].cur = 1 - E->lv[l].cur;
+                h->launches += E->graph_launches;
+                h->updates += E->graph_updates;
+            }
+        }
         E->coarse_steps += 1;
         h->steps += 1;
-        if (cudaGetLastError() != cudaSuccess) return LBMP_ERR_CUDA;
+        if (cudaGetLastError() != cudaSuccess) return amr_cuda_error(h, "kernel launch");
         if (h->cfg.regrid_interval > 0 && h->has_particle && E->coarse_steps % h->cfg.regrid_interval == 0) {
             const lbmp_status s = amr_regrid(h);
             if (s != LBMP_OK) return s;
@@ -1366,7 +1468,7 @@ lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, 
         using S = std::remove_pointer_t<decltype(tag)>;
         using A = typename Store<S>::A;
         const A inv = (A)(h->cfg.precision == LBMP_FP16 ? std::ldexp(1.0, -h->cfg.fp16_scale_log2) : 1.0);
-        k_amr_export<S><<<V.nreal, 256, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], dx, dg, inv);
+        k_amr_export<S><<<(unsigned)V.nreal * 16, 256, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], dx, dg, inv);
     });
     cudaError_t e = cudaMemcpyAsync(xyz, dx, sizeof(int32_t) * 3 * cells, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(g, dg, sizeof(double) * 19 * cells, cudaMemcpyDeviceToHost, h->stream);
@@ -1434,7 +1536,7 @@ int amr_launches_per_coarse_step(const lbmp_handle* h) {
     const AmrEngine* E = h->amr;
     int per = 0;
     for (int l = E->L - 1; l >= 0; --l) {
-        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nghost > 0) ? 1 : 0) +
+        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nghost > 0) ? 1 : 0) + (E->lv[l].nglist > 0 ? 1 : 0) +
                   ((l == E->L - 1 && h->has_particle) ? 7 : 0);
         per = own + 2 * per;
     }

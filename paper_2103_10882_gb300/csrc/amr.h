@@ -8,6 +8,7 @@
 
 namespace lbmp {
 
+lbmp_status amr_cuda_error(lbmp_handle* h, const char* where);   // records the CUDA error text in h->err
 lbmp_status amr_create(lbmp_handle* h);   // sets h->amr; starts unrefined (all level 0)
 void amr_destroy(lbmp_handle* h);
 lbmp_status amr_add_sphere(lbmp_handle* h);            // h->h_ps filled by the caller

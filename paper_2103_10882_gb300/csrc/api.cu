@@ -390,7 +390,7 @@ lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter
     const double shell = 4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri);
     h->list_cap = (int)std::min<double>((double)B.cells, std::ceil(shell) + 64.0);
     h->list = (int*)dev_alloc(h, sizeof(int) * (size_t)h->list_cap);
-    const int max_blocks = (h->list_cap + 127) / 128;
+    const int max_blocks = boundary_grid(h->list_cap);
     h->partials = (double*)dev_alloc(h, sizeof(double) * 6 * (size_t)max_blocks);
     h->link_mask = (uint8_t*)dev_alloc(h, (size_t)B.cells);
     h->link_blocks = (int*)dev_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));
@@ -604,7 +604,7 @@ lbmp_status lbmp_step_async(lbmp_handle* h, int n) {
     if (!h || n < 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_step: bad argument");
     if (h->amr) {
         const lbmp_status st = amr_step(h, n);
-        if (st != LBMP_OK) return fail(h, st, "lbmp_step: refined step failed");
+        if (st != LBMP_OK) return fail(h, st, "lbmp_step: " + h->err);
         return LBMP_OK;
     }
     for (int i = 0; i < n; ++i) enqueue_step(h);

@@ -37,6 +37,13 @@ struct BoxDesc {
     long long cells;
 };
 
+// Grid of the warp-per-cell boundary kernels (8 cells per block at a time,
+// grid-stride over the boundary list); also the number of force partials.
+inline int boundary_grid(int capacity) {
+    const int b = (capacity + 7) / 8;
+    return b < 1 ? 1 : (b > 608 ? 608 : b);
+}
+
 // Launchers (uniform.cu).  All are asynchronous on `stream`.
 template <typename S>
 void launch_bulk(const S* src, S* dst, const GridDesc& g, const CollideParams<typename Store<S>::A>& p,

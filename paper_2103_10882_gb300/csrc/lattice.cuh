@@ -76,6 +76,8 @@ struct ParticleState {
     int pad;
 };
 
+static_assert(sizeof(ParticleState) % sizeof(int) == 0, "particle record is copied as ints");
+
 // Status bits written by kernels (read by the host after a step).
 enum : int { STATUS_UNSTABLE_FLUID = 1, STATUS_PARTICLE_JUMP = 2, STATUS_LINK_OVERFLOW = 4 };
 

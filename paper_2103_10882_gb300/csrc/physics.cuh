@@ -89,3 +89,91 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
 }
 
 }  // namespace lbmp
+
+namespace lbmp {
+
+// Warp-cooperative TRT collision: lane q (< 19) holds population q of one
+// cell; lanes 19..31 hold 0 and take part in the shuffles.  Returns the
+// post-collision value of the lane's population (same arithmetic as
+// trt_collide, reduced across the warp).
+template <typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__device__ __forceinline__ int lane_c(int lane, int axis) {
+    // c_q components for q = lane < 19 (0 for idle lanes)
+    const int q = lane < 19 ? lane : 0;
+    switch (axis) {
+        case 0: return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+                     : ((q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0);
+        case 1: return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+                     : ((q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0);
+        default: return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+                      : ((q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0);
+    }
+}
+
+template <typename A, bool FORCED>
+__device__ __forceinline__ A warp_trt_collide(A gq, int lane, const CollideParams<A>& P, int* status) {
+    const int c0 = lane_c(lane, 0), c1 = lane_c(lane, 1), c2 = lane_c(lane, 2);
+    const A drho = warp_sum<A>(gq);
+    A ux = warp_sum<A>(A(c0) * gq), uy = warp_sum<A>(A(c1) * gq), uz = warp_sum<A>(A(c2) * gq);
+    if (FORCED) {
+        ux += A(0.5) * P.F[0];
+        uy += A(0.5) * P.F[1];
+        uz += A(0.5) * P.F[2];
+    }
+    const A uu = ux * ux + uy * uy + uz * uz;
+    if (lane == 0 && !(uu <= A(0.09))) atomicOr(status, STATUS_UNSTABLE_FLUID);
+    const int partner = lane == 0 ? 0 : (lane < 19 ? ((lane & 1) ? lane + 1 : lane - 1) : lane);
+    const A gb = __shfl_sync(0xffffffffu, gq, partner);
+    const A w = lane == 0 ? A(1) / A(3) : (lane <= 6 ? A(1) / A(18) : A(1) / A(36));
+    const A cu = A(c0) * ux + A(c1) * uy + A(c2) * uz;
+    const A ep = w * (drho + A(4.5) * cu * cu - A(1.5) * uu);
+    const A em = w * (A(3) * cu);
+    const A gp = A(0.5) * (gq + gb), gm = A(0.5) * (gq - gb);
+    A out = gq - P.sp * (gp - ep) - P.sm * (gm - em);
+    if (FORCED) {
+        const A cF = A(c0) * P.F[0] + A(c1) * P.F[1] + A(c2) * P.F[2];
+        const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
+        out += (A(1) - A(0.5) * P.sp) * w * (A(9) * cu * cF - A(3) * uF) + (A(1) - A(0.5) * P.sm) * w * (A(3) * cF);
+    }
+    return lane < 19 ? out : A(0);
+}
+
+// CLI link of Sec. 2.3 for the fluid cell at distance d from the sphere
+// centre, incoming direction q (k = opp(q) points into the solid):
+// returns the new deviation g_q and adds the link's momentum-exchange force
+// and torque (FP64, on full populations).
+template <typename A>
+__device__ __forceinline__ A cli_link(int q, const double d[3], double r, double delta, A gt_k, A gt_q, A gt_far,
+                                      const ParticleState& Pp, double F[3], double T[3]) {
+    const int k = opp(q);
+    const int ck[3] = {lane_c(k, 0), lane_c(k, 1), lane_c(k, 2)};
+    const double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
+    const double alpha = 4.0 / (1.0 + 2.0 * delta);
+    const double arm[3] = {d[0] + delta * ck[0], d[1] + delta * ck[1], d[2] + delta * ck[2]};
+    const double vb[3] = {Pp.u[0] + (Pp.w[1] * arm[2] - Pp.w[2] * arm[1]),
+                          Pp.u[1] + (Pp.w[2] * arm[0] - Pp.w[0] * arm[2]),
+                          Pp.u[2] + (Pp.w[0] * arm[1] - Pp.w[1] * arm[0])};
+    const double vc = vb[0] * ck[0] + vb[1] * ck[1] + vb[2] * ck[2];
+    const double wk = k == 0 ? 1.0 / 3.0 : (k <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    const A gnew = gt_k + A(kappa0) * gt_far - A(kappa0) * gt_q - A(alpha * 3.0 * wk * vc);
+    const double ftk = wk + (double)gt_k;
+    const double fnew = wk + (double)gnew;
+    const double Fl[3] = {(ck[0] + vb[0]) * fnew + (ck[0] - vb[0]) * ftk,
+                          (ck[1] + vb[1]) * fnew + (ck[1] - vb[1]) * ftk,
+                          (ck[2] + vb[2]) * fnew + (ck[2] - vb[2]) * ftk};
+    F[0] += Fl[0];
+    F[1] += Fl[1];
+    F[2] += Fl[2];
+    T[0] += arm[1] * Fl[2] - arm[2] * Fl[1];
+    T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
+    T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
+    return gnew;
+}
+
+}  // namespace lbmp

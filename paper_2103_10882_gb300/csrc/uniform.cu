@@ -14,7 +14,6 @@ namespace lbmp {
 namespace {
 
 constexpr int BULK_THREADS = 256;
-constexpr int BND_THREADS = 128;
 
 // Source coordinate x - c along one axis; -1 when it leaves through a wall.
 __device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
@@ -81,106 +80,83 @@ __global__ void __launch_bounds__(BULK_THREADS)
 }
 
 // -------------------------------------------------------------- boundary
-// One thread per fluid cell that has a solid neighbour.  Recomputes the
-// whole cell update, replacing pulls from solid cells by the CLI rule of
-// Sec. 2.3 and summing the link forces (Galilean-invariant form) in FP64.
-template <typename S>
-__global__ void __launch_bounds__(BND_THREADS)
+// One warp per fluid cell that has a solid neighbour, lane q handling
+// population q: pulls from solid cells are replaced by the CLI rule of
+// Sec. 2.3 (momentum-exchange force and torque summed in FP64), then the
+// warp collides the cell cooperatively and writes it.
+constexpr int BNDW_THREADS = 256;
+template <typename S, bool FORCED>
+__global__ void __launch_bounds__(BNDW_THREADS)
     k_boundary(const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ flags,
                const int* __restrict__ list, const int* __restrict__ count, GridDesc G,
                CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
                double* __restrict__ partials, int* __restrict__ status) {
     using A = typename Store<S>::A;
-    __shared__ double red[6][BND_THREADS / 32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double red[6][BNDW_THREADS / 32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = gridDim.x * (BNDW_THREADS / 32);
+    const int cnt = *count;
+    const size_t n = (size_t)G.n;
+    const ParticleState& Pp = *ps;
     double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
-    if (i < *count) {
-        const int cell = list[i];
-        const size_t n = (size_t)G.n;
-        const size_t nx = (size_t)G.nx, nxy = (size_t)G.nx * (size_t)G.ny;
-        const int x = cell % G.nx;
-        const int y = (cell / G.nx) % G.ny;
-        const int z = cell / (G.nx * G.ny);
-        const int xs[3] = {src_coord(x, -1, G.nx, G.periodic[0]), x, src_coord(x, 1, G.nx, G.periodic[0])};
-        const int ys[3] = {src_coord(y, -1, G.ny, G.periodic[1]), y, src_coord(y, 1, G.ny, G.periodic[1])};
-        const int zs[3] = {src_coord(z, -1, G.nz, G.periodic[2]), z, src_coord(z, 1, G.nz, G.periodic[2])};
-        const ParticleState& Pp = *ps;
-        const double d[3] = {wrap_diff((x + 0.5) - Pp.x[0], G.nx, G.periodic[0]),
-                             wrap_diff((y + 0.5) - Pp.x[1], G.ny, G.periodic[1]),
-                             wrap_diff((z + 0.5) - Pp.x[2], G.nz, G.periodic[2])};
-        A g[19];
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const int sx = xs[cx(q) + 1], sy = ys[cy(q) + 1], sz = zs[cz(q) + 1];
-            if (sx < 0 || sy < 0 || sz < 0) {
-                g[q] = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
-                continue;
+    for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
+        const int cell = list[w];
+        const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
+        A gq = A(0);
+        if (lane < 19) {
+            const int q = lane;
+            const int c[3] = {lane_c(q, 0), lane_c(q, 1), lane_c(q, 2)};
+            const int xyz[3] = {x, y, z};
+            const int n3[3] = {G.nx, G.ny, G.nz};
+            int s3[3], f3[3];
+            bool wall = false, far_ok = true;
+            for (int a = 0; a < 3; ++a) {
+                s3[a] = src_coord(xyz[a], c[a], n3[a], G.periodic[a]);    // x - c_q
+                f3[a] = src_coord(xyz[a], -c[a], n3[a], G.periodic[a]);   // x + c_q
+                wall |= s3[a] < 0;
+                far_ok &= f3[a] >= 0;
             }
-            const size_t s = (size_t)sx + nx * (size_t)sy + nxy * (size_t)sz;
-            if (q == 0 || flags[s] == 0) {
-                g[q] = Store<S>::load(src + (size_t)q * n + s, P.inv_scale);
-                continue;
+            if (wall) {
+                gq = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
+            } else {
+                const size_t sidx = (size_t)s3[0] + (size_t)G.nx * ((size_t)s3[1] + (size_t)G.ny * (size_t)s3[2]);
+                if (q == 0 || flags[sidx] == 0) {
+                    gq = Store<S>::load(src + (size_t)q * n + sidx, P.inv_scale);
+                } else {
+                    const int k = opp(q);
+                    size_t far = 0;
+                    if (far_ok) {
+                        far = (size_t)f3[0] + (size_t)G.nx * ((size_t)f3[1] + (size_t)G.ny * (size_t)f3[2]);
+                        far_ok = flags[far] == 0;
+                    }
+                    const double d[3] = {wrap_diff((x + 0.5) - Pp.x[0], G.nx, G.periodic[0]),
+                                         wrap_diff((y + 0.5) - Pp.x[1], G.ny, G.periodic[1]),
+                                         wrap_diff((z + 0.5) - Pp.x[2], G.nz, G.periodic[2])};
+                    const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+                    const A gt_k = Store<S>::load(src + (size_t)k * n + cell, P.inv_scale);
+                    const A gt_q = Store<S>::load(src + (size_t)q * n + cell, P.inv_scale);
+                    const A gt_far = far_ok ? Store<S>::load(src + (size_t)k * n + far, P.inv_scale) : A(0);
+                    gq = cli_link<A>(q, d, Pp.r, delta, gt_k, gt_q, gt_far, Pp, F, T);
+                }
             }
-            // Link: k = opp(q) points from x into the solid; the unknown is
-            // f_q(x, t+1).  The CLI needs the cell x - c_k = x + c_q.
-            const int k = opp(q);
-            const int fx = xs[cx(k) + 1], fy = ys[cy(k) + 1], fz = zs[cz(k) + 1];
-            bool far_ok = fx >= 0 && fy >= 0 && fz >= 0;
-            size_t far = 0;
-            if (far_ok) {
-                far = (size_t)fx + nx * (size_t)fy + nxy * (size_t)fz;
-                far_ok = flags[far] == 0;
-            }
-            double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
-            const double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
-            const double alpha = 4.0 / (1.0 + 2.0 * delta);
-            const double arm[3] = {d[0] + delta * cx(k), d[1] + delta * cy(k), d[2] + delta * cz(k)};
-            const double vb[3] = {Pp.u[0] + (Pp.w[1] * arm[2] - Pp.w[2] * arm[1]),
-                                  Pp.u[1] + (Pp.w[2] * arm[0] - Pp.w[0] * arm[2]),
-                                  Pp.u[2] + (Pp.w[0] * arm[1] - Pp.w[1] * arm[0])};
-            const double vc = vb[0] * cx(k) + vb[1] * cy(k) + vb[2] * cz(k);
-            const A gt_k = Store<S>::load(src + (size_t)k * n + cell, P.inv_scale);
-            const A gt_q = Store<S>::load(src + (size_t)q * n + cell, P.inv_scale);
-            const A gt_far = far_ok ? Store<S>::load(src + (size_t)k * n + far, P.inv_scale) : A(0);
-            // CLI on deviations (the w_q parts cancel since w_q = w_qbar):
-            // g_q = gt_k + kappa0 gt_k(x - c_k) - kappa0 gt_q - alpha w_k / c_s^2 (v . c_k)
-            const A gnew = gt_k + A(kappa0) * gt_far - A(kappa0) * gt_q -
-                           A(alpha * 3.0 * wgt<double>(k) * vc);
-            g[q] = gnew;
-            // link force on full populations, FP64: (c_k - v) ft_k - (c_q - v) f_q(t+1)
-            const double ftk = wgt<double>(k) + (double)gt_k;
-            const double fnew = wgt<double>(q) + (double)gnew;
-            const double Fl[3] = {(cx(k) - vb[0]) * ftk - (cx(q) - vb[0]) * fnew,
-                                  (cy(k) - vb[1]) * ftk - (cy(q) - vb[1]) * fnew,
-                                  (cz(k) - vb[2]) * ftk - (cz(q) - vb[2]) * fnew};
-            F[0] += Fl[0];
-            F[1] += Fl[1];
-            F[2] += Fl[2];
-            T[0] += arm[1] * Fl[2] - arm[2] * Fl[1];
-            T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
-            T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
         }
-        if (P.forced) trt_collide<A, true>(g, P, status);
-        else trt_collide<A, false>(g, P, status);
-#pragma unroll
-        for (int q = 0; q < 19; ++q) Store<S>::store(dst + (size_t)q * n + cell, g[q], P.scale);
+        gq = warp_trt_collide<A, FORCED>(gq, lane, P, status);
+        if (lane < 19) Store<S>::store(dst + (size_t)lane * n + cell, gq, P.scale);
     }
-    // deterministic block reduction of the six sums
+    // deterministic reduction: warp tree, then warps in order
     double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int k = 0; k < 6; ++k)
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
     if (lane == 0)
 #pragma unroll
-        for (int c = 0; c < 6; ++c) red[c][warp] = v[c];
+        for (int k = 0; k < 6; ++k) red[k][wib] = v[k];
     __syncthreads();
     if (threadIdx.x < 6) {
-        double s = 0.0;
-        for (int w = 0; w < BND_THREADS / 32; ++w) s += red[threadIdx.x][w];
-        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = s;
+        double sum = 0.0;
+        for (int k = 0; k < BNDW_THREADS / 32; ++k) sum += red[threadIdx.x][k];
+        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = sum;
     }
 }
 
@@ -190,6 +166,9 @@ __global__ void __launch_bounds__(BND_THREADS)
 // virtual force/torque from the previous accelerations, and Velocity
 // Verlet (kick-drift-kick) with m = (rho_p + C_v) V, I = 2/5 (rho_p + C_vw) V r^2.
 constexpr int PART_THREADS = 256;
+__device__ void particle_advance(ParticleState& P, const double (*red)[PART_THREADS], const GridDesc& G,
+                                 double* __restrict__ history, int hist_cap, int* __restrict__ status);
+
 __global__ void __launch_bounds__(PART_THREADS)
     k_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials, int nblocks, GridDesc G,
                double* __restrict__ history, int hist_cap, int* __restrict__ status) {
@@ -207,13 +186,35 @@ __global__ void __launch_bounds__(PART_THREADS)
             for (int c = 0; c < 6; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x != 0) return;
-    ParticleState& P = *ps;
+    // stage the particle record in shared memory (one coalesced read and write
+    // instead of dependent global accesses by a single thread)
+    __shared__ ParticleState sP;
+    {
+        const int words = (int)(sizeof(ParticleState) / sizeof(int));
+        const int* srcw = reinterpret_cast<const int*>(ps);
+        int* dstw = reinterpret_cast<int*>(&sP);
+        for (int i = threadIdx.x; i < words; i += PART_THREADS) dstw[i] = srcw[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) particle_advance(sP, red, G, history, hist_cap, status);
+    __syncthreads();
+    {
+        const int words = (int)(sizeof(ParticleState) / sizeof(int));
+        const int* srcw = reinterpret_cast<const int*>(&sP);
+        int* dstw = reinterpret_cast<int*>(ps);
+        for (int i = threadIdx.x; i < words; i += PART_THREADS) dstw[i] = srcw[i];
+    }
+}
+
+// Algorithm 1 after the LBM step, on the staged particle record.
+__device__ void particle_advance(ParticleState& P, const double (*red)[PART_THREADS], const GridDesc& G,
+                                 double* __restrict__ history, int hist_cap, int* __restrict__ status) {
     const double Fh[3] = {red[0][0], red[1][0], red[2][0]};
     const double Th[3] = {red[3][0], red[4][0], red[5][0]};
     const double V = P.V, r = P.r;
     const double m = (P.rho_p + P.cv) * V;
     const double I = 0.4 * (P.rho_p + P.cvw) * V * r * r;
+    const double inv_m = 1.0 / m, inv_I = 1.0 / I;
     const bool avg = P.force_average && P.steps > 0;
     double xold[3];
     for (int a = 0; a < 3; ++a) {
@@ -230,19 +231,20 @@ __global__ void __launch_bounds__(PART_THREADS)
         const double Tp = Tbar + Tv;
         P.Fp[a] = Fp;
         xold[a] = P.x[a];
+        const double acc = Fp * inv_m, bet = Tp * inv_I;
         if (!P.fixed) {
-            if (P.steps > 0) {
-                P.u[a] += Fp / (2.0 * m);
-                P.w[a] += Tp / (2.0 * I);
+            if (P.steps > 0) {   // second half kick of the previous step completes u(t)
+                P.u[a] += 0.5 * acc;
+                P.w[a] += 0.5 * bet;
             }
-            P.a[a] = Fp / m;
-            P.b[a] = Tp / I;
-            P.u[a] += Fp / (2.0 * m);
-            P.w[a] += Tp / (2.0 * I);
+            P.a[a] = acc;
+            P.b[a] = bet;
+            P.u[a] += 0.5 * acc;   // first half kick, then drift with u(t + 1/2)
+            P.w[a] += 0.5 * bet;
             P.x[a] += P.u[a];
         } else {
-            P.a[a] = Fp / m;
-            P.b[a] = Tp / I;
+            P.a[a] = acc;
+            P.b[a] = bet;
         }
     }
     const int n3[3] = {G.nx, G.ny, G.nz};
@@ -573,9 +575,12 @@ template <typename S>
 void launch_boundary(const S* src, S* dst, const uint8_t* flags, const int* list, const int* count, int max_cells,
                      const GridDesc& g, const CollideParams<typename Store<S>::A>& p, const ParticleState* ps,
                      int cli, double* partials, int* nblocks_out, int* status, cudaStream_t stream) {
-    const int nb = max_cells > 0 ? (int)blocks_for(max_cells, BND_THREADS) : 1;
+    const int nb = boundary_grid(max_cells);
     *nblocks_out = nb;
-    k_boundary<S><<<nb, BND_THREADS, 0, stream>>>(src, dst, flags, list, count, g, p, ps, cli, partials, status);
+    if (p.forced)
+        k_boundary<S, true><<<nb, BNDW_THREADS, 0, stream>>>(src, dst, flags, list, count, g, p, ps, cli, partials, status);
+    else
+        k_boundary<S, false><<<nb, BNDW_THREADS, 0, stream>>>(src, dst, flags, list, count, g, p, ps, cli, partials, status);
 }
 
 void launch_particle_update(ParticleState* ps, const double* partials, int nblocks, const GridDesc& g,
