@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uniform", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -346,6 +348,32 @@ def main():
                                  if e == 512 else None),
             "roofline_mlups": measured_peak()[0] * 1e9 / (38 * bpp) / 1e6,
             "clocks": clk_u.summary(),
+        }
+    # --------------------------------------------- batched parameter sweep
+    if not args.no_batch:
+        sims = []
+        for d in workloads.batch_sweep(0, 64):
+            e = d["edge"]
+            tau_b, gm_b = ga_tau_g(d["ga"], 0.01, d["diameter"], d["density_ratio"])
+            sims.append(dict(edge=e, pos=e / 2 + d["offset"], diameter=d["diameter"],
+                             density_ratio=d["density_ratio"], cv=0.5, tau=tau_b, gravity=(0.0, 0.0, -gm_b)))
+        bs = L.BatchSimulation(sims, precision=prec)
+        bs.autotune(5)
+        info = bs.info()
+        bs.step(4)
+        with ClockSampler(local) as clk_b:
+            bms, _, b0, b1 = timed(bs, args.batch_steps, bs.stream, torch, profile=False)
+            _, bprof, _, _ = timed(bs, 4, bs.stream, torch, profile=True)
+        bs.close()
+        line["batch64"] = {
+            "workload": "64 independent periodic boxes, edges from {32,48,64,96}, d = edge/6, pi_p in [0.1,0.9], "
+                        "Ga in [100,400], C_v=0.5, seed 0, %s" % prec,
+            "value": (b1[1] - b0[1]) / (bms * 1e-3) / 1e6, "unit": "MLUPS", "cells": int(info[1]),
+            "ms_per_step": bms / args.batch_steps, "launches_per_step": (b1[2] - b0[2]) / args.batch_steps,
+            "autotuner": {"threads_per_tile": int(info[2]), "z_cells_per_thread": int(info[3]),
+                          "candidate_us": [v / 1e3 for v in info[4:8]]},
+            "roofline": roofline(bprof, "k_batch_bulk (%s)" % prec, None),
+            "clocks": clk_b.summary(),
         }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

@@ -188,6 +188,38 @@ lbmp_status lbmp_get_level_cells(lbmp_handle* h, int level, int32_t* xyz, double
 /* Cell updates and kernel launches of one (level-0) step. */
 lbmp_status lbmp_updates_per_step(lbmp_handle* h, int64_t* updates, int32_t* launches);
 
+/* ------------------------------------------------------------------------
+ * Batched sweep: n independent uniform periodic simulations of different
+ * sizes (the (density ratio, Ga) parameter study of Sec. 5 run as one job).
+ * Each simulation is a cubic box of `edge` cells (a multiple of 16) with
+ * one sphere; relaxation time and gravity are per simulation (set them from
+ * Ga with lbmp_ga_parameters).  cfg supplies precision, magic parameter,
+ * boundary scheme, force averaging, history capacity, stream and allocator;
+ * its grid fields are ignored.  The fluid starts at rest.  lbmp_step
+ * advances every simulation; lbmp_get_particle / lbmp_get_history take the
+ * simulation index as id.  Every phase of a step is one launch for all
+ * simulations; two steps are replayed from a CUDA graph.
+ */
+typedef struct {
+    int edge;                 /* cells per side (multiple of 16, >= 16) */
+    double pos[3];            /* sphere centre */
+    double diameter;
+    double density_ratio;
+    double cv, cv_omega;      /* virtual-mass coefficients (Sec. 3.3) */
+    double tau;               /* relaxation time of this simulation */
+    double gravity[3];
+} lbmp_batch_sim;
+
+lbmp_status lbmp_batch_create(const lbmp_config* cfg, const lbmp_batch_sim* sims, int n, lbmp_handle** out);
+/* Times the candidate stream-collide tile shapes on the batch (reps launches
+ * each, without advancing the simulations) and keeps the fastest. */
+lbmp_status lbmp_batch_autotune(lbmp_handle* h, int reps);
+/* [0] simulations, [1] cells, [2] threads per tile, [3] cells per thread
+ * along z, [4..7] measured ns per launch of the four candidate shapes. */
+lbmp_status lbmp_batch_info(lbmp_handle* h, int64_t out[8]);
+/* FP64 deviations [19][edge^3] of one simulation (host memory). */
+lbmp_status lbmp_batch_get_populations(lbmp_handle* h, int sim, double* out, size_t cap);
+
 /* Counters: [0] steps, [1] cell updates (MLUPS numerator), [2] kernel
  * launches, [3] host-to-device bytes, [4] device-to-host bytes copied by
  * the library since the handle was created. */

@@ -22,7 +22,8 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
            "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error",
            "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_level_shape", "lbmp_get_block_map",
-           "lbmp_get_level_cells", "lbmp_updates_per_step", "PRECISIONS"]
+           "lbmp_get_level_cells", "lbmp_updates_per_step", "lbmp_batch_create", "lbmp_batch_autotune",
+           "lbmp_batch_info", "lbmp_batch_get_populations", "BatchSimulation", "PRECISIONS"]
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
 BC = {"periodic": 0, "noslip": 1}
@@ -275,6 +276,39 @@ def lbmp_updates_per_step(h):
     return u.value, l.value
 
 
+def lbmp_batch_create(cfg, sims):
+    """sims: sequence of dicts with edge, pos, diameter, density_ratio, cv, cv_omega, tau, gravity."""
+    arr = (_native.LbmpBatchSim * len(sims))()
+    for i, d in enumerate(sims):
+        arr[i].edge = int(d["edge"])
+        arr[i].pos = (ctypes.c_double * 3)(*[float(v) for v in d["pos"]])
+        arr[i].diameter = float(d["diameter"])
+        arr[i].density_ratio = float(d["density_ratio"])
+        arr[i].cv = float(d.get("cv", 0.0))
+        arr[i].cv_omega = float(d.get("cv_omega", d.get("cv", 0.0)))
+        arr[i].tau = float(d["tau"])
+        arr[i].gravity = (ctypes.c_double * 3)(*[float(v) for v in d.get("gravity", (0.0, 0.0, 0.0))])
+    h = ctypes.c_void_p()
+    _check(None, _lib().lbmp_batch_create(ctypes.byref(cfg), arr, len(sims), ctypes.byref(h)))
+    return h
+
+
+def lbmp_batch_autotune(h, reps=5):
+    _check(h, _lib().lbmp_batch_autotune(h, int(reps)))
+
+
+def lbmp_batch_info(h):
+    out = (ctypes.c_int64 * 8)()
+    _check(h, _lib().lbmp_batch_info(h, out))
+    return tuple(out)
+
+
+def lbmp_batch_get_populations(h, sim, edge):
+    out = np.empty(19 * int(edge) ** 3, dtype=np.float64)
+    _check(h, _lib().lbmp_batch_get_populations(h, int(sim), _dp(out), out.size))
+    return out.reshape(19, -1)
+
+
 def lbmp_last_error(h=None):
     m = _lib().lbmp_last_error(h)
     return m.decode() if m else ""
@@ -440,4 +474,73 @@ class Simulation:
 
     def profile_result(self):
         """(stream-collide ms, its launches, step ms, steps, algorithmic bytes, cell updates)."""
+        return lbmp_get_profile(self.h)
+
+
+class BatchSimulation:
+    """Many independent uniform periodic simulations advanced together."""
+
+    def __init__(self, sims, precision="fp32", magic=3.0 / 16.0, boundary="cli", force_average=True,
+                 history_capacity=4096, stream=None, torch_allocator=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise LbmpError(3, "no CUDA device: this library has no CPU path")
+        cfg = lbmp_config_default()
+        cfg.precision = PRECISIONS[precision]
+        cfg.magic = float(magic)
+        cfg.boundary = BOUNDARY[boundary]
+        cfg.force_average = int(bool(force_average))
+        cfg.history_capacity = int(history_capacity)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        cfg.cuda_stream = ctypes.c_void_p(self.stream.cuda_stream)
+        self._allocator = None
+        if torch_allocator:
+            self._allocator = _TorchAllocator(torch.cuda.current_device(), self.stream)
+            cfg.alloc = self._allocator.alloc
+            cfg.free = self._allocator.free
+        self.sims = [dict(d) for d in sims]
+        self.h = lbmp_batch_create(cfg, self.sims)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbmp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        lbmp_step(self.h, n)
+
+    def step_async(self, n=1):
+        lbmp_step_async(self.h, n)
+
+    def check(self):
+        lbmp_check_status(self.h)
+
+    def autotune(self, reps=5):
+        lbmp_batch_autotune(self.h, reps)
+
+    def info(self):
+        return lbmp_batch_info(self.h)
+
+    def particle(self, i):
+        return lbmp_get_particle(self.h, i)
+
+    def history(self, i, max_steps=None):
+        return lbmp_get_history(self.h, i, max_steps)
+
+    def populations(self, i):
+        return lbmp_batch_get_populations(self.h, i, self.sims[i]["edge"])
+
+    def counters(self):
+        return lbmp_get_counters(self.h)
+
+    def profile(self, enable=True):
+        lbmp_profile(self.h, enable)
+
+    def profile_result(self):
         return lbmp_get_profile(self.h)

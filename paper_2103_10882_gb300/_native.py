@@ -31,6 +31,19 @@ class LbmpConfig(ctypes.Structure):
     ]
 
 
+class LbmpBatchSim(ctypes.Structure):
+    _fields_ = [
+        ("edge", ctypes.c_int),
+        ("pos", ctypes.c_double * 3),
+        ("diameter", ctypes.c_double),
+        ("density_ratio", ctypes.c_double),
+        ("cv", ctypes.c_double),
+        ("cv_omega", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3),
+    ]
+
+
 # name -> (restype, argtypes); every entry point declared in include/lbmp.h
 SIGNATURES = {
     "lbmp_config_default": (ctypes.c_int, [ctypes.POINTER(LbmpConfig)]),
@@ -80,6 +93,11 @@ SIGNATURES = {
                                             c_double_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "lbmp_updates_per_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int32)]),
+    "lbmp_batch_create": (ctypes.c_int, [ctypes.POINTER(LbmpConfig), ctypes.POINTER(LbmpBatchSim), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]),
+    "lbmp_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "lbmp_batch_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "lbmp_batch_get_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, ctypes.c_size_t]),
     "lbmp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
 }
 

@@ -13,6 +13,7 @@
 
 #include "internal.h"
 #include "amr.h"
+#include "batch.h"
 
 using namespace lbmp;
 
@@ -335,6 +336,7 @@ lbmp_status lbmp_destroy(lbmp_handle* h) {
     if (!h) return LBMP_OK;
     cudaStreamSynchronize(h->stream);
     amr_destroy(h);
+    batch_destroy(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     while (!h->allocations.empty()) dev_free(h, h->allocations.back().first);
@@ -607,6 +609,12 @@ lbmp_status lbmp_step_async(lbmp_handle* h, int n) {
         if (st != LBMP_OK) return fail(h, st, "lbmp_step: " + h->err);
         return LBMP_OK;
     }
+    if (h->batch) {
+        const lbmp_status st = batch_step(h, n);
+        if (st != LBMP_OK) return fail(h, st, std::string("lbmp_step: batched step failed: ") +
+                                              cudaGetErrorString(cudaGetLastError()));
+        return LBMP_OK;
+    }
     for (int i = 0; i < n; ++i) enqueue_step(h);
     LBMP_CK(h, cudaGetLastError());
     return LBMP_OK;
@@ -631,10 +639,16 @@ lbmp_status lbmp_synchronize(lbmp_handle* h) {
 
 lbmp_status lbmp_get_particle(lbmp_handle* h, int id, double out[24]) {
     if (!h || !out) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: NULL argument");
-    if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: no such sphere");
-    lbmp_status s = download_particle(h);
-    if (s != LBMP_OK) return s;
-    const ParticleState& P = h->h_ps;
+    ParticleState tmp;
+    if (h->batch) {
+        if (batch_get_particle(h, id, &tmp) != LBMP_OK) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: no such simulation");
+    } else {
+        if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: no such sphere");
+        lbmp_status s = download_particle(h);
+        if (s != LBMP_OK) return s;
+        tmp = h->h_ps;
+    }
+    const ParticleState& P = tmp;
     for (int a = 0; a < 3; ++a) {
         out[a] = P.Fh[a];
         out[3 + a] = P.Th[a];
@@ -650,18 +664,28 @@ lbmp_status lbmp_get_particle(lbmp_handle* h, int id, double out[24]) {
 
 lbmp_status lbmp_get_history(lbmp_handle* h, int id, double* out, int max_steps, int* n) {
     if (!h) return LBMP_ERR_INVALID_ARG;
-    if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_history: no such sphere");
-    lbmp_status s = download_particle(h);
-    if (s != LBMP_OK) return s;
-    const long long steps = h->h_ps.steps;
+    ParticleState tmp;
+    if (h->batch) {
+        if (batch_get_particle(h, id, &tmp) != LBMP_OK) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_history: no such simulation");
+    } else {
+        if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_history: no such sphere");
+        lbmp_status s = download_particle(h);
+        if (s != LBMP_OK) return s;
+        tmp = h->h_ps;
+    }
+    const long long steps = tmp.steps;
     const int cap = h->cfg.history_capacity;
     const long long avail = std::min<long long>(steps, cap);
     if (n) *n = (int)avail;
     if (!out || max_steps <= 0 || avail == 0) return LBMP_OK;
     std::vector<double> ring((size_t)cap * 15);
-    LBMP_CK(h, cudaMemcpyAsync(ring.data(), h->history, sizeof(double) * 15 * (size_t)cap, cudaMemcpyDeviceToHost,
-                               h->stream));
-    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    if (h->batch) {
+        if (batch_history(h, id, ring.data(), cap) != LBMP_OK) return fail(h, LBMP_ERR_CUDA, "lbmp_get_history: copy failed");
+    } else {
+        LBMP_CK(h, cudaMemcpyAsync(ring.data(), h->history, sizeof(double) * 15 * (size_t)cap, cudaMemcpyDeviceToHost,
+                                   h->stream));
+        LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    }
     const long long m = std::min<long long>(avail, max_steps);
     const long long first = steps - m;   // oldest step returned
     for (long long i = 0; i < m; ++i) {
@@ -848,6 +872,57 @@ lbmp_status lbmp_updates_per_step(lbmp_handle* h, int64_t* updates, int32_t* lau
         if (launches) *launches = h->has_particle ? 7 : 1;
     }
     return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_create(const lbmp_config* cfg, const lbmp_batch_sim* sims, int n, lbmp_handle** out) {
+    if (!cfg || !sims || !out || n < 1) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_batch_create: bad argument");
+    *out = nullptr;
+    long long cells = 0;
+    for (int s = 0; s < n; ++s) {
+        const lbmp_batch_sim& b = sims[s];
+        if (b.edge < 16 || b.edge % 16 || b.edge > 1024)
+            return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_batch_create: edges must be multiples of 16 in [16, 1024]");
+        if (!(b.tau > 0.5) || !(b.diameter > 0.0) || !(b.density_ratio > 0.0) || b.cv < 0 || b.cv_omega < 0 ||
+            b.diameter + 4.0 > b.edge)
+            return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_batch_create: invalid simulation parameters");
+        for (int a = 0; a < 3; ++a)
+            if (!(b.pos[a] >= 0.0 && b.pos[a] <= (double)b.edge))
+                return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_batch_create: centre outside its box");
+        cells += (long long)b.edge * b.edge * b.edge;
+    }
+    if (cells >= (1LL << 31)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_batch_create: more than 2^31 - 1 cells");
+    lbmp_config c = *cfg;
+    c.nx = c.ny = c.nz = 16;
+    c.levels = 1;
+    c.bc[0] = c.bc[1] = c.bc[2] = LBMP_PERIODIC;
+    lbmp_handle* h = nullptr;
+    lbmp_status st = lbmp_create(&c, &h);
+    if (st != LBMP_OK) return st;
+    st = batch_create(h, sims, n);
+    if (st != LBMP_OK) {
+        lbmp_destroy(h);
+        return fail(nullptr, st, "lbmp_batch_create: setting up the batch failed");
+    }
+    *out = h;
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_autotune(lbmp_handle* h, int reps) {
+    if (!h || !h->batch || reps < 1) return LBMP_ERR_INVALID_ARG;
+    const lbmp_status st = batch_autotune(h, reps);
+    return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_batch_autotune: failed");
+}
+
+lbmp_status lbmp_batch_info(lbmp_handle* h, int64_t out[8]) {
+    if (!h || !h->batch || !out) return LBMP_ERR_INVALID_ARG;
+    batch_info(h, out);
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_batch_get_populations(lbmp_handle* h, int sim, double* out, size_t cap) {
+    if (!h || !h->batch || !out) return LBMP_ERR_INVALID_ARG;
+    const lbmp_status st = batch_populations(h, sim, out, cap);
+    return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_batch_get_populations: bad simulation index or capacity");
 }
 
 const char* lbmp_last_error(const lbmp_handle* h) {

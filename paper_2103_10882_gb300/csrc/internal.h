@@ -84,6 +84,7 @@ template <typename S>
 void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStream_t stream);
 
 struct AmrEngine;
+struct BatchEngine;
 
 // Profiling events on the handle's stream (api.cu); -1 when profiling is off.
 long long profile_mark(lbmp_handle* h);
@@ -131,5 +132,6 @@ struct lbmp_handle {
     std::vector<std::pair<void*, size_t>> allocations;
     std::string err;
     lbmp::AmrEngine* amr = nullptr;     // refined hierarchy (levels > 1), else null
+    lbmp::BatchEngine* batch = nullptr; // batched sweep, else null
 };
 

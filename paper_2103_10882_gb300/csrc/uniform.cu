@@ -15,24 +15,6 @@ namespace {
 
 constexpr int BULK_THREADS = 256;
 
-// Source coordinate x - c along one axis; -1 when it leaves through a wall.
-__device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
-    int s = x - c;
-    if (s < 0) return periodic ? s + n : -1;
-    if (s >= n) return periodic ? s - n : -1;
-    return s;
-}
-
-// Cell centre inside the closed ball.  Explicit round-to-nearest products and
-// sums (no contraction) so the predicate is evaluated exactly as written.
-__device__ __forceinline__ bool inside_ball(int i, int j, int k, const GridDesc& G, const ParticleState& P) {
-    double dx = wrap_diff(__dsub_rn((double)i + 0.5, P.x[0]), G.nx, G.periodic[0]);
-    double dy = wrap_diff(__dsub_rn((double)j + 0.5, P.x[1]), G.ny, G.periodic[1]);
-    double dz = wrap_diff(__dsub_rn((double)k + 0.5, P.x[2]), G.nz, G.periodic[2]);
-    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return d2 <= __dmul_rn(P.r, P.r);
-}
-
 // ------------------------------------------------------------------ bulk
 // One thread per cell, pull form: g_q(x, t+1) = g~_q(x - c_q, t), then TRT.
 // WALLS: some axis has no-slip walls (bounce-back at the domain edge);
@@ -166,8 +148,6 @@ __global__ void __launch_bounds__(BNDW_THREADS)
 // virtual force/torque from the previous accelerations, and Velocity
 // Verlet (kick-drift-kick) with m = (rho_p + C_v) V, I = 2/5 (rho_p + C_vw) V r^2.
 constexpr int PART_THREADS = 256;
-__device__ void particle_advance(ParticleState& P, const double (*red)[PART_THREADS], const GridDesc& G,
-                                 double* __restrict__ history, int hist_cap, int* __restrict__ status);
 
 __global__ void __launch_bounds__(PART_THREADS)
     k_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials, int nblocks, GridDesc G,
@@ -196,7 +176,10 @@ __global__ void __launch_bounds__(PART_THREADS)
         for (int i = threadIdx.x; i < words; i += PART_THREADS) dstw[i] = srcw[i];
     }
     __syncthreads();
-    if (threadIdx.x == 0) particle_advance(sP, red, G, history, hist_cap, status);
+    if (threadIdx.x == 0) {
+        const double FT[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
+        particle_advance(sP, FT, G, history, hist_cap, status);
+    }
     __syncthreads();
     {
         const int words = (int)(sizeof(ParticleState) / sizeof(int));
@@ -206,98 +189,7 @@ __global__ void __launch_bounds__(PART_THREADS)
     }
 }
 
-// Algorithm 1 after the LBM step, on the staged particle record.
-__device__ void particle_advance(ParticleState& P, const double (*red)[PART_THREADS], const GridDesc& G,
-                                 double* __restrict__ history, int hist_cap, int* __restrict__ status) {
-    const double Fh[3] = {red[0][0], red[1][0], red[2][0]};
-    const double Th[3] = {red[3][0], red[4][0], red[5][0]};
-    const double V = P.V, r = P.r;
-    const double m = (P.rho_p + P.cv) * V;
-    const double I = 0.4 * (P.rho_p + P.cvw) * V * r * r;
-    const double inv_m = 1.0 / m, inv_I = 1.0 / I;
-    const bool avg = P.force_average && P.steps > 0;
-    double xold[3];
-    for (int a = 0; a < 3; ++a) {
-        const double Fbar = avg ? 0.5 * (Fh[a] + P.Fh_old[a]) : Fh[a];
-        const double Tbar = avg ? 0.5 * (Th[a] + P.Th_old[a]) : Th[a];
-        P.Fh[a] = Fh[a];
-        P.Th[a] = Th[a];
-        P.Fh_old[a] = Fh[a];
-        P.Th_old[a] = Th[a];
-        const double Fg = (P.rho_p - 1.0) * P.g[a] * V;
-        const double Fv = P.cv * V * P.a[a];
-        const double Tv = 0.4 * P.cvw * V * r * r * P.b[a];
-        const double Fp = Fbar + Fg + Fv;
-        const double Tp = Tbar + Tv;
-        P.Fp[a] = Fp;
-        xold[a] = P.x[a];
-        const double acc = Fp * inv_m, bet = Tp * inv_I;
-        if (!P.fixed) {
-            if (P.steps > 0) {   // second half kick of the previous step completes u(t)
-                P.u[a] += 0.5 * acc;
-                P.w[a] += 0.5 * bet;
-            }
-            P.a[a] = acc;
-            P.b[a] = bet;
-            P.u[a] += 0.5 * acc;   // first half kick, then drift with u(t + 1/2)
-            P.w[a] += 0.5 * bet;
-            P.x[a] += P.u[a];
-        } else {
-            P.a[a] = acc;
-            P.b[a] = bet;
-        }
-    }
-    const int n3[3] = {G.nx, G.ny, G.nz};
-    for (int a = 0; a < 3; ++a) {
-        if (fabs(P.x[a] - xold[a]) > 0.5 || !(fabs(P.u[a]) < 0.5)) atomicOr(status, STATUS_PARTICLE_JUMP);
-        if (G.periodic[a]) {   // keep the centre inside the periodic box
-            const double L = (double)n3[a];
-            if (P.x[a] >= L) P.x[a] -= L;
-            else if (P.x[a] < 0.0) P.x[a] += L;
-        }
-    }
-    if (hist_cap > 0) {
-        double* h = history + (size_t)(P.steps % hist_cap) * 15;
-        for (int a = 0; a < 3; ++a) {
-            h[a] = Fh[a];
-            h[3 + a] = Th[a];
-            h[6 + a] = P.x[a];
-            h[9 + a] = P.u[a];
-            h[12 + a] = P.w[a];
-        }
-    }
-    P.steps += 1;
-}
-
 // ------------------------------------------------------------------ remap
-// Box of cells around the sphere: cell (o + t) for t in [0, E), o from the
-// current centre.  Returns false for cells outside a walled domain.
-__device__ __forceinline__ bool box_cell(int t, const GridDesc& G, const BoxDesc& B, const ParticleState& P,
-                                         int* ci, int* cj, int* ck) {
-    const int e0 = B.E[0], e1 = B.E[1];
-    const int tk = t / (e0 * e1);
-    const int r = t - tk * e0 * e1;
-    const int tj = r / e0;
-    const int ti = r - tj * e0;
-    const int n3[3] = {G.nx, G.ny, G.nz};
-    const int tt[3] = {ti, tj, tk};
-    int c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int o = (B.E[a] >= n3[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
-        int v = o + tt[a];
-        if (v < 0 || v >= n3[a]) {
-            if (!G.periodic[a]) return false;
-            v = v < 0 ? v + n3[a] : v - n3[a];   // |v| stays within one period: the box is narrower than the domain
-        }
-        c[a] = v;
-    }
-    *ci = c[0];
-    *cj = c[1];
-    *ck = c[2];
-    return true;
-}
-
 __global__ void k_flags_full(uint8_t* __restrict__ flags, GridDesc G, const ParticleState* __restrict__ ps) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= G.n) return;
