@@ -31,6 +31,17 @@ class OrcParams(ctypes.Structure):
     ]
 
 
+class OrcDragParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("tau", ctypes.c_double), ("magic", ctypes.c_double),
+        ("body_force", ctypes.c_double * 3),
+        ("boundary", ctypes.c_int),
+        ("pos", ctypes.c_double * 3),
+        ("diameter", ctypes.c_double),
+    ]
+
+
 class OrcAmrParams(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
@@ -103,6 +114,8 @@ def lib():
         L.orc_amr_get_particle.argtypes = [vp, dp]
         L.orc_amr_get_history.restype = ctypes.c_int64
         L.orc_amr_get_history.argtypes = [vp, dp, ctypes.c_int64]
+        L.orc_drag_tangent.restype = ctypes.c_double
+        L.orc_drag_tangent.argtypes = [ctypes.POINTER(OrcDragParams), dp, ip, ctypes.c_double, dp, dp, ip, dp, dp]
         _lib = L
     return _lib
 
@@ -347,3 +360,36 @@ class RefinedSim:
         out = np.empty((n, 15))
         self._L.orc_amr_get_history(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
         return out
+
+
+def drag_tangent(shape, tau, pos, diameter, nsteps, u0=None, body_force=(0.0, 0.0, 0.0), magic=3.0 / 16.0,
+                 boundary="cli", dtau=0.0, dforce=(0.0, 0.0, 0.0), du0=None, axis=0):
+    """Mean drag J = (1/N) sum_n F_axis^n on a fixed sphere in a periodic box
+    and its derivative along (dtau, dforce, du0), by the tangent-linear model
+    of tangent.cpp.  u0, du0: arrays (3, nz, ny, nx) or None.  Returns
+    (J, dJ, forces[nsteps, 3])."""
+    L = lib()
+    p = OrcDragParams()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    p.tau = float(tau)
+    p.magic = float(magic)
+    p.body_force = (ctypes.c_double * 3)(*[float(v) for v in body_force])
+    p.boundary = {"cli": 0, "sbb": 1}[boundary]
+    p.pos = (ctypes.c_double * 3)(*[float(v) for v in pos])
+    p.diameter = float(diameter)
+    n = p.nx * p.ny * p.nz
+    keep = []
+
+    def field(a):
+        if a is None:
+            return None
+        arr, ptr = _d(np.asarray(a).reshape(3, n))
+        keep.append(arr)
+        return ptr
+
+    df, pdf = _d(dforce)
+    forces = np.zeros((int(nsteps), 3))
+    dJ = ctypes.c_double(0.0)
+    J = L.orc_drag_tangent(ctypes.byref(p), field(u0), int(nsteps), float(dtau), pdf, field(du0), int(axis),
+                           ctypes.byref(dJ), forces.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return J, dJ.value, forces

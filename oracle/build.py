@@ -10,7 +10,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
-SOURCES = ["uniform.cpp", "refined.cpp"]
+SOURCES = ["uniform.cpp", "refined.cpp", "tangent.cpp"]
 
 
 def build(force: bool = False) -> str:

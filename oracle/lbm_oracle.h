@@ -80,6 +80,26 @@ void orc_particle_only_step(orc_sim* s, const double F_hyd[3], const double T_hy
 int orc_set_threads(int n);
 
 /* ------------------------------------------------------------------------
+ * Tangent-linear model of the mean drag on a fixed sphere, tangent.cpp.
+ * Periodic box, sphere at rest at pos, CLI (boundary 0) or simple
+ * bounce-back (1), fluid started at the equilibrium of u0 ([3][cells] with
+ * x fastest, NULL = rest).  Returns J = (1/nsteps) sum_n F_axis^n of the
+ * momentum-exchange force; *dJ receives its derivative along (dtau, dforce,
+ * du0) (dforce or du0 NULL = 0), force_out ([nsteps][3], may be NULL) the
+ * force of every step.
+ */
+typedef struct {
+    int nx, ny, nz;
+    double tau, magic;
+    double body_force[3];
+    int boundary;
+    double pos[3];
+    double diameter;
+} orc_drag_params;
+double orc_drag_tangent(const orc_drag_params* p, const double* u0, int nsteps, double dtau, const double dforce[3],
+                        const double* du0, int axis, double* dJ, double* force_out);
+
+/* ------------------------------------------------------------------------
  * Refined (block-structured) grid, refined.cpp.  Levels 0..levels-1, blocks
  * of 16^3 cells, nx, ny, nz = level-0 cells (multiples of 16), positions and
  * diameters in finest-level lattice units, tau of the finest level.

@@ -57,3 +57,44 @@ def batch_sweep(seed: int = 0, count: int = 64):
         sims.append(dict(edge=edge, diameter=float(round(edge / 6.0)), density_ratio=0.1 + 0.8 * u[i, 1],
                          ga=100.0 + 300.0 * u[i, 2], offset=u[i, 3:6].copy()))
     return sims
+
+
+# Differentiation workload: periodic 64^3 box, sphere of 12 cells held fixed
+# near the centre, fluid body force g_x = 1e-6, initial velocity from
+# divergence-free Fourier modes |k| <= 4 of amplitude 1e-3, 500 steps with a
+# checkpoint every 50.  tau is not fixed by the workload; 0.6 is used.
+ADJOINT_64 = dict(shape=(64, 64, 64), diameter=12.0, tau=0.6, magic=3.0 / 16.0, body_force=1e-6, kmax=4,
+                  amplitude=1e-3, steps=500, checkpoint=50)
+
+
+def fourier_velocity_field(shape, kmax: float, amplitude: float, seed: int) -> np.ndarray:
+    """Seeded divergence-free velocity field (3, nz, ny, nx) at the cell
+    centres: a sum over the integer wave vectors 0 < |k| <= kmax (one of each
+    +-k pair) of a_k cos(2 pi k.x / L) + b_k sin(2 pi k.x / L), with a_k and b_k
+    uniform in [-1, 1]^3 projected normal to k / L, scaled so that the largest
+    speed on the grid equals `amplitude`."""
+    nx, ny, nz = (int(v) for v in shape)
+    r = int(np.floor(kmax))
+    modes = []
+    for kx in range(-r, r + 1):
+        for ky in range(-r, r + 1):
+            for kz in range(-r, r + 1):
+                k = (kx, ky, kz)
+                if k == (0, 0, 0) or kx * kx + ky * ky + kz * kz > kmax * kmax:
+                    continue
+                first = next(v for v in k if v != 0)
+                if first > 0:
+                    modes.append(k)
+    coef = 2.0 * uniform01(seed, 6 * len(modes)).reshape(len(modes), 2, 3) - 1.0
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    u = np.zeros((3, nz, ny, nx))
+    for m, (kx, ky, kz) in enumerate(modes):
+        kv = np.array([kx / nx, ky / ny, kz / nz])
+        phase = 2.0 * np.pi * (kv[0] * x + kv[1] * y + kv[2] * z)
+        c, s = np.cos(phase), np.sin(phase)
+        for j, wave in ((0, c), (1, s)):
+            a = coef[m, j] - (coef[m, j] @ kv) / (kv @ kv) * kv
+            for d in range(3):
+                u[d] += a[d] * wave
+    speed = np.sqrt((u * u).sum(axis=0)).max()
+    return u * (amplitude / speed)
