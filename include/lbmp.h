@@ -264,6 +264,38 @@ lbmp_status lbmp_boundary_cells_noalloc(const uint8_t* flags, int nx, int ny, in
  * when h is NULL).  Never NULL. */
 const char* lbmp_last_error(const lbmp_handle* h);
 
+/* ------------------------------------------------------------------------
+ * Differentiation.  (No counterpart in the paper, which only runs the
+ * forward method: a reverse-mode derivative of its uniform-grid step.)
+ * Objective: the mean drag J = (1/nsteps) sum_{n=1..nsteps} F_axis^n of the
+ * momentum-exchange force (Sec. 2.3) on the handle's sphere, held fixed at
+ * rest (lbmp_set_particle_fixed, zero velocity) in a periodic box, with the
+ * fluid started at the incompressible equilibrium (rho = 1) of the velocity
+ * field u0 and the handle's tau, magic parameter and body force
+ * (lbmp_set_tau, lbmp_set_body_force).  FP32 or FP64 storage; the adjoint
+ * runs in the storage's arithmetic.
+ *
+ * lbmp_drag_forward runs the nsteps steps (the handle's populations end at
+ * the last one) and keeps every checkpoint_interval-th field for the reverse
+ * pass (ceil(nsteps / interval) + interval fields of device memory).
+ *   u0  device array [3][nz][ny][nx] of doubles (x fastest), read during the call
+ *   J   device double, receives J
+ * lbmp_drag_backward then forms, by the adjoint of the step with checkpoint
+ * and recompute, the derivatives of J times the device scalar dJ:
+ *   grad_tau    device double, dJ * dJ/dtau               (may be NULL)
+ *   grad_force  device double[3], dJ * dJ/dF (body force)  (may be NULL)
+ *   grad_u0     device array like u0, dJ * dJ/du0          (may be NULL)
+ * It needs the preceding forward call with the same tau and body force.
+ * Both calls are asynchronous on the handle's stream except for one
+ * synchronisation on the first forward call after the geometry is set.
+ * Errors: LBMP_ERR_UNSUPPORTED for a refined or batched handle, FP16
+ * storage, walls, or a sphere that moves; LBMP_ERR_INVALID_ARG for bad
+ * arguments or a backward call without its forward call; LBMP_ERR_OOM. */
+lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int checkpoint_interval, int axis,
+                              double* J);
+lbmp_status lbmp_drag_backward(lbmp_handle* h, const double* dJ, double* grad_tau, double* grad_force,
+                               double* grad_u0);
+
 #ifdef __cplusplus
 }
 #endif

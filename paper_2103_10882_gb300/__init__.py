@@ -23,7 +23,8 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error",
            "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_level_shape", "lbmp_get_block_map",
            "lbmp_get_level_cells", "lbmp_updates_per_step", "lbmp_batch_create", "lbmp_batch_autotune",
-           "lbmp_batch_info", "lbmp_batch_get_populations", "BatchSimulation", "PRECISIONS"]
+           "lbmp_batch_info", "lbmp_batch_get_populations", "BatchSimulation", "PRECISIONS", "lbmp_drag_forward",
+           "lbmp_drag_backward", "mean_drag"]
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
 BC = {"periodic": 0, "noslip": 1}
@@ -314,6 +315,19 @@ def lbmp_last_error(h=None):
     return m.decode() if m else ""
 
 
+def lbmp_drag_forward(h, u0_ptr, nsteps, checkpoint_interval, axis, J_ptr):
+    """Device pointers: u0 [3][nz][ny][nx] float64, J one float64."""
+    _check(h, _lib().lbmp_drag_forward(h, ctypes.c_void_p(u0_ptr), int(nsteps), int(checkpoint_interval), int(axis),
+                                       ctypes.c_void_p(J_ptr)))
+
+
+def lbmp_drag_backward(h, dJ_ptr, grad_tau_ptr, grad_force_ptr, grad_u0_ptr):
+    """Device pointers (the three outputs may be 0 for 'not wanted')."""
+    _check(h, _lib().lbmp_drag_backward(h, ctypes.c_void_p(dJ_ptr), ctypes.c_void_p(grad_tau_ptr or None),
+                                        ctypes.c_void_p(grad_force_ptr or None),
+                                        ctypes.c_void_p(grad_u0_ptr or None)))
+
+
 # ------------------------------------------------------------ convenience
 class _TorchAllocator:
     """Routes the library's device allocations through PyTorch's caching allocator."""
@@ -393,6 +407,10 @@ class Simulation:
 
     def set_fixed(self, fixed=True):
         lbmp_set_particle_fixed(self.h, 0, fixed)
+
+    def mean_drag(self, tau, force, u0, nsteps, checkpoint_interval=50, axis=0):
+        """Differentiable mean drag on the fixed sphere; see mean_drag()."""
+        return mean_drag(self, tau, force, u0, nsteps, checkpoint_interval, axis)
 
     def set_ga(self, ga, u_g=0.01, direction=(0.0, 0.0, -1.0)):
         lbmp_set_ga(self.h, ga, u_g, direction)
@@ -544,3 +562,63 @@ class BatchSimulation:
 
     def profile_result(self):
         return lbmp_get_profile(self.h)
+
+
+# ----------------------------------------------------------- differentiation
+_MEAN_DRAG = None
+
+
+def _mean_drag_function():
+    global _MEAN_DRAG
+    if _MEAN_DRAG is not None:
+        return _MEAN_DRAG
+    import torch
+
+    class MeanDrag(torch.autograd.Function):
+        """J = (1/N) sum_n F_axis^n on the fixed sphere of a Simulation; the
+        backward pass is the library's adjoint (lbmp_drag_backward)."""
+
+        @staticmethod
+        def forward(ctx, tau, force, u0, sim, nsteps, interval, axis):
+            sim.set_tau(float(tau))
+            sim.set_body_force([float(v) for v in force.detach().cpu()])
+            dev = torch.device("cuda", torch.cuda.current_device())
+            u = u0.detach().to(device=dev, dtype=torch.float64).contiguous()
+            if tuple(u.shape) != (3, sim.shape[2], sim.shape[1], sim.shape[0]):
+                raise ValueError("u0 must have shape (3, nz, ny, nx)")
+            J = torch.empty((), dtype=torch.float64, device=dev)
+            sim.stream.wait_stream(torch.cuda.current_stream())
+            lbmp_drag_forward(sim.h, u.data_ptr(), nsteps, interval, axis, J.data_ptr())
+            torch.cuda.current_stream().wait_stream(sim.stream)
+            u.record_stream(sim.stream)
+            ctx.sim = sim
+            ctx.meta = (tau.dtype, tau.device, force.dtype, force.device, u0.dtype, u0.device, tuple(u0.shape))
+            return J
+
+        @staticmethod
+        def backward(ctx, gJ):
+            sim = ctx.sim
+            tdt, tdev, fdt, fdev, udt, udev, ushape = ctx.meta
+            dev = torch.device("cuda", torch.cuda.current_device())
+            g = gJ.detach().to(device=dev, dtype=torch.float64).contiguous()
+            gt = torch.empty((), dtype=torch.float64, device=dev)
+            gf = torch.empty(3, dtype=torch.float64, device=dev)
+            gu = torch.empty(ushape, dtype=torch.float64, device=dev) if ctx.needs_input_grad[2] else None
+            sim.stream.wait_stream(torch.cuda.current_stream())
+            lbmp_drag_backward(sim.h, g.data_ptr(), gt.data_ptr(), gf.data_ptr(), gu.data_ptr() if gu is not None else 0)
+            torch.cuda.current_stream().wait_stream(sim.stream)
+            return (gt.to(dtype=tdt, device=tdev) if ctx.needs_input_grad[0] else None,
+                    gf.to(dtype=fdt, device=fdev) if ctx.needs_input_grad[1] else None,
+                    gu.to(dtype=udt, device=udev) if gu is not None else None, None, None, None, None)
+
+    _MEAN_DRAG = MeanDrag
+    return MeanDrag
+
+
+def mean_drag(sim, tau, force, u0, nsteps, checkpoint_interval=50, axis=0):
+    """Mean drag J = (1/nsteps) sum_n F_axis^n on the fixed sphere of `sim`
+    (a uniform periodic Simulation, FP32 or FP64) from the equilibrium of u0,
+    as a torch scalar that autograd differentiates with respect to tau (0-d
+    tensor), the body force (3-tensor) and u0 (tensor (3, nz, ny, nx)) by the
+    library's adjoint with checkpoints every `checkpoint_interval` steps."""
+    return _mean_drag_function().apply(tau, force, u0, sim, int(nsteps), int(checkpoint_interval), int(axis))

@@ -287,7 +287,9 @@ __device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int l
 constexpr int BNDW_THREADS = 256;
 
 // One warp per boundary cell of the finest level, lane q handling population
-// q (CLI links of Sec. 2.3, FP64 force partials), cooperative collision.
+// q (CLI links of Sec. 2.3: geometry in the population arithmetic, FP64
+// force partials), cooperative collision.  Blocks past the end of the list
+// write zero partials.
 template <typename S>
 __global__ void __launch_bounds__(BNDW_THREADS)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
@@ -295,12 +297,17 @@ __global__ void __launch_bounds__(BNDW_THREADS)
                    CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
                    double* __restrict__ partials, int* __restrict__ status) {
     using A = typename Store<S>::A;
-    __shared__ double red[6][BNDW_THREADS / 32];
+    __shared__ LinkFrame<A> Fr;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = gridDim.x * (BNDW_THREADS / 32);
     const int cnt = *count;
-    const ParticleState& Pp = *ps;
-    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    if ((int)blockIdx.x * (BNDW_THREADS / 32) >= cnt) {   // uniform across the block
+        if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 6 + threadIdx.x] = 0.0;
+        return;
+    }
+    if (threadIdx.x == 0) Fr.init(*ps);
+    __syncthreads();
+    LinkSums acc;
     for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
         const int e = list[w];
         const int b = e >> 12, c = e & 4095;
@@ -323,77 +330,39 @@ __global__ void __launch_bounds__(BNDW_THREADS)
                 const int fb = nbr_cell(D, b, lx, ly, lz, cq[0], cq[1], cq[2], &fc);   // x - c_k
                 const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
                 const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly, D.bpos[3 * b + 2] * BS + lz};
-                const double d[3] = {wrap_diff((g[0] + 0.5) - Pp.x[0], D.n[0], D.periodic[0]),
-                                     wrap_diff((g[1] + 0.5) - Pp.x[1], D.n[1], D.periodic[1]),
-                                     wrap_diff((g[2] + 0.5) - Pp.x[2], D.n[2], D.periodic[2])};
-                const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+                A d[3], fl[3], tl[3];
+                int pu[3];
+                Fr.offset(g, D.n, D.periodic, d, pu);
                 const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
                 const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
                 const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
-                gq = cli_link<A>(q, d, Pp.r, delta, gt_k, gt_q, gt_far, Pp, F, T);
+                gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, fl, tl);
+                acc.add(k, pu, fl, tl);
             }
         }
         gq = warp_trt_collide<A, false>(gq, lane, P, status);
         if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
     }
-    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[k][wib] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        double sum = 0.0;
-        for (int k = 0; k < BNDW_THREADS / 32; ++k) sum += red[threadIdx.x][k];
-        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = sum;
-    }
-}
-
-__device__ __forceinline__ bool ball(const int g[3], const LevelView& D, const ParticleState& P) {
-    const double dx = wrap_diff(__dsub_rn((double)g[0] + 0.5, P.x[0]), D.n[0], D.periodic[0]);
-    const double dy = wrap_diff(__dsub_rn((double)g[1] + 0.5, P.x[1]), D.n[1], D.periodic[1]);
-    const double dz = wrap_diff(__dsub_rn((double)g[2] + 0.5, P.x[2]), D.n[2], D.periodic[2]);
-    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    return d2 <= __dmul_rn(P.r, P.r);
+    block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
 }
 
 // Box of finest cells around the sphere (same box as the uniform engine's).
-__device__ __forceinline__ bool amr_box_cell(int t, const LevelView& D, const BoxDesc& B, const ParticleState& P,
-                                             int g[3]) {
-    const int e0 = B.E[0], e1 = B.E[1];
-    const int tk = t / (e0 * e1);
-    const int r = t - tk * e0 * e1;
-    const int tt[3] = {r - (r / e0) * e0, r / e0, tk};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int o = (B.E[a] >= D.n[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
-        int v = o + tt[a];
-        if (v < 0 || v >= D.n[a]) {
-            if (!D.periodic[a]) return false;
-            v = v < 0 ? v + D.n[a] : v - D.n[a];
-        }
-        g[a] = v;
-    }
-    return true;
-}
-
 __global__ void k_amr_flags_box(LevelView D, uint8_t* __restrict__ fnext, BoxDesc B,
                                 const ParticleState* __restrict__ ps, int* __restrict__ status) {
+    __shared__ BoxFrame F;
+    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
+    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.cells) return;
-    const ParticleState P = *ps;
     int g[3];
-    if (!amr_box_cell(t, D, B, P, g)) return;
+    if (!box_cell(t, D.n, D.periodic, B, F, g)) return;
     int c;
     const int b = locate(D, g, &c);
     if (b < 0 || b >= D.nreal) {
         atomicOr(status, STATUS_NOT_FINEST);
         return;
     }
-    fnext[(size_t)b * B3 + c] = ball(g, D, P) ? 1 : 0;
+    fnext[(size_t)b * B3 + c] = ball_flag(g, D.n, D.periodic, F, *ps) ? 1 : 0;
 }
 
 template <typename S>
@@ -401,11 +370,14 @@ __global__ void k_amr_refill(LevelView D, S* __restrict__ pops, const uint8_t* _
                              const uint8_t* __restrict__ fnext, BoxDesc B, const ParticleState* __restrict__ ps,
                              typename Store<S>::A scale, typename Store<S>::A inv_scale) {
     using A = typename Store<S>::A;
+    __shared__ BoxFrame F;
+    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
+    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.cells) return;
-    const ParticleState P = *ps;
+    const ParticleState& P = *ps;
     int g[3];
-    if (!amr_box_cell(t, D, B, P, g)) return;
+    if (!box_cell(t, D.n, D.periodic, B, F, g)) return;
     int c;
     const int b = locate(D, g, &c);
     if (b < 0 || b >= D.nreal) return;
@@ -445,11 +417,14 @@ constexpr int LINK_THREADS = 256;
 __global__ void __launch_bounds__(LINK_THREADS)
     k_amr_links_mark(LevelView D, const uint8_t* __restrict__ flags, BoxDesc B, const ParticleState* __restrict__ ps,
                      uint8_t* __restrict__ mask, int* __restrict__ block_count) {
+    __shared__ BoxFrame F;
+    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
+    __syncthreads();
     const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
     int is_b = 0;
     if (t < B.cells) {
         int g[3];
-        if (amr_box_cell(t, D, B, *ps, g)) {
+        if (box_cell(t, D.n, D.periodic, B, F, g)) {
             int c;
             const int b = locate(D, g, &c);
             if (b >= 0 && b < D.nreal && flags[(size_t)b * B3 + c] == 0) {
@@ -481,6 +456,8 @@ __global__ void __launch_bounds__(LINK_THREADS)
                      int capacity, int* __restrict__ status) {
     __shared__ int red[LINK_THREADS];
     __shared__ int wsum[LINK_THREADS / 32];
+    __shared__ BoxFrame F;
+    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
     int s = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += LINK_THREADS) s += block_count[b];
     red[threadIdx.x] = s;
@@ -500,7 +477,7 @@ __global__ void __launch_bounds__(LINK_THREADS)
     for (int w = 0; w < warp; ++w) wbase += wsum[w];
     if (is_b) {
         int g[3], c;
-        amr_box_cell(t, D, B, *ps, g);
+        box_cell(t, D.n, D.periodic, B, F, g);
         const int b = locate(D, g, &c);
         const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
         if (pos < capacity) list[pos] = (b << 12) | c;
@@ -559,7 +536,7 @@ __global__ void k_amr_flags_full(LevelView D, uint8_t* __restrict__ f0, uint8_t*
     {
         const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
         const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
-        const uint8_t v = (P.present && ball(g, D, P)) ? 1 : 0;
+        const uint8_t v = (P.present && inside_ball_exact(g, D.n, D.periodic, P)) ? 1 : 0;
         f0[(size_t)b * B3 + c] = v;
         f1[(size_t)b * B3 + c] = v;
     }
@@ -1180,7 +1157,6 @@ void enqueue_advance(lbmp_handle* h, int l) {
         E->substep[l + 1] = 1;
         enqueue_advance<S>(h, l + 1);
     }
-    const int np = V.nreal + V.nghost;
     UpdateArgs<S> U;
     U.D = view(E, V);
     U.src = (const S*)V.d_pops[V.cur];

@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "adjoint.h"
 #include "amr.h"
 #include "batch.h"
 
@@ -62,31 +63,6 @@ void dev_free(lbmp_handle* h, void* p) {
             return;
         }
     }
-}
-
-// s- from the magic parameter: Lambda = (1/s+ - 1/2)(1/s- - 1/2)  (Sec. 2.1)
-void relaxation_rates(double tau, double magic, double* sp, double* sm) {
-    *sp = 1.0 / tau;
-    *sm = 1.0 / (0.5 + magic / (tau - 0.5));
-}
-
-template <typename A>
-CollideParams<A> collide_params(const lbmp_handle* h) {
-    CollideParams<A> p;
-    double sp, sm;
-    relaxation_rates(h->tau, h->magic, &sp, &sm);
-    p.sp = (A)sp;
-    p.sm = (A)sm;
-    for (int a = 0; a < 3; ++a) p.F[a] = (A)h->body_force[a];
-    p.forced = (h->body_force[0] != 0.0 || h->body_force[1] != 0.0 || h->body_force[2] != 0.0) ? 1 : 0;
-    if (h->cfg.precision == LBMP_FP16) {
-        p.scale = (A)std::ldexp(1.0, h->cfg.fp16_scale_log2);
-        p.inv_scale = (A)std::ldexp(1.0, -h->cfg.fp16_scale_log2);
-    } else {
-        p.scale = (A)1;
-        p.inv_scale = (A)1;
-    }
-    return p;
 }
 
 double fp16_scale(const lbmp_handle* h, bool inverse) {
@@ -337,6 +313,7 @@ lbmp_status lbmp_destroy(lbmp_handle* h) {
     cudaStreamSynchronize(h->stream);
     amr_destroy(h);
     batch_destroy(h);
+    adjoint_destroy(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
     while (!h->allocations.empty()) dev_free(h, h->allocations.back().first);
@@ -923,6 +900,36 @@ lbmp_status lbmp_batch_get_populations(lbmp_handle* h, int sim, double* out, siz
     if (!h || !h->batch || !out) return LBMP_ERR_INVALID_ARG;
     const lbmp_status st = batch_populations(h, sim, out, cap);
     return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_batch_get_populations: bad simulation index or capacity");
+}
+
+lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int checkpoint_interval, int axis,
+                              double* J) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (!u0 || !J) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_forward: NULL argument");
+    if (nsteps < 1 || checkpoint_interval < 1 || axis < 0 || axis > 2)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_forward: need nsteps >= 1, checkpoint_interval >= 1, axis 0..2");
+    lbmp_status s = h->has_particle ? download_particle(h) : LBMP_OK;
+    if (s != LBMP_OK) return s;
+    std::string why;
+    s = adjoint_check(h, &why);
+    if (s != LBMP_OK) return fail(h, s, "lbmp_drag_forward: " + why);
+    s = adjoint_forward(h, u0, nsteps, checkpoint_interval, axis, J);
+    if (s == LBMP_ERR_OOM) return fail(h, s, "lbmp_drag_forward: out of device memory for the checkpoints");
+    if (s != LBMP_OK) return fail(h, s, "lbmp_drag_forward: CUDA launch failed");
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_drag_backward(lbmp_handle* h, const double* dJ, double* grad_tau, double* grad_force,
+                               double* grad_u0) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (!dJ) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_backward: NULL dJ");
+    std::string why;
+    lbmp_status s = adjoint_check(h, &why);
+    if (s != LBMP_OK) return fail(h, s, "lbmp_drag_backward: " + why);
+    s = adjoint_backward(h, dJ, grad_tau, grad_force, grad_u0, &why);
+    if (s == LBMP_ERR_CUDA) why = "CUDA launch failed";
+    if (s != LBMP_OK) return fail(h, s, "lbmp_drag_backward: " + why);
+    return LBMP_OK;
 }
 
 const char* lbmp_last_error(const lbmp_handle* h) {

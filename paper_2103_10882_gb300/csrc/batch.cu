@@ -29,6 +29,7 @@ struct SimDev {
     int list_off, list_cap;
     int mask_off;        // scratch: one byte per box cell
     int blk_off;         // scratch: one int per link block
+    int bnd_off, bnd_n;  // boundary-kernel blocks of the simulation (and their force partials)
     BoxDesc box;
     double sp, sm;
     long long hist_off;  // records
@@ -84,38 +85,51 @@ __global__ void __launch_bounds__(512) k_batch_bulk(const S* __restrict__ src, S
 }
 
 // ----------------------------------------------------------------- boundary
+// Warp per boundary cell as in the single-simulation engine.  The grid is
+// flat: block b belongs to simulation bnd_sim[b], which owns bnd_n blocks
+// (one per 32 entries of its list capacity) and as many force partials.
 template <typename S>
 __global__ void __launch_bounds__(BW)
     k_batch_boundary(const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ flags,
                      const int* __restrict__ lists, const int* __restrict__ counts, const SimDev* __restrict__ sims,
-                     const ParticleState* __restrict__ ps, int cli, typename Store<S>::A scale,
-                     typename Store<S>::A inv, double* __restrict__ partials, int* __restrict__ status) {
+                     const int* __restrict__ bnd_sim, const ParticleState* __restrict__ ps, int cli,
+                     typename Store<S>::A scale, typename Store<S>::A inv, double* __restrict__ partials,
+                     int* __restrict__ status) {
     using A = typename Store<S>::A;
-    __shared__ double red[6][BW / 32];
-    const int sim = blockIdx.y;
+    __shared__ LinkFrame<A> Fr;
+    const int sim = bnd_sim[blockIdx.x];
     const SimDev& D = sims[sim];
-    const CollideParams<A> P = sim_params<S>(D, scale, inv);
+    const int jb = blockIdx.x - D.bnd_off;
+    const int cnt = counts[sim];
+    if (jb * (BW / 32) >= cnt) {   // uniform across the block
+        if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 6 + threadIdx.x] = 0.0;
+        return;
+    }
     const ParticleState& Pp = ps[sim];
+    if (threadIdx.x == 0) Fr.init(Pp);
+    const CollideParams<A> P = sim_params<S>(D, scale, inv);
     const GridDesc& G = D.G;
     const S* s0 = src + D.pop_off;
     S* d0 = dst + D.pop_off;
     const uint8_t* fl = flags + D.flag_off;
     const int* list = lists + D.list_off;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (BW / 32);
-    const int cnt = counts[sim];
+    const int nwarps = D.bnd_n * (BW / 32);
     const size_t n = (size_t)G.n;
-    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
-    for (int w = blockIdx.x * (BW / 32) + wib; w < cnt; w += nwarps) {
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    const int per3[3] = {1, 1, 1};
+    LinkSums acc;
+    __syncthreads();
+    for (int w = jb * (BW / 32) + wib; w < cnt; w += nwarps) {
         const int cell = list[w];
         const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
         A gq = A(0);
         if (lane < 19) {
             const int q = lane;
-            const int c[3] = {lane_c(q, 0), lane_c(q, 1), lane_c(q, 2)};
+            const int c[3] = {cx(q), cy(q), cz(q)};
             const int xyz[3] = {x, y, z};
-            const int n3[3] = {G.nx, G.ny, G.nz};
             int s3[3], f3[3];
+#pragma unroll
             for (int a = 0; a < 3; ++a) {
                 s3[a] = src_coord(xyz[a], c[a], n3[a], 1);
                 f3[a] = src_coord(xyz[a], -c[a], n3[a], 1);
@@ -127,44 +141,34 @@ __global__ void __launch_bounds__(BW)
                 const int k = opp(q);
                 const size_t far = (size_t)f3[0] + (size_t)G.nx * ((size_t)f3[1] + (size_t)G.ny * (size_t)f3[2]);
                 const bool far_ok = fl[far] == 0;
-                const double d[3] = {wrap_diff((x + 0.5) - Pp.x[0], G.nx, 1), wrap_diff((y + 0.5) - Pp.x[1], G.ny, 1),
-                                     wrap_diff((z + 0.5) - Pp.x[2], G.nz, 1)};
-                const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+                A d[3], flk[3], tl[3];
+                int pu[3];
+                Fr.offset(xyz, n3, per3, d, pu);
                 const A gt_k = Store<S>::load(s0 + (size_t)k * n + cell, P.inv_scale);
                 const A gt_q = Store<S>::load(s0 + (size_t)q * n + cell, P.inv_scale);
                 const A gt_far = far_ok ? Store<S>::load(s0 + (size_t)k * n + far, P.inv_scale) : A(0);
-                gq = cli_link<A>(q, d, Pp.r, delta, gt_k, gt_q, gt_far, Pp, F, T);
+                gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, flk, tl);
+                acc.add(k, pu, flk, tl);
             }
         }
         gq = warp_trt_collide<A, false>(gq, lane, P, status);
         if (lane < 19) Store<S>::store(d0 + (size_t)lane * n + cell, gq, P.scale);
     }
-    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    if (lane == 0)
-        for (int k = 0; k < 6; ++k) red[k][wib] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        double sum = 0.0;
-        for (int k = 0; k < BW / 32; ++k) sum += red[threadIdx.x][k];
-        partials[((size_t)sim * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = sum;
-    }
+    block_link_sums<BW>(acc, Pp.x, partials + (size_t)blockIdx.x * 6);
 }
 
 // ----------------------------------------------------------------- particle
 __global__ void __launch_bounds__(BW)
-    k_batch_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials, int nblocks,
+    k_batch_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials,
                      const SimDev* __restrict__ sims, double* __restrict__ history, int hist_cap,
                      int* __restrict__ status) {
     __shared__ double red[6][BW];
     __shared__ ParticleState sP;
     const int sim = blockIdx.x;
+    const SimDev& D = sims[sim];
     double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += BW)
-        for (int k = 0; k < 6; ++k) v[k] += partials[((size_t)sim * nblocks + b) * 6 + k];
+    for (int b = threadIdx.x; b < D.bnd_n; b += BW)
+        for (int k = 0; k < 6; ++k) v[k] += partials[((size_t)D.bnd_off + b) * 6 + k];
     for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = v[k];
     {
         const int words = (int)(sizeof(ParticleState) / sizeof(int));
@@ -173,14 +177,16 @@ __global__ void __launch_bounds__(BW)
         for (int i = threadIdx.x; i < words; i += BW) dw[i] = sw[i];
     }
     __syncthreads();
-    for (int s = BW / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+    for (int h = BW / 2; h > 0; h >>= 1) {
+        for (int idx = threadIdx.x; idx < 6 * h; idx += BW) {
+            const int c = idx / h, i = idx - c * h;
+            red[c][i] += red[c][i + h];
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         const double FT[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
-        particle_advance(sP, FT, sims[sim].G, history + (size_t)sims[sim].hist_off * 15, hist_cap, status);
+        particle_advance(sP, FT, D.G, history + (size_t)D.hist_off * 15, hist_cap, status);
     }
     __syncthreads();
     {
@@ -194,15 +200,19 @@ __global__ void __launch_bounds__(BW)
 // -------------------------------------------------------------------- remap
 __global__ void k_batch_flags_box(uint8_t* __restrict__ fnext, const SimDev* __restrict__ sims,
                                   const ParticleState* __restrict__ ps) {
+    __shared__ BoxFrame F;
     const int sim = blockIdx.y;
     const SimDev& D = sims[sim];
+    if ((long long)blockIdx.x * blockDim.x >= D.box.cells) return;   // uniform across the block
+    const int n3[3] = {D.G.nx, D.G.ny, D.G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, D.G.periodic, D.box, ps[sim]);
+    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= D.box.cells) return;
-    const ParticleState P = ps[sim];
-    int i, j, k;
-    if (!box_cell(t, D.G, D.box, P, &i, &j, &k)) return;
-    fnext[D.flag_off + (size_t)i + (size_t)D.G.nx * ((size_t)j + (size_t)D.G.ny * (size_t)k)] =
-        inside_ball(i, j, k, D.G, P) ? 1 : 0;
+    int p[3];
+    box_cell(t, n3, D.G.periodic, D.box, F, p);   // periodic: always inside
+    fnext[D.flag_off + (size_t)p[0] + (size_t)D.G.nx * ((size_t)p[1] + (size_t)D.G.ny * (size_t)p[2])] =
+        ball_flag(p, n3, D.G.periodic, F, ps[sim]) ? 1 : 0;
 }
 
 // refill of uncovered cells, zeroing of solid ones, and the boundary-cell mark
@@ -213,15 +223,21 @@ __global__ void __launch_bounds__(BW)
                         typename Store<S>::A scale, typename Store<S>::A inv, uint8_t* __restrict__ mask,
                         int* __restrict__ block_count) {
     using A = typename Store<S>::A;
+    __shared__ BoxFrame F;
     const int sim = blockIdx.y;
     const SimDev& D = sims[sim];
     const GridDesc& G = D.G;
+    if ((long long)blockIdx.x * BW >= D.box.cells) return;   // uniform across the block
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, D.box, ps[sim]);
+    __syncthreads();
     const int t = blockIdx.x * BW + threadIdx.x;
     int is_b = 0;
     if (t < D.box.cells) {
-        const ParticleState P = ps[sim];
-        int i, j, k;
-        box_cell(t, G, D.box, P, &i, &j, &k);   // periodic: always inside
+        const ParticleState& P = ps[sim];
+        int p[3];
+        box_cell(t, n3, G.periodic, D.box, F, p);   // periodic: always inside
+        const int i = p[0], j = p[1], k = p[2];
         const size_t n = (size_t)G.n;
         const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
         const uint8_t* fc = fcur + D.flag_off;
@@ -232,7 +248,6 @@ __global__ void __launch_bounds__(BW)
         } else {
             A rsum = A(0);
             int cnt = 0;
-            const int n3[3] = {G.nx, G.ny, G.nz};
             for (int q = 1; q < 19; ++q) {
                 int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
                 for (int a = 0; a < 3; ++a) v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
@@ -279,10 +294,13 @@ __global__ void __launch_bounds__(BW)
                        int* __restrict__ counts, int* __restrict__ status) {
     __shared__ int red[BW];
     __shared__ int wsum[BW / 32];
+    __shared__ BoxFrame F;
     const int sim = blockIdx.y;
     const SimDev& D = sims[sim];
     const int nb = (D.box.cells + BW - 1) / BW;
     if ((int)blockIdx.x >= nb) return;   // uniform across the block
+    const int n3[3] = {D.G.nx, D.G.ny, D.G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, D.G.periodic, D.box, ps[sim]);
     int s = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += BW) s += block_count[D.blk_off + b];
     red[threadIdx.x] = s;
@@ -301,10 +319,10 @@ __global__ void __launch_bounds__(BW)
     int wbase = 0;
     for (int w = 0; w < warp; ++w) wbase += wsum[w];
     if (is_b) {
-        int i, j, k;
-        box_cell(t, D.G, D.box, ps[sim], &i, &j, &k);
+        int p[3];
+        box_cell(t, n3, D.G.periodic, D.box, F, p);
         const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
-        if (pos < D.list_cap) lists[D.list_off + pos] = i + D.G.nx * (j + D.G.ny * k);
+        if (pos < D.list_cap) lists[D.list_off + pos] = p[0] + D.G.nx * (p[1] + D.G.ny * p[2]);
         else atomicOr(status, STATUS_LINK_OVERFLOW);
     }
     if ((int)blockIdx.x == nb - 1 && threadIdx.x == 0) {
@@ -377,7 +395,8 @@ struct BatchEngine {
     uint8_t* mask = nullptr;
     int* blk = nullptr;
     double* partials = nullptr;
-    int bnd_blocks = 1;     // boundary grid columns (per simulation)
+    int bnd_blocks = 1;     // boundary-kernel blocks of all simulations
+    int* d_bnd_sim = nullptr;   // simulation of each boundary-kernel block
     int max_box_blocks = 1;
     double* history = nullptr;
     // stream-collide tiles for every candidate shape
@@ -434,11 +453,11 @@ void enqueue_batch_step(lbmp_handle* h) {
     const long long ev = profile_mark(h);
     launch_bulk_choice<S>(h, B, B->tile_choice, src, dst);
     profile_kernel(h, ev, profile_mark(h), 38.0 * sizeof(S) * (double)B->total_cells, (double)B->total_cells);
-    const dim3 gb(B->bnd_blocks, B->nsims);
-    k_batch_boundary<S><<<gb, BW, 0, h->stream>>>(src, dst, B->flags[B->fcur], B->lists, B->counts, B->d_sims, B->d_ps,
-                                                  h->cfg.boundary == LBMP_CLI ? 1 : 0, scale, inv, B->partials,
-                                                  h->status);
-    k_batch_particle<<<B->nsims, BW, 0, h->stream>>>(B->d_ps, B->partials, B->bnd_blocks, B->d_sims, B->history,
+    k_batch_boundary<S><<<B->bnd_blocks, BW, 0, h->stream>>>(src, dst, B->flags[B->fcur], B->lists, B->counts,
+                                                             B->d_sims, B->d_bnd_sim, B->d_ps,
+                                                             h->cfg.boundary == LBMP_CLI ? 1 : 0, scale, inv,
+                                                             B->partials, h->status);
+    k_batch_particle<<<B->nsims, BW, 0, h->stream>>>(B->d_ps, B->partials, B->d_sims, B->history,
                                                      h->cfg.history_capacity, h->status);
     uint8_t* fnext = B->flags[1 - B->fcur];
     const dim3 gr(B->max_box_blocks, B->nsims);
@@ -474,6 +493,7 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
     const size_t es = h->cfg.precision == LBMP_FP64 ? 8 : (h->cfg.precision == LBMP_FP32 ? 4 : 2);
     long long cells = 0, list_total = 0, mask_total = 0, blk_total = 0;
     int max_box = 1, max_list = 1;
+    std::vector<int> bnd_sim;
     for (int s = 0; s < n; ++s) {
         const lbmp_batch_sim& in = sims[s];
         SimDev& D = B->sims[s];
@@ -521,12 +541,15 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
         blk_total += nbx;
         max_box = std::max(max_box, nbx);
         max_list = std::max(max_list, D.list_cap);
+        D.bnd_off = (int)bnd_sim.size();
+        D.bnd_n = boundary_grid(D.list_cap);
+        for (int j = 0; j < D.bnd_n; ++j) bnd_sim.push_back(s);
         D.hist_off = (long long)s * std::max(1, h->cfg.history_capacity);
     }
     B->cell_off[n] = cells;
     B->total_cells = cells;
     B->max_box_blocks = max_box;
-    B->bnd_blocks = std::max(1, std::min(64, (max_list + 7) / 8));
+    B->bnd_blocks = (int)bnd_sim.size();
     const size_t pop_bytes = es * 19 * (size_t)cells;
     B->pops[0] = handle_alloc(h, pop_bytes);
     B->pops[1] = handle_alloc(h, pop_bytes);
@@ -539,11 +562,13 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
     B->counts = (int*)handle_alloc(h, sizeof(int) * n);
     B->mask = (uint8_t*)handle_alloc(h, (size_t)mask_total);
     B->blk = (int*)handle_alloc(h, sizeof(int) * (size_t)blk_total);
-    B->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)B->bnd_blocks * n);
+    B->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)B->bnd_blocks);
+    B->d_bnd_sim = (int*)handle_alloc(h, sizeof(int) * (size_t)B->bnd_blocks);
     B->history = (double*)handle_alloc(h, sizeof(double) * 15 * (size_t)n * std::max(1, h->cfg.history_capacity));
     if (!B->pops[0] || !B->pops[1] || !B->flags[0] || !B->flags[1] || !B->d_sims || !B->d_cell_off || !B->d_ps ||
-        !B->lists || !B->counts || !B->mask || !B->blk || !B->partials || !B->history)
+        !B->lists || !B->counts || !B->mask || !B->blk || !B->partials || !B->d_bnd_sim || !B->history)
         return LBMP_ERR_OOM;
+    cudaMemcpyAsync(B->d_bnd_sim, bnd_sim.data(), sizeof(int) * bnd_sim.size(), cudaMemcpyHostToDevice, h->stream);
     // stream-collide tiles for every candidate shape (edges are multiples of 16)
     for (int c = 0; c < 4; ++c) {
         std::vector<int4> tiles;
@@ -580,7 +605,8 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
         k_batch_links_emit<<<gr, BW, 0, h->stream>>>(B->mask, B->blk, B->d_sims, B->d_ps, B->lists, B->counts,
                                                      h->status);
     });
-    h->h2d += (long long)(sizeof(SimDev) + sizeof(ParticleState) + sizeof(long long)) * n;
+    h->h2d += (long long)(sizeof(SimDev) + sizeof(ParticleState) + sizeof(long long)) * n +
+              (long long)(sizeof(int) * bnd_sim.size());
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     h->has_particle = true;
     return LBMP_OK;

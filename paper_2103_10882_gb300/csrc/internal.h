@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+
+#include <cmath>
 #include <stdint.h>
 
 #include <string>
@@ -37,11 +39,15 @@ struct BoxDesc {
     long long cells;
 };
 
-// Grid of the warp-per-cell boundary kernels (8 cells per block at a time,
-// grid-stride over the boundary list); also the number of force partials.
+// Grid of the warp-per-cell boundary kernels (8 warps per block, grid-stride
+// over the boundary list); also the number of force partials.  The list
+// capacity is about three times the boundary cells of the sphere, so one
+// block per 32 entries of capacity gives each warp one or two cells: enough
+// warps to hide the gathers' latency, few enough that the per-block set-up
+// and the FP64 reduction stay small.  At most eight blocks per SM.
 inline int boundary_grid(int capacity) {
-    const int b = (capacity + 7) / 8;
-    return b < 1 ? 1 : (b > 608 ? 608 : b);
+    const int b = (capacity + 31) / 32;
+    return b < 1 ? 1 : (b > 1216 ? 1216 : b);
 }
 
 // Launchers (uniform.cu).  All are asynchronous on `stream`.
@@ -85,6 +91,7 @@ void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStr
 
 struct AmrEngine;
 struct BatchEngine;
+struct AdjointEngine;
 
 // Profiling events on the handle's stream (api.cu); -1 when profiling is off.
 long long profile_mark(lbmp_handle* h);
@@ -133,5 +140,35 @@ struct lbmp_handle {
     std::string err;
     lbmp::AmrEngine* amr = nullptr;     // refined hierarchy (levels > 1), else null
     lbmp::BatchEngine* batch = nullptr; // batched sweep, else null
+    lbmp::AdjointEngine* adj = nullptr; // drag adjoint workspace, else null
 };
+
+namespace lbmp {
+
+// s- from the magic parameter: Lambda = (1/s+ - 1/2)(1/s- - 1/2)  (Sec. 2.1)
+inline void relaxation_rates(double tau, double magic, double* sp, double* sm) {
+    *sp = 1.0 / tau;
+    *sm = 1.0 / (0.5 + magic / (tau - 0.5));
+}
+
+template <typename A>
+inline CollideParams<A> collide_params(const lbmp_handle* h) {
+    CollideParams<A> p;
+    double sp, sm;
+    relaxation_rates(h->tau, h->magic, &sp, &sm);
+    p.sp = (A)sp;
+    p.sm = (A)sm;
+    for (int a = 0; a < 3; ++a) p.F[a] = (A)h->body_force[a];
+    p.forced = (h->body_force[0] != 0.0 || h->body_force[1] != 0.0 || h->body_force[2] != 0.0) ? 1 : 0;
+    if (h->cfg.precision == LBMP_FP16) {
+        p.scale = (A)std::ldexp(1.0, h->cfg.fp16_scale_log2);
+        p.inv_scale = (A)std::ldexp(1.0, -h->cfg.fp16_scale_log2);
+    } else {
+        p.scale = (A)1;
+        p.inv_scale = (A)1;
+    }
+    return p;
+}
+
+}  // namespace lbmp
 

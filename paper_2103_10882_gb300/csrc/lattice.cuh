@@ -10,18 +10,23 @@
 namespace lbmp {
 
 // Direction q: 0 rest, 1..6 faces, 7..18 edges; opposite pairs are (odd, odd+1).
-__host__ __device__ constexpr int cx(int q) {
-    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-    return t[q];
+// Components are packed two bits per direction (value + 1), so a run-time q
+// costs a shift and a mask instead of a table in local memory.
+//   cx: 0, 1,-1, 0, 0, 0, 0, 1,-1, 1,-1, 1,-1, 1,-1, 0, 0, 0, 0
+//   cy: 0, 0, 0, 1,-1, 0, 0, 1,-1,-1, 1, 0, 0, 0, 0, 1,-1, 1,-1
+//   cz: 0, 0, 0, 0, 0, 1,-1, 0, 0, 0, 0, 1,-1,-1, 1, 1,-1,-1, 1
+__host__ __device__ constexpr unsigned long long pack_dirs(const int (&v)[19]) {
+    unsigned long long p = 0;
+    for (int q = 0; q < 19; ++q) p |= (unsigned long long)(v[q] + 1) << (2 * q);
+    return p;
 }
-__host__ __device__ constexpr int cy(int q) {
-    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-    return t[q];
-}
-__host__ __device__ constexpr int cz(int q) {
-    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-    return t[q];
-}
+constexpr int kCX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+constexpr int kCY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+constexpr int kCZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+constexpr unsigned long long kPX = pack_dirs(kCX), kPY = pack_dirs(kCY), kPZ = pack_dirs(kCZ);
+__host__ __device__ constexpr int cx(int q) { return (int)((kPX >> (2 * q)) & 3ull) - 1; }
+__host__ __device__ constexpr int cy(int q) { return (int)((kPY >> (2 * q)) & 3ull) - 1; }
+__host__ __device__ constexpr int cz(int q) { return (int)((kPZ >> (2 * q)) & 3ull) - 1; }
 __host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
 // weights: 1/3 rest, 1/18 faces, 1/36 edges
 template <typename T>

@@ -104,16 +104,8 @@ __device__ __forceinline__ A warp_sum(A v) {
 }
 
 __device__ __forceinline__ int lane_c(int lane, int axis) {
-    // c_q components for q = lane < 19 (0 for idle lanes)
-    const int q = lane < 19 ? lane : 0;
-    switch (axis) {
-        case 0: return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
-                     : ((q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0);
-        case 1: return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
-                     : ((q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0);
-        default: return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
-                      : ((q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0);
-    }
+    const int q = lane < 19 ? lane : 0;   // c_q component (0 for idle lanes)
+    return axis == 0 ? cx(q) : (axis == 1 ? cy(q) : cz(q));
 }
 
 template <typename A, bool FORCED>
@@ -144,43 +136,183 @@ __device__ __forceinline__ A warp_trt_collide(A gq, int lane, const CollideParam
     return lane < 19 ? out : A(0);
 }
 
-// CLI link of Sec. 2.3 for the fluid cell at distance d from the sphere
-// centre, incoming direction q (k = opp(q) points into the solid):
-// returns the new deviation g_q and adds the link's momentum-exchange force
-// and torque (FP64, on full populations).
+// Particle quantities the link kernels need, converted once per block
+// (thread 0 fills a shared copy): Xi = floor(X) and Xh = 1/2 - (X - Xi), so
+// the offset of a cell centre p + 1/2 from the centre X is (p - Xi) + Xh
+// without cancellation in A; radius and velocities u(t + 1/2), omega(t + 1/2) in A.
 template <typename A>
-__device__ __forceinline__ A cli_link(int q, const double d[3], double r, double delta, A gt_k, A gt_q, A gt_far,
-                                      const ParticleState& Pp, double F[3], double T[3]) {
+struct LinkFrame {
+    int Xi[3];
+    A Xh[3], r, u[3], w[3];
+    __device__ __forceinline__ void init(const ParticleState& P) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double f = floor(P.x[a]);
+            Xi[a] = (int)f;
+            Xh[a] = A(0.5 - (P.x[a] - f));
+            u[a] = A(P.u[a]);
+            w[a] = A(P.w[a]);
+        }
+        r = A(P.r);
+    }
+    // d = p + 1/2 - X for cell p (minimum image on periodic axes) and the
+    // matching unwrapped coordinate pu, with d = pu + 1/2 - X.
+    __device__ __forceinline__ void offset(const int p[3], const int n[3], const int periodic[3], A d[3],
+                                           int pu[3]) const {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int v = p[a];
+            if (periodic[a]) {
+                const A t = A(v - Xi[a]) + Xh[a];
+                const A half = A(0.5) * A(n[a]);
+                v += t > half ? -n[a] : (t < -half ? n[a] : 0);
+            }
+            pu[a] = v;
+            d[a] = A(v - Xi[a]) + Xh[a];
+        }
+    }
+};
+
+// CLI link of Sec. 2.3 for the fluid cell at offset d from the sphere
+// centre, incoming direction q (k = opp(q) points into the solid): returns
+// the new deviation g_q and the link's momentum-exchange force and torque
+// without their lattice-weight part.  On full populations f = w + g the
+// link force is (c_k - v) f~_k + (c_k + v) f_q = 2 w_k c_k + fl with
+// fl = (c_k - v) g~_k + (c_k + v) g_q; the 2 w_k c_k part (and its torque
+// d x 2 w_k c_k) is summed exactly by LinkSums.  Geometry and fl are
+// evaluated in the arithmetic type A of the populations (FP64 on the FP64
+// path); use_delta = false takes the wall half-way (delta = 1/2).
+// Wall distance delta along c_k (k = opp(q)) from the cell at offset d and
+// the CLI coefficients kappa0 = (1 - 2 delta) / (1 + 2 delta) and
+// alpha = 4 / (1 + 2 delta) of Sec. 2.3; use_delta = false takes delta = 1/2.
+template <typename A>
+__device__ __forceinline__ void cli_coeffs(int q, const A d[3], bool use_delta, A r, A* delta_out, A* kappa0,
+                                           A* alpha) {
     const int k = opp(q);
-    const int ck[3] = {lane_c(k, 0), lane_c(k, 1), lane_c(k, 2)};
-    const double kappa0 = (1.0 - 2.0 * delta) / (1.0 + 2.0 * delta);
-    const double alpha = 4.0 / (1.0 + 2.0 * delta);
-    const double arm[3] = {d[0] + delta * ck[0], d[1] + delta * ck[1], d[2] + delta * ck[2]};
-    const double vb[3] = {Pp.u[0] + (Pp.w[1] * arm[2] - Pp.w[2] * arm[1]),
-                          Pp.u[1] + (Pp.w[2] * arm[0] - Pp.w[0] * arm[2]),
-                          Pp.u[2] + (Pp.w[0] * arm[1] - Pp.w[1] * arm[0])};
-    const double vc = vb[0] * ck[0] + vb[1] * ck[1] + vb[2] * ck[2];
-    const double wk = k == 0 ? 1.0 / 3.0 : (k <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-    const A gnew = gt_k + A(kappa0) * gt_far - A(kappa0) * gt_q - A(alpha * 3.0 * wk * vc);
-    const double ftk = wk + (double)gt_k;
-    const double fnew = wk + (double)gnew;
-    const double Fl[3] = {(ck[0] + vb[0]) * fnew + (ck[0] - vb[0]) * ftk,
-                          (ck[1] + vb[1]) * fnew + (ck[1] - vb[1]) * ftk,
-                          (ck[2] + vb[2]) * fnew + (ck[2] - vb[2]) * ftk};
-    F[0] += Fl[0];
-    F[1] += Fl[1];
-    F[2] += Fl[2];
-    T[0] += arm[1] * Fl[2] - arm[2] * Fl[1];
-    T[1] += arm[2] * Fl[0] - arm[0] * Fl[2];
-    T[2] += arm[0] * Fl[1] - arm[1] * Fl[0];
+    A delta = A(0.5);
+    if (use_delta) {   // smallest root in (0,1] of |d + s c_k|^2 = r^2 (|c_k|^2 is 1 or 2)
+        const A dc = d[0] * A(cx(k)) + d[1] * A(cy(k)) + d[2] * A(cz(k));
+        const A e = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - r * r;
+        const bool face = k <= 6;
+        A disc = dc * dc - (face ? e : A(2) * e);
+        disc = disc < A(0) ? A(0) : disc;
+        const A s = (-dc - sqrt(disc)) * (face ? A(1) : A(0.5));
+        delta = s < A(0) ? A(0) : (s > A(1) ? A(1) : s);
+    }
+    const A inv = A(1) / (A(1) + A(2) * delta);
+    *delta_out = delta;
+    *kappa0 = (A(1) - A(2) * delta) * inv;
+    *alpha = A(4) * inv;
+}
+
+template <typename A>
+__device__ __forceinline__ A cli_link(int q, const A d[3], bool use_delta, A gt_k, A gt_q, A gt_far,
+                                      const LinkFrame<A>& Fr, A fl[3], A tl[3]) {
+    const int k = opp(q);
+    const A c[3] = {A(cx(k)), A(cy(k)), A(cz(k))};
+    A delta, kappa0, alpha;
+    cli_coeffs<A>(q, d, use_delta, Fr.r, &delta, &kappa0, &alpha);
+    const A arm[3] = {d[0] + delta * c[0], d[1] + delta * c[1], d[2] + delta * c[2]};
+    const A vb[3] = {Fr.u[0] + (Fr.w[1] * arm[2] - Fr.w[2] * arm[1]), Fr.u[1] + (Fr.w[2] * arm[0] - Fr.w[0] * arm[2]),
+                     Fr.u[2] + (Fr.w[0] * arm[1] - Fr.w[1] * arm[0])};
+    const A vc = vb[0] * c[0] + vb[1] * c[1] + vb[2] * c[2];
+    const A wk3 = k <= 6 ? A(1) / A(6) : A(1) / A(12);   // 3 w_k
+    const A gnew = gt_k + kappa0 * gt_far - kappa0 * gt_q - alpha * wk3 * vc;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) fl[a] = (c[a] - vb[a]) * gt_k + (c[a] + vb[a]) * gnew;
+    tl[0] = arm[1] * fl[2] - arm[2] * fl[1];
+    tl[1] = arm[2] * fl[0] - arm[0] * fl[2];
+    tl[2] = arm[0] * fl[1] - arm[1] * fl[0];
     return gnew;
 }
 
-}  // namespace lbmp
+// Per-lane sums of the link forces and torques of one particle.  fl and tl
+// of every link are added in FP64.  The lattice-weight part 2 w_k c_k is
+// summed in integers: 36 * 2 w_k is 4 on faces and 2 on edges, and its
+// torque (pu + 1/2 - X) x 2 w_k c_k is carried as (2 pu + 1) x (36 * 2 w_k c_k)
+// over 72 minus X x (the force part), so it cancels exactly wherever the
+// links close around the body.
+struct LinkSums {
+    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    int iF[3] = {0, 0, 0};
+    long long iT[3] = {0, 0, 0};
 
-namespace lbmp {
+    template <typename A>
+    __device__ __forceinline__ void add(int k, const int pu[3], const A fl[3], const A tl[3]) {
+        const int m = k <= 6 ? 4 : 2;
+        const int mc[3] = {m * cx(k), m * cy(k), m * cz(k)};
+        const long long p2[3] = {2LL * pu[0] + 1, 2LL * pu[1] + 1, 2LL * pu[2] + 1};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            F[a] += (double)fl[a];
+            T[a] += (double)tl[a];
+            iF[a] += mc[a];
+        }
+        iT[0] += p2[1] * mc[2] - p2[2] * mc[1];
+        iT[1] += p2[2] * mc[0] - p2[0] * mc[2];
+        iT[2] += p2[0] * mc[1] - p2[1] * mc[0];
+    }
+    // force (v[0..2]) and torque about X (v[3..5]) of this lane's links
+    __device__ __forceinline__ void total(const double X[3], double v[6]) const {
+        const double fr[3] = {iF[0] / 36.0, iF[1] / 36.0, iF[2] / 36.0};
+        v[0] = F[0] + fr[0];
+        v[1] = F[1] + fr[1];
+        v[2] = F[2] + fr[2];
+        v[3] = T[0] + ((double)iT[0] / 72.0 - (X[1] * fr[2] - X[2] * fr[1]));
+        v[4] = T[1] + ((double)iT[1] / 72.0 - (X[2] * fr[0] - X[0] * fr[2]));
+        v[5] = T[2] + ((double)iT[2] / 72.0 - (X[0] * fr[1] - X[1] * fr[0]));
+    }
+};
 
-// Source coordinate x - c along one axis; -1 when it leaves through a wall.
+// Deterministic block sum of the threads' link sums: the FP64 parts go
+// through a shared-memory tree in a fixed order, the integer parts through
+// warp shuffles; thread 0 writes force and torque about X to out[0..5].
+// Every thread of the block must call it.
+template <int NT>
+__device__ __forceinline__ void block_link_sums(const LinkSums& acc, const double X[3], double* __restrict__ out) {
+    __shared__ double sd[6][NT];
+    __shared__ long long si[6][NT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        sd[c][tid] = acc.F[c];
+        sd[3 + c][tid] = acc.T[c];
+    }
+    long long iv[6] = {acc.iF[0], acc.iF[1], acc.iF[2], acc.iT[0], acc.iT[1], acc.iT[2]};
+#pragma unroll
+    for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) iv[c] += __shfl_down_sync(0xffffffffu, iv[c], off);
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) si[c][wid] = iv[c];
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        for (int idx = tid; idx < 6 * h; idx += NT) {
+            const int c = idx / h, i = idx - c * h;
+            sd[c][i] += sd[c][i + h];
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        LinkSums t;
+        for (int c = 0; c < 3; ++c) {
+            t.F[c] = sd[c][0];
+            t.T[c] = sd[3 + c][0];
+            long long a = 0, b = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                a += si[c][w];
+                b += si[3 + c][w];
+            }
+            t.iF[c] = (int)a;
+            t.iT[c] = b;
+        }
+        double v[6];
+        t.total(X, v);
+        for (int c = 0; c < 6; ++c) out[c] = v[c];
+    }
+}
+
 __device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
     int s = x - c;
     if (s < 0) return periodic ? s + n : -1;
@@ -188,14 +320,91 @@ __device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
     return s;
 }
 
-// Cell centre inside the closed ball.  Explicit round-to-nearest products and
-// sums (no contraction) so the predicate is evaluated exactly as written.
-__device__ __forceinline__ bool inside_ball(int i, int j, int k, const GridDesc& G, const ParticleState& P) {
-    double dx = wrap_diff(__dsub_rn((double)i + 0.5, P.x[0]), G.nx, G.periodic[0]);
-    double dy = wrap_diff(__dsub_rn((double)j + 0.5, P.x[1]), G.ny, G.periodic[1]);
-    double dz = wrap_diff(__dsub_rn((double)k + 0.5, P.x[2]), G.nz, G.periodic[2]);
-    double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+// Cell centre p + 1/2 inside the closed ball |p + 1/2 - X| <= r: the flag
+// definition, evaluated in FP64 with explicit round-to-nearest products and
+// sums (no contraction), minimum image on periodic axes.
+__device__ __forceinline__ bool inside_ball_exact(const int p[3], const int n[3], const int periodic[3],
+                                                  const ParticleState& P) {
+    const double dx = wrap_diff(__dsub_rn((double)p[0] + 0.5, P.x[0]), n[0], periodic[0]);
+    const double dy = wrap_diff(__dsub_rn((double)p[1] + 0.5, P.x[1]), n[1], periodic[1]);
+    const double dz = wrap_diff(__dsub_rn((double)p[2] + 0.5, P.x[2]), n[2], periodic[2]);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     return d2 <= __dmul_rn(P.r, P.r);
+}
+
+__device__ __forceinline__ bool inside_ball(int i, int j, int k, const GridDesc& G, const ParticleState& P) {
+    const int p[3] = {i, j, k}, n[3] = {G.nx, G.ny, G.nz};
+    return inside_ball_exact(p, n, G.periodic, P);
+}
+
+// Per-block constants of the kernels that walk the box of cells around the
+// sphere (cell o + t for t in [0, E) per axis, o from the current centre),
+// filled once by thread 0 (all of their FP64 set-up work): the box
+// origin and an FP32 pre-test of the ball predicate.  The FP32 squared
+// distance (p - Xi + Xh)^2 differs from the FP64 one by less than
+// 1e-6 (|d|^2 + 1); cells whose estimate lies below lo = r^2 - 1e-5 (r^2 + 1)
+// are inside, above hi = r^2 + 1e-5 (r^2 + 1) outside, and only the thin shell
+// in between evaluates inside_ball_exact, so every flag equals the FP64
+// definition.
+struct BoxFrame {
+    int o[3];      // first box cell per axis (0 where the box spans a periodic axis)
+    int Xi[3];     // floor(X)
+    float Xh[3];   // 1/2 - (X - Xi)
+    float lo, hi;
+};
+
+__device__ __forceinline__ void box_frame_init(BoxFrame& F, const int n[3], const int periodic[3], const BoxDesc& B,
+                                               const ParticleState& P) {
+    bool wide = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        F.o[a] = (B.E[a] >= n[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
+        const double f = floor(P.x[a]);
+        F.Xi[a] = (int)f;
+        F.Xh[a] = (float)(0.5 - (P.x[a] - f));
+        wide |= periodic[a] && P.r > 0.4 * n[a];
+    }
+    const double rr = P.r * P.r, m = 1e-5 * (rr + 1.0);
+    F.lo = wide ? -1.0f : (float)(rr - m);   // a sphere this wide takes the FP64 path everywhere
+    F.hi = wide ? 3.0e38f : (float)(rr + m);
+}
+
+// Box cell t (x fastest) -> cell p; false where the box leaves a wall-bounded axis.
+__device__ __forceinline__ bool box_cell(int t, const int n[3], const int periodic[3], const BoxDesc& B,
+                                         const BoxFrame& F, int p[3]) {
+    const int e0 = B.E[0], e1 = B.E[1];
+    const int tk = t / (e0 * e1);
+    const int r = t - tk * e0 * e1;
+    const int tj = r / e0;
+    const int tt[3] = {r - tj * e0, tj, tk};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = F.o[a] + tt[a];
+        if (v < 0 || v >= n[a]) {
+            if (!periodic[a]) return false;
+            v = v < 0 ? v + n[a] : v - n[a];   // the box is never wider than the domain
+        }
+        p[a] = v;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool ball_flag(const int p[3], const int n[3], const int periodic[3], const BoxFrame& F,
+                                          const ParticleState& P) {
+    float e = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = p[a] - F.Xi[a];
+        if (periodic[a]) {
+            const float t = (float)v + F.Xh[a], half = 0.5f * (float)n[a];
+            v += t > half ? -n[a] : (t < -half ? n[a] : 0);
+        }
+        const float t = (float)v + F.Xh[a];
+        e = fmaf(t, t, e);
+    }
+    if (e < F.lo) return true;
+    if (e > F.hi) return false;
+    return inside_ball_exact(p, n, periodic, P);
 }
 
 // Algorithm 1 after the LBM step, on the staged particle record.
@@ -260,34 +469,6 @@ __device__ __forceinline__ void particle_advance(ParticleState& P, const double 
         }
     }
     P.steps += 1;
-}
-
-// Box of cells around the sphere: cell (o + t) for t in [0, E), o from the
-// current centre.  Returns false for cells outside a walled domain.
-__device__ __forceinline__ bool box_cell(int t, const GridDesc& G, const BoxDesc& B, const ParticleState& P,
-                                         int* ci, int* cj, int* ck) {
-    const int e0 = B.E[0], e1 = B.E[1];
-    const int tk = t / (e0 * e1);
-    const int r = t - tk * e0 * e1;
-    const int tj = r / e0;
-    const int ti = r - tj * e0;
-    const int n3[3] = {G.nx, G.ny, G.nz};
-    const int tt[3] = {ti, tj, tk};
-    int c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int o = (B.E[a] >= n3[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
-        int v = o + tt[a];
-        if (v < 0 || v >= n3[a]) {
-            if (!G.periodic[a]) return false;
-            v = v < 0 ? v + n3[a] : v - n3[a];   // |v| stays within one period: the box is narrower than the domain
-        }
-        c[a] = v;
-    }
-    *ci = c[0];
-    *cj = c[1];
-    *ck = c[2];
-    return true;
 }
 
 }  // namespace lbmp

@@ -64,8 +64,10 @@ __global__ void __launch_bounds__(BULK_THREADS)
 // -------------------------------------------------------------- boundary
 // One warp per fluid cell that has a solid neighbour, lane q handling
 // population q: pulls from solid cells are replaced by the CLI rule of
-// Sec. 2.3 (momentum-exchange force and torque summed in FP64), then the
-// warp collides the cell cooperatively and writes it.
+// Sec. 2.3 (link geometry in the population arithmetic, force and torque
+// summed in FP64), then the warp collides the cell cooperatively and writes
+// it.  Each block covers 8 list entries per pass; blocks past the end of the
+// list write zero partials.
 constexpr int BNDW_THREADS = 256;
 template <typename S, bool FORCED>
 __global__ void __launch_bounds__(BNDW_THREADS)
@@ -74,24 +76,30 @@ __global__ void __launch_bounds__(BNDW_THREADS)
                CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
                double* __restrict__ partials, int* __restrict__ status) {
     using A = typename Store<S>::A;
-    __shared__ double red[6][BNDW_THREADS / 32];
+    __shared__ LinkFrame<A> Fr;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nwarps = gridDim.x * (BNDW_THREADS / 32);
     const int cnt = *count;
+    if ((int)blockIdx.x * (BNDW_THREADS / 32) >= cnt) {   // uniform across the block
+        if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 6 + threadIdx.x] = 0.0;
+        return;
+    }
+    if (threadIdx.x == 0) Fr.init(*ps);
+    __syncthreads();
     const size_t n = (size_t)G.n;
-    const ParticleState& Pp = *ps;
-    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    LinkSums acc;
     for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
         const int cell = list[w];
         const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
         A gq = A(0);
         if (lane < 19) {
             const int q = lane;
-            const int c[3] = {lane_c(q, 0), lane_c(q, 1), lane_c(q, 2)};
+            const int c[3] = {cx(q), cy(q), cz(q)};
             const int xyz[3] = {x, y, z};
-            const int n3[3] = {G.nx, G.ny, G.nz};
             int s3[3], f3[3];
             bool wall = false, far_ok = true;
+#pragma unroll
             for (int a = 0; a < 3; ++a) {
                 s3[a] = src_coord(xyz[a], c[a], n3[a], G.periodic[a]);    // x - c_q
                 f3[a] = src_coord(xyz[a], -c[a], n3[a], G.periodic[a]);   // x + c_q
@@ -111,35 +119,21 @@ __global__ void __launch_bounds__(BNDW_THREADS)
                         far = (size_t)f3[0] + (size_t)G.nx * ((size_t)f3[1] + (size_t)G.ny * (size_t)f3[2]);
                         far_ok = flags[far] == 0;
                     }
-                    const double d[3] = {wrap_diff((x + 0.5) - Pp.x[0], G.nx, G.periodic[0]),
-                                         wrap_diff((y + 0.5) - Pp.x[1], G.ny, G.periodic[1]),
-                                         wrap_diff((z + 0.5) - Pp.x[2], G.nz, G.periodic[2])};
-                    const double delta = (cli && far_ok) ? link_delta(d, k, Pp.r) : 0.5;
+                    A d[3], fl[3], tl[3];
+                    int pu[3];
+                    Fr.offset(xyz, n3, G.periodic, d, pu);
                     const A gt_k = Store<S>::load(src + (size_t)k * n + cell, P.inv_scale);
                     const A gt_q = Store<S>::load(src + (size_t)q * n + cell, P.inv_scale);
                     const A gt_far = far_ok ? Store<S>::load(src + (size_t)k * n + far, P.inv_scale) : A(0);
-                    gq = cli_link<A>(q, d, Pp.r, delta, gt_k, gt_q, gt_far, Pp, F, T);
+                    gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, fl, tl);
+                    acc.add(k, pu, fl, tl);
                 }
             }
         }
         gq = warp_trt_collide<A, FORCED>(gq, lane, P, status);
         if (lane < 19) Store<S>::store(dst + (size_t)lane * n + cell, gq, P.scale);
     }
-    // deterministic reduction: warp tree, then warps in order
-    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 6; ++k) red[k][wib] = v[k];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        double sum = 0.0;
-        for (int k = 0; k < BNDW_THREADS / 32; ++k) sum += red[threadIdx.x][k];
-        partials[(size_t)blockIdx.x * 6 + threadIdx.x] = sum;
-    }
+    block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
 }
 
 // -------------------------------------------------------------- particle
@@ -200,13 +194,16 @@ __global__ void k_flags_full(uint8_t* __restrict__ flags, GridDesc G, const Part
 
 __global__ void k_flags_box(uint8_t* __restrict__ flags_next, GridDesc G, BoxDesc B,
                             const ParticleState* __restrict__ ps) {
+    __shared__ BoxFrame F;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, B, *ps);
+    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.cells) return;
-    const ParticleState P = *ps;
-    int i, j, k;
-    if (!box_cell(t, G, B, P, &i, &j, &k)) return;
-    const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
-    flags_next[c] = inside_ball(i, j, k, G, P) ? 1 : 0;
+    int p[3];
+    if (!box_cell(t, n3, G.periodic, B, F, p)) return;
+    const size_t c = (size_t)p[0] + (size_t)G.nx * ((size_t)p[1] + (size_t)G.ny * (size_t)p[2]);
+    flags_next[c] = ball_flag(p, n3, G.periodic, F, *ps) ? 1 : 0;
 }
 
 // Cells now solid are zeroed; cells the sphere uncovered are refilled with
@@ -217,11 +214,15 @@ __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
                          GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
                          typename Store<S>::A scale, typename Store<S>::A inv_scale) {
     using A = typename Store<S>::A;
+    __shared__ BoxFrame F;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, B, *ps);
+    __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= B.cells) return;
-    const ParticleState P = *ps;
-    int i, j, k;
-    if (!box_cell(t, G, B, P, &i, &j, &k)) return;
+    int p[3];
+    if (!box_cell(t, n3, G.periodic, B, F, p)) return;
+    const int i = p[0], j = p[1], k = p[2];
     const size_t n = (size_t)G.n;
     const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
     if (fnext[c] != 0) {
@@ -231,9 +232,9 @@ __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
     }
     if (fcur[c] == 0) return;
     // uncovered cell
+    const ParticleState& P = *ps;
     A rsum = A(0);
     int cnt = 0;
-    const int n3[3] = {G.nx, G.ny, G.nz};
     for (int q = 1; q < 19; ++q) {
         int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
         bool ok = true;
@@ -278,11 +279,16 @@ __device__ __forceinline__ int wrap_idx(int v, int n) { return v < 0 ? v + n : (
 __global__ void __launch_bounds__(LINK_THREADS)
     k_links_mark(const uint8_t* __restrict__ flags, GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
                  uint8_t* __restrict__ mask, int* __restrict__ block_count) {
+    __shared__ BoxFrame F;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, B, *ps);
+    __syncthreads();
     const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
     int is_b = 0;
     if (t < B.cells) {
-        int i, j, k;
-        if (box_cell(t, G, B, *ps, &i, &j, &k)) {
+        int p[3];
+        if (box_cell(t, n3, G.periodic, B, F, p)) {
+            const int i = p[0], j = p[1], k = p[2];
             const int nx = G.nx, ny = G.ny;
             const int c = i + nx * (j + ny * k);
             if (flags[c] == 0) {
@@ -316,6 +322,9 @@ __global__ void __launch_bounds__(LINK_THREADS)
                  int* __restrict__ status) {
     __shared__ int red[LINK_THREADS];
     __shared__ int wsum[LINK_THREADS / 32];
+    __shared__ BoxFrame F;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, B, *ps);
     // offset of this block: sum of the counts of all earlier blocks
     int s = 0;
     for (int b = threadIdx.x; b < (int)blockIdx.x; b += LINK_THREADS) s += block_count[b];
@@ -335,10 +344,10 @@ __global__ void __launch_bounds__(LINK_THREADS)
     int wbase = 0;
     for (int w = 0; w < warp; ++w) wbase += wsum[w];
     if (is_b) {
-        int i, j, k;
-        box_cell(t, G, B, *ps, &i, &j, &k);
+        int p[3];
+        box_cell(t, n3, G.periodic, B, F, p);
         const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
-        if (pos < capacity) list[pos] = i + G.nx * (j + G.ny * k);
+        if (pos < capacity) list[pos] = p[0] + G.nx * (p[1] + G.ny * p[2]);
         else atomicOr(status, STATUS_LINK_OVERFLOW);
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
