@@ -278,8 +278,10 @@ const char* lbmp_last_error(const lbmp_handle* h);
  * lbmp_drag_forward runs the nsteps steps (the handle's populations end at
  * the last one) and keeps every checkpoint_interval-th field for the reverse
  * pass (ceil(nsteps / interval) + interval fields of device memory).
- *   u0  device array [3][nz][ny][nx] of doubles (x fastest), read during the call
- *   J   device double, receives J
+ *   u0      device array [3][nz][ny][nx] of doubles (x fastest), read during the call
+ *   J       device double, receives J
+ *   forces  device array [nsteps][3] of doubles receiving the force of every
+ *           step (may be NULL)
  * lbmp_drag_backward then forms, by the adjoint of the step with checkpoint
  * and recompute, the derivatives of J times the device scalar dJ:
  *   grad_tau    device double, dJ * dJ/dtau               (may be NULL)
@@ -292,7 +294,7 @@ const char* lbmp_last_error(const lbmp_handle* h);
  * storage, walls, or a sphere that moves; LBMP_ERR_INVALID_ARG for bad
  * arguments or a backward call without its forward call; LBMP_ERR_OOM. */
 lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int checkpoint_interval, int axis,
-                              double* J);
+                              double* J, double* forces);
 lbmp_status lbmp_drag_backward(lbmp_handle* h, const double* dJ, double* grad_tau, double* grad_force,
                                double* grad_u0);
 

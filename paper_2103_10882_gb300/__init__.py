@@ -315,10 +315,10 @@ def lbmp_last_error(h=None):
     return m.decode() if m else ""
 
 
-def lbmp_drag_forward(h, u0_ptr, nsteps, checkpoint_interval, axis, J_ptr):
-    """Device pointers: u0 [3][nz][ny][nx] float64, J one float64."""
+def lbmp_drag_forward(h, u0_ptr, nsteps, checkpoint_interval, axis, J_ptr, forces_ptr=0):
+    """Device pointers: u0 [3][nz][ny][nx] float64, J one float64, forces [nsteps][3] float64 (0: not wanted)."""
     _check(h, _lib().lbmp_drag_forward(h, ctypes.c_void_p(u0_ptr), int(nsteps), int(checkpoint_interval), int(axis),
-                                       ctypes.c_void_p(J_ptr)))
+                                       ctypes.c_void_p(J_ptr), ctypes.c_void_p(forces_ptr or None)))
 
 
 def lbmp_drag_backward(h, dJ_ptr, grad_tau_ptr, grad_force_ptr, grad_u0_ptr):

@@ -100,7 +100,7 @@ SIGNATURES = {
     "lbmp_batch_get_populations": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, ctypes.c_size_t]),
     "lbmp_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "lbmp_drag_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                         ctypes.c_void_p]),
+                                         ctypes.c_void_p, ctypes.c_void_p]),
     "lbmp_drag_backward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p]),
 }

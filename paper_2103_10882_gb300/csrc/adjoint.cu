@@ -243,14 +243,15 @@ __global__ void __launch_bounds__(AT)
             for (int q = 0; q < 19; ++q) nu_out[(size_t)q * n + x] = A(0);
         } else if (kd == KIND_PLAIN) {
             const int i = (int)(x % G.nx), j = (int)((x / G.nx) % G.ny), k = (int)(x / ((long long)G.nx * G.ny));
+            // xs[1 + d] = i - d: the pull source x - c_q at index 1 + c, x + c_q at 1 - c
             const int xs[3] = {wrapc(i + 1, G.nx), i, wrapc(i - 1, G.nx)};
             const int ys[3] = {wrapc(j + 1, G.ny), j, wrapc(j - 1, G.ny)};
             const int zs[3] = {wrapc(k + 1, G.nz), k, wrapc(k - 1, G.nz)};
             A h[19], lam[19];
 #pragma unroll
             for (int q = 0; q < 19; ++q) {
-                const size_t src = (size_t)xs[1 - cx(q)] + (size_t)G.nx * ((size_t)ys[1 - cy(q)] + (size_t)G.ny * zs[1 - cz(q)]);
-                const size_t dn = (size_t)xs[1 + cx(q)] + (size_t)G.nx * ((size_t)ys[1 + cy(q)] + (size_t)G.ny * zs[1 + cz(q)]);
+                const size_t src = (size_t)xs[1 + cx(q)] + (size_t)G.nx * ((size_t)ys[1 + cy(q)] + (size_t)G.ny * zs[1 + cz(q)]);
+                const size_t dn = (size_t)xs[1 - cx(q)] + (size_t)G.nx * ((size_t)ys[1 - cy(q)] + (size_t)G.ny * zs[1 - cz(q)]);
                 h[q] = Store<S>::load(gprev + (size_t)q * n + src, A(1));
                 lam[q] = nu_next[(size_t)q * n + dn];
             }
@@ -532,7 +533,8 @@ lbmp_status adjoint_check(const lbmp_handle* h, std::string* why) {
     return LBMP_OK;
 }
 
-lbmp_status adjoint_forward(lbmp_handle* h, const double* u0, int nsteps, int interval, int axis, double* J) {
+lbmp_status adjoint_forward(lbmp_handle* h, const double* u0, int nsteps, int interval, int axis, double* J,
+                            double* forces) {
     if (!h->adj) h->adj = new AdjointEngine();
     AdjointEngine* E = h->adj;
     const size_t n = (size_t)h->G.n;
@@ -600,6 +602,8 @@ lbmp_status adjoint_forward(lbmp_handle* h, const double* u0, int nsteps, int in
     });
     k_adj_mean<<<1, 32, 0, h->stream>>>(E->forces, nsteps, axis, J);
     h->launches += 3;
+    if (forces)
+        cudaMemcpyAsync(forces, E->forces, sizeof(double) * 3 * (size_t)nsteps, cudaMemcpyDeviceToDevice, h->stream);
     E->forward_done = true;
     if (cudaGetLastError() != cudaSuccess) return LBMP_ERR_CUDA;
     return LBMP_OK;

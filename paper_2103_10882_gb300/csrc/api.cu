@@ -903,7 +903,7 @@ lbmp_status lbmp_batch_get_populations(lbmp_handle* h, int sim, double* out, siz
 }
 
 lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int checkpoint_interval, int axis,
-                              double* J) {
+                              double* J, double* forces) {
     if (!h) return LBMP_ERR_INVALID_ARG;
     if (!u0 || !J) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_forward: NULL argument");
     if (nsteps < 1 || checkpoint_interval < 1 || axis < 0 || axis > 2)
@@ -913,7 +913,7 @@ lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int 
     std::string why;
     s = adjoint_check(h, &why);
     if (s != LBMP_OK) return fail(h, s, "lbmp_drag_forward: " + why);
-    s = adjoint_forward(h, u0, nsteps, checkpoint_interval, axis, J);
+    s = adjoint_forward(h, u0, nsteps, checkpoint_interval, axis, J, forces);
     if (s == LBMP_ERR_OOM) return fail(h, s, "lbmp_drag_forward: out of device memory for the checkpoints");
     if (s != LBMP_OK) return fail(h, s, "lbmp_drag_forward: CUDA launch failed");
     return LBMP_OK;
