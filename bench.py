@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -260,6 +262,69 @@ def roofline(prof, kernel, traffic):
             "kernel_ms_total": kms}
 
 
+def adjoint_line(L, workloads, torch, prec, reps):
+    """Gradient of the mean drag on the differentiation workload: forward
+    (500 steps, checkpoints every 50) and backward (recompute + reverse
+    sweep) timed with CUDA events, and the roofline of the reverse-step
+    kernel from events around each of its launches."""
+    import numpy as np
+    c = workloads.ADJOINT_64
+    off = workloads.sub_cell_offset(7)
+    pos = tuple(0.5 * n + o for n, o in zip(c["shape"], off))
+    sim = L.Simulation(c["shape"], precision=prec, tau=c["tau"])
+    sim.add_sphere(pos, c["diameter"], 1.0)
+    sim.set_fixed(True)
+    sim.set_body_force((c["body_force"], 0.0, 0.0))
+    dev = torch.device("cuda")
+    u0 = torch.tensor(workloads.fourier_velocity_field(c["shape"], c["kmax"], c["amplitude"], 7),
+                      dtype=torch.float64, device=dev)
+    J = torch.empty((), dtype=torch.float64, device=dev)
+    one = torch.ones((), dtype=torch.float64, device=dev)
+    gt = torch.empty((), dtype=torch.float64, device=dev)
+    gf = torch.empty(3, dtype=torch.float64, device=dev)
+    gu = torch.empty_like(u0)
+    N, K = c["steps"], c["checkpoint"]
+
+    def fwd():
+        L.lbmp_drag_forward(sim.h, u0.data_ptr(), N, K, 0, J.data_ptr())
+
+    def bwd():
+        L.lbmp_drag_backward(sim.h, one.data_ptr(), gt.data_ptr(), gf.data_ptr(), gu.data_ptr())
+
+    fwd()
+    bwd()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tf, tb = [], []
+    for _ in range(reps):
+        ev[0].record(sim.stream)
+        fwd()
+        ev[1].record(sim.stream)
+        bwd()
+        ev[2].record(sim.stream)
+        torch.cuda.synchronize()
+        tf.append(ev[0].elapsed_time(ev[1]))
+        tb.append(ev[1].elapsed_time(ev[2]))
+    sim.check()
+    sim.profile(True)
+    bwd()
+    torch.cuda.synchronize()
+    prof = sim.profile_result()
+    sim.profile(False)
+    n = int(np.prod(c["shape"]))
+    out = {
+        "workload": "gradient of the mean drag over 500 steps: 64^3 periodic, fixed sphere d=12, g_x=1e-6, "
+                    "Fourier u0 |k|<=4 amplitude 1e-3, checkpoints every 50, %s" % prec,
+        "ms_forward": float(np.median(tf)), "ms_backward": float(np.median(tb)),
+        "reverse_mlups": N * n / (float(np.median(tb)) * 1e-3) / 1e6,
+        "J": J.item(), "dJ_dtau": gt.item(), "dJ_dgx": gf[0].item(),
+        "roofline": roofline(prof, "k_adj_plain (reverse stream-collide, %s)" % prec, None),
+        "bytes_per_cell_reverse": 19 * (8 if prec == "fp64" else 4) * 3,
+    }
+    sim.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -375,6 +440,9 @@ def main():
             "roofline": roofline(bprof, "k_batch_bulk (%s)" % prec, None),
             "clocks": clk_b.summary(),
         }
+    # --------------------------------------------- differentiation (adjoint)
+    if not args.no_adjoint:
+        line["adjoint64"] = adjoint_line(L, workloads, torch, "fp64" if prec == "fp64" else "fp32", args.adjoint_reps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if dist:

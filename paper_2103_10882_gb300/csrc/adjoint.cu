@@ -640,7 +640,11 @@ lbmp_status adjoint_backward(lbmp_handle* h, const double* dJ, double* grad_tau,
                 const S* gprev = state<S>(E, m, s - 1 - s0, n);
                 const A* nu_next = (const A*)E->nu[cur];
                 A* nu_out = (A*)E->nu[1 - cur];
+                const long long ev = profile_mark(h);
                 k_adj_plain<S><<<gb, AT, 0, h->stream>>>(gprev, nu_next, nu_out, E->kind, h->G, P, E->acc);
+                // algorithmic bytes: 19 populations of g^{n-1} read, 19 adjoint values read and written per cell
+                const double cells = (double)n - (double)E->near_cells;
+                profile_kernel(h, ev, profile_mark(h), cells * (19.0 * sizeof(S) + 38.0 * sizeof(A)), cells);
                 k_adj_near<S><<<gn, AT, 0, h->stream>>>(gprev, nu_next, nu_out, h->flags[h->fcur], E->near_list,
                                                        E->near_count, h->G, P, h->d_ps, cli, s < N ? 1 : 0,
                                                        E->acc + (size_t)5 * E->plain_blocks);

@@ -115,14 +115,15 @@ template <typename S>
 __global__ void __launch_bounds__(UPD_THREADS)
     k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0, S* __restrict__ f1,
               typename Store<S>::A kp, typename Store<S>::A km, int rescale, typename Store<S>::A scale,
-              typename Store<S>::A inv_scale, int* __restrict__ status) {
+              typename Store<S>::A inv_scale, const int* __restrict__ list, int n, int* __restrict__ status) {
     using A = typename Store<S>::A;
-    const int gb = blockIdx.x >> 4;
-    const int b = F.nreal + gb;
+    const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
+    if (i >= n) return;
+    const int e = list[i];   // ghost cell in use: pool block << 12 | cell
+    const int b = e >> 12;
     const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
     {
-        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
-        if (!F.gkind[(size_t)gb * B3 + c]) return;
+        const int c = e & 4095;
         const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
         int pc;
         const int pb = locate(C, p, &pc);
@@ -226,11 +227,15 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
                         g[q] = A(0);
                         continue;
                     }
-                    A f[19];
+                    if (U.rescale) {   // the rescaled value needs the whole cell
+                        A f[19];
 #pragma unroll
-                    for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
-                    if (U.rescale) rescale19<A>(f, U.ckp, U.ckm);
-                    g[q] = f[q];
+                        for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
+                        rescale19<A>(f, U.ckp, U.ckm);
+                        g[q] = f[q];
+                    } else {
+                        g[q] = Store<S>::load(U.csrc + paddr(pb, q, pc), inv);
+                    }
                     continue;
                 }
             }
@@ -242,33 +247,35 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
     for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], scale);
 }
 
-// Real blocks: one CTA per z-slice of a block (256 cells, full warps).
+// One launch per level step: the first gblocks CTAs stream the active ghost
+// cells of the level (from a list of pool block << 12 | cell, no collision;
+// static ghost cells keep the values the explosion wrote into both
+// buffers); the others update the real blocks, one CTA per z-slice of a
+// block (256 cells, full warps).  Both read src and write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
-__global__ void __launch_bounds__(UPD_THREADS) k_update(UpdateArgs<S> U) {
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int gblocks) {
     using A = typename Store<S>::A;
+    if (HAS_COARSE && (int)blockIdx.x < gblocks) {   // uniform across the block
+        const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
+        if (i < nglist) {
+            const int e = glist[i];
+            const int b = e >> 12, c = e & 4095;
+            update_cell<S, false, true, false>(U, b, c, U.D.nbr + (size_t)b * 27);
+        }
+        return;
+    }
     __shared__ int nb27[27];
-    const int b = blockIdx.x >> 4;
+    const int b = (blockIdx.x - gblocks) >> 4;
     if (threadIdx.x < 27) nb27[threadIdx.x] = U.D.nbr[b * 27 + threadIdx.x];
     __syncthreads();
-    const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
+    const int c = (((blockIdx.x - gblocks) & 15) << 8) + threadIdx.x;
     if (COUPLED && U.solid[(size_t)b * B3 + c]) {
 #pragma unroll
         for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), U.P.scale);
         return;
     }
     update_cell<S, HAS_FINE, HAS_COARSE, true>(U, b, c, nb27);
-}
-
-// Active ghost cells (sub-cells of the coarser level's hosts), from a list of
-// (pool block << 12 | cell): stream without collision.  Static ghost cells
-// keep the values the explosion wrote into both buffers.
-template <typename S>
-__global__ void __launch_bounds__(UPD_THREADS) k_ghost_stream(UpdateArgs<S> U, const int* __restrict__ list, int n) {
-    const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
-    if (i >= n) return;
-    const int e = list[i];
-    const int b = e >> 12, c = e & 4095;
-    update_cell<S, false, true, false>(U, b, c, U.D.nbr + (size_t)b * 27);
 }
 
 // ---------------------------------------------------------------- coupling
@@ -289,13 +296,14 @@ constexpr int BNDW_THREADS = 256;
 // One warp per boundary cell of the finest level, lane q handling population
 // q (CLI links of Sec. 2.3: geometry in the population arithmetic, FP64
 // force partials), cooperative collision.  Blocks past the end of the list
-// write zero partials.
+// write zero partials.  The block that finishes last sums the partials and
+// runs the particle update of Algorithm 1 (no separate launch).
 template <typename S>
 __global__ void __launch_bounds__(BNDW_THREADS)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
                    const int* __restrict__ list, const int* __restrict__ count,
-                   CollideParams<typename Store<S>::A> P, const ParticleState* __restrict__ ps, int cli,
-                   double* __restrict__ partials, int* __restrict__ status) {
+                   CollideParams<typename Store<S>::A> P, ParticleState* ps, int cli, double* partials,
+                   int* done, GridDesc G, double* __restrict__ history, int hist_cap, int* __restrict__ status) {
     using A = typename Store<S>::A;
     __shared__ LinkFrame<A> Fr;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -303,123 +311,73 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     const int cnt = *count;
     if ((int)blockIdx.x * (BNDW_THREADS / 32) >= cnt) {   // uniform across the block
         if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 6 + threadIdx.x] = 0.0;
-        return;
-    }
-    if (threadIdx.x == 0) Fr.init(*ps);
-    __syncthreads();
-    LinkSums acc;
-    for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
-        const int e = list[w];
-        const int b = e >> 12, c = e & 4095;
-        const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
-        A gq = A(0);
-        if (lane < 19) {
-            const int q = lane;
-            const int cq[3] = {lane_c(q, 0), lane_c(q, 1), lane_c(q, 2)};
-            int sc;
-            const int sb = nbr_cell(D, b, lx, ly, lz, -cq[0], -cq[1], -cq[2], &sc);
-            if (sb == -2) {
-                gq = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
-            } else if (sb < 0) {
-                atomicOr(status, STATUS_AMR_MISSING);
-            } else if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] == 0) {
-                gq = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
-            } else {
-                const int k = opp(q);
-                int fc;
-                const int fb = nbr_cell(D, b, lx, ly, lz, cq[0], cq[1], cq[2], &fc);   // x - c_k
-                const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
-                const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly, D.bpos[3 * b + 2] * BS + lz};
-                A d[3], fl[3], tl[3];
-                int pu[3];
-                Fr.offset(g, D.n, D.periodic, d, pu);
-                const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
-                const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
-                const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
-                gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, fl, tl);
-                acc.add(k, pu, fl, tl);
+    } else {
+        if (threadIdx.x == 0) Fr.init(*ps);
+        __syncthreads();
+        LinkSums acc;
+        for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
+            const int e = list[w];
+            const int b = e >> 12, c = e & 4095;
+            const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
+            A gq = A(0);
+            if (lane < 19) {
+                const int q = lane;
+                const int cq[3] = {cx(q), cy(q), cz(q)};
+                int sc;
+                const int sb = nbr_cell(D, b, lx, ly, lz, -cq[0], -cq[1], -cq[2], &sc);
+                if (sb == -2) {
+                    gq = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
+                } else if (sb < 0) {
+                    atomicOr(status, STATUS_AMR_MISSING);
+                } else if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] == 0) {
+                    gq = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
+                } else {
+                    const int k = opp(q);
+                    int fc;
+                    const int fb = nbr_cell(D, b, lx, ly, lz, cq[0], cq[1], cq[2], &fc);   // x - c_k
+                    const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
+                    const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly,
+                                      D.bpos[3 * b + 2] * BS + lz};
+                    A d[3], fl[3], tl[3];
+                    int pu[3];
+                    Fr.offset(g, D.n, D.periodic, d, pu);
+                    const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
+                    const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
+                    const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
+                    gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, fl, tl);
+                    acc.add(k, pu, fl, tl);
+                }
             }
+            gq = warp_trt_collide<A, false>(gq, lane, P, status);
+            if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
         }
-        gq = warp_trt_collide<A, false>(gq, lane, P, status);
-        if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
+        block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
     }
-    block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
-}
-
-// Box of finest cells around the sphere (same box as the uniform engine's).
-__global__ void k_amr_flags_box(LevelView D, uint8_t* __restrict__ fnext, BoxDesc B,
-                                const ParticleState* __restrict__ ps, int* __restrict__ status) {
-    __shared__ BoxFrame F;
-    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= B.cells) return;
-    int g[3];
-    if (!box_cell(t, D.n, D.periodic, B, F, g)) return;
-    int c;
-    const int b = locate(D, g, &c);
-    if (b < 0 || b >= D.nreal) {
-        atomicOr(status, STATUS_NOT_FINEST);
-        return;
-    }
-    fnext[(size_t)b * B3 + c] = ball_flag(g, D.n, D.periodic, F, *ps) ? 1 : 0;
-}
-
-template <typename S>
-__global__ void k_amr_refill(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ fcur,
-                             const uint8_t* __restrict__ fnext, BoxDesc B, const ParticleState* __restrict__ ps,
-                             typename Store<S>::A scale, typename Store<S>::A inv_scale) {
-    using A = typename Store<S>::A;
-    __shared__ BoxFrame F;
-    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= B.cells) return;
-    const ParticleState& P = *ps;
-    int g[3];
-    if (!box_cell(t, D.n, D.periodic, B, F, g)) return;
-    int c;
-    const int b = locate(D, g, &c);
-    if (b < 0 || b >= D.nreal) return;
-    const size_t x = (size_t)b * B3 + c;
-    if (fnext[x] != 0) {
-        for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
-        return;
-    }
-    if (fcur[x] == 0) return;
-    A rsum = A(0);
-    int cnt = 0;
-    for (int q = 1; q < 19; ++q) {
-        int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
-        if (!wrap3(v, D)) continue;
-        int vc;
-        const int vb = locate(D, v, &vc);
-        if (vb < 0 || vb >= D.nreal) continue;
-        const size_t y = (size_t)vb * B3 + vc;
-        if (fcur[y] != 0 || fnext[y] != 0) continue;
-        A r = A(1);
-        for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
-        rsum += r;
-        cnt += 1;
-    }
-    const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
-    const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
-                         wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
-                         wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
-    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
-                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
-    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), geq_dev<A>(q, rho - A(1), u, uu), scale);
+    if (last_block_done(done)) particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status);
 }
 
 constexpr int LINK_THREADS = 256;
 
+// Remap of Sec. 2.3 after the particle moved, over the box of finest cells
+// around the sphere, in one pass: the new solid flag of every cell (the
+// exact ball predicate); covered cells drop their populations; uncovered
+// cells are refilled with the equilibrium at the mean density of the
+// neighbours that are fluid before and after and the rigid-body velocity
+// u_p + omega_p x (x - x_p); fluid cells with a solid neighbour are marked
+// for the boundary list (counts per block for the ordered compaction).
+// Neighbour flags are evaluated from the same predicate instead of being
+// read back, so no second pass is needed.
+template <typename S>
 __global__ void __launch_bounds__(LINK_THREADS)
-    k_amr_links_mark(LevelView D, const uint8_t* __restrict__ flags, BoxDesc B, const ParticleState* __restrict__ ps,
-                     uint8_t* __restrict__ mask, int* __restrict__ block_count) {
+    k_amr_remap(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
+                BoxDesc B, const ParticleState* __restrict__ ps, typename Store<S>::A scale,
+                typename Store<S>::A inv_scale, uint8_t* __restrict__ mask, int* __restrict__ block_count,
+                int* __restrict__ status) {
+    using A = typename Store<S>::A;
     __shared__ BoxFrame F;
     if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
     __syncthreads();
+    const ParticleState& P = *ps;
     const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
     int is_b = 0;
     if (t < B.cells) {
@@ -427,13 +385,45 @@ __global__ void __launch_bounds__(LINK_THREADS)
         if (box_cell(t, D.n, D.periodic, B, F, g)) {
             int c;
             const int b = locate(D, g, &c);
-            if (b >= 0 && b < D.nreal && flags[(size_t)b * B3 + c] == 0) {
-                for (int q = 1; q < 19; ++q) {
-                    int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
-                    if (!wrap3(v, D)) continue;
-                    int vc;
-                    const int vb = locate(D, v, &vc);
-                    if (vb >= 0 && vb < D.nreal && flags[(size_t)vb * B3 + vc] != 0) is_b = 1;
+            if (b < 0 || b >= D.nreal) {
+                atomicOr(status, STATUS_NOT_FINEST);
+            } else {
+                const size_t x = (size_t)b * B3 + c;
+                const bool solid = ball_flag(g, D.n, D.periodic, F, P);
+                fnext[x] = solid ? 1 : 0;
+                if (solid) {
+#pragma unroll
+                    for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
+                } else {
+                    const bool uncovered = fcur[x] != 0;
+                    A rsum = A(0);
+                    int cnt = 0;
+                    for (int q = 1; q < 19; ++q) {
+                        int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
+                        if (!wrap3(v, D)) continue;
+                        const bool vs = ball_flag(v, D.n, D.periodic, F, P);
+                        is_b |= vs ? 1 : 0;
+                        if (!uncovered || vs) continue;
+                        int vc;
+                        const int vb = locate(D, v, &vc);
+                        if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] != 0) continue;
+                        A r = A(1);
+                        for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
+                        rsum += r;
+                        cnt += 1;
+                    }
+                    if (uncovered) {
+                        const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
+                        const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
+                                             wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
+                                             wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
+                        const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])),
+                                        A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                                        A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+                        const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                        for (int q = 0; q < 19; ++q)
+                            Store<S>::store(pops + paddr(b, q, c), geq_dev<A>(q, rho - A(1), u, uu), scale);
+                    }
                 }
             }
         }
@@ -699,6 +689,8 @@ struct Level {
     uint8_t* d_gkind = nullptr;
     int* d_glist = nullptr;      // active ghost cells: pool block << 12 | cell
     int nglist = 0;
+    int* d_xlist = nullptr;      // every ghost cell in use (active or static), same encoding
+    int nxlist = 0;
     void* d_pops[2] = {nullptr, nullptr};
     int cur = 0;
     uint8_t* d_flags[2] = {nullptr, nullptr};   // finest level only
@@ -724,6 +716,7 @@ struct AmrEngine {
     long long graph_launches = 0, graph_updates = 0;
     double graph_tau = 0.0;
     cudaStream_t capture_stream = nullptr;   // private stream used only for capturing
+    int* d_done = nullptr;   // last-block-done counter of the boundary kernel (zero between launches)
 };
 
 void amr_drop_graphs(AmrEngine* E) {
@@ -898,6 +891,7 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_host);
     handle_free(h, V.d_gkind);
     handle_free(h, V.d_glist);
+    handle_free(h, V.d_xlist);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
     handle_free(h, V.d_flags[0]);
@@ -1041,14 +1035,20 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             cudaStreamSynchronize(h->stream) != cudaSuccess)
             return LBMP_ERR_CUDA;
         h->d2h += (long long)kinds.size();
-        std::vector<int> list;
+        std::vector<int> list, used;
         for (int gb = 0; gb < F.nghost; ++gb)
-            for (int c = 0; c < B3; ++c)
-                if (kinds[(size_t)gb * B3 + c] == 1) list.push_back(((F.nreal + gb) << 12) | c);
+            for (int c = 0; c < B3; ++c) {
+                const uint8_t k = kinds[(size_t)gb * B3 + c];
+                if (k == 1) list.push_back(((F.nreal + gb) << 12) | c);
+                if (k != 0) used.push_back(((F.nreal + gb) << 12) | c);
+            }
         F.nglist = (int)list.size();
         F.d_glist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>(list.size(), 1));
-        if (!F.d_glist) return LBMP_ERR_OOM;
+        F.nxlist = (int)used.size();
+        F.d_xlist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>(used.size(), 1));
+        if (!F.d_glist || !F.d_xlist) return LBMP_ERR_OOM;
         if (upload(h, F.d_glist, list.data(), sizeof(int) * list.size())) return LBMP_ERR_CUDA;
+        if (upload(h, F.d_xlist, used.data(), sizeof(int) * used.size())) return LBMP_ERR_CUDA;
     }
     // populations from the old layout
     if (!old.empty()) {
@@ -1091,13 +1091,18 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             });
         }
         Ff.fcur = 0;
+        // boundary cells of the current position (both flag buffers already hold its flags,
+        // so the remap pass only marks: nothing is covered or uncovered)
         const unsigned nb = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
-        k_amr_links_mark<<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), Ff.d_flags[0], h->box, h->d_ps,
-                                                             h->link_mask, h->link_blocks);
+        with_storage_amr(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            using A = typename Store<S>::A;
+            k_amr_remap<S><<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), (S*)Ff.d_pops[Ff.cur], Ff.d_flags[1],
+                                                               Ff.d_flags[0], h->box, h->d_ps, (A)1, (A)1,
+                                                               h->link_mask, h->link_blocks, h->status);
+        });
         k_amr_links_emit<<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), h->link_mask, h->link_blocks, h->box, h->d_ps,
                                                              h->list, h->count, h->list_cap, h->status);
-        k_amr_flags_box<<<(unsigned)((h->box.cells + 255) / 256), 256, 0, h->stream>>>(view(E, Ff), Ff.d_flags[1], h->box,
-                                                                                       h->d_ps, h->status);
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return LBMP_OK;
@@ -1146,10 +1151,10 @@ void enqueue_advance(lbmp_handle* h, int l) {
         Level& F = E->lv[l + 1];
         double kp, km;
         kappa_post(V, F, &kp, &km);
-        if (F.nghost > 0) {
-            k_explode<S><<<(unsigned)F.nghost * 16, UPD_THREADS, 0, h->stream>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
-                                                                  (S*)F.d_pops[0], (S*)F.d_pops[1], (A)kp, (A)km,
-                                                                  rescale, P.scale, P.inv_scale, h->status);
+        if (F.nxlist > 0) {
+            k_explode<S><<<(unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, h->stream>>>(
+                view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[0], (S*)F.d_pops[1], (A)kp, (A)km,
+                rescale, P.scale, P.inv_scale, F.d_xlist, F.nxlist, h->status);
             h->launches += 1;
         }
         E->substep[l + 1] = 0;
@@ -1193,19 +1198,17 @@ void enqueue_advance(lbmp_handle* h, int l) {
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) U.solid = V.d_flags[V.fcur];
     const long long ev0 = profile_mark(h);
-    if (V.nreal > 0) {
-        const unsigned grid = (unsigned)V.nreal * 16;
-        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
-        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
-        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, h->stream>>>(U);
-        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
-        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, h->stream>>>(U);
-        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U);
-        h->launches += 1;
-    }
-    if (V.nglist > 0 && has_coarse) {
-        k_ghost_stream<S><<<(unsigned)((V.nglist + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, h->stream>>>(
-            U, V.d_glist, V.nglist);
+    const int ng = has_coarse ? V.nglist : 0;
+    const int gblocks = (ng + UPD_THREADS - 1) / UPD_THREADS;
+    if (V.nreal > 0 || gblocks > 0) {
+        const unsigned grid = (unsigned)(V.nreal * 16 + gblocks);
+        const int* gl = V.d_glist;
+        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
+        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
+        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
+        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
+        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
+        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
         h->launches += 1;
     }
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
@@ -1213,27 +1216,24 @@ void enqueue_advance(lbmp_handle* h, int l) {
     if (coupled) {
         const LevelView D = view(E, V);
         const int nb = E->boundary_blocks;
-        k_amr_boundary<S><<<nb, BNDW_THREADS, 0, h->stream>>>(D, U.src, U.dst, U.solid, h->list, h->count, P, h->d_ps,
-                                                              h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials,
-                                                              h->status);
         GridDesc G;
         G.nx = V.n[0];
         G.ny = V.n[1];
         G.nz = V.n[2];
         for (int a = 0; a < 3; ++a) G.periodic[a] = E->periodic[a];
         G.n = (long long)V.n[0] * V.n[1] * V.n[2];
-        launch_particle_update(h->d_ps, h->partials, nb, G, h->history, h->cfg.history_capacity, h->status, h->stream);
+        k_amr_boundary<S><<<nb, BNDW_THREADS, 0, h->stream>>>(D, U.src, U.dst, U.solid, h->list, h->count, P, h->d_ps,
+                                                              h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials,
+                                                              E->d_done, G, h->history, h->cfg.history_capacity,
+                                                              h->status);
         uint8_t* fnext = V.d_flags[1 - V.fcur];
-        const unsigned bc = (unsigned)((h->box.cells + 255) / 256);
-        k_amr_flags_box<<<bc, 256, 0, h->stream>>>(D, fnext, h->box, h->d_ps, h->status);
-        k_amr_refill<S><<<bc, 256, 0, h->stream>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
-                                                    P.inv_scale);
         const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
-        k_amr_links_mark<<<nl, LINK_THREADS, 0, h->stream>>>(D, fnext, h->box, h->d_ps, h->link_mask, h->link_blocks);
+        k_amr_remap<S><<<nl, LINK_THREADS, 0, h->stream>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
+                                                           P.inv_scale, h->link_mask, h->link_blocks, h->status);
         k_amr_links_emit<<<nl, LINK_THREADS, 0, h->stream>>>(D, h->link_mask, h->link_blocks, h->box, h->d_ps, h->list,
                                                              h->count, h->list_cap, h->status);
         V.fcur = 1 - V.fcur;
-        h->launches += 7;
+        h->launches += 3;
     }
     V.cur = 1 - V.cur;
 }
@@ -1256,6 +1256,9 @@ lbmp_status amr_create(lbmp_handle* h) {
     E->n0[2] = h->cfg.nz;
     for (int a = 0; a < 3; ++a) E->periodic[a] = h->cfg.bc[a] == LBMP_PERIODIC ? 1 : 0;
     h->amr = E;
+    E->d_done = (int*)handle_alloc(h, sizeof(int));
+    if (!E->d_done) return LBMP_ERR_OOM;
+    if (cudaMemsetAsync(E->d_done, 0, sizeof(int), h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return regrid_now(h);
 }
 
@@ -1512,8 +1515,8 @@ int amr_launches_per_coarse_step(const lbmp_handle* h) {
     const AmrEngine* E = h->amr;
     int per = 0;
     for (int l = E->L - 1; l >= 0; --l) {
-        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nghost > 0) ? 1 : 0) + (E->lv[l].nglist > 0 ? 1 : 0) +
-                  ((l == E->L - 1 && h->has_particle) ? 7 : 0);
+        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nxlist > 0) ? 1 : 0) +
+                  ((l == E->L - 1 && h->has_particle) ? 3 : 0);
         per = own + 2 * per;
     }
     return per;

@@ -471,4 +471,64 @@ __device__ __forceinline__ void particle_advance(ParticleState& P, const double 
     P.steps += 1;
 }
 
+// Particle update by one thread block of NT threads: sums the nblocks
+// force partials in a fixed order, stages the record in shared memory,
+// advances it on thread 0 (particle_advance) and writes it back.  The
+// partials may come from other blocks of the same launch: they are read
+// through L2.
+template <int NT>
+__device__ __forceinline__ void particle_block_update(ParticleState* __restrict__ ps, const double* partials,
+                                                      int nblocks, const GridDesc& G, double* __restrict__ history,
+                                                      int hist_cap, int* __restrict__ status) {
+    __shared__ double red[6][NT];
+    __shared__ ParticleState sP;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += NT)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) v[c] += __ldcg(partials + (size_t)b * 6 + c);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) red[c][threadIdx.x] = v[c];
+    {
+        const int words = (int)(sizeof(ParticleState) / sizeof(int));
+        const int* srcw = reinterpret_cast<const int*>(ps);
+        int* dstw = reinterpret_cast<int*>(&sP);
+        for (int i = threadIdx.x; i < words; i += NT) dstw[i] = __ldcg(srcw + i);
+    }
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        for (int idx = threadIdx.x; idx < 6 * h; idx += NT) {
+            const int c = idx / h, i = idx - c * h;
+            red[c][i] += red[c][i + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double FT[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
+        particle_advance(sP, FT, G, history, hist_cap, status);
+    }
+    __syncthreads();
+    {
+        const int words = (int)(sizeof(ParticleState) / sizeof(int));
+        const int* srcw = reinterpret_cast<const int*>(&sP);
+        int* dstw = reinterpret_cast<int*>(ps);
+        for (int i = threadIdx.x; i < words; i += NT) dstw[i] = srcw[i];
+    }
+}
+
+// Last-block-done hand-off: every block calls it after writing its partials;
+// the block that finishes last (a device counter, reset by that block) gets
+// true.  No block waits for another.
+__device__ __forceinline__ bool last_block_done(int* counter) {
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+        if (last) *counter = 0;
+        __threadfence();
+    }
+    __syncthreads();
+    return last != 0;
+}
+
 }  // namespace lbmp
