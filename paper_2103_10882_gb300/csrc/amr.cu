@@ -42,6 +42,9 @@ constexpr int B3 = BS * BS * BS;
 constexpr int MAXL = 6;
 constexpr int UPD_THREADS = 256;
 constexpr int STATUS_AMR_MISSING = 8;    // a pull found no source cell
+// Finest-level cell flags: fluid, solid (centre inside the sphere), and
+// fluid with a solid D3Q19 neighbour (updated by k_amr_boundary).
+constexpr uint8_t FLAG_FLUID = 0, FLAG_SOLID = 1, FLAG_BOUNDARY = 2;
 constexpr int STATUS_NOT_FINEST = 16;    // the sphere's box left the finest level
 
 // Device view of one level.
@@ -175,10 +178,10 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
     const A scale = U.P.scale, inv = U.P.inv_scale;
     const bool real = REAL;
     const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
-    const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
     A g[19];
     if (HAS_FINE && real && D.host[(size_t)b * B3 + c] == 1) {
         // coalescence: mean of the eight ghost sub-cells after the finer level's two steps
+        const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
 #pragma unroll
         for (int q = 0; q < 19; ++q) g[q] = A(0);
         const int gx = 2 * (bx * BS + lx), gy = 2 * (by * BS + ly), gz = 2 * (bz * BS + lz);
@@ -197,13 +200,17 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
         for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
         if (U.rescale) rescale19<A>(g, U.fkp, U.fkm);
     } else {
+        // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate
+        const int bsx[3] = {lx == 0 ? -1 : 0, 0, lx == 15 ? 1 : 0};
+        const int bsy[3] = {ly == 0 ? -1 : 0, 0, ly == 15 ? 1 : 0};
+        const int bsz[3] = {lz == 0 ? -1 : 0, 0, lz == 15 ? 1 : 0};
+        const int lsx[3] = {(lx - 1) & 15, lx, (lx + 1) & 15};
+        const int lsy[3] = {((ly - 1) & 15) * BS, ly * BS, ((ly + 1) & 15) * BS};
+        const int lsz[3] = {((lz - 1) & 15) * BS * BS, lz * BS * BS, ((lz + 1) & 15) * BS * BS};
 #pragma unroll
         for (int q = 0; q < 19; ++q) {
-            const int sx = lx - cx(q), sy = ly - cy(q), sz = lz - cz(q);
-            const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
-            const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
-            const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
-            const int nbk = nb27[(oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];   // entry 13 is b itself
+            const int ix = 1 - cx(q), iy = 1 - cy(q), iz = 1 - cz(q);
+            const int nbk = nb27[13 + bsx[ix] + 3 * bsy[iy] + 9 * bsz[iz]];   // entry 13 is b itself
             if (nbk == -2) {   // domain wall: bounce-back
                 g[q] = Store<S>::load(U.src + paddr(b, opp(q), c), inv);
                 continue;
@@ -213,11 +220,12 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
                 g[q] = A(0);
                 continue;
             }
-            const int sc = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
+            const int sc = lsx[ix] + lsy[iy] + lsz[iz];
             if (HAS_COARSE && nbk >= D.nreal && U.substep == 1 &&
                 D.gkind[(size_t)(nbk - D.nreal) * B3 + sc] == 2) {
                 // static ghost at the second step: content of the coarser cell one more step upwind
-                int t[3] = {bx * BS + sx - cx(q), by * BS + sy - cy(q), bz * BS + sz - cz(q)};
+                const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+                int t[3] = {bx * BS + lx - 2 * cx(q), by * BS + ly - 2 * cy(q), bz * BS + lz - 2 * cz(q)};
                 if (wrap3(t, D)) {
                     const int p[3] = {t[0] >> 1, t[1] >> 1, t[2] >> 1};
                     int pc;
@@ -270,10 +278,14 @@ __global__ void __launch_bounds__(UPD_THREADS)
     if (threadIdx.x < 27) nb27[threadIdx.x] = U.D.nbr[b * 27 + threadIdx.x];
     __syncthreads();
     const int c = (((blockIdx.x - gblocks) & 15) << 8) + threadIdx.x;
-    if (COUPLED && U.solid[(size_t)b * B3 + c]) {
+    if (COUPLED) {   // finest level flags: 1 solid, 2 fluid next to the sphere (k_amr_boundary's cells)
+        const uint8_t f = U.solid[(size_t)b * B3 + c];
+        if (f == FLAG_SOLID) {
 #pragma unroll
-        for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), U.P.scale);
-        return;
+            for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), U.P.scale);
+            return;
+        }
+        if (f == FLAG_BOUNDARY) return;
     }
     update_cell<S, HAS_FINE, HAS_COARSE, true>(U, b, c, nb27);
 }
@@ -293,67 +305,72 @@ __device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int l
 
 constexpr int BNDW_THREADS = 256;
 
-// One warp per boundary cell of the finest level, lane q handling population
-// q (CLI links of Sec. 2.3: geometry in the population arithmetic, FP64
-// force partials), cooperative collision.  Blocks past the end of the list
-// write zero partials.  The block that finishes last sums the partials and
-// runs the particle update of Algorithm 1 (no separate launch).
+// Boundary cells of the finest level (flag 2: fluid with a solid
+// neighbour), found from the mask the remap wrote in box order: each warp
+// takes 32 consecutive box cells and processes the marked ones one at a
+// time, lane q handling population q (CLI links of Sec. 2.3, geometry in the
+// population arithmetic, FP64 force partials), with a cooperative
+// collision.  The level update skips these cells, so this kernel runs
+// beside it.  The block that finishes last sums the partials and runs the
+// particle update of Algorithm 1.
 template <typename S>
 __global__ void __launch_bounds__(BNDW_THREADS)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
-                   const int* __restrict__ list, const int* __restrict__ count,
-                   CollideParams<typename Store<S>::A> P, ParticleState* ps, int cli, double* partials,
-                   int* done, GridDesc G, double* __restrict__ history, int hist_cap, int* __restrict__ status) {
+                   const uint8_t* __restrict__ mask, BoxDesc B, CollideParams<typename Store<S>::A> P,
+                   ParticleState* ps, int cli, double* partials, int* done, GridDesc G,
+                   double* __restrict__ history, int hist_cap, int* __restrict__ status) {
     using A = typename Store<S>::A;
     __shared__ LinkFrame<A> Fr;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = gridDim.x * (BNDW_THREADS / 32);
-    const int cnt = *count;
-    if ((int)blockIdx.x * (BNDW_THREADS / 32) >= cnt) {   // uniform across the block
-        if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 6 + threadIdx.x] = 0.0;
-    } else {
-        if (threadIdx.x == 0) Fr.init(*ps);
-        __syncthreads();
-        LinkSums acc;
-        for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
-            const int e = list[w];
-            const int b = e >> 12, c = e & 4095;
-            const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
-            A gq = A(0);
-            if (lane < 19) {
-                const int q = lane;
-                const int cq[3] = {cx(q), cy(q), cz(q)};
-                int sc;
-                const int sb = nbr_cell(D, b, lx, ly, lz, -cq[0], -cq[1], -cq[2], &sc);
-                if (sb == -2) {
-                    gq = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
-                } else if (sb < 0) {
-                    atomicOr(status, STATUS_AMR_MISSING);
-                } else if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] == 0) {
-                    gq = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
-                } else {
-                    const int k = opp(q);
-                    int fc;
-                    const int fb = nbr_cell(D, b, lx, ly, lz, cq[0], cq[1], cq[2], &fc);   // x - c_k
-                    const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] == 0;
-                    const int g[3] = {D.bpos[3 * b] * BS + lx, D.bpos[3 * b + 1] * BS + ly,
-                                      D.bpos[3 * b + 2] * BS + lz};
-                    A d[3], fl[3], tl[3];
-                    int pu[3];
-                    Fr.offset(g, D.n, D.periodic, d, pu);
-                    const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
-                    const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
-                    const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
-                    gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, fl, tl);
-                    acc.add(k, pu, fl, tl);
-                }
-            }
-            gq = warp_trt_collide<A, false>(gq, lane, P, status);
-            if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
-        }
-        block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
+    __shared__ BoxFrame Bf;
+    if (threadIdx.x == 0) {
+        Fr.init(*ps);
+        box_frame_init(Bf, D.n, D.periodic, B, *ps);
     }
-    if (last_block_done(done)) particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long t0 = ((long long)blockIdx.x * (BNDW_THREADS / 32) + wib) * 32;
+    const long long tl = t0 + lane;
+    unsigned bits = __ballot_sync(0xffffffffu, tl < B.cells && mask[tl] != 0);
+    LinkSums acc;
+    while (bits) {
+        const int j = __ffs(bits) - 1;
+        bits &= bits - 1;
+        int g[3], c;
+        box_cell((int)(t0 + j), D.n, D.periodic, B, Bf, g);   // marked cells are inside the domain
+        const int b = locate(D, g, &c);
+        const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
+        A gq = A(0);
+        if (lane < 19) {
+            const int q = lane;
+            const int cq[3] = {cx(q), cy(q), cz(q)};
+            int sc;
+            const int sb = nbr_cell(D, b, lx, ly, lz, -cq[0], -cq[1], -cq[2], &sc);
+            if (sb == -2) {
+                gq = Store<S>::load(src + paddr(b, opp(q), c), P.inv_scale);
+            } else if (sb < 0) {
+                atomicOr(status, STATUS_AMR_MISSING);
+            } else if (q == 0 || sb >= D.nreal || solid[(size_t)sb * B3 + sc] != FLAG_SOLID) {
+                gq = Store<S>::load(src + paddr(sb, q, sc), P.inv_scale);
+            } else {
+                const int k = opp(q);
+                int fc;
+                const int fb = nbr_cell(D, b, lx, ly, lz, cq[0], cq[1], cq[2], &fc);   // x - c_k
+                const bool far_ok = fb >= 0 && fb < D.nreal && solid[(size_t)fb * B3 + fc] != FLAG_SOLID;
+                A d[3], fl[3], tl3[3];
+                int pu[3];
+                Fr.offset(g, D.n, D.periodic, d, pu);
+                const A gt_k = Store<S>::load(src + paddr(b, k, c), P.inv_scale);
+                const A gt_q = Store<S>::load(src + paddr(b, q, c), P.inv_scale);
+                const A gt_far = far_ok ? Store<S>::load(src + paddr(fb, k, fc), P.inv_scale) : A(0);
+                gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, fl, tl3);
+                acc.add(k, pu, fl, tl3);
+            }
+        }
+        gq = warp_trt_collide<A, false>(gq, lane, P, status);
+        if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
+    }
+    block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
+    if (last_block_done(done, (int)gridDim.x)) particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status);
 }
 
 constexpr int LINK_THREADS = 256;
@@ -390,12 +407,12 @@ __global__ void __launch_bounds__(LINK_THREADS)
             } else {
                 const size_t x = (size_t)b * B3 + c;
                 const bool solid = ball_flag(g, D.n, D.periodic, F, P);
-                fnext[x] = solid ? 1 : 0;
                 if (solid) {
+                    fnext[x] = FLAG_SOLID;
 #pragma unroll
                     for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
                 } else {
-                    const bool uncovered = fcur[x] != 0;
+                    const bool uncovered = fcur[x] == FLAG_SOLID;
                     A rsum = A(0);
                     int cnt = 0;
                     for (int q = 1; q < 19; ++q) {
@@ -406,12 +423,13 @@ __global__ void __launch_bounds__(LINK_THREADS)
                         if (!uncovered || vs) continue;
                         int vc;
                         const int vb = locate(D, v, &vc);
-                        if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] != 0) continue;
+                        if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] == FLAG_SOLID) continue;
                         A r = A(1);
                         for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
                         rsum += r;
                         cnt += 1;
                     }
+                    fnext[x] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
                     if (uncovered) {
                         const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
                         const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
@@ -554,7 +572,7 @@ __global__ void k_amr_init(LevelView D, S* __restrict__ pops, const uint8_t* __r
         double u[3] = {u0, u1, u2};
         if (amp != 0.0) u[dir] += amp * sin(2.0 * M_PI * (g[axis] + 0.5) * h / Lax);
         const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const bool s = solid && solid[(size_t)b * B3 + c];
+        const bool s = solid && solid[(size_t)b * B3 + c] == FLAG_SOLID;
         for (int q = 0; q < 19; ++q) {
             const double cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
             const double e = wgt<double>(q) * ((rho - 1.0) + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
@@ -663,7 +681,7 @@ __global__ void k_amr_export_links(LevelView D, const uint8_t* __restrict__ flag
         int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
         int vc, vb = -1;
         if (wrap3(v, D)) vb = locate(D, v, &vc);
-        if (vb >= 0 && vb < D.nreal && flags[(size_t)vb * B3 + vc] != 0) {
+        if (vb >= 0 && vb < D.nreal && flags[(size_t)vb * B3 + vc] == FLAG_SOLID) {
             q_out[slot] = q;
             delta_out[slot] = link_delta(d, q, P.r);
         } else {
@@ -717,6 +735,9 @@ struct AmrEngine {
     double graph_tau = 0.0;
     cudaStream_t capture_stream = nullptr;   // private stream used only for capturing
     int* d_done = nullptr;   // last-block-done counter of the boundary kernel (zero between launches)
+    std::vector<std::vector<uint8_t>> cover;      // block coverage per level of the current layout
+    cudaStream_t side = nullptr;                  // k_amr_boundary runs here, beside the finest update
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 void amr_drop_graphs(AmrEngine* E) {
@@ -1101,14 +1122,16 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
                                                                Ff.d_flags[0], h->box, h->d_ps, (A)1, (A)1,
                                                                h->link_mask, h->link_blocks, h->status);
         });
-        k_amr_links_emit<<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), h->link_mask, h->link_blocks, h->box, h->d_ps,
-                                                             h->list, h->count, h->list_cap, h->status);
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return LBMP_OK;
 }
 
-lbmp_status regrid_now(lbmp_handle* h) {
+// keep_if_unchanged: a periodic regrid whose block coverage equals the
+// current one changes nothing (the populations would be copied onto the
+// same blocks and the flags are already those of the current position),
+// so the layout, its lists and the captured graphs are kept.
+lbmp_status regrid_now(lbmp_handle* h, bool keep_if_unchanged = false) {
     AmrEngine* E = h->amr;
     int nb[3];
     lattice_of(E, E->L - 1, nb);
@@ -1118,7 +1141,12 @@ lbmp_status regrid_now(lbmp_handle* h) {
         const Mask mb = required_from_box(E);
         for (size_t i = 0; i < m.size(); ++i) m[i] |= mb[i];
     }
-    return build_layout(h, coverage(E, m));
+    std::vector<Mask> R = coverage(E, m);
+    if (keep_if_unchanged && R == E->cover) return LBMP_OK;
+    const lbmp_status s = build_layout(h, R);
+    if (s == LBMP_OK) E->cover.swap(R);
+    else E->cover.clear();
+    return s;
 }
 
 template <typename S>
@@ -1196,7 +1224,24 @@ void enqueue_advance(lbmp_handle* h, int l) {
         U.ckm = (A)km;
     }
     const bool coupled = (l == L - 1) && h->has_particle;
-    if (coupled) U.solid = V.d_flags[V.fcur];
+    if (coupled) {
+        U.solid = V.d_flags[V.fcur];
+        // the boundary cells (flag 2) go to k_amr_boundary on the side stream, beside the update
+        const LevelView D = view(E, V);
+        GridDesc G;
+        G.nx = V.n[0];
+        G.ny = V.n[1];
+        G.nz = V.n[2];
+        for (int a = 0; a < 3; ++a) G.periodic[a] = E->periodic[a];
+        G.n = (long long)V.n[0] * V.n[1] * V.n[2];
+        cudaEventRecord(E->ev_fork, h->stream);
+        cudaStreamWaitEvent(E->side, E->ev_fork, 0);
+        k_amr_boundary<S><<<E->boundary_blocks, BNDW_THREADS, 0, E->side>>>(
+            D, U.src, U.dst, U.solid, h->link_mask, h->box, P, h->d_ps, h->cfg.boundary == LBMP_CLI ? 1 : 0,
+            h->partials, E->d_done, G, h->history, h->cfg.history_capacity, h->status);
+        cudaEventRecord(E->ev_join, E->side);
+        h->launches += 1;
+    }
     const long long ev0 = profile_mark(h);
     const int ng = has_coarse ? V.nglist : 0;
     const int gblocks = (ng + UPD_THREADS - 1) / UPD_THREADS;
@@ -1214,26 +1259,14 @@ void enqueue_advance(lbmp_handle* h, int l) {
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
     h->updates += (long long)V.nreal * B3;
     if (coupled) {
+        cudaStreamWaitEvent(h->stream, E->ev_join, 0);
         const LevelView D = view(E, V);
-        const int nb = E->boundary_blocks;
-        GridDesc G;
-        G.nx = V.n[0];
-        G.ny = V.n[1];
-        G.nz = V.n[2];
-        for (int a = 0; a < 3; ++a) G.periodic[a] = E->periodic[a];
-        G.n = (long long)V.n[0] * V.n[1] * V.n[2];
-        k_amr_boundary<S><<<nb, BNDW_THREADS, 0, h->stream>>>(D, U.src, U.dst, U.solid, h->list, h->count, P, h->d_ps,
-                                                              h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials,
-                                                              E->d_done, G, h->history, h->cfg.history_capacity,
-                                                              h->status);
         uint8_t* fnext = V.d_flags[1 - V.fcur];
         const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
         k_amr_remap<S><<<nl, LINK_THREADS, 0, h->stream>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
                                                            P.inv_scale, h->link_mask, h->link_blocks, h->status);
-        k_amr_links_emit<<<nl, LINK_THREADS, 0, h->stream>>>(D, h->link_mask, h->link_blocks, h->box, h->d_ps, h->list,
-                                                             h->count, h->list_cap, h->status);
         V.fcur = 1 - V.fcur;
-        h->launches += 3;
+        h->launches += 1;
     }
     V.cur = 1 - V.cur;
 }
@@ -1258,6 +1291,10 @@ lbmp_status amr_create(lbmp_handle* h) {
     h->amr = E;
     E->d_done = (int*)handle_alloc(h, sizeof(int));
     if (!E->d_done) return LBMP_ERR_OOM;
+    if (cudaStreamCreateWithFlags(&E->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return LBMP_ERR_CUDA;
     if (cudaMemsetAsync(E->d_done, 0, sizeof(int), h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return regrid_now(h);
 }
@@ -1266,6 +1303,9 @@ void amr_destroy(lbmp_handle* h) {
     if (!h->amr) return;
     amr_drop_graphs(h->amr);
     if (h->amr->capture_stream) cudaStreamDestroy(h->amr->capture_stream);
+    if (h->amr->side) cudaStreamDestroy(h->amr->side);
+    if (h->amr->ev_fork) cudaEventDestroy(h->amr->ev_fork);
+    if (h->amr->ev_join) cudaEventDestroy(h->amr->ev_join);
     for (auto& V : h->amr->lv) free_level(h, V);
     delete h->amr;
     h->amr = nullptr;
@@ -1288,7 +1328,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
     const double shell = 4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri);
     h->list_cap = (int)std::min<double>((double)B.cells, std::ceil(shell) + 64.0);
     h->list = (int*)handle_alloc(h, sizeof(int) * (size_t)h->list_cap);
-    E->boundary_blocks = boundary_grid(h->list_cap);
+    E->boundary_blocks = (int)((B.cells + BNDW_THREADS - 1) / BNDW_THREADS);   // a warp per 32 box cells
     h->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)E->boundary_blocks);
     h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
     h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));
@@ -1318,7 +1358,7 @@ lbmp_status amr_regrid(lbmp_handle* h) {
             return LBMP_ERR_CUDA;
         h->d2h += sizeof(ParticleState);
     }
-    return regrid_now(h);
+    return regrid_now(h, true);
 }
 
 lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis) {
@@ -1462,6 +1502,13 @@ lbmp_status amr_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, 
     AmrEngine* E = h->amr;
     *n = 0;
     if (!h->has_particle) return LBMP_OK;
+    // the step keeps the boundary cells as a mask in box order; compact it for the export
+    {
+        const Level& Vf = E->lv[E->L - 1];
+        const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
+        k_amr_links_emit<<<nl, LINK_THREADS, 0, h->stream>>>(view(E, Vf), h->link_mask, h->link_blocks, h->box,
+                                                             h->d_ps, h->list, h->count, h->list_cap, h->status);
+    }
     int cnt = 0;
     if (cudaMemcpyAsync(&cnt, h->count, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -1516,7 +1563,7 @@ int amr_launches_per_coarse_step(const lbmp_handle* h) {
     int per = 0;
     for (int l = E->L - 1; l >= 0; --l) {
         int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nxlist > 0) ? 1 : 0) +
-                  ((l == E->L - 1 && h->has_particle) ? 3 : 0);
+                  ((l == E->L - 1 && h->has_particle) ? 2 : 0);
         per = own + 2 * per;
     }
     return per;

@@ -26,9 +26,7 @@ struct SimDev {
     GridDesc G;
     long long pop_off;   // element offset of the simulation in each population pool
     long long flag_off;  // byte offset in each flag pool
-    int list_off, list_cap;
-    int mask_off;        // scratch: one byte per box cell
-    int blk_off;         // scratch: one int per link block
+    int mask_off;        // boundary mask: one byte per box cell
     int bnd_off, bnd_n;  // boundary-kernel blocks of the simulation (and their force partials)
     BoxDesc box;
     double sp, sm;
@@ -36,6 +34,9 @@ struct SimDev {
 };
 
 constexpr int BW = 256;   // threads of the boundary, particle and remap kernels
+// Cell flags: fluid, solid (centre inside the sphere), fluid with a solid
+// D3Q19 neighbour (updated by k_batch_boundary instead of the bulk kernel).
+constexpr uint8_t FLAG_FLUID = 0, FLAG_SOLID = 1, FLAG_BOUNDARY = 2;
 
 template <typename S>
 __host__ __device__ __forceinline__ CollideParams<typename Store<S>::A> sim_params(const SimDev& D, typename Store<S>::A scale,
@@ -54,6 +55,7 @@ __host__ __device__ __forceinline__ CollideParams<typename Store<S>::A> sim_para
 // tile = (simulation, x0, y0, z0); block (16, TY); each thread ZC cells along z.
 template <typename S, int ZC>
 __global__ void __launch_bounds__(512) k_batch_bulk(const S* __restrict__ src, S* __restrict__ dst,
+                                                    const uint8_t* __restrict__ flags,
                                                     const int4* __restrict__ tiles, const SimDev* __restrict__ sims,
                                                     typename Store<S>::A scale, typename Store<S>::A inv,
                                                     int* __restrict__ status) {
@@ -66,68 +68,77 @@ __global__ void __launch_bounds__(512) k_batch_bulk(const S* __restrict__ src, S
     const size_t n = (size_t)D.G.n;
     const S* s0 = src + D.pop_off;
     S* d0 = dst + D.pop_off;
+    const uint8_t* fl = flags + D.flag_off;
     const int xs[3] = {x + 1 < e ? x + 1 : 0, x, x > 0 ? x - 1 : e - 1};
     const int ys[3] = {y + 1 < e ? y + 1 : 0, y, y > 0 ? y - 1 : e - 1};
 #pragma unroll
     for (int k = 0; k < ZC; ++k) {
         const int z = t.w + threadIdx.z * ZC + k;
         const int zs[3] = {z + 1 < e ? z + 1 : 0, z, z > 0 ? z - 1 : e - 1};
+        const size_t cell = (size_t)(x + e * (y + e * z));
+        if (fl[cell] != FLAG_FLUID) continue;   // solid (zeroed by the remap) or done by k_batch_boundary
         A g[19];
 #pragma unroll
         for (int q = 0; q < 19; ++q)
             g[q] = Store<S>::load(s0 + (size_t)q * n + (size_t)(xs[cx(q) + 1] + e * (ys[cy(q) + 1] + e * zs[cz(q) + 1])),
                                   P.inv_scale);
         trt_collide<A, false>(g, P, status);
-        const size_t cell = (size_t)(x + e * (y + e * z));
 #pragma unroll
         for (int q = 0; q < 19; ++q) Store<S>::store(d0 + (size_t)q * n + cell, g[q], P.scale);
     }
 }
 
 // ----------------------------------------------------------------- boundary
-// Warp per boundary cell as in the single-simulation engine.  The grid is
-// flat: block b belongs to simulation bnd_sim[b], which owns bnd_n blocks
-// (one per 32 entries of its list capacity) and as many force partials.
+// Boundary cells of every simulation (flag 2), found from the remap's mask
+// in box order: each warp takes 32 consecutive cells of its simulation's
+// box and processes the marked ones, lane q handling population q (CLI
+// links, geometry in the population arithmetic, FP64 force partials), with
+// a cooperative collision.  The grid is flat: block b belongs to simulation
+// bnd_sim[b], which owns bnd_n blocks (a warp per 32 box cells) and as many
+// partials; the last of them to finish runs that simulation's particle
+// update (Algorithm 1).  The bulk kernel skips these cells, so this kernel
+// runs beside it.
 template <typename S>
 __global__ void __launch_bounds__(BW)
     k_batch_boundary(const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ flags,
-                     const int* __restrict__ lists, const int* __restrict__ counts, const SimDev* __restrict__ sims,
-                     const int* __restrict__ bnd_sim, const ParticleState* __restrict__ ps, int cli,
-                     typename Store<S>::A scale, typename Store<S>::A inv, double* __restrict__ partials,
-                     int* __restrict__ status) {
+                     const uint8_t* __restrict__ mask, const SimDev* __restrict__ sims,
+                     const int* __restrict__ bnd_sim, ParticleState* ps, int cli, typename Store<S>::A scale,
+                     typename Store<S>::A inv, double* partials, int* done, double* __restrict__ history,
+                     int hist_cap, int* __restrict__ status) {
     using A = typename Store<S>::A;
     __shared__ LinkFrame<A> Fr;
+    __shared__ BoxFrame Bf;
     const int sim = bnd_sim[blockIdx.x];
     const SimDev& D = sims[sim];
-    const int jb = blockIdx.x - D.bnd_off;
-    const int cnt = counts[sim];
-    if (jb * (BW / 32) >= cnt) {   // uniform across the block
-        if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 6 + threadIdx.x] = 0.0;
-        return;
-    }
-    const ParticleState& Pp = ps[sim];
-    if (threadIdx.x == 0) Fr.init(Pp);
-    const CollideParams<A> P = sim_params<S>(D, scale, inv);
     const GridDesc& G = D.G;
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    const int per3[3] = {1, 1, 1};
+    if (threadIdx.x == 0) {
+        Fr.init(ps[sim]);
+        box_frame_init(Bf, n3, per3, D.box, ps[sim]);
+    }
+    __syncthreads();
+    const CollideParams<A> P = sim_params<S>(D, scale, inv);
     const S* s0 = src + D.pop_off;
     S* d0 = dst + D.pop_off;
     const uint8_t* fl = flags + D.flag_off;
-    const int* list = lists + D.list_off;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int nwarps = D.bnd_n * (BW / 32);
     const size_t n = (size_t)G.n;
-    const int n3[3] = {G.nx, G.ny, G.nz};
-    const int per3[3] = {1, 1, 1};
+    const long long t0 = ((long long)(blockIdx.x - D.bnd_off) * (BW / 32) + wib) * 32;
+    const long long tl = t0 + lane;
+    unsigned bits = __ballot_sync(0xffffffffu, tl < D.box.cells && mask[D.mask_off + tl] != 0);
     LinkSums acc;
-    __syncthreads();
-    for (int w = jb * (BW / 32) + wib; w < cnt; w += nwarps) {
-        const int cell = list[w];
-        const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
+    while (bits) {
+        const int j = __ffs(bits) - 1;
+        bits &= bits - 1;
+        int xyz[3];
+        box_cell((int)(t0 + j), n3, per3, D.box, Bf, xyz);
+        const int x = xyz[0], y = xyz[1], z = xyz[2];
+        const size_t cell = (size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * (size_t)z);
         A gq = A(0);
         if (lane < 19) {
             const int q = lane;
             const int c[3] = {cx(q), cy(q), cz(q)};
-            const int xyz[3] = {x, y, z};
             int s3[3], f3[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
@@ -135,93 +146,43 @@ __global__ void __launch_bounds__(BW)
                 f3[a] = src_coord(xyz[a], -c[a], n3[a], 1);
             }
             const size_t sidx = (size_t)s3[0] + (size_t)G.nx * ((size_t)s3[1] + (size_t)G.ny * (size_t)s3[2]);
-            if (q == 0 || fl[sidx] == 0) {
+            if (q == 0 || fl[sidx] != FLAG_SOLID) {
                 gq = Store<S>::load(s0 + (size_t)q * n + sidx, P.inv_scale);
             } else {
                 const int k = opp(q);
                 const size_t far = (size_t)f3[0] + (size_t)G.nx * ((size_t)f3[1] + (size_t)G.ny * (size_t)f3[2]);
-                const bool far_ok = fl[far] == 0;
-                A d[3], flk[3], tl[3];
+                const bool far_ok = fl[far] != FLAG_SOLID;
+                A d[3], flk[3], tl3[3];
                 int pu[3];
                 Fr.offset(xyz, n3, per3, d, pu);
                 const A gt_k = Store<S>::load(s0 + (size_t)k * n + cell, P.inv_scale);
                 const A gt_q = Store<S>::load(s0 + (size_t)q * n + cell, P.inv_scale);
                 const A gt_far = far_ok ? Store<S>::load(s0 + (size_t)k * n + far, P.inv_scale) : A(0);
-                gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, flk, tl);
-                acc.add(k, pu, flk, tl);
+                gq = cli_link<A>(q, d, cli && far_ok, gt_k, gt_q, gt_far, Fr, flk, tl3);
+                acc.add(k, pu, flk, tl3);
             }
         }
         gq = warp_trt_collide<A, false>(gq, lane, P, status);
         if (lane < 19) Store<S>::store(d0 + (size_t)lane * n + cell, gq, P.scale);
     }
-    block_link_sums<BW>(acc, Pp.x, partials + (size_t)blockIdx.x * 6);
-}
-
-// ----------------------------------------------------------------- particle
-__global__ void __launch_bounds__(BW)
-    k_batch_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials,
-                     const SimDev* __restrict__ sims, double* __restrict__ history, int hist_cap,
-                     int* __restrict__ status) {
-    __shared__ double red[6][BW];
-    __shared__ ParticleState sP;
-    const int sim = blockIdx.x;
-    const SimDev& D = sims[sim];
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < D.bnd_n; b += BW)
-        for (int k = 0; k < 6; ++k) v[k] += partials[((size_t)D.bnd_off + b) * 6 + k];
-    for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = v[k];
-    {
-        const int words = (int)(sizeof(ParticleState) / sizeof(int));
-        const int* sw = reinterpret_cast<const int*>(ps + sim);
-        int* dw = reinterpret_cast<int*>(&sP);
-        for (int i = threadIdx.x; i < words; i += BW) dw[i] = sw[i];
-    }
-    __syncthreads();
-    for (int h = BW / 2; h > 0; h >>= 1) {
-        for (int idx = threadIdx.x; idx < 6 * h; idx += BW) {
-            const int c = idx / h, i = idx - c * h;
-            red[c][i] += red[c][i + h];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double FT[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
-        particle_advance(sP, FT, D.G, history + (size_t)D.hist_off * 15, hist_cap, status);
-    }
-    __syncthreads();
-    {
-        const int words = (int)(sizeof(ParticleState) / sizeof(int));
-        const int* sw = reinterpret_cast<const int*>(&sP);
-        int* dw = reinterpret_cast<int*>(ps + sim);
-        for (int i = threadIdx.x; i < words; i += BW) dw[i] = sw[i];
-    }
+    block_link_sums<BW>(acc, ps[sim].x, partials + (size_t)blockIdx.x * 6);
+    if (last_block_done(done + sim, D.bnd_n))
+        particle_block_update<BW>(ps + sim, partials + (size_t)D.bnd_off * 6, D.bnd_n, G,
+                                  history + (size_t)D.hist_off * 15, hist_cap, status);
 }
 
 // -------------------------------------------------------------------- remap
-__global__ void k_batch_flags_box(uint8_t* __restrict__ fnext, const SimDev* __restrict__ sims,
-                                  const ParticleState* __restrict__ ps) {
-    __shared__ BoxFrame F;
-    const int sim = blockIdx.y;
-    const SimDev& D = sims[sim];
-    if ((long long)blockIdx.x * blockDim.x >= D.box.cells) return;   // uniform across the block
-    const int n3[3] = {D.G.nx, D.G.ny, D.G.nz};
-    if (threadIdx.x == 0) box_frame_init(F, n3, D.G.periodic, D.box, ps[sim]);
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= D.box.cells) return;
-    int p[3];
-    box_cell(t, n3, D.G.periodic, D.box, F, p);   // periodic: always inside
-    fnext[D.flag_off + (size_t)p[0] + (size_t)D.G.nx * ((size_t)p[1] + (size_t)D.G.ny * (size_t)p[2])] =
-        ball_flag(p, n3, D.G.periodic, F, ps[sim]) ? 1 : 0;
-}
-
-// refill of uncovered cells, zeroing of solid ones, and the boundary-cell mark
+// Remap of Sec. 2.3 in one pass over each simulation's box: the new flag of
+// every cell (the exact ball predicate; 2 for fluid cells with a solid
+// neighbour, evaluated from the same predicate), covered cells zeroed,
+// uncovered cells refilled with the equilibrium at the mean density of the
+// neighbours fluid before and after and the rigid-body velocity, and the
+// mask of boundary cells in box order for the next step's k_batch_boundary.
 template <typename S>
 __global__ void __launch_bounds__(BW)
-    k_batch_refill_mark(S* __restrict__ pops, const uint8_t* __restrict__ fcur, const uint8_t* __restrict__ fnext,
-                        const SimDev* __restrict__ sims, const ParticleState* __restrict__ ps,
-                        typename Store<S>::A scale, typename Store<S>::A inv, uint8_t* __restrict__ mask,
-                        int* __restrict__ block_count) {
+    k_batch_remap(S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
+                  const SimDev* __restrict__ sims, const ParticleState* __restrict__ ps,
+                  typename Store<S>::A scale, typename Store<S>::A inv, uint8_t* __restrict__ mask) {
     using A = typename Store<S>::A;
     __shared__ BoxFrame F;
     const int sim = blockIdx.y;
@@ -232,104 +193,54 @@ __global__ void __launch_bounds__(BW)
     if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, D.box, ps[sim]);
     __syncthreads();
     const int t = blockIdx.x * BW + threadIdx.x;
+    if (t >= D.box.cells) return;
+    const ParticleState& P = ps[sim];
+    int p[3];
+    box_cell(t, n3, G.periodic, D.box, F, p);   // periodic: always inside
+    const int i = p[0], j = p[1], k = p[2];
+    const size_t n = (size_t)G.n;
+    const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+    const uint8_t* fc = fcur + D.flag_off;
+    uint8_t* fn = fnext + D.flag_off;
+    S* p0 = pops + D.pop_off;
     int is_b = 0;
-    if (t < D.box.cells) {
-        const ParticleState& P = ps[sim];
-        int p[3];
-        box_cell(t, n3, G.periodic, D.box, F, p);   // periodic: always inside
-        const int i = p[0], j = p[1], k = p[2];
-        const size_t n = (size_t)G.n;
-        const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
-        const uint8_t* fc = fcur + D.flag_off;
-        const uint8_t* fn = fnext + D.flag_off;
-        S* p0 = pops + D.pop_off;
-        if (fn[c] != 0) {
-            for (int q = 0; q < 19; ++q) Store<S>::store(p0 + (size_t)q * n + c, A(0), scale);
-        } else {
-            A rsum = A(0);
-            int cnt = 0;
-            for (int q = 1; q < 19; ++q) {
-                int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
-                for (int a = 0; a < 3; ++a) v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
-                const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
-                if (fn[y] != 0) is_b = 1;
-                if (fc[c] != 0 && fc[y] == 0 && fn[y] == 0) {
-                    A r = A(1);
-                    for (int p = 0; p < 19; ++p) r += Store<S>::load(p0 + (size_t)p * n + y, inv);
-                    rsum += r;
-                    cnt += 1;
-                }
-            }
-            if (fc[c] != 0) {   // uncovered: equilibrium refill
-                const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
-                const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, 1), wrap_diff((j + 0.5) - P.x[1], G.ny, 1),
-                                     wrap_diff((k + 0.5) - P.x[2], G.nz, 1)};
-                const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])),
-                                A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
-                                A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
-                const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                for (int q = 0; q < 19; ++q) {
-                    const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
-                    Store<S>::store(p0 + (size_t)q * n + c,
-                                    wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu), scale);
-                }
+    if (ball_flag(p, n3, G.periodic, F, P)) {
+        fn[c] = FLAG_SOLID;
+        for (int q = 0; q < 19; ++q) Store<S>::store(p0 + (size_t)q * n + c, A(0), scale);
+    } else {
+        const bool uncovered = fc[c] == FLAG_SOLID;
+        A rsum = A(0);
+        int cnt = 0;
+        for (int q = 1; q < 19; ++q) {
+            int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
+            for (int a = 0; a < 3; ++a) v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
+            const bool vs = ball_flag(v, n3, G.periodic, F, P);
+            is_b |= vs ? 1 : 0;
+            if (!uncovered || vs) continue;
+            const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+            if (fc[y] == FLAG_SOLID) continue;
+            A r = A(1);
+            for (int q2 = 0; q2 < 19; ++q2) r += Store<S>::load(p0 + (size_t)q2 * n + y, inv);
+            rsum += r;
+            cnt += 1;
+        }
+        fn[c] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
+        if (uncovered) {   // equilibrium refill
+            const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
+            const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, 1), wrap_diff((j + 0.5) - P.x[1], G.ny, 1),
+                                 wrap_diff((k + 0.5) - P.x[2], G.nz, 1)};
+            const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])),
+                            A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                            A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+            const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            for (int q = 0; q < 19; ++q) {
+                const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
+                Store<S>::store(p0 + (size_t)q * n + c,
+                                wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu), scale);
             }
         }
-        mask[D.mask_off + t] = (uint8_t)is_b;
     }
-    const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
-    __shared__ int wsum[BW / 32];
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(ballot);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < BW / 32; ++w) s += wsum[w];
-        block_count[D.blk_off + blockIdx.x] = s;
-    }
-}
-
-__global__ void __launch_bounds__(BW)
-    k_batch_links_emit(const uint8_t* __restrict__ mask, const int* __restrict__ block_count,
-                       const SimDev* __restrict__ sims, const ParticleState* __restrict__ ps, int* __restrict__ lists,
-                       int* __restrict__ counts, int* __restrict__ status) {
-    __shared__ int red[BW];
-    __shared__ int wsum[BW / 32];
-    __shared__ BoxFrame F;
-    const int sim = blockIdx.y;
-    const SimDev& D = sims[sim];
-    const int nb = (D.box.cells + BW - 1) / BW;
-    if ((int)blockIdx.x >= nb) return;   // uniform across the block
-    const int n3[3] = {D.G.nx, D.G.ny, D.G.nz};
-    if (threadIdx.x == 0) box_frame_init(F, n3, D.G.periodic, D.box, ps[sim]);
-    int s = 0;
-    for (int b = threadIdx.x; b < (int)blockIdx.x; b += BW) s += block_count[D.blk_off + b];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = BW / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
-    const int base = red[0];
-    const int t = blockIdx.x * BW + threadIdx.x;
-    const int is_b = t < D.box.cells ? mask[D.mask_off + t] : 0;
-    const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) wsum[warp] = __popc(ballot);
-    __syncthreads();
-    int wbase = 0;
-    for (int w = 0; w < warp; ++w) wbase += wsum[w];
-    if (is_b) {
-        int p[3];
-        box_cell(t, n3, D.G.periodic, D.box, F, p);
-        const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
-        if (pos < D.list_cap) lists[D.list_off + pos] = p[0] + D.G.nx * (p[1] + D.G.ny * p[2]);
-        else atomicOr(status, STATUS_LINK_OVERFLOW);
-    }
-    if ((int)blockIdx.x == nb - 1 && threadIdx.x == 0) {
-        int tot = base;
-        for (int w = 0; w < BW / 32; ++w) tot += wsum[w];
-        counts[sim] = tot < D.list_cap ? tot : D.list_cap;
-    }
+    mask[D.mask_off + t] = (uint8_t)is_b;
 }
 
 template <typename S>
@@ -390,10 +301,8 @@ struct BatchEngine {
     int fcur = 0;
     ParticleState* d_ps = nullptr;
     std::vector<ParticleState> h_ps;
-    int* lists = nullptr;
-    int* counts = nullptr;
     uint8_t* mask = nullptr;
-    int* blk = nullptr;
+    int* done = nullptr;        // last-block-done counter per simulation
     double* partials = nullptr;
     int bnd_blocks = 1;     // boundary-kernel blocks of all simulations
     int* d_bnd_sim = nullptr;   // simulation of each boundary-kernel block
@@ -407,6 +316,8 @@ struct BatchEngine {
     cudaGraphExec_t graph = nullptr;
     cudaStream_t capture_stream = nullptr;
     long long graph_launches = 0;
+    cudaStream_t side = nullptr;               // k_batch_boundary runs here, beside the bulk kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -435,10 +346,10 @@ void launch_bulk_choice(lbmp_handle* h, BatchEngine* B, int choice, const S* src
     const Tile t = TILES[choice];
     const dim3 block(16, t.threads_y, 1);
     if (t.zc == 1)
-        k_batch_bulk<S, 1><<<B->ntiles[choice], block, 0, h->stream>>>(src, dst, B->d_tiles[choice], B->d_sims, scale,
+        k_batch_bulk<S, 1><<<B->ntiles[choice], block, 0, h->stream>>>(src, dst, B->flags[B->fcur], B->d_tiles[choice], B->d_sims, scale,
                                                                        inv, h->status);
     else
-        k_batch_bulk<S, 2><<<B->ntiles[choice], block, 0, h->stream>>>(src, dst, B->d_tiles[choice], B->d_sims, scale,
+        k_batch_bulk<S, 2><<<B->ntiles[choice], block, 0, h->stream>>>(src, dst, B->flags[B->fcur], B->d_tiles[choice], B->d_sims, scale,
                                                                        inv, h->status);
 }
 
@@ -450,24 +361,24 @@ void enqueue_batch_step(lbmp_handle* h) {
     batch_scales<S>(h, &scale, &inv);
     const S* src = (const S*)B->pops[B->cur];
     S* dst = (S*)B->pops[1 - B->cur];
+    // boundary cells (flag 2) and the particle updates beside the bulk kernel, which skips them
+    cudaEventRecord(B->ev_fork, h->stream);
+    cudaStreamWaitEvent(B->side, B->ev_fork, 0);
+    k_batch_boundary<S><<<B->bnd_blocks, BW, 0, B->side>>>(src, dst, B->flags[B->fcur], B->mask, B->d_sims,
+                                                           B->d_bnd_sim, B->d_ps, h->cfg.boundary == LBMP_CLI ? 1 : 0,
+                                                           scale, inv, B->partials, B->done, B->history,
+                                                           h->cfg.history_capacity, h->status);
+    cudaEventRecord(B->ev_join, B->side);
     const long long ev = profile_mark(h);
     launch_bulk_choice<S>(h, B, B->tile_choice, src, dst);
     profile_kernel(h, ev, profile_mark(h), 38.0 * sizeof(S) * (double)B->total_cells, (double)B->total_cells);
-    k_batch_boundary<S><<<B->bnd_blocks, BW, 0, h->stream>>>(src, dst, B->flags[B->fcur], B->lists, B->counts,
-                                                             B->d_sims, B->d_bnd_sim, B->d_ps,
-                                                             h->cfg.boundary == LBMP_CLI ? 1 : 0, scale, inv,
-                                                             B->partials, h->status);
-    k_batch_particle<<<B->nsims, BW, 0, h->stream>>>(B->d_ps, B->partials, B->d_sims, B->history,
-                                                     h->cfg.history_capacity, h->status);
+    cudaStreamWaitEvent(h->stream, B->ev_join, 0);
     uint8_t* fnext = B->flags[1 - B->fcur];
     const dim3 gr(B->max_box_blocks, B->nsims);
-    k_batch_flags_box<<<gr, BW, 0, h->stream>>>(fnext, B->d_sims, B->d_ps);
-    k_batch_refill_mark<S><<<gr, BW, 0, h->stream>>>(dst, B->flags[B->fcur], fnext, B->d_sims, B->d_ps, scale, inv,
-                                                     B->mask, B->blk);
-    k_batch_links_emit<<<gr, BW, 0, h->stream>>>(B->mask, B->blk, B->d_sims, B->d_ps, B->lists, B->counts, h->status);
+    k_batch_remap<S><<<gr, BW, 0, h->stream>>>(dst, B->flags[B->fcur], fnext, B->d_sims, B->d_ps, scale, inv, B->mask);
     B->cur = 1 - B->cur;
     B->fcur = 1 - B->fcur;
-    h->launches += 6;
+    h->launches += 3;
     h->updates += B->total_cells;
 }
 
@@ -478,6 +389,9 @@ void batch_destroy(lbmp_handle* h) {
     if (!B) return;
     if (B->graph) cudaGraphExecDestroy(B->graph);
     if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+    if (B->side) cudaStreamDestroy(B->side);
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+    if (B->ev_join) cudaEventDestroy(B->ev_join);
     delete B;
     h->batch = nullptr;   // device memory is released with the handle's allocations
 }
@@ -491,8 +405,8 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
     B->h_ps.resize(n);
     B->cell_off.resize(n + 1, 0);
     const size_t es = h->cfg.precision == LBMP_FP64 ? 8 : (h->cfg.precision == LBMP_FP32 ? 4 : 2);
-    long long cells = 0, list_total = 0, mask_total = 0, blk_total = 0;
-    int max_box = 1, max_list = 1;
+    long long cells = 0, mask_total = 0;
+    int max_box = 1;
     std::vector<int> bnd_sim;
     for (int s = 0; s < n; ++s) {
         const lbmp_batch_sim& in = sims[s];
@@ -529,20 +443,12 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
             if (X.E[a] >= in.edge) X.E[a] = in.edge;
             X.cells *= X.E[a];
         }
-        const double h3 = 0.5 * std::sqrt(3.0);
-        const double ro = P.r + std::sqrt(2.0) + h3, ri = std::max(0.0, P.r - h3);
-        D.list_cap = (int)std::min<double>((double)X.cells, std::ceil(4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri)) + 64.0);
-        D.list_off = (int)list_total;
-        list_total += D.list_cap;
         D.mask_off = (int)mask_total;
         mask_total += X.cells;
         const int nbx = (int)((X.cells + BW - 1) / BW);
-        D.blk_off = (int)blk_total;
-        blk_total += nbx;
         max_box = std::max(max_box, nbx);
-        max_list = std::max(max_list, D.list_cap);
         D.bnd_off = (int)bnd_sim.size();
-        D.bnd_n = boundary_grid(D.list_cap);
+        D.bnd_n = nbx;   // a warp per 32 box cells
         for (int j = 0; j < D.bnd_n; ++j) bnd_sim.push_back(s);
         D.hist_off = (long long)s * std::max(1, h->cfg.history_capacity);
     }
@@ -558,16 +464,18 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
     B->d_sims = (SimDev*)handle_alloc(h, sizeof(SimDev) * n);
     B->d_cell_off = (long long*)handle_alloc(h, sizeof(long long) * (n + 1));
     B->d_ps = (ParticleState*)handle_alloc(h, sizeof(ParticleState) * n);
-    B->lists = (int*)handle_alloc(h, sizeof(int) * (size_t)list_total);
-    B->counts = (int*)handle_alloc(h, sizeof(int) * n);
     B->mask = (uint8_t*)handle_alloc(h, (size_t)mask_total);
-    B->blk = (int*)handle_alloc(h, sizeof(int) * (size_t)blk_total);
+    B->done = (int*)handle_alloc(h, sizeof(int) * n);
     B->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)B->bnd_blocks);
     B->d_bnd_sim = (int*)handle_alloc(h, sizeof(int) * (size_t)B->bnd_blocks);
     B->history = (double*)handle_alloc(h, sizeof(double) * 15 * (size_t)n * std::max(1, h->cfg.history_capacity));
     if (!B->pops[0] || !B->pops[1] || !B->flags[0] || !B->flags[1] || !B->d_sims || !B->d_cell_off || !B->d_ps ||
-        !B->lists || !B->counts || !B->mask || !B->blk || !B->partials || !B->d_bnd_sim || !B->history)
+        !B->mask || !B->done || !B->partials || !B->d_bnd_sim || !B->history)
         return LBMP_ERR_OOM;
+    if (cudaStreamCreateWithFlags(&B->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return LBMP_ERR_CUDA;
     cudaMemcpyAsync(B->d_bnd_sim, bnd_sim.data(), sizeof(int) * bnd_sim.size(), cudaMemcpyHostToDevice, h->stream);
     // stream-collide tiles for every candidate shape (edges are multiples of 16)
     for (int c = 0; c < 4; ++c) {
@@ -589,7 +497,7 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
     cudaMemcpyAsync(B->d_ps, B->h_ps.data(), sizeof(ParticleState) * n, cudaMemcpyHostToDevice, h->stream);
     cudaMemsetAsync(B->pops[0], 0, pop_bytes, h->stream);
     cudaMemsetAsync(B->pops[1], 0, pop_bytes, h->stream);
-    cudaMemsetAsync(B->counts, 0, sizeof(int) * n, h->stream);
+    cudaMemsetAsync(B->done, 0, sizeof(int) * n, h->stream);
     // flags, zero solid (fluid at rest everywhere else), initial boundary lists
     const unsigned gcells = (unsigned)((cells + 255) / 256);
     k_batch_flags_full<<<gcells, 256, 0, h->stream>>>(B->flags[0], B->flags[1], B->d_sims, B->d_ps, B->d_cell_off, n,
@@ -599,11 +507,10 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
         using A = typename Store<S>::A;
         A scale, inv;
         batch_scales<S>(h, &scale, &inv);
+        // boundary flags and mask of the start position (both flag buffers hold its solid cells)
         const dim3 gr(B->max_box_blocks, B->nsims);
-        k_batch_refill_mark<S><<<gr, BW, 0, h->stream>>>((S*)B->pops[0], B->flags[0], B->flags[0], B->d_sims, B->d_ps,
-                                                         scale, inv, B->mask, B->blk);
-        k_batch_links_emit<<<gr, BW, 0, h->stream>>>(B->mask, B->blk, B->d_sims, B->d_ps, B->lists, B->counts,
-                                                     h->status);
+        k_batch_remap<S><<<gr, BW, 0, h->stream>>>((S*)B->pops[0], B->flags[1], B->flags[0], B->d_sims, B->d_ps,
+                                                   scale, inv, B->mask);
     });
     h->h2d += (long long)(sizeof(SimDev) + sizeof(ParticleState) + sizeof(long long)) * n +
               (long long)(sizeof(int) * bnd_sim.size());

@@ -515,15 +515,15 @@ __device__ __forceinline__ void particle_block_update(ParticleState* __restrict_
     }
 }
 
-// Last-block-done hand-off: every block calls it after writing its partials;
-// the block that finishes last (a device counter, reset by that block) gets
-// true.  No block waits for another.
-__device__ __forceinline__ bool last_block_done(int* counter) {
+// Last-block-done hand-off: each of nblocks blocks calls it after writing
+// its partials; the block that finishes last (a device counter, reset by
+// that block) gets true.  No block waits for another.
+__device__ __forceinline__ bool last_block_done(int* counter, int nblocks) {
     __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(counter, 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1;
+        last = atomicAdd(counter, 1) == nblocks - 1;
         if (last) *counter = 0;
         __threadfence();
     }

@@ -53,8 +53,11 @@ def test_batch_fp64_matches_oracle_per_simulation(orc, lib):
 
 
 def test_batch_fp32_matches_single_runs_and_graphs(lib):
-    """The batched kernels do the single-simulation arithmetic; odd step
-    counts exercise the graph (two steps) and the plain path together."""
+    """The batched kernels do the single-simulation arithmetic (up to FP32
+    rounding: the two engines' boundary kernels are different code); odd
+    step counts exercise the graph (two steps) and the plain path together.
+    Forces, torques and accelerations are compared against the largest
+    component of their group, positions and velocities relatively."""
     sims = small_batch(1)
     b = lib.BatchSimulation(sims, precision="fp32")
     b.autotune(3)
@@ -71,7 +74,12 @@ def test_batch_fp32_matches_single_runs_and_graphs(lib):
         g.step(13)
         a, c = g.populations(), b.populations(i)
         assert np.abs(a - c).max() <= 1e-6 * max(np.abs(a).max(), 1e-12)
-        np.testing.assert_allclose(b.particle(i), g.particle(), rtol=1e-6, atol=1e-12)
+        pb, ps = b.particle(i), g.particle()
+        for lo, hi in ((0, 3), (3, 6), (15, 18), (18, 21), (21, 24)):
+            scale = max(np.abs(ps[lo:hi]).max(), 1e-30)
+            assert np.abs(pb[lo:hi] - ps[lo:hi]).max() <= 1e-5 * scale, (lo, pb[lo:hi], ps[lo:hi])
+        np.testing.assert_allclose(pb[6:9], ps[6:9], rtol=1e-9)
+        np.testing.assert_allclose(pb[9:15], ps[9:15], rtol=1e-5, atol=1e-5 * np.abs(ps[9:15]).max())
 
 
 def test_batch_rest_state_and_errors(lib):

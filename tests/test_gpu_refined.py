@@ -191,3 +191,20 @@ def test_refined_walls(orc, lib):
     o.step(4)
     g.step(4)
     cells_close(o, g, 2, 1e-10)
+
+
+def test_refined_fp16_against_fp64_oracle(orc, lib):
+    """FP16 deviation storage (2^11-scaled, FP32 arithmetic) on three levels
+    against the FP64 oracle: populations within 5e-3 of their largest
+    magnitude, forces within 2e-2 of the buoyancy scale."""
+    pos = (30.7, 33.2, 31.6)
+    o, g = pair(orc, lib, (16, 16, 16), 3, tau=0.7, precision="fp16", sphere=(pos, 10.0, 0.3, 0.5),
+                gravity=(0, 0, -2e-4))
+    o.init_equilibrium()
+    g.init_fluid()
+    o.step(3)
+    g.step(3)
+    cells_close(o, g, 3, 5e-3)
+    ho, hg = o.history(), g.history()
+    Fs = 0.7 * 2e-4 * math.pi * 1000 / 6
+    assert np.abs(hg[:, 0:3] - ho[:, 0:3]).max() < 2e-2 * Fs
