@@ -318,7 +318,8 @@ def adjoint_line(L, workloads, torch, prec, reps):
         "ms_forward": float(np.median(tf)), "ms_backward": float(np.median(tb)),
         "reverse_mlups": N * n / (float(np.median(tb)) * 1e-3) / 1e6,
         "J": J.item(), "dJ_dtau": gt.item(), "dJ_dgx": gf[0].item(),
-        "roofline": roofline(prof, "k_adj_plain (reverse stream-collide, %s)" % prec, None),
+        "roofline": roofline(prof, "k_adj_plain (reverse stream-collide, %s)" % prec,
+                             profiled_traffic("k_adj_plain_%s_adjoint64.md" % prec, "traffic_bytes_per_launch")),
         "bytes_per_cell_reverse": 19 * (8 if prec == "fp64" else 4) * 3,
     }
     sim.close()
@@ -437,7 +438,8 @@ def main():
             "ms_per_step": bms / args.batch_steps, "launches_per_step": (b1[2] - b0[2]) / args.batch_steps,
             "autotuner": {"threads_per_tile": int(info[2]), "z_cells_per_thread": int(info[3]),
                           "candidate_us": [v / 1e3 for v in info[4:8]]},
-            "roofline": roofline(bprof, "k_batch_bulk (%s)" % prec, None),
+            "roofline": roofline(bprof, "k_batch_bulk (%s)" % prec,
+                                 profiled_traffic("k_batch_bulk_%s_batch64.md" % prec, "traffic_bytes_per_launch")),
             "clocks": clk_b.summary(),
         }
     # --------------------------------------------- differentiation (adjoint)

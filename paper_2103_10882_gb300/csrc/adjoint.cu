@@ -479,7 +479,16 @@ struct AdjointEngine {
     int* near_count = nullptr;
     int near_cap = 0;
     bool forward_done = false;
+    bool geometry_done = false;   // kind bytes and near list of the (fixed) sphere
     double tau = 0, F[3] = {0, 0, 0};
+    // the forward pass (one per parity of the handle's buffers) and the reverse
+    // sweep replayed from CUDA graphs; dropped when tau, the body force or the
+    // objective's axis change
+    cudaGraphExec_t gfwd[2] = {nullptr, nullptr};
+    cudaGraphExec_t gbwd = nullptr;
+    double graph_tau = -1.0, graph_F[3] = {0, 0, 0};
+    int graph_axis = -1;
+    cudaStream_t capture_stream = nullptr;
 };
 
 namespace {
@@ -494,8 +503,6 @@ void forward_step(lbmp_handle* h, const S* src, S* dst, double* force_out) {
                        h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials, &nb, h->status, h->stream);
     launch_refill<S>(dst, h->flags[h->fcur], h->flags[h->fcur], h->G, h->box, h->d_ps, A(1), A(1), h->stream);
     if (force_out) k_adj_force<<<1, 32, 0, h->stream>>>(h->partials, nb, force_out);
-    h->launches += force_out ? 4 : 3;
-    h->updates += h->G.n;
 }
 
 template <typename S>
@@ -504,7 +511,57 @@ S* state(AdjointEngine* E, int m, int j, size_t n) {
     return (S*)E->seg + (size_t)j * 19 * n;
 }
 
+void drop_graphs(AdjointEngine* E) {
+    for (auto& g : E->gfwd)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    if (E->gbwd) {
+        cudaGraphExecDestroy(E->gbwd);
+        E->gbwd = nullptr;
+    }
+}
+
+// Enqueues `body` on the handle's stream: replayed from *graph, captured on a
+// private stream the first time (the caller's stream may be the legacy
+// default stream, which cannot be captured).  Profiling runs plain launches.
+template <typename F>
+lbmp_status captured(lbmp_handle* h, AdjointEngine* E, cudaGraphExec_t* graph, F&& body) {
+    if (h->profiling) {
+        body();
+        return LBMP_OK;
+    }
+    if (!*graph) {
+        if (!E->capture_stream && cudaStreamCreateWithFlags(&E->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return LBMP_ERR_CUDA;
+        // the capture stream starts after the work already queued on the caller's stream
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return LBMP_ERR_CUDA;
+        cudaEventRecord(ev, h->stream);
+        cudaStreamWaitEvent(E->capture_stream, ev, 0);
+        cudaEventDestroy(ev);
+        cudaStream_t user = h->stream;
+        h->stream = E->capture_stream;
+        if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            h->stream = user;
+            return LBMP_ERR_CUDA;
+        }
+        body();
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+        h->stream = user;
+        if (e != cudaSuccess) return LBMP_ERR_CUDA;
+        const cudaError_t e2 = cudaGraphInstantiate(graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) return LBMP_ERR_CUDA;
+    }
+    return cudaGraphLaunch(*graph, h->stream) == cudaSuccess ? LBMP_OK : LBMP_ERR_CUDA;
+}
+
 void release(lbmp_handle* h, AdjointEngine* E) {
+    drop_graphs(E);
+    if (E->capture_stream) cudaStreamDestroy(E->capture_stream);
     void* ptrs[] = {E->ckpt, E->seg, E->nu[0], E->nu[1], E->u0, E->forces, E->acc, E->kind, E->blk, E->near_list,
                     E->near_count};
     for (void* p : ptrs)
@@ -516,6 +573,8 @@ void release(lbmp_handle* h, AdjointEngine* E) {
 
 void adjoint_destroy(lbmp_handle* h) {
     if (!h->adj) return;
+    drop_graphs(h->adj);
+    if (h->adj->capture_stream) cudaStreamDestroy(h->adj->capture_stream);
     delete h->adj;   // device memory is released with the handle's allocations
     h->adj = nullptr;
 }
@@ -571,37 +630,53 @@ lbmp_status adjoint_forward(lbmp_handle* h, const double* u0, int nsteps, int in
     E->axis = axis;
     E->tau = h->tau;
     for (int a = 0; a < 3; ++a) E->F[a] = h->body_force[a];
-    // geometry of the reverse step (the sphere is fixed)
-    const unsigned gb = (unsigned)E->plain_blocks;
-    k_adj_kind<<<gb, AT, 0, h->stream>>>(h->flags[h->fcur], h->G, E->kind, E->blk);
-    k_adj_near_list<<<gb, AT, 0, h->stream>>>(E->kind, E->blk, h->G, E->near_list, E->near_count);
-    h->launches += 2;
-    // the near list is fixed while the sphere is: size its grid once
-    if (cudaMemcpyAsync(&E->near_cells, E->near_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess)
-        return LBMP_ERR_CUDA;
-    h->d2h += sizeof(int);
-    E->near_blocks = std::max(1, (E->near_cells + AT - 1) / AT);
+    if (E->graph_tau != h->tau || E->graph_F[0] != h->body_force[0] || E->graph_F[1] != h->body_force[1] ||
+        E->graph_F[2] != h->body_force[2] || E->graph_axis != axis) {
+        drop_graphs(E);
+        E->graph_tau = h->tau;
+        E->graph_axis = axis;
+        for (int a = 0; a < 3; ++a) E->graph_F[a] = h->body_force[a];
+    }
+    if (!E->geometry_done) {   // cells of the reverse step next to the (fixed) sphere
+        const unsigned gb = (unsigned)E->plain_blocks;
+        k_adj_kind<<<gb, AT, 0, h->stream>>>(h->flags[h->fcur], h->G, E->kind, E->blk);
+        k_adj_near_list<<<gb, AT, 0, h->stream>>>(E->kind, E->blk, h->G, E->near_list, E->near_count);
+        h->launches += 2;
+        if (cudaMemcpyAsync(&E->near_cells, E->near_count, sizeof(int), cudaMemcpyDeviceToHost, h->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess)
+            return LBMP_ERR_CUDA;
+        h->d2h += sizeof(int);
+        E->near_blocks = std::max(1, (E->near_cells + AT - 1) / AT);
+        E->geometry_done = true;
+    }
     cudaMemcpyAsync(E->u0, u0, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, h->stream);
-    with_adj_storage(h->cfg.precision, [&](auto tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        const double zero[3] = {0.0, 0.0, 0.0};
-        S* a = (S*)h->pops[h->cur];
-        S* b = (S*)h->pops[1 - h->cur];
-        launch_init_equilibrium<S>(a, h->flags[h->fcur], h->G, 1.0, zero, u0, (typename Store<S>::A)1, h->stream);
-        cudaMemcpyAsync(E->ckpt, a, E->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
-        for (int s = 1; s <= nsteps; ++s) {
-            forward_step<S>(h, a, b, E->forces + (size_t)(s - 1) * 3);
-            std::swap(a, b);
-            h->cur = 1 - h->cur;
-            h->steps += 1;
-            if (s % interval == 0 && s / interval < nckpt)
-                cudaMemcpyAsync((char*)E->ckpt + E->state_bytes * (size_t)(s / interval), a, E->state_bytes,
-                                cudaMemcpyDeviceToDevice, h->stream);
-        }
+    const int par = h->cur;
+    const lbmp_status st = captured(h, E, &E->gfwd[par], [&]() {
+        with_adj_storage(h->cfg.precision, [&](auto tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            const double zero[3] = {0.0, 0.0, 0.0};
+            S* a = (S*)h->pops[par];
+            S* b = (S*)h->pops[1 - par];
+            launch_init_equilibrium<S>(a, h->flags[h->fcur], h->G, 1.0, zero, E->u0, (typename Store<S>::A)1,
+                                       h->stream);
+            cudaMemcpyAsync(E->ckpt, a, E->state_bytes, cudaMemcpyDeviceToDevice, h->stream);
+            for (int s = 1; s <= nsteps; ++s) {
+                forward_step<S>(h, a, b, E->forces + (size_t)(s - 1) * 3);
+                std::swap(a, b);
+                if (s % interval == 0 && s / interval < nckpt)
+                    cudaMemcpyAsync((char*)E->ckpt + E->state_bytes * (size_t)(s / interval), a, E->state_bytes,
+                                    cudaMemcpyDeviceToDevice, h->stream);
+            }
+        });
     });
+    if (st != LBMP_OK) return st;
+    h->cur = (par + nsteps) & 1;
+    h->steps += nsteps;
+    h->launches += 1 + 4LL * nsteps;
+    h->updates += (long long)nsteps * h->G.n;
     k_adj_mean<<<1, 32, 0, h->stream>>>(E->forces, nsteps, axis, J);
-    h->launches += 3;
+    h->launches += 1;
     if (forces)
         cudaMemcpyAsync(forces, E->forces, sizeof(double) * 3 * (size_t)nsteps, cudaMemcpyDeviceToDevice, h->stream);
     E->forward_done = true;
@@ -618,10 +693,8 @@ lbmp_status adjoint_backward(lbmp_handle* h, const double* dJ, double* grad_tau,
     const size_t n = (size_t)h->G.n;
     const int N = E->nsteps, K = E->interval;
     const int cli = h->cfg.boundary == LBMP_CLI ? 1 : 0;
-    cudaMemsetAsync(E->acc, 0, sizeof(double) * 5 * (size_t)E->acc_blocks, h->stream);
-    cudaMemsetAsync(E->nu[0], 0, E->nu_bytes, h->stream);
-    int cur = 0;   // nu[cur] holds nu^{n+1}
     const unsigned gb = (unsigned)E->plain_blocks, gn = (unsigned)E->near_blocks;
+    lbmp_status st = LBMP_OK;
     with_adj_storage(h->cfg.precision, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         using A = typename Store<S>::A;
@@ -633,31 +706,38 @@ lbmp_status adjoint_backward(lbmp_handle* h, const double* dJ, double* grad_tau,
         for (int a = 0; a < 3; ++a) P.F[a] = (A)h->body_force[a];
         P.seed = (A)(1.0 / (double)N);
         P.axis = E->axis;
-        for (int m = E->nckpt - 1; m >= 0; --m) {
-            const int s0 = m * K, len = std::min(K, N - s0);
-            for (int j = 1; j < len; ++j) forward_step<S>(h, state<S>(E, m, j - 1, n), state<S>(E, m, j, n), nullptr);
-            for (int s = s0 + len; s > s0; --s) {
-                const S* gprev = state<S>(E, m, s - 1 - s0, n);
-                const A* nu_next = (const A*)E->nu[cur];
-                A* nu_out = (A*)E->nu[1 - cur];
-                const long long ev = profile_mark(h);
-                k_adj_plain<S><<<gb, AT, 0, h->stream>>>(gprev, nu_next, nu_out, E->kind, h->G, P, E->acc);
-                // algorithmic bytes: 19 populations of g^{n-1} read, 19 adjoint values read and written per cell
-                const double cells = (double)n - (double)E->near_cells;
-                profile_kernel(h, ev, profile_mark(h), cells * (19.0 * sizeof(S) + 38.0 * sizeof(A)), cells);
-                k_adj_near<S><<<gn, AT, 0, h->stream>>>(gprev, nu_next, nu_out, h->flags[h->fcur], E->near_list,
-                                                       E->near_count, h->G, P, h->d_ps, cli, s < N ? 1 : 0,
-                                                       E->acc + (size_t)5 * E->plain_blocks);
-                cur = 1 - cur;
-                h->launches += 2;
+        st = captured(h, E, &E->gbwd, [&]() {
+            cudaMemsetAsync(E->acc, 0, sizeof(double) * 5 * (size_t)E->acc_blocks, h->stream);
+            cudaMemsetAsync(E->nu[0], 0, E->nu_bytes, h->stream);
+            int cur = 0;   // nu[cur] holds nu^{n+1}
+            for (int m = E->nckpt - 1; m >= 0; --m) {
+                const int s0 = m * K, len = std::min(K, N - s0);
+                for (int j = 1; j < len; ++j)
+                    forward_step<S>(h, state<S>(E, m, j - 1, n), state<S>(E, m, j, n), nullptr);
+                for (int s = s0 + len; s > s0; --s) {
+                    const S* gprev = state<S>(E, m, s - 1 - s0, n);
+                    const A* nu_next = (const A*)E->nu[cur];
+                    A* nu_out = (A*)E->nu[1 - cur];
+                    const long long ev = profile_mark(h);
+                    k_adj_plain<S><<<gb, AT, 0, h->stream>>>(gprev, nu_next, nu_out, E->kind, h->G, P, E->acc);
+                    // algorithmic bytes: 19 populations of g^{n-1} read, 19 adjoint values read and written per cell
+                    const double cells = (double)n - (double)E->near_cells;
+                    profile_kernel(h, ev, profile_mark(h), cells * (19.0 * sizeof(S) + 38.0 * sizeof(A)), cells);
+                    k_adj_near<S><<<gn, AT, 0, h->stream>>>(gprev, nu_next, nu_out, h->flags[h->fcur], E->near_list,
+                                                           E->near_count, h->G, P, h->d_ps, cli, s < N ? 1 : 0,
+                                                           E->acc + (size_t)5 * E->plain_blocks);
+                    cur = 1 - cur;
+                }
             }
-        }
-        if (grad_u0) {
-            k_adj_init_grad<A><<<gb, AT, 0, h->stream>>>((const A*)E->nu[cur], h->flags[h->fcur], E->kind, h->G, E->u0,
-                                                         h->d_ps, cli, P.seed, E->axis, dJ, grad_u0);
+        });
+        h->launches += 3LL * (N - E->nckpt) + 2LL * N;
+        if (st == LBMP_OK && grad_u0) {   // nu^1 sits in nu[N % 2] after N reverse steps
+            k_adj_init_grad<A><<<gb, AT, 0, h->stream>>>((const A*)E->nu[N & 1], h->flags[h->fcur], E->kind, h->G,
+                                                         E->u0, h->d_ps, cli, P.seed, E->axis, dJ, grad_u0);
             h->launches += 1;
         }
     });
+    if (st != LBMP_OK) return st;
     k_adj_params<<<1, AT, 0, h->stream>>>(E->acc, E->plain_blocks + E->near_blocks, h->tau, h->magic, dJ, grad_tau,
                                           grad_force);
     h->launches += 1;

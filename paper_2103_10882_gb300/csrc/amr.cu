@@ -8,7 +8,8 @@
 // resolution) in one pool, real blocks first, both in block-position order.
 // One level-l step (recursive, finer levels sub-cycled twice, Rohde's scheme
 // named in Sec. 4.1):
-//   k_explode   ghost cells of level l+1 <- post-collision level-l cell containing them
+//   k_explode   ghost cells of level l+1 in use <- post-collision level-l cell
+//               containing them (into the buffer of the first sub-step)
 //   (two level-(l+1) steps)
 //   k_update    real level-l cells: pull from real/ghost neighbours, or, for
 //               hosts (neighbours of the finer region), the mean of their
@@ -116,7 +117,7 @@ __device__ __forceinline__ void rescale19(A f[19], A kp, A km) {
 // --------------------------------------------------------------- explosion
 template <typename S>
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0, S* __restrict__ f1,
+    k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0,
               typename Store<S>::A kp, typename Store<S>::A km, int rescale, typename Store<S>::A scale,
               typename Store<S>::A inv_scale, const int* __restrict__ list, int n, int* __restrict__ status) {
     using A = typename Store<S>::A;
@@ -139,10 +140,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
         for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(csrc + paddr(pb, q, pc), inv_scale);
         if (rescale) rescale19<A>(f, kp, km);
 #pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
-            Store<S>::store(f1 + paddr(b, q, c), f[q], scale);
-        }
+        for (int q = 0; q < 19; ++q) Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
     }
 }
 
@@ -246,6 +244,10 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
                     }
                     continue;
                 }
+                // upwind position outside a walled domain: the ghost's exploded value, kept in the
+                // buffer of the first sub-step (this step's dst; static ghosts are never written)
+                g[q] = Store<S>::load(U.dst + (unsigned)((nbk * 19 + q) * B3 + sc), inv);
+                continue;
             }
             g[q] = Store<S>::load(U.src + (unsigned)((nbk * 19 + q) * B3 + sc), inv);   // pools hold < 2^31 elements
         }
@@ -257,8 +259,9 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 
 // One launch per level step: the first gblocks CTAs stream the active ghost
 // cells of the level (from a list of pool block << 12 | cell, no collision;
-// static ghost cells keep the values the explosion wrote into both
-// buffers); the others update the real blocks, one CTA per z-slice of a
+// static ghost cells keep the exploded values in the first sub-step's
+// buffer, and the second sub-step pulls through them from the coarser level
+// directly); the others update the real blocks, one CTA per z-slice of a
 // block (256 cells, full warps).  Both read src and write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
 __global__ void __launch_bounds__(UPD_THREADS)
@@ -304,11 +307,13 @@ __device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int l
 }
 
 constexpr int BNDW_THREADS = 256;
+constexpr int BND_CHUNK = 128;   // box cells per boundary block
 
 // Boundary cells of the finest level (flag 2: fluid with a solid
-// neighbour), found from the mask the remap wrote in box order: each warp
-// takes 32 consecutive box cells and processes the marked ones one at a
-// time, lane q handling population q (CLI links of Sec. 2.3, geometry in the
+// neighbour), found from the mask the remap wrote in box order: each block
+// compacts the marked cells of its chunk of BND_CHUNK box cells and its
+// warps take them in turn, one cell per warp at a time, lane q handling
+// population q (CLI links of Sec. 2.3, geometry in the
 // population arithmetic, FP64 force partials), with a cooperative
 // collision.  The level update skips these cells, so this kernel runs
 // beside it.  The block that finishes last sums the partials and runs the
@@ -328,15 +333,13 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long t0 = ((long long)blockIdx.x * (BNDW_THREADS / 32) + wib) * 32;
-    const long long tl = t0 + lane;
-    unsigned bits = __ballot_sync(0xffffffffu, tl < B.cells && mask[tl] != 0);
+    __shared__ int sl[BND_CHUNK];
+    const long long t0 = (long long)blockIdx.x * BND_CHUNK;
+    const int nm = block_compact_mask(mask, t0, B.cells, BND_CHUNK, sl);
     LinkSums acc;
-    while (bits) {
-        const int j = __ffs(bits) - 1;
-        bits &= bits - 1;
+    for (int i = wib; i < nm; i += BNDW_THREADS / 32) {
         int g[3], c;
-        box_cell((int)(t0 + j), D.n, D.periodic, B, Bf, g);   // marked cells are inside the domain
+        box_cell((int)(t0 + sl[i]), D.n, D.periodic, B, Bf, g);   // marked cells are inside the domain
         const int b = locate(D, g, &c);
         const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
         A gq = A(0);
@@ -373,7 +376,7 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     if (last_block_done(done, (int)gridDim.x)) particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status);
 }
 
-constexpr int LINK_THREADS = 256;
+constexpr int LINK_THREADS = 64;   // remap and compaction blocks: small, so the box spreads over the SMs
 
 // Remap of Sec. 2.3 after the particle moved, over the box of finest cells
 // around the sphere, in one pass: the new solid flag of every cell (the
@@ -406,21 +409,21 @@ __global__ void __launch_bounds__(LINK_THREADS)
                 atomicOr(status, STATUS_NOT_FINEST);
             } else {
                 const size_t x = (size_t)b * B3 + c;
-                const bool solid = ball_flag(g, D.n, D.periodic, F, P);
+                bool any_nb = false;
+                const bool solid = ball_flag_and_neighbours(g, D.n, D.periodic, F, P, &any_nb);
                 if (solid) {
                     fnext[x] = FLAG_SOLID;
 #pragma unroll
                     for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
                 } else {
                     const bool uncovered = fcur[x] == FLAG_SOLID;
+                    is_b = any_nb ? 1 : 0;
                     A rsum = A(0);
                     int cnt = 0;
-                    for (int q = 1; q < 19; ++q) {
+                    for (int q = 1; uncovered && q < 19; ++q) {
                         int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
                         if (!wrap3(v, D)) continue;
-                        const bool vs = ball_flag(v, D.n, D.periodic, F, P);
-                        is_b |= vs ? 1 : 0;
-                        if (!uncovered || vs) continue;
+                        if (ball_flag(v, D.n, D.periodic, F, P)) continue;
                         int vc;
                         const int vb = locate(D, v, &vc);
                         if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] == FLAG_SOLID) continue;
@@ -738,6 +741,7 @@ struct AmrEngine {
     std::vector<std::vector<uint8_t>> cover;      // block coverage per level of the current layout
     cudaStream_t side = nullptr;                  // k_amr_boundary runs here, beside the finest update
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
 };
 
 void amr_drop_graphs(AmrEngine* E) {
@@ -1181,8 +1185,8 @@ void enqueue_advance(lbmp_handle* h, int l) {
         kappa_post(V, F, &kp, &km);
         if (F.nxlist > 0) {
             k_explode<S><<<(unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, h->stream>>>(
-                view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[0], (S*)F.d_pops[1], (A)kp, (A)km,
-                rescale, P.scale, P.inv_scale, F.d_xlist, F.nxlist, h->status);
+                view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[F.cur], (A)kp, (A)km, rescale,
+                P.scale, P.inv_scale, F.d_xlist, F.nxlist, h->status);
             h->launches += 1;
         }
         E->substep[l + 1] = 0;
@@ -1248,12 +1252,13 @@ void enqueue_advance(lbmp_handle* h, int l) {
     if (V.nreal > 0 || gblocks > 0) {
         const unsigned grid = (unsigned)(V.nreal * 16 + gblocks);
         const int* gl = V.d_glist;
-        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
-        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
-        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
-        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
-        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
-        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, h->stream>>>(U, gl, ng, gblocks);
+        cudaStream_t st = h->stream;
+        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
         h->launches += 1;
     }
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
@@ -1295,6 +1300,7 @@ lbmp_status amr_create(lbmp_handle* h) {
         cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return LBMP_ERR_CUDA;
+
     if (cudaMemsetAsync(E->d_done, 0, sizeof(int), h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return regrid_now(h);
 }
@@ -1306,6 +1312,7 @@ void amr_destroy(lbmp_handle* h) {
     if (h->amr->side) cudaStreamDestroy(h->amr->side);
     if (h->amr->ev_fork) cudaEventDestroy(h->amr->ev_fork);
     if (h->amr->ev_join) cudaEventDestroy(h->amr->ev_join);
+
     for (auto& V : h->amr->lv) free_level(h, V);
     delete h->amr;
     h->amr = nullptr;
@@ -1328,7 +1335,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
     const double shell = 4.0 / 3.0 * M_PI * (ro * ro * ro - ri * ri * ri);
     h->list_cap = (int)std::min<double>((double)B.cells, std::ceil(shell) + 64.0);
     h->list = (int*)handle_alloc(h, sizeof(int) * (size_t)h->list_cap);
-    E->boundary_blocks = (int)((B.cells + BNDW_THREADS - 1) / BNDW_THREADS);   // a warp per 32 box cells
+    E->boundary_blocks = (int)((B.cells + BND_CHUNK - 1) / BND_CHUNK);
     h->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)E->boundary_blocks);
     h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
     h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -449,10 +450,14 @@ lbmp_status lbmp_set_tau(lbmp_handle* h, double tau) {
 
 lbmp_status lbmp_set_gravity(lbmp_handle* h, const double g[3]) {
     if (!h || !g) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_gravity: NULL argument");
-    lbmp_status s = download_particle(h);
-    if (s != LBMP_OK) return s;
+    if (h->batch) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_set_gravity: gravity is set per simulation of a batch");
     for (int a = 0; a < 3; ++a) h->h_ps.g[a] = g[a];
-    return upload_particle(h);
+    // kernels only read the gravity field, so it is written alone, ordered on the
+    // stream (the copy from the caller's memory is staged before the call returns)
+    LBMP_CK(h, cudaMemcpyAsync(reinterpret_cast<char*>(h->d_ps) + offsetof(ParticleState, g), h->h_ps.g,
+                               sizeof(h->h_ps.g), cudaMemcpyHostToDevice, h->stream));
+    h->h2d += sizeof(h->h_ps.g);
+    return LBMP_OK;
 }
 
 lbmp_status lbmp_set_body_force(lbmp_handle* h, const double f[3]) {

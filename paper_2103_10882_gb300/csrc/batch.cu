@@ -34,6 +34,7 @@ struct SimDev {
 };
 
 constexpr int BW = 256;   // threads of the boundary, particle and remap kernels
+constexpr int BND_CHUNK = 512;   // box cells per boundary block (fewer, fuller blocks: the fixed cost per block dominates)
 // Cell flags: fluid, solid (centre inside the sphere), fluid with a solid
 // D3Q19 neighbour (updated by k_batch_boundary instead of the bulk kernel).
 constexpr uint8_t FLAG_FLUID = 0, FLAG_SOLID = 1, FLAG_BOUNDARY = 2;
@@ -90,8 +91,9 @@ __global__ void __launch_bounds__(512) k_batch_bulk(const S* __restrict__ src, S
 
 // ----------------------------------------------------------------- boundary
 // Boundary cells of every simulation (flag 2), found from the remap's mask
-// in box order: each warp takes 32 consecutive cells of its simulation's
-// box and processes the marked ones, lane q handling population q (CLI
+// in box order: each block compacts the marked cells of its chunk of
+// BND_CHUNK box cells and its warps take them in turn, lane q handling
+// population q (CLI
 // links, geometry in the population arithmetic, FP64 force partials), with
 // a cooperative collision.  The grid is flat: block b belongs to simulation
 // bnd_sim[b], which owns bnd_n blocks (a warp per 32 box cells) and as many
@@ -124,15 +126,13 @@ __global__ void __launch_bounds__(BW)
     const uint8_t* fl = flags + D.flag_off;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const size_t n = (size_t)G.n;
-    const long long t0 = ((long long)(blockIdx.x - D.bnd_off) * (BW / 32) + wib) * 32;
-    const long long tl = t0 + lane;
-    unsigned bits = __ballot_sync(0xffffffffu, tl < D.box.cells && mask[D.mask_off + tl] != 0);
+    __shared__ int sl[BND_CHUNK];
+    const long long t0 = (long long)(blockIdx.x - D.bnd_off) * BND_CHUNK;
+    const int nm = block_compact_mask(mask + D.mask_off, t0, D.box.cells, BND_CHUNK, sl);
     LinkSums acc;
-    while (bits) {
-        const int j = __ffs(bits) - 1;
-        bits &= bits - 1;
+    for (int i = wib; i < nm; i += BW / 32) {
         int xyz[3];
-        box_cell((int)(t0 + j), n3, per3, D.box, Bf, xyz);
+        box_cell((int)(t0 + sl[i]), n3, per3, D.box, Bf, xyz);
         const int x = xyz[0], y = xyz[1], z = xyz[2];
         const size_t cell = (size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * (size_t)z);
         A gq = A(0);
@@ -204,19 +204,19 @@ __global__ void __launch_bounds__(BW)
     uint8_t* fn = fnext + D.flag_off;
     S* p0 = pops + D.pop_off;
     int is_b = 0;
-    if (ball_flag(p, n3, G.periodic, F, P)) {
+    bool any_nb = false;
+    if (ball_flag_and_neighbours(p, n3, G.periodic, F, P, &any_nb)) {
         fn[c] = FLAG_SOLID;
         for (int q = 0; q < 19; ++q) Store<S>::store(p0 + (size_t)q * n + c, A(0), scale);
     } else {
         const bool uncovered = fc[c] == FLAG_SOLID;
+        is_b = any_nb ? 1 : 0;
         A rsum = A(0);
         int cnt = 0;
-        for (int q = 1; q < 19; ++q) {
+        for (int q = 1; uncovered && q < 19; ++q) {
             int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
             for (int a = 0; a < 3; ++a) v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
-            const bool vs = ball_flag(v, n3, G.periodic, F, P);
-            is_b |= vs ? 1 : 0;
-            if (!uncovered || vs) continue;
+            if (ball_flag(v, n3, G.periodic, F, P)) continue;
             const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
             if (fc[y] == FLAG_SOLID) continue;
             A r = A(1);
@@ -448,7 +448,7 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
         const int nbx = (int)((X.cells + BW - 1) / BW);
         max_box = std::max(max_box, nbx);
         D.bnd_off = (int)bnd_sim.size();
-        D.bnd_n = nbx;   // a warp per 32 box cells
+        D.bnd_n = (int)((X.cells + BND_CHUNK - 1) / BND_CHUNK);
         for (int j = 0; j < D.bnd_n; ++j) bnd_sim.push_back(s);
         D.hist_off = (long long)s * std::max(1, h->cfg.history_capacity);
     }

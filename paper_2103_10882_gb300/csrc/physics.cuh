@@ -362,7 +362,8 @@ __device__ __forceinline__ void box_frame_init(BoxFrame& F, const int n[3], cons
         const double f = floor(P.x[a]);
         F.Xi[a] = (int)f;
         F.Xh[a] = (float)(0.5 - (P.x[a] - f));
-        wide |= periodic[a] && P.r > 0.4 * n[a];
+        // a sphere reaching within two cells of half a period: the FP32 tests skip minimum images
+        wide |= periodic[a] && (P.r > 0.4 * n[a] || P.r + 2.0 >= 0.5 * n[a]);
     }
     const double rr = P.r * P.r, m = 1e-5 * (rr + 1.0);
     F.lo = wide ? -1.0f : (float)(rr - m);   // a sphere this wide takes the FP64 path everywhere
@@ -407,73 +408,120 @@ __device__ __forceinline__ bool ball_flag(const int p[3], const int n[3], const 
     return inside_ball_exact(p, n, periodic, P);
 }
 
-// Algorithm 1 after the LBM step, on the staged particle record.
-__device__ __forceinline__ void particle_advance(ParticleState& P, const double FT[6], const GridDesc& G,
-                                                 double* __restrict__ history, int hist_cap,
-                                                 int* __restrict__ status) {
-    const double Fh[3] = {FT[0], FT[1], FT[2]};
-    const double Th[3] = {FT[3], FT[4], FT[5]};
+// Solid flag of cell p and whether any of its 18 D3Q19 neighbours is solid,
+// both as defined by the exact ball predicate.  The neighbours' FP32
+// squared distances follow from the cell's own FP32 offset t as
+// (t + c_q)^2, one more rounding per component than ball_flag, well inside
+// the same margin; undecided cells take the FP64 expression at the wrapped
+// neighbour position.  A box wider than half a period takes the FP64 path
+// everywhere (lo < 0, see box_frame_init), so no minimum image is needed for
+// the neighbours here.
+__device__ __forceinline__ bool ball_flag_and_neighbours(const int p[3], const int n[3], const int periodic[3],
+                                                         const BoxFrame& F, const ParticleState& P, bool* any_nb) {
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        int v = p[a] - F.Xi[a];
+        if (periodic[a]) {
+            const float u = (float)v + F.Xh[a], half = 0.5f * (float)n[a];
+            v += u > half ? -n[a] : (u < -half ? n[a] : 0);
+        }
+        t[a] = (float)v + F.Xh[a];
+    }
+    const float e0 = fmaf(t[2], t[2], fmaf(t[1], t[1], t[0] * t[0]));
+    const bool own = e0 < F.lo ? true : (e0 > F.hi ? false : inside_ball_exact(p, n, periodic, P));
+    bool any = false;
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {
+        const float a0 = t[0] + (float)cx(q), a1 = t[1] + (float)cy(q), a2 = t[2] + (float)cz(q);
+        const float e = fmaf(a2, a2, fmaf(a1, a1, a0 * a0));
+        if (e < F.lo) any = true;
+        else if (e <= F.hi && !any) {
+            int v[3] = {p[0] + cx(q), p[1] + cy(q), p[2] + cz(q)};
+            bool ok = true;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (v[a] < 0 || v[a] >= n[a]) {
+                    if (!periodic[a]) ok = false;
+                    v[a] = v[a] < 0 ? v[a] + n[a] : v[a] - n[a];
+                }
+            }
+            if (ok && inside_ball_exact(v, n, periodic, P)) any = true;
+        }
+    }
+    *any_nb = any;
+    return own;
+}
+
+// One axis a of Algorithm 1's particle update: average of the hydrodynamic
+// force and torque over two steps, gravity/buoyancy, the virtual force and
+// torque from the previous accelerations, and the kick-drift-kick update
+// with the virtually increased mass and moment of inertia.  The axes are
+// independent; P.steps is advanced once afterwards.
+__device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, double Fh, double Th, const GridDesc& G,
+                                                      double* __restrict__ history, int hist_cap,
+                                                      int* __restrict__ status) {
     const double V = P.V, r = P.r;
     const double m = (P.rho_p + P.cv) * V;
     const double I = 0.4 * (P.rho_p + P.cvw) * V * r * r;
     const double inv_m = 1.0 / m, inv_I = 1.0 / I;
     const bool avg = P.force_average && P.steps > 0;
-    double xold[3];
-    for (int a = 0; a < 3; ++a) {
-        const double Fbar = avg ? 0.5 * (Fh[a] + P.Fh_old[a]) : Fh[a];
-        const double Tbar = avg ? 0.5 * (Th[a] + P.Th_old[a]) : Th[a];
-        P.Fh[a] = Fh[a];
-        P.Th[a] = Th[a];
-        P.Fh_old[a] = Fh[a];
-        P.Th_old[a] = Th[a];
-        const double Fg = (P.rho_p - 1.0) * P.g[a] * V;
-        const double Fv = P.cv * V * P.a[a];
-        const double Tv = 0.4 * P.cvw * V * r * r * P.b[a];
-        const double Fp = Fbar + Fg + Fv;
-        const double Tp = Tbar + Tv;
-        P.Fp[a] = Fp;
-        xold[a] = P.x[a];
-        const double acc = Fp * inv_m, bet = Tp * inv_I;
-        if (!P.fixed) {
-            if (P.steps > 0) {   // second half kick of the previous step completes u(t)
-                P.u[a] += 0.5 * acc;
-                P.w[a] += 0.5 * bet;
-            }
-            P.a[a] = acc;
-            P.b[a] = bet;
-            P.u[a] += 0.5 * acc;   // first half kick, then drift with u(t + 1/2)
+    const double Fbar = avg ? 0.5 * (Fh + P.Fh_old[a]) : Fh;
+    const double Tbar = avg ? 0.5 * (Th + P.Th_old[a]) : Th;
+    P.Fh[a] = Fh;
+    P.Th[a] = Th;
+    P.Fh_old[a] = Fh;
+    P.Th_old[a] = Th;
+    const double Fg = (P.rho_p - 1.0) * P.g[a] * V;
+    const double Fv = P.cv * V * P.a[a];
+    const double Tv = 0.4 * P.cvw * V * r * r * P.b[a];
+    const double Fp = Fbar + Fg + Fv;
+    const double Tp = Tbar + Tv;
+    P.Fp[a] = Fp;
+    const double xold = P.x[a];
+    const double acc = Fp * inv_m, bet = Tp * inv_I;
+    if (!P.fixed) {
+        if (P.steps > 0) {   // second half kick of the previous step completes u(t)
+            P.u[a] += 0.5 * acc;
             P.w[a] += 0.5 * bet;
-            P.x[a] += P.u[a];
-        } else {
-            P.a[a] = acc;
-            P.b[a] = bet;
         }
+        P.a[a] = acc;
+        P.b[a] = bet;
+        P.u[a] += 0.5 * acc;   // first half kick, then drift with u(t + 1/2)
+        P.w[a] += 0.5 * bet;
+        P.x[a] += P.u[a];
+    } else {
+        P.a[a] = acc;
+        P.b[a] = bet;
     }
-    const int n3[3] = {G.nx, G.ny, G.nz};
-    for (int a = 0; a < 3; ++a) {
-        if (fabs(P.x[a] - xold[a]) > 0.5 || !(fabs(P.u[a]) < 0.5)) atomicOr(status, STATUS_PARTICLE_JUMP);
-        if (G.periodic[a]) {   // keep the centre inside the periodic box
-            const double L = (double)n3[a];
-            if (P.x[a] >= L) P.x[a] -= L;
-            else if (P.x[a] < 0.0) P.x[a] += L;
-        }
+    if (fabs(P.x[a] - xold) > 0.5 || !(fabs(P.u[a]) < 0.5)) atomicOr(status, STATUS_PARTICLE_JUMP);
+    const int n = a == 0 ? G.nx : (a == 1 ? G.ny : G.nz);
+    if (G.periodic[a]) {   // keep the centre inside the periodic box
+        const double L = (double)n;
+        if (P.x[a] >= L) P.x[a] -= L;
+        else if (P.x[a] < 0.0) P.x[a] += L;
     }
     if (hist_cap > 0) {
         double* h = history + (size_t)(P.steps % hist_cap) * 15;
-        for (int a = 0; a < 3; ++a) {
-            h[a] = Fh[a];
-            h[3 + a] = Th[a];
-            h[6 + a] = P.x[a];
-            h[9 + a] = P.u[a];
-            h[12 + a] = P.w[a];
-        }
+        h[a] = Fh;
+        h[3 + a] = Th;
+        h[6 + a] = P.x[a];
+        h[9 + a] = P.u[a];
+        h[12 + a] = P.w[a];
     }
+}
+
+// Algorithm 1 after the LBM step, on the staged particle record (one thread).
+__device__ __forceinline__ void particle_advance(ParticleState& P, const double FT[6], const GridDesc& G,
+                                                 double* __restrict__ history, int hist_cap,
+                                                 int* __restrict__ status) {
+    for (int a = 0; a < 3; ++a) particle_advance_axis(P, a, FT[a], FT[3 + a], G, history, hist_cap, status);
     P.steps += 1;
 }
 
 // Particle update by one thread block of NT threads: sums the nblocks
 // force partials in a fixed order, stages the record in shared memory,
-// advances it on thread 0 (particle_advance) and writes it back.  The
+// advances its three axes on threads 0..2 and writes it back.  The
 // partials may come from other blocks of the same launch: they are read
 // through L2.
 template <int NT>
@@ -502,10 +550,11 @@ __device__ __forceinline__ void particle_block_update(ParticleState* __restrict_
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        const double FT[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
-        particle_advance(sP, FT, G, history, hist_cap, status);
-    }
+    if (threadIdx.x < 3)   // the three axes in parallel
+        particle_advance_axis(sP, threadIdx.x, red[threadIdx.x][0], red[3 + threadIdx.x][0], G, history, hist_cap,
+                              status);
+    __syncthreads();
+    if (threadIdx.x == 0) sP.steps += 1;
     __syncthreads();
     {
         const int words = (int)(sizeof(ParticleState) / sizeof(int));
@@ -529,6 +578,33 @@ __device__ __forceinline__ bool last_block_done(int* counter, int nblocks) {
     }
     __syncthreads();
     return last != 0;
+}
+
+// Box cells of [t0, t0 + chunk) whose mask byte is set, in box order, into
+// the shared list sl (offsets from t0); returns their number.  blockDim.x
+// is a multiple of 32; chunk may be smaller or larger.  Every thread of the
+// block must call it.
+__device__ __forceinline__ int block_compact_mask(const uint8_t* __restrict__ mask, long long t0, long long cells,
+                                                  int chunk, int* sl) {
+    __shared__ int wcount[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    int total = 0;
+    for (int off = 0; off < chunk; off += (int)blockDim.x) {
+        const long long t = t0 + off + threadIdx.x;
+        const bool m = off + (int)threadIdx.x < chunk && t < cells && mask[t] != 0;
+        const unsigned bits = __ballot_sync(0xffffffffu, m);
+        if (lane == 0) wcount[wid] = __popc(bits);
+        __syncthreads();
+        int base = total, add = 0;
+        for (int w = 0; w < nw; ++w) {
+            if (w < wid) base += wcount[w];
+            add += wcount[w];
+        }
+        if (m) sl[base + __popc(bits & ((1u << lane) - 1u))] = off + threadIdx.x;
+        total += add;
+        __syncthreads();
+    }
+    return total;
 }
 
 }  // namespace lbmp

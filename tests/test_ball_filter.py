@@ -89,3 +89,48 @@ def test_fp32_pretest_adversarial_radii():
                     assert not ref[0]
                 bad_without_margin += int((e[0] <= np.float32(rr)) != ref[0])
     assert bad_without_margin > 0   # the cases do exercise the FP32 rounding
+
+
+C18 = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1],
+                [1, 1, 0], [-1, -1, 0], [1, -1, 0], [-1, 1, 0], [1, 0, 1], [-1, 0, -1],
+                [1, 0, -1], [-1, 0, 1], [0, 1, 1], [0, -1, -1], [0, 1, -1], [0, -1, 1]])
+
+
+def test_neighbour_pretest_never_contradicts_fp64_predicate():
+    """The remap decides the neighbours of a cell from the cell's own FP32
+    offset t as (t + c_q)^2 (one more FP32 rounding per component); the
+    margin still covers it, including cells near half a period of small
+    periodic boxes (spheres reaching within two cells of half a period take
+    the FP64 path everywhere)."""
+    rng = np.random.default_rng(2)
+    f32 = np.float32
+    checked = 0
+    for trial in range(80):
+        n = np.array(rng.choice([10, 16, 24, 64, 512], size=3), dtype=np.int64)
+        r = float(rng.uniform(1.5, 0.45 * n.min()))
+        if np.any(r > 0.4 * n) or np.any(r + 2.0 >= 0.5 * n):
+            continue   # the kernels take the FP64 path for every cell here
+        X = rng.uniform(0, n)
+        m = 4000
+        dirs = rng.normal(size=(m, 3))
+        dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+        rad = r + rng.uniform(-2.0, 2.0, size=m)
+        p = np.floor(X + dirs * rad[:, None]).astype(np.int64) % n
+        Xi = np.floor(X)
+        Xh = (0.5 - (X - Xi)).astype(f32)
+        v = p - Xi.astype(np.int64)
+        t = v.astype(f32) + Xh
+        half = (0.5 * n).astype(f32)
+        v = np.where(t > half, v - n, np.where(t < -half, v + n, v))
+        t = v.astype(f32) + Xh
+        rr = r * r
+        mg = 1e-5 * (rr + 1.0)
+        lo, hi = f32(rr - mg), f32(rr + mg)
+        for c in C18:
+            a = t + c.astype(f32)
+            e = ((a[:, 0] * a[:, 0]) + (a[:, 1] * a[:, 1])) + (a[:, 2] * a[:, 2])
+            ref = exact((p + c) % n, X, r, n)
+            assert not np.any((e < lo) & ~ref)
+            assert not np.any((e > hi) & ref)
+            checked += m
+    assert checked > 0
