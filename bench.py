@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--validate", type=int, default=0,
+                    help="instead of timing: run the refined workload this many level-0 steps in FP64, FP32 and FP16 "
+                         "and report the reduced precisions' errors on the particle's path")
     ap.add_argument("--adjoint-reps", type=int, default=3)
     return ap.parse_args()
 
@@ -262,6 +265,56 @@ def roofline(prof, kernel, traffic):
             "kernel_ms_total": kms}
 
 
+def validate(args):
+    """The refined rising-sphere workload run for args.validate level-0 steps
+    in FP64, FP32 and FP16 storage: rise velocity, lateral drift and
+    trajectory of the reduced precisions against the FP64 run, and each run's
+    MLUPS (one JSON line)."""
+    import numpy as np
+    import torch
+    import paper_2103_10882_gb300 as L
+    w = REFINED
+    tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    runs = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        sim = L.Simulation(w["shape"], precision=prec, tau=tau, bc=w["bc"], levels=w["levels"],
+                           regrid_interval=w["regrid"], history_capacity=1 << 17)
+        sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+                       cv=w["cv"])
+        sim.set_ga(w["ga"], w["u_g"], (0.0, 0.0, -1.0))
+        sim.init_fluid()
+        c0 = sim.counters()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(sim.stream)
+        sim.step_async(args.validate)
+        stop.record(sim.stream)
+        torch.cuda.synchronize()
+        sim.check()
+        c1 = sim.counters()
+        h = sim.history()
+        runs[prec] = dict(hist=h, mlups=(c1[1] - c0[1]) / (start.elapsed_time(stop) * 1e-3) / 1e6)
+        sim.close()
+    ref = runs["fp64"]["hist"]
+    d = w["diameter"]
+    out = {"validate": "refined rising sphere (headline workload), %d level-0 steps = %d finest steps"
+                       % (args.validate, len(ref)),
+           "fp64": {"u_z_end": ref[-1, 11], "z_end": ref[-1, 8], "mlups": runs["fp64"]["mlups"]}}
+    for prec in ("fp32", "fp16"):
+        h = runs[prec]["hist"]
+        n = min(len(h), len(ref))
+        traj = np.sqrt(((h[:n, 6:9] - ref[:n, 6:9]) ** 2).sum(axis=1))
+        lat = np.sqrt((h[n - 1, 6] - h[0, 6]) ** 2 + (h[n - 1, 7] - h[0, 7]) ** 2)
+        lat_ref = np.sqrt((ref[n - 1, 6] - ref[0, 6]) ** 2 + (ref[n - 1, 7] - ref[0, 7]) ** 2)
+        out[prec] = {"u_z_end": h[n - 1, 11],
+                     "u_z_rel_err": abs(h[n - 1, 11] - ref[n - 1, 11]) / abs(ref[n - 1, 11]),
+                     "trajectory_max_err_over_d": float(traj.max() / d),
+                     "lateral_drift": float(lat), "lateral_drift_fp64": float(lat_ref),
+                     "mlups": runs[prec]["mlups"], "speedup_over_fp64": runs[prec]["mlups"] / runs["fp64"]["mlups"]}
+    print(json.dumps(out))
+    return 0
+
+
 def adjoint_line(L, workloads, torch, prec, reps):
     """Gradient of the mean drag on the differentiation workload: forward
     (500 steps, checkpoints every 50) and backward (recompute + reverse
@@ -330,6 +383,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.validate > 0:
+        return validate(args)
     import numpy as np
     import torch
 
