@@ -169,7 +169,7 @@ struct UpdateArgs {
 // Update of one cell of pool block b: real cells pull (or, for hosts,
 // coalesce) and collide; active ghost cells pull only.  nb27 lists the pool
 // ids of block b's 26 neighbours (and itself at index 13).
-template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL>
+template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL, bool RESCALE>
 __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27) {
     using A = typename Store<S>::A;
     const LevelView& D = U.D;
@@ -196,7 +196,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
         }
 #pragma unroll
         for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
-        if (U.rescale) rescale19<A>(g, U.fkp, U.fkm);
+        if (RESCALE) rescale19<A>(g, U.fkp, U.fkm);
     } else {
         // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate
         const int bsx[3] = {lx == 0 ? -1 : 0, 0, lx == 15 ? 1 : 0};
@@ -233,7 +233,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
                         g[q] = A(0);
                         continue;
                     }
-                    if (U.rescale) {   // the rescaled value needs the whole cell
+                    if (RESCALE) {   // the rescaled value needs the whole cell
                         A f[19];
 #pragma unroll
                         for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
@@ -263,7 +263,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 // buffer, and the second sub-step pulls through them from the coarser level
 // directly); the others update the real blocks, one CTA per z-slice of a
 // block (256 cells, full warps).  Both read src and write dst only.
-template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
+template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED, bool RESCALE>
 __global__ void __launch_bounds__(UPD_THREADS)
     k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int gblocks) {
     using A = typename Store<S>::A;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
         if (i < nglist) {
             const int e = glist[i];
             const int b = e >> 12, c = e & 4095;
-            update_cell<S, false, true, false>(U, b, c, U.D.nbr + (size_t)b * 27);
+            update_cell<S, false, true, false, RESCALE>(U, b, c, U.D.nbr + (size_t)b * 27);
         }
         return;
     }
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
         }
         if (f == FLAG_BOUNDARY) return;
     }
-    update_cell<S, HAS_FINE, HAS_COARSE, true>(U, b, c, nb27);
+    update_cell<S, HAS_FINE, HAS_COARSE, true, RESCALE>(U, b, c, nb27);
 }
 
 // ---------------------------------------------------------------- coupling
@@ -1253,12 +1253,18 @@ void enqueue_advance(lbmp_handle* h, int l) {
         const unsigned grid = (unsigned)(V.nreal * 16 + gblocks);
         const int* gl = V.d_glist;
         cudaStream_t st = h->stream;
-        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        // the rescaling option is a template parameter: without it the kernel carries none of its code
+        auto go = [&](auto rs) {
+            constexpr bool R = decltype(rs)::value;
+            if (has_fine && has_coarse) k_update<S, true, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+            else if (has_fine) k_update<S, true, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+            else if (has_coarse && coupled) k_update<S, false, true, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+            else if (has_coarse) k_update<S, false, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+            else if (coupled) k_update<S, false, false, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+            else k_update<S, false, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+        };
+        if (rescale) go(std::true_type{});
+        else go(std::false_type{});
         h->launches += 1;
     }
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
@@ -1338,7 +1344,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
     E->boundary_blocks = (int)((B.cells + BND_CHUNK - 1) / BND_CHUNK);
     h->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)E->boundary_blocks);
     h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
-    h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + 255) / 256));
+    h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + LINK_THREADS - 1) / LINK_THREADS));
     if (!h->list || !h->partials || !h->link_mask || !h->link_blocks) return LBMP_ERR_OOM;
     if (cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return LBMP_ERR_CUDA;
