@@ -100,6 +100,11 @@ def lib():
         L.orc_amr_regrid.restype = ip
         L.orc_amr_regrid.argtypes = [vp]
         L.orc_amr_init_equilibrium.argtypes = [vp, ctypes.c_double, dp, ctypes.c_double, ip, ip]
+        L.orc_amr_set_sensor.restype = ip
+        L.orc_amr_set_sensor.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+        L.orc_amr_block_sensor.restype = ctypes.c_int64
+        L.orc_amr_block_sensor.argtypes = [vp, ip, dp, ctypes.c_int64]
+        L.orc_amr_init_linear.argtypes = [vp, ctypes.c_double, dp, dp, dp]
         L.orc_amr_step.restype = ip
         L.orc_amr_step.argtypes = [vp, ip]
         L.orc_amr_error.restype = ip
@@ -315,6 +320,24 @@ class RefinedSim:
     def init_equilibrium(self, rho=1.0, u=(0.0, 0.0, 0.0), shear=0.0, shear_dir=0, shear_axis=2):
         a, pa = _d(u)
         self._L.orc_amr_init_equilibrium(self._h, float(rho), pa, float(shear), int(shear_dir), int(shear_axis))
+
+    def set_sensor(self, sigma, c=0.2):
+        """Flow sensor of Sec. 4.2.2 (sigma = 0 turns it off); consulted by regrid()."""
+        self._rc(self._L.orc_amr_set_sensor(self._h, float(sigma), float(c)))
+
+    def block_sensor(self, level):
+        """Scaled curl (largest over the block's cells) of every real block of a level."""
+        n = self._L.orc_amr_block_sensor(self._h, int(level), None, 0)
+        out = np.empty(max(n, 0))
+        self._L.orc_amr_block_sensor(self._h, int(level), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return out
+
+    def init_linear(self, A, u0=(0.0, 0.0, 0.0), x0=(0.0, 0.0, 0.0), rho=1.0):
+        """Equilibrium with the linear velocity u0 + A (x - x0) (finest-level units)."""
+        _, pu = _d(u0)
+        Am, pA = _d(np.asarray(A, dtype=np.float64).reshape(9))
+        _, px = _d(x0)
+        self._L.orc_amr_init_linear(self._h, float(rho), pu, pA, px)
 
     def step(self, n=1):
         self._rc(self._L.orc_amr_step(self._h, int(n)))

@@ -124,7 +124,18 @@ int orc_amr_add_sphere(orc_amr* a, const double pos[3], double diameter, double 
                        double cv_omega, int fixed);
 void orc_amr_set_gravity(orc_amr* a, const double g[3]);
 void orc_amr_set_particle_velocity(orc_amr* a, const double u[3], const double w[3]);
+/* Rebuilds the hierarchy for the sphere (and box); with the flow sensor on,
+ * also for the sensor's wishes of every real block (Sec. 4.2.2). */
 int orc_amr_regrid(orc_amr* a);
+/* Flow sensor: refine a block whose scaled curl exceeds sigma, coarsen below
+ * c sigma; sigma = 0 turns it off.  -1 unless 0 < c < 2^-1.5. */
+int orc_amr_set_sensor(orc_amr* a, double sigma, double c);
+/* Scaled curl of every real block of a level (position order); returns the
+ * number of real blocks, -1 for a bad level. */
+int64_t orc_amr_block_sensor(const orc_amr* a, int level, double* out, int64_t cap);
+/* Equilibrium everywhere with the linear velocity u0 + A (x - x0), A row
+ * major, x the cell centre in finest-level units. */
+void orc_amr_init_linear(orc_amr* a, double rho, const double u0[3], const double A[9], const double x0[3]);
 /* Equilibrium everywhere with velocity u + amp sin(2 pi x_axis / L_axis) e_dir. */
 void orc_amr_init_equilibrium(orc_amr* a, double rho, const double u[3], double amp, int dir, int axis);
 /* n coarse (level-0) steps; returns 0 or an error code (1: missing source, 2: sphere not on the finest level). */

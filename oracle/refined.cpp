@@ -74,6 +74,8 @@ struct orc_amr {
     std::vector<int> substep;           // per level: index (0 or 1) of the current step within the coarser step
     bool have_box = false;
     double box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
+    double sensor_sigma = 0.0;          // flow sensor threshold sigma_c (0: off)
+    double sensor_c = 0.0;              // coarsening factor c
 };
 
 namespace {
@@ -257,18 +259,26 @@ Mask grow26(const orc_amr* a, const Mask& m, int l) {
     return out;
 }
 
-// R[l]: level-l block positions covered by blocks of level >= l.
-std::vector<Mask> covered_sets(const orc_amr* a, const Mask& finest) {
+// R[l]: level-l block positions covered by blocks of level >= l.  demand[l]
+// (optional, l >= 1) adds level-l positions that must be covered at level
+// >= l (the flow sensor's wishes); the finest mask is demand[L-1]'s
+// particle part.
+std::vector<Mask> covered_sets(const orc_amr* a, const Mask& finest, const std::vector<Mask>* demand = nullptr) {
     const int L = a->L;
     std::vector<Mask> R(L);
     int nb[3];
     level_lattice(a, 0, nb);
     R[0].assign((size_t)nb[0] * nb[1] * nb[2], 1);
     if (L == 1) return R;
-    R[L - 1] = children_of(a, parents_of(a, finest, L - 1), L - 2);   // all eight siblings
+    Mask top = finest;
+    if (demand)
+        for (size_t i = 0; i < top.size(); ++i) top[i] |= (*demand)[L - 1][i];
+    R[L - 1] = children_of(a, parents_of(a, top, L - 1), L - 2);   // all eight siblings
     for (int l = L - 2; l >= 1; --l) {
         Mask P = parents_of(a, R[l + 1], l + 1);
         Mask X = grow26(a, P, l);
+        if (demand)
+            for (size_t i = 0; i < X.size(); ++i) X[i] |= (*demand)[l][i];
         R[l] = children_of(a, parents_of(a, X, l), l - 1);
     }
     return R;
@@ -491,7 +501,89 @@ void finest_flags(orc_amr* a, std::vector<uint8_t>& nf) {
             }
 }
 
-void regrid_now(orc_amr* a) {
+// ---------------------------------------------------------- flow sensor
+// Scaled curl of the velocity (Sec. 4.2.2, Eq. "sensor_curl"):
+// phi_c = |curl u| s^((r+1)/r) with r = 2 and s the cell size; positions and
+// derivatives are in finest-level units, so s = 2^(L-1-l) on level l.  The
+// velocity of a cell is u = sum_q g_q c_q, the momentum of its stored
+// (post-collision) deviations; a uniform body force shifts it by a constant,
+// which the curl does not see.  Derivatives (the paper gives no stencil):
+// central differences between the block's own cells, one-sided differences
+// on the block's faces, so a block's value depends on its own cells only.
+// A block's value is the largest phi_c of its cells.
+double block_sensor(const orc_amr* a, int l, int b) {
+    const LevelData& D = a->lv[l];
+    const double s = (double)(1 << (a->L - 1 - l));
+    std::vector<double> u((size_t)B3 * 3, 0.0);
+    for (int c = 0; c < B3; ++c)
+        for (int q = 0; q < 19; ++q)
+            for (int k = 0; k < 3; ++k) u[(size_t)c * 3 + k] += D.rg[pidx(b, q, c)] * C[q][k];
+    // d u_comp / d x_axis at local cell p
+    auto deriv = [&](int comp, int axis, const int p[3]) {
+        int lo[3] = {p[0], p[1], p[2]}, hi[3] = {p[0], p[1], p[2]};
+        if (p[axis] > 0) lo[axis] -= 1;
+        if (p[axis] < BS - 1) hi[axis] += 1;
+        const double du = u[(size_t)local_index(hi[0], hi[1], hi[2]) * 3 + comp] -
+                          u[(size_t)local_index(lo[0], lo[1], lo[2]) * 3 + comp];
+        return du / ((double)(hi[axis] - lo[axis]) * s);
+    };
+    double phi = 0.0;
+    for (int z = 0; z < BS; ++z)
+        for (int y = 0; y < BS; ++y)
+            for (int x = 0; x < BS; ++x) {
+                const int p[3] = {x, y, z};
+                const double wx = deriv(2, 1, p) - deriv(1, 2, p);
+                const double wy = deriv(0, 2, p) - deriv(2, 0, p);
+                const double wz = deriv(1, 0, p) - deriv(0, 1, p);
+                const double curl = std::sqrt(wx * wx + wy * wy + wz * wz);
+                phi = std::max(phi, curl * std::pow(s, 1.5));
+            }
+    return phi;
+}
+
+// Positions each level must keep covered because of the flow sensor
+// (Sec. 4.2.2): a real block of level l asks for level l+1 (capped at the
+// finest) when its value exceeds sigma_c, for level l-1 when it is below
+// c sigma_c, else for its own level.  Asking for level t means the block's
+// region is covered at level >= t: its children (t = l+1), itself (t = l)
+// or its parent (t = l-1).  Coarsening then happens only where all eight
+// siblings agree, one level per regrid.
+std::vector<Mask> sensor_demands(const orc_amr* a) {
+    const int L = a->L;
+    std::vector<Mask> dm(L);
+    for (int l = 0; l < L; ++l) {
+        int nb[3];
+        level_lattice(a, l, nb);
+        dm[l].assign((size_t)nb[0] * nb[1] * nb[2], 0);
+    }
+    for (int l = 0; l < L; ++l) {
+        const LevelData& D = a->lv[l];
+        for (size_t b = 0; b < D.rpos.size(); ++b) {
+            const double phi = block_sensor(a, l, (int)b);
+            int t = l;
+            if (phi > a->sensor_sigma) t = std::min(l + 1, L - 1);
+            else if (phi < a->sensor_c * a->sensor_sigma) t = std::max(l - 1, 0);
+            const int* p = D.rpos[b].data();
+            if (t == l + 1) {
+                int nf[3];
+                level_lattice(a, t, nf);
+                for (int s = 0; s < 8; ++s)
+                    dm[t][(2 * p[0] + (s & 1)) + nf[0] * ((2 * p[1] + ((s >> 1) & 1)) + nf[1] * (2 * p[2] + (s >> 2)))] = 1;
+            } else if (t == l) {
+                dm[l][bpos_index(D, p[0], p[1], p[2])] = 1;
+            } else {
+                int nc[3];
+                level_lattice(a, t, nc);
+                dm[t][p[0] / 2 + nc[0] * (p[1] / 2 + nc[1] * (p[2] / 2))] = 1;
+            }
+        }
+    }
+    return dm;
+}
+
+// use_sensor: explicit regrids consult the flow sensor (when it is on);
+// creation, a new sphere and a refined box do not.
+void regrid_now(orc_amr* a, bool use_sensor = false) {
     Mask m;
     int nb[3];
     level_lattice(a, a->L - 1, nb);
@@ -502,7 +594,12 @@ void regrid_now(orc_amr* a) {
         Mask mb = box_mask(a);
         for (size_t i = 0; i < m.size(); ++i) m[i] |= mb[i];
     }
-    build_layout(a, covered_sets(a, m));
+    if (use_sensor && a->sensor_sigma > 0.0) {
+        const std::vector<Mask> dm = sensor_demands(a);
+        build_layout(a, covered_sets(a, m, &dm));
+    } else {
+        build_layout(a, covered_sets(a, m));
+    }
     LevelData& D = a->lv[a->L - 1];
     finest_flags(a, D.flag);
     for (size_t b = 0; b < D.rpos.size(); ++b)
@@ -803,8 +900,42 @@ void orc_amr_set_particle_velocity(orc_amr* a, const double u[3], const double w
 }
 
 int orc_amr_regrid(orc_amr* a) {
-    regrid_now(a);
+    regrid_now(a, true);
     return a->error;
+}
+
+int orc_amr_set_sensor(orc_amr* a, double sigma, double c) {
+    if (sigma < 0.0 || (sigma > 0.0 && !(c > 0.0 && c < std::pow(2.0, -1.5)))) return -1;
+    a->sensor_sigma = sigma;
+    a->sensor_c = c;
+    return 0;
+}
+
+int64_t orc_amr_block_sensor(const orc_amr* a, int level, double* out, int64_t cap) {
+    if (level < 0 || level >= a->L) return -1;
+    const LevelData& D = a->lv[level];
+    const int64_t n = (int64_t)D.rpos.size();
+    if (out)
+        for (int64_t b = 0; b < n && b < cap; ++b) out[b] = block_sensor(a, level, (int)b);
+    return n;
+}
+
+void orc_amr_init_linear(orc_amr* a, double rho, const double u0[3], const double A[9], const double x0[3]) {
+    const int L = a->L;
+    for (int l = 0; l < L; ++l) {
+        LevelData& D = a->lv[l];
+        const double h = (double)(1 << (L - 1 - l));
+        for (size_t b = 0; b < D.rpos.size(); ++b)
+            for (int c = 0; c < B3; ++c) {
+                const int g[3] = {D.rpos[b][0] * BS + c % BS, D.rpos[b][1] * BS + (c / BS) % BS,
+                                  D.rpos[b][2] * BS + c / (BS * BS)};
+                double xr[3], uu[3];
+                for (int k = 0; k < 3; ++k) xr[k] = (g[k] + 0.5) * h - x0[k];
+                for (int i = 0; i < 3; ++i) uu[i] = u0[i] + A[3 * i] * xr[0] + A[3 * i + 1] * xr[1] + A[3 * i + 2] * xr[2];
+                const bool solid = (l == L - 1) && D.flag[b * B3 + c];
+                for (int q = 0; q < 19; ++q) D.rg[pidx((int)b, q, c)] = solid ? 0.0 : geq(q, rho - 1.0, uu);
+            }
+    }
 }
 
 void orc_amr_init_equilibrium(orc_amr* a, double rho, const double u[3], double amp, int dir, int axis) {
