@@ -4,7 +4,8 @@ Default workload (the single rising light sphere on a refined grid): level-0
 box of 64 x 64 x 256 cells in 16^3 blocks, 3 levels (finest 256 x 256 x
 1024), sphere of 20 finest cells, density ratio 0.5, Ga = 200 at u_g = 0.01,
 C_v = 0.5, no-slip walls on x and y, periodic z, regrid every 50 level-0
-steps, FP32 deviation storage.  A timed step is one level-0 step of the full
+steps with the particle criterion and the flow-based curl sensor (Sec.
+4.2.2: sigma_c = 1e-3, c = 0.2), FP32 deviation storage.  A timed step is one level-0 step of the full
 coupled method (Algorithm 1 on the finest level, sub-cycling, explosion and
 coalescence, regrids when due).  MLUPS counts real cell updates of all levels.
 
@@ -38,7 +39,7 @@ BYTES_PER_POP = {"fp64": 8, "fp32": 4, "fp16": 2}
 DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math"}
 
 REFINED = dict(shape=(64, 64, 256), levels=3, diameter=20.0, density_ratio=0.5, ga=200.0, u_g=0.01, cv=0.5,
-               bc=("noslip", "noslip", "periodic"), regrid=50)
+               bc=("noslip", "noslip", "periodic"), regrid=50, sensor=(1e-3, 0.2))
 UNIFORM = dict(shape=(512, 512, 512), diameter=40.0, density_ratio=0.5, ga=200.0, u_g=0.01, cv=0.5)
 
 
@@ -68,7 +69,8 @@ def parse():
 
 def refined_name(prec):
     return ("refined rising sphere: level-0 64x64x256 (16^3 blocks), 3 levels, d=20 finest, pi_p=0.5, Ga=200, "
-            "C_v=0.5, walls x/y, periodic z, regrid every 50 level-0 steps, %s" % prec)
+            "C_v=0.5, walls x/y, periodic z, regrid every 50 level-0 steps (particle + curl sensor sigma_c=1e-3, "
+            "c=0.2), %s" % prec)
 
 
 def uniform_name(edge, prec):
@@ -173,6 +175,21 @@ def refined_start(shape, levels, d):
     return (shape[0] * f / 2 + off[0], shape[1] * f / 2 + off[1], 0.6 * d + off[2])
 
 
+def refined_sim(L, prec, history_capacity=1 << 16):
+    """The headline workload through the public API: hierarchy, sphere,
+    gravity from Ga, refinement sensor, fluid at rest."""
+    w = REFINED
+    tau, _ = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    sim = L.Simulation(w["shape"], precision=prec, tau=tau, bc=w["bc"], levels=w["levels"],
+                       regrid_interval=w["regrid"], history_capacity=history_capacity)
+    sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+                   cv=w["cv"])
+    sim.set_ga(w["ga"], w["u_g"], (0.0, 0.0, -1.0))
+    sim.set_refinement_sensor(*w["sensor"])
+    sim.init_fluid()
+    return sim
+
+
 def cpu_baseline(seconds):
     """The FP64 refined oracle on the host cores, on a bounded sample of the
     same workload: the same hierarchy and sphere for as many level-0 steps as
@@ -184,6 +201,7 @@ def cpu_baseline(seconds):
     o.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
                  cv=w["cv"])
     o.set_gravity((0, 0, -gm))
+    o.set_sensor(*w["sensor"])
     o.init_equilibrium()
     upd = sum((o.block_map(l) >= 0).sum() * 4096 * (1 << l) for l in range(w["levels"]))
     t0 = time.perf_counter()
@@ -277,12 +295,7 @@ def validate(args):
     tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
     runs = {}
     for prec in ("fp64", "fp32", "fp16"):
-        sim = L.Simulation(w["shape"], precision=prec, tau=tau, bc=w["bc"], levels=w["levels"],
-                           regrid_interval=w["regrid"], history_capacity=1 << 17)
-        sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
-                       cv=w["cv"])
-        sim.set_ga(w["ga"], w["u_g"], (0.0, 0.0, -1.0))
-        sim.init_fluid()
+        sim = refined_sim(L, prec, history_capacity=1 << 17)
         c0 = sim.counters()
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -406,12 +419,7 @@ def main():
     # ------------------------------------------------- refined (headline)
     w = REFINED
     tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
-    sim = L.Simulation(w["shape"], precision=prec, tau=tau, bc=w["bc"], levels=w["levels"],
-                       regrid_interval=w["regrid"], history_capacity=1 << 16)
-    sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
-                   cv=w["cv"])
-    sim.set_ga(w["ga"], w["u_g"], (0.0, 0.0, -1.0))
-    sim.init_fluid()
+    sim = refined_sim(L, prec)
     upd_step, launches_step = sim.updates_per_step()
     sim.step(args.warmup)
     if dist:

@@ -174,8 +174,29 @@ lbmp_status lbmp_init_fluid_wave(lbmp_handle* h, double rho, const double u[3], 
 /* Refines the finest-level blocks intersecting [lo, hi) (finest units), in
  * addition to the sphere's blocks, and rebuilds the hierarchy now. */
 lbmp_status lbmp_refine_box(lbmp_handle* h, const double lo[3], const double hi[3]);
-/* Rebuilds the hierarchy for the sphere's current position (regrid). */
+/* Rebuilds the hierarchy for the sphere's current position (regrid); with
+ * the flow sensor on, also for the sensor's reading of every real block. */
 lbmp_status lbmp_regrid(lbmp_handle* h);
+/* Flow-based refinement sensor (Sec. 4.2.2, Eq. "sensor_curl"): per cell
+ * phi_c = |curl u| s^((r+1)/r) with r = 2, s the cell size and derivatives
+ * in finest-level units; u = sum_q g_q c_q of the stored deviations;
+ * central differences inside a block, one-sided on its faces.  A real block
+ * of level l whose largest phi_c exceeds sigma_c asks for level l+1 (at most
+ * the finest), below c sigma_c for level l-1, else for level l; eight
+ * siblings coarsen only together, and the 2:1 balance and the sphere's
+ * blocks come on top.  Consulted by lbmp_regrid and the periodic regrid
+ * (which then runs even without a sphere), not by lbmp_create,
+ * lbmp_add_sphere or lbmp_refine_box.  sigma_c = 0 turns it off (default).
+ * Errors: LBMP_ERR_INVALID_ARG unless sigma_c >= 0 and, for sigma_c > 0,
+ * 0 < c < 2^-1.5 (the bound that keeps a coarsened block from refining
+ * again at once); LBMP_ERR_UNSUPPORTED on a one-level or batched handle. */
+lbmp_status lbmp_set_refinement_sensor(lbmp_handle* h, double sigma_c, double c);
+/* Largest phi_c of every real block of a level (the sensor above), in block
+ * order, computed now on the device from the current populations: out[cap]
+ * caller-owned host memory, *n = real blocks of the level (cap = 0 or
+ * out = NULL queries).  Errors: LBMP_ERR_INVALID_ARG for a bad level,
+ * LBMP_ERR_UNSUPPORTED on a one-level or batched handle. */
+lbmp_status lbmp_get_block_sensor(lbmp_handle* h, int level, double* out, size_t cap, size_t* n);
 /* Cells of a level across the domain. */
 lbmp_status lbmp_level_shape(lbmp_handle* h, int level, int out[3]);
 /* Block-position map of a level (x fastest): real block index in position

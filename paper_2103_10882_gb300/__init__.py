@@ -21,7 +21,8 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_get_populations", "lbmp_gather_populations", "lbmp_step", "lbmp_step_async", "lbmp_check_status", "lbmp_synchronize",
            "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
            "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error",
-           "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_level_shape", "lbmp_get_block_map",
+           "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_set_refinement_sensor", "lbmp_get_block_sensor",
+           "lbmp_level_shape", "lbmp_get_block_map",
            "lbmp_get_level_cells", "lbmp_updates_per_step", "lbmp_batch_create", "lbmp_batch_autotune",
            "lbmp_batch_info", "lbmp_batch_get_populations", "BatchSimulation", "PRECISIONS", "lbmp_drag_forward",
            "lbmp_drag_backward", "mean_drag"]
@@ -251,6 +252,18 @@ def lbmp_level_shape(h, level):
     return tuple(out)
 
 
+def lbmp_set_refinement_sensor(h, sigma_c, c):
+    _check(h, _lib().lbmp_set_refinement_sensor(h, float(sigma_c), float(c)))
+
+
+def lbmp_get_block_sensor(h, level):
+    n = ctypes.c_size_t(0)
+    _check(h, _lib().lbmp_get_block_sensor(h, int(level), None, 0, ctypes.byref(n)))
+    out = np.empty(n.value, dtype=np.float64)
+    _check(h, _lib().lbmp_get_block_sensor(h, int(level), _dp(out), out.size, ctypes.byref(n)))
+    return out
+
+
 def lbmp_get_block_map(h, level):
     n = ctypes.c_size_t(0)
     _check(h, _lib().lbmp_get_block_map(h, int(level), None, 0, ctypes.byref(n)))
@@ -469,6 +482,14 @@ class Simulation:
 
     def regrid(self):
         lbmp_regrid(self.h)
+
+    def set_refinement_sensor(self, sigma_c=1e-3, c=0.2):
+        """Flow-based refinement sensor of Sec. 4.2.2 (sigma_c = 0 turns it off)."""
+        lbmp_set_refinement_sensor(self.h, sigma_c, c)
+
+    def block_sensor(self, level):
+        """Largest scaled curl of every real block of a level (block order)."""
+        return lbmp_get_block_sensor(self.h, level)
 
     def level_shape(self, level):
         return lbmp_level_shape(self.h, level)

@@ -664,6 +664,77 @@ __global__ void k_amr_export(LevelView D, const S* __restrict__ pops, int32_t* _
     }
 }
 
+// Flow sensor (Sec. 4.2.2): the largest scaled curl phi_c = |curl u| s^1.5
+// (r = 2; s and the derivatives in finest-level units) over the cells of
+// each real block of one level.  u = sum_q g_q c_q summed in q order;
+// derivatives are central differences inside the block and one-sided on its
+// faces; products, sums, quotients and the root are rounded one by one (no
+// contraction), so the FP64 form reproduces the plain definition exactly.
+// One CTA per real block; the block's velocities are staged in shared
+// memory ([3][4096] of the arithmetic type), the maximum is reduced across
+// the CTA, and out[b] = max |curl u| * s^1.5 (weight = s^1.5 from the host).
+constexpr int SENSOR_THREADS = 512;
+
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float rn_div(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double rn_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ float rn_sqrt(float a) { return __fsqrt_rn(a); }
+
+template <typename S>
+__global__ void __launch_bounds__(SENSOR_THREADS)
+    k_block_sensor(const S* __restrict__ pops, typename Store<S>::A inv, typename Store<S>::A s, double weight,
+                   double* __restrict__ out) {
+    using A = typename Store<S>::A;
+    extern __shared__ __align__(16) unsigned char sensor_smem[];
+    A* u = reinterpret_cast<A*>(sensor_smem);   // [3][B3]
+    __shared__ A warp_best[SENSOR_THREADS / 32];
+    const S* p = pops + (size_t)blockIdx.x * 19 * B3;
+    for (int c = threadIdx.x; c < B3; c += SENSOR_THREADS) {
+        A m0 = A(0), m1 = A(0), m2 = A(0);
+#pragma unroll
+        for (int q = 1; q < 19; ++q) {   // q = 0 has c = 0
+            const A g = Store<S>::load(p + q * B3 + c, inv);
+            if (cx(q)) m0 = rn_add(m0, cx(q) > 0 ? g : -g);
+            if (cy(q)) m1 = rn_add(m1, cy(q) > 0 ? g : -g);
+            if (cz(q)) m2 = rn_add(m2, cz(q) > 0 ? g : -g);
+        }
+        u[c] = m0;
+        u[B3 + c] = m1;
+        u[2 * B3 + c] = m2;
+    }
+    __syncthreads();
+    A best = A(0);
+    for (int c = threadIdx.x; c < B3; c += SENSOR_THREADS) {
+        const int pc[3] = {c & (BS - 1), (c >> 4) & (BS - 1), c >> 8};
+        // d u_k / d x_a
+        auto d = [&](int k, int a) -> A {
+            const int st = a == 0 ? 1 : (a == 1 ? BS : BS * BS);
+            const int lo = pc[a] > 0 ? c - st : c, hi = pc[a] < BS - 1 ? c + st : c;
+            const A span = (pc[a] > 0 && pc[a] < BS - 1) ? A(2) : A(1);
+            return rn_div(rn_add(u[k * B3 + hi], -u[k * B3 + lo]), rn_mul(span, s));
+        };
+        const A wx = rn_add(d(2, 1), -d(1, 2));
+        const A wy = rn_add(d(0, 2), -d(2, 0));
+        const A wz = rn_add(d(1, 0), -d(0, 1));
+        const A c2 = rn_add(rn_add(rn_mul(wx, wx), rn_mul(wy, wy)), rn_mul(wz, wz));
+        best = fmax(best, rn_sqrt(c2));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if ((threadIdx.x & 31) == 0) warp_best[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        A m = warp_best[0];
+        for (int w = 1; w < SENSOR_THREADS / 32; ++w) m = fmax(m, warp_best[w]);
+        out[blockIdx.x] = __dmul_rn((double)m, weight);
+    }
+}
+
+
 __global__ void k_amr_export_links(LevelView D, const uint8_t* __restrict__ flags, const int* __restrict__ list,
                                    const int* __restrict__ count, const ParticleState* __restrict__ ps,
                                    int64_t* __restrict__ cell_out, int32_t* __restrict__ q_out,
@@ -741,6 +812,9 @@ struct AmrEngine {
     std::vector<std::vector<uint8_t>> cover;      // block coverage per level of the current layout
     cudaStream_t side = nullptr;                  // k_amr_boundary runs here, beside the finest update
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double sensor_sigma = 0.0, sensor_c = 0.0;   // flow sensor (sigma_c = 0: off)
+    double* d_sensor = nullptr;                   // per real block of all levels
+    size_t sensor_cap = 0;
 
 };
 
@@ -843,19 +917,63 @@ Mask dilate(const AmrEngine* E, const Mask& m, int l) {
 
 // Level-l block positions covered by blocks of level >= l (Sec. 4.1, 4.2.1):
 // finest = siblings of the required set; each coarser level adds the 26
-// neighbours of the parents of the next finer level (2:1 balance).
-std::vector<Mask> coverage(const AmrEngine* E, const Mask& finest) {
+// neighbours of the parents of the next finer level (2:1 balance).  wish
+// (optional) holds, per level l >= 1, positions the flow sensor wants
+// covered at level >= l; they join the required set of their level before
+// the siblings are added.
+std::vector<Mask> coverage(const AmrEngine* E, const Mask& finest, const std::vector<Mask>* wish = nullptr) {
     std::vector<Mask> R(E->L);
     int nb[3];
     lattice_of(E, 0, nb);
     R[0].assign((size_t)nb[0] * nb[1] * nb[2], 1);
     if (E->L == 1) return R;
-    R[E->L - 1] = children(E, parents(E, finest, E->L - 1), E->L - 2);
+    Mask need = finest;
+    if (wish)
+        for (size_t i = 0; i < need.size(); ++i) need[i] |= (*wish)[E->L - 1][i];
+    R[E->L - 1] = children(E, parents(E, need, E->L - 1), E->L - 2);
     for (int l = E->L - 2; l >= 1; --l) {
-        const Mask grown = dilate(E, parents(E, R[l + 1], l + 1), l);
+        Mask grown = dilate(E, parents(E, R[l + 1], l + 1), l);
+        if (wish)
+            for (size_t i = 0; i < grown.size(); ++i) grown[i] |= (*wish)[l][i];
         R[l] = children(E, parents(E, grown, l), l - 1);
     }
     return R;
+}
+
+// What the flow sensor asks of each real block (Sec. 4.2.2), as positions to
+// keep covered per level: above sigma_c a block asks for level l+1 (its
+// eight children; the finest level asks for itself), below c sigma_c for
+// level l-1 (its parent), in between for level l (itself).  A block that no
+// wish, balance or sphere keeps is coarsened; since its siblings' wishes
+// keep the whole octet, octets coarsen only together, one level per regrid.
+std::vector<Mask> sensor_wishes(const AmrEngine* E, const std::vector<std::vector<double>>& phi) {
+    std::vector<Mask> W(E->L);
+    for (int l = 0; l < E->L; ++l) {
+        int nb[3];
+        lattice_of(E, l, nb);
+        W[l].assign((size_t)nb[0] * nb[1] * nb[2], 0);
+    }
+    for (int l = 0; l < E->L; ++l) {
+        const Level& V = E->lv[l];
+        for (int b = 0; b < V.nreal; ++b) {
+            const int* p = &V.bpos[3 * (size_t)b];
+            const double v = phi[l][b];
+            int want = l;
+            if (v > E->sensor_sigma) want = std::min(l + 1, E->L - 1);
+            else if (v < E->sensor_c * E->sensor_sigma) want = std::max(l - 1, 0);
+            int nb[3];
+            lattice_of(E, want, nb);
+            if (want > l) {
+                for (int k = 0; k < 8; ++k)
+                    W[want][bidx(nb, 2 * p[0] + (k & 1), 2 * p[1] + ((k >> 1) & 1), 2 * p[2] + (k >> 2))] = 1;
+            } else if (want == l) {
+                W[l][bidx(nb, p[0], p[1], p[2])] = 1;
+            } else {
+                W[want][bidx(nb, p[0] >> 1, p[1] >> 1, p[2] >> 1)] = 1;
+            }
+        }
+    }
+    return W;
 }
 
 Mask required_from_particle(const AmrEngine* E, const ParticleState& P) {
@@ -1135,7 +1253,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
 // current one changes nothing (the populations would be copied onto the
 // same blocks and the flags are already those of the current position),
 // so the layout, its lists and the captured graphs are kept.
-lbmp_status regrid_now(lbmp_handle* h, bool keep_if_unchanged = false) {
+lbmp_status regrid_now(lbmp_handle* h, bool keep_if_unchanged = false, const std::vector<Mask>* wish = nullptr) {
     AmrEngine* E = h->amr;
     int nb[3];
     lattice_of(E, E->L - 1, nb);
@@ -1145,7 +1263,7 @@ lbmp_status regrid_now(lbmp_handle* h, bool keep_if_unchanged = false) {
         const Mask mb = required_from_box(E);
         for (size_t i = 0; i < m.size(); ++i) m[i] |= mb[i];
     }
-    std::vector<Mask> R = coverage(E, m);
+    std::vector<Mask> R = coverage(E, m, wish);
     if (keep_if_unchanged && R == E->cover) return LBMP_OK;
     const lbmp_status s = build_layout(h, R);
     if (s == LBMP_OK) E->cover.swap(R);
@@ -1320,6 +1438,7 @@ void amr_destroy(lbmp_handle* h) {
     if (h->amr->ev_join) cudaEventDestroy(h->amr->ev_join);
 
     for (auto& V : h->amr->lv) free_level(h, V);
+    handle_free(h, h->amr->d_sensor);
     delete h->amr;
     h->amr = nullptr;
 }
@@ -1363,7 +1482,64 @@ lbmp_status amr_refine_box(lbmp_handle* h, const double lo[3], const double hi[3
     return regrid_now(h);
 }
 
+namespace {
+
+// Sensor value of every real block of every level (k_block_sensor, one
+// launch per level into one device array, one copy back).
+lbmp_status sensor_values(lbmp_handle* h, std::vector<std::vector<double>>& phi) {
+    AmrEngine* E = h->amr;
+    size_t total = 0;
+    for (const Level& V : E->lv) total += (size_t)V.nreal;
+    phi.assign(E->L, std::vector<double>());
+    if (total == 0) return LBMP_OK;
+    if (total > E->sensor_cap) {
+        handle_free(h, E->d_sensor);
+        E->d_sensor = (double*)handle_alloc(h, sizeof(double) * total);
+        E->sensor_cap = E->d_sensor ? total : 0;
+        if (!E->d_sensor) return LBMP_ERR_OOM;
+    }
+    bool launched = true;
+    with_storage_amr(h->cfg.precision, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        using A = typename Store<S>::A;
+        const size_t smem = 3 * (size_t)B3 * sizeof(A);
+        if (cudaFuncSetAttribute(k_block_sensor<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            launched = false;
+            return;
+        }
+        const A inv = (A)(h->cfg.precision == LBMP_FP16 ? std::ldexp(1.0, -h->cfg.fp16_scale_log2) : 1.0);
+        size_t off = 0;
+        for (int l = 0; l < E->L; ++l) {
+            const Level& V = E->lv[l];
+            if (V.nreal == 0) continue;
+            const double sz = (double)(1 << (E->L - 1 - l));   // cell size in finest units
+            k_block_sensor<S><<<(unsigned)V.nreal, SENSOR_THREADS, smem, h->stream>>>(
+                (const S*)V.d_pops[V.cur], inv, (A)sz, std::pow(sz, 1.5), E->d_sensor + off);
+            h->launches += 1;
+            off += (size_t)V.nreal;
+        }
+    });
+    if (!launched || cudaGetLastError() != cudaSuccess) return amr_cuda_error(h, "k_block_sensor");
+    std::vector<double> all(total);
+    if (cudaMemcpyAsync(all.data(), E->d_sensor, sizeof(double) * total, cudaMemcpyDeviceToHost, h->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return amr_cuda_error(h, "sensor copy");
+    h->d2h += (long long)(sizeof(double) * total);
+    size_t off = 0;
+    for (int l = 0; l < E->L; ++l) {
+        const int n = E->lv[l].nreal;
+        phi[l].assign(all.begin() + off, all.begin() + off + n);
+        off += (size_t)n;
+    }
+    return LBMP_OK;
+}
+
+}  // namespace
+
 lbmp_status amr_regrid(lbmp_handle* h) {
+    AmrEngine* E = h->amr;
     if (h->has_particle) {
         if (cudaMemcpyAsync(&h->h_ps, h->d_ps, sizeof(ParticleState), cudaMemcpyDeviceToHost, h->stream) !=
                 cudaSuccess ||
@@ -1371,7 +1547,33 @@ lbmp_status amr_regrid(lbmp_handle* h) {
             return LBMP_ERR_CUDA;
         h->d2h += sizeof(ParticleState);
     }
+    if (E->sensor_sigma > 0.0) {
+        std::vector<std::vector<double>> phi;
+        const lbmp_status s = sensor_values(h, phi);
+        if (s != LBMP_OK) return s;
+        const std::vector<Mask> wish = sensor_wishes(E, phi);
+        return regrid_now(h, true, &wish);
+    }
     return regrid_now(h, true);
+}
+
+lbmp_status amr_set_sensor(lbmp_handle* h, double sigma, double c) {
+    AmrEngine* E = h->amr;
+    E->sensor_sigma = sigma;
+    E->sensor_c = sigma > 0.0 ? c : 0.0;
+    return LBMP_OK;
+}
+
+lbmp_status amr_block_sensor(lbmp_handle* h, int level, double* out, size_t cap, size_t* n) {
+    AmrEngine* E = h->amr;
+    if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
+    *n = (size_t)E->lv[level].nreal;
+    if (!out || cap == 0 || *n == 0) return LBMP_OK;
+    std::vector<std::vector<double>> phi;
+    const lbmp_status s = sensor_values(h, phi);
+    if (s != LBMP_OK) return s;
+    for (size_t b = 0; b < *n && b < cap; ++b) out[b] = phi[level][b];
+    return LBMP_OK;
 }
 
 lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis) {
@@ -1456,7 +1658,8 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
         E->coarse_steps += 1;
         h->steps += 1;
         if (cudaGetLastError() != cudaSuccess) return amr_cuda_error(h, "kernel launch");
-        if (h->cfg.regrid_interval > 0 && h->has_particle && E->coarse_steps % h->cfg.regrid_interval == 0) {
+        if (h->cfg.regrid_interval > 0 && (h->has_particle || E->sensor_sigma > 0.0) &&
+            E->coarse_steps % h->cfg.regrid_interval == 0) {
             const lbmp_status s = amr_regrid(h);
             if (s != LBMP_OK) return s;
         }

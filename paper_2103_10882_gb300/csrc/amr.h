@@ -13,7 +13,9 @@ lbmp_status amr_create(lbmp_handle* h);   // sets h->amr; starts unrefined (all 
 void amr_destroy(lbmp_handle* h);
 lbmp_status amr_add_sphere(lbmp_handle* h);            // h->h_ps filled by the caller
 lbmp_status amr_refine_box(lbmp_handle* h, const double lo[3], const double hi[3]);
-lbmp_status amr_regrid(lbmp_handle* h);
+lbmp_status amr_regrid(lbmp_handle* h);                 // with the flow sensor when it is on
+lbmp_status amr_set_sensor(lbmp_handle* h, double sigma, double c);   // arguments checked by the caller
+lbmp_status amr_block_sensor(lbmp_handle* h, int level, double* out, size_t cap, size_t* n);
 lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis);
 lbmp_status amr_step(lbmp_handle* h, int n_coarse);   // enqueues; status read by the caller
 lbmp_status amr_level_shape(lbmp_handle* h, int level, int out[3]);

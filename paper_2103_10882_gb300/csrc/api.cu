@@ -817,6 +817,23 @@ lbmp_status lbmp_regrid(lbmp_handle* h) {
     return read_status(h);
 }
 
+lbmp_status lbmp_set_refinement_sensor(lbmp_handle* h, double sigma_c, double c) {
+    if (!h) return LBMP_ERR_INVALID_ARG;
+    if (!h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_set_refinement_sensor: the grid has one level");
+    if (!(sigma_c >= 0.0) || !std::isfinite(sigma_c) ||
+        (sigma_c > 0.0 && !(c > 0.0 && c < std::pow(2.0, -1.5))))
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_refinement_sensor: need sigma_c >= 0 and 0 < c < 2^-1.5");
+    return amr_set_sensor(h, sigma_c, c);
+}
+
+lbmp_status lbmp_get_block_sensor(lbmp_handle* h, int level, double* out, size_t cap, size_t* n) {
+    if (!h || !n) return LBMP_ERR_INVALID_ARG;
+    if (!h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_get_block_sensor: the grid has one level");
+    const lbmp_status st = amr_block_sensor(h, level, out, cap, n);
+    if (st == LBMP_ERR_INVALID_ARG) return fail(h, st, "lbmp_get_block_sensor: no such level");
+    return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_get_block_sensor: failed");
+}
+
 lbmp_status lbmp_level_shape(lbmp_handle* h, int level, int out[3]) {
     if (!h || !out) return LBMP_ERR_INVALID_ARG;
     if (!h->amr) {
