@@ -115,33 +115,34 @@ __device__ __forceinline__ void rescale19(A f[19], A kp, A km) {
 }
 
 // --------------------------------------------------------------- explosion
-template <typename S>
+// Explosion for one coarse step of level l: every ghost cell of level l+1
+// in use takes the (optionally rescaled) post-collision populations of the
+// level-l cell that contains it, into f0, the source of the first sub-step.
+template <typename S, bool RESCALE>
 __global__ void __launch_bounds__(UPD_THREADS)
     k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0,
-              typename Store<S>::A kp, typename Store<S>::A km, int rescale, typename Store<S>::A scale,
+              typename Store<S>::A kp, typename Store<S>::A km, typename Store<S>::A scale,
               typename Store<S>::A inv_scale, const int* __restrict__ list, int n, int* __restrict__ status) {
     using A = typename Store<S>::A;
     const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
     if (i >= n) return;
     const int e = list[i];   // ghost cell in use: pool block << 12 | cell
     const int b = e >> 12;
-    const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
-    {
-        const int c = e & 4095;
-        const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
-        int pc;
-        const int pb = locate(C, p, &pc);
-        if (pb < 0 || pb >= C.nreal) {
-            atomicOr(status, STATUS_AMR_MISSING);
-            return;
-        }
-        A f[19];
-#pragma unroll
-        for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(csrc + paddr(pb, q, pc), inv_scale);
-        if (rescale) rescale19<A>(f, kp, km);
-#pragma unroll
-        for (int q = 0; q < 19; ++q) Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
+    const int c = e & 4095;
+    const int p[3] = {(F.bpos[3 * b] * BS + (c & 15)) >> 1, (F.bpos[3 * b + 1] * BS + ((c >> 4) & 15)) >> 1,
+                      (F.bpos[3 * b + 2] * BS + (c >> 8)) >> 1};
+    int pc;
+    const int pb = locate(C, p, &pc);
+    if (pb < 0 || pb >= C.nreal) {
+        atomicOr(status, STATUS_AMR_MISSING);
+        return;
     }
+    A f[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(csrc + paddr(pb, q, pc), inv_scale);
+    if (RESCALE) rescale19<A>(f, kp, km);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
 }
 
 // ----------------------------------------------------------------- update
@@ -152,25 +153,25 @@ struct UpdateArgs {
     const S* src;
     S* dst;
     CollideParams<A> P;
-    int substep;              // index of this step within the coarser level's step
-    int rescale;
     // coalescence from the next finer level
     LevelView F;
     const S* fsrc;
     A fkp, fkm;
-    // rigid translation through static ghosts: exploded values of the next coarser level
-    LevelView Cc;
-    const S* csrc;
-    A ckp, ckm;
     const uint8_t* solid;     // finest level with a sphere: solid flags of real cells
     int* status;
 };
 
 // Update of one cell of pool block b: real cells pull (or, for hosts,
-// coalesce) and collide; active ghost cells pull only.  nb27 lists the pool
-// ids of block b's 26 neighbours (and itself at index 13).
+// coalesce) and collide; ghost cells pull only.  nb27 lists the pool ids of
+// block b's 26 neighbours (and itself at index 13).  rigid (static ghost
+// cells at the first sub-step): the pull carries the exploded field one
+// cell along c_q, so that at the second sub-step a static ghost holds, for
+// each q, the exploded value of the coarse cell one cell further upwind
+// (coarse content translating rigidly); beyond a wall, or where no block
+// exists (a value no update reads), the cell keeps its own value.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL, bool RESCALE>
-__device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27) {
+__device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
+                                            bool rigid = false) {
     using A = typename Store<S>::A;
     const LevelView& D = U.D;
     const A scale = U.P.scale, inv = U.P.inv_scale;
@@ -198,81 +199,52 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
         for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
         if (RESCALE) rescale19<A>(g, U.fkp, U.fkm);
     } else {
-        // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate
+        // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate.
+        // Every population is one load: from the neighbouring cell (real or
+        // ghost), or at a domain wall (-2) the cell's own opposite population
+        // (bounce-back).  No block (-1) is an error: the value is 0 and the
+        // status word says so.
         const int bsx[3] = {lx == 0 ? -1 : 0, 0, lx == 15 ? 1 : 0};
         const int bsy[3] = {ly == 0 ? -1 : 0, 0, ly == 15 ? 1 : 0};
         const int bsz[3] = {lz == 0 ? -1 : 0, 0, lz == 15 ? 1 : 0};
         const int lsx[3] = {(lx - 1) & 15, lx, (lx + 1) & 15};
         const int lsy[3] = {((ly - 1) & 15) * BS, ly * BS, ((ly + 1) & 15) * BS};
         const int lsz[3] = {((lz - 1) & 15) * BS * BS, lz * BS * BS, ((lz + 1) & 15) * BS * BS};
+        bool missing = false;
 #pragma unroll
         for (int q = 0; q < 19; ++q) {
             const int ix = 1 - cx(q), iy = 1 - cy(q), iz = 1 - cz(q);
             const int nbk = nb27[13 + bsx[ix] + 3 * bsy[iy] + 9 * bsz[iz]];   // entry 13 is b itself
-            if (nbk == -2) {   // domain wall: bounce-back
-                g[q] = Store<S>::load(U.src + paddr(b, opp(q), c), inv);
-                continue;
-            }
-            if (nbk < 0) {
-                atomicOr(U.status, STATUS_AMR_MISSING);
-                g[q] = A(0);
-                continue;
-            }
-            const int sc = lsx[ix] + lsy[iy] + lsz[iz];
-            if (HAS_COARSE && nbk >= D.nreal && U.substep == 1 &&
-                D.gkind[(size_t)(nbk - D.nreal) * B3 + sc] == 2) {
-                // static ghost at the second step: content of the coarser cell one more step upwind
-                const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-                int t[3] = {bx * BS + lx - 2 * cx(q), by * BS + ly - 2 * cy(q), bz * BS + lz - 2 * cz(q)};
-                if (wrap3(t, D)) {
-                    const int p[3] = {t[0] >> 1, t[1] >> 1, t[2] >> 1};
-                    int pc;
-                    const int pb = locate(U.Cc, p, &pc);
-                    if (pb < 0 || pb >= U.Cc.nreal) {
-                        atomicOr(U.status, STATUS_AMR_MISSING);
-                        g[q] = A(0);
-                        continue;
-                    }
-                    if (RESCALE) {   // the rescaled value needs the whole cell
-                        A f[19];
-#pragma unroll
-                        for (int k = 0; k < 19; ++k) f[k] = Store<S>::load(U.csrc + paddr(pb, k, pc), inv);
-                        rescale19<A>(f, U.ckp, U.ckm);
-                        g[q] = f[q];
-                    } else {
-                        g[q] = Store<S>::load(U.csrc + paddr(pb, q, pc), inv);
-                    }
-                    continue;
-                }
-                // upwind position outside a walled domain: the ghost's exploded value, kept in the
-                // buffer of the first sub-step (this step's dst; static ghosts are never written)
-                g[q] = Store<S>::load(U.dst + (unsigned)((nbk * 19 + q) * B3 + sc), inv);
-                continue;
-            }
-            g[q] = Store<S>::load(U.src + (unsigned)((nbk * 19 + q) * B3 + sc), inv);   // pools hold < 2^31 elements
+            const bool own = nbk < 0;
+            const int sb = own ? b : nbk, sq = (own && !rigid) ? opp(q) : q;
+            const int sc = own ? c : lsx[ix] + lsy[iy] + lsz[iz];
+            const A v = Store<S>::load(U.src + (unsigned)((sb * 19 + sq) * B3 + sc), inv);   // pools hold < 2^31 elements
+            const bool lost = nbk == -1 && !rigid;
+            missing |= lost;
+            g[q] = lost ? A(0) : v;
         }
+        if (missing) atomicOr(U.status, STATUS_AMR_MISSING);
     }
     if (REAL) trt_collide<A, false>(g, U.P, U.status);
 #pragma unroll
     for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], scale);
 }
 
-// One launch per level step: the first gblocks CTAs stream the active ghost
-// cells of the level (from a list of pool block << 12 | cell, no collision;
-// static ghost cells keep the exploded values in the first sub-step's
-// buffer, and the second sub-step pulls through them from the coarser level
-// directly); the others update the real blocks, one CTA per z-slice of a
+// One launch per level step: the first gblocks CTAs stream ghost cells of
+// the level (a list of pool block << 12 | cell, the active ghost cells
+// first, then at the first sub-step the static ones, which pull rigidly; no
+// collision); the others update the real blocks, one CTA per z-slice of a
 // block (256 cells, full warps).  Both read src and write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED, bool RESCALE>
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int gblocks) {
+    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks) {
     using A = typename Store<S>::A;
     if (HAS_COARSE && (int)blockIdx.x < gblocks) {   // uniform across the block
         const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
         if (i < nglist) {
             const int e = glist[i];
             const int b = e >> 12, c = e & 4095;
-            update_cell<S, false, true, false, RESCALE>(U, b, c, U.D.nbr + (size_t)b * 27);
+            update_cell<S, false, true, false, RESCALE>(U, b, c, U.D.nbr + (size_t)b * 27, i >= nactive);
         }
         return;
     }
@@ -307,24 +279,67 @@ __device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int l
 }
 
 constexpr int BNDW_THREADS = 256;
-constexpr int BND_CHUNK = 128;   // box cells per boundary block
+constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid)
+constexpr int LINK_THREADS = 64;   // remap blocks: small, so the box spreads over the SMs; one count per block
+
+// Exclusive prefix of n counts into pre[0..n] (pre[n] = total), computed by
+// the whole CTA (NT threads); every thread must call it.
+template <int NT>
+__device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n, int* pre) {
+    __shared__ int wsum[NT / 32];
+    __shared__ int carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += NT) {
+        const int i = base + (int)threadIdx.x;
+        int v = i < n ? count[i] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, off);
+            if (lane >= off) v += y;
+        }
+        if (lane == 31) wsum[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            int w = lane < NT / 32 ? wsum[lane] : 0;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            if (lane < NT / 32) wsum[lane] = w;
+        }
+        __syncthreads();
+        if (i < n) pre[i + 1] = carry + (wid > 0 ? wsum[wid - 1] : 0) + v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[NT / 32 - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pre[0] = 0;
+    __syncthreads();
+    return pre[n];
+}
 
 // Boundary cells of the finest level (flag 2: fluid with a solid
-// neighbour), found from the mask the remap wrote in box order: each block
-// compacts the marked cells of its chunk of BND_CHUNK box cells and its
-// warps take them in turn, one cell per warp at a time, lane q handling
-// population q (CLI links of Sec. 2.3, geometry in the
-// population arithmetic, FP64 force partials), with a cooperative
-// collision.  The level update skips these cells, so this kernel runs
-// beside it.  The block that finishes last sums the partials and runs the
-// particle update of Algorithm 1.
+// neighbour), from the mask the remap wrote in box order and its count of
+// marked cells per run of LINK_THREADS box cells.  The marked cells are
+// spread evenly over all warps of the grid: every CTA turns the counts into
+// a prefix, and warp w of W takes the marked cells w, w + W, ... (box
+// order), one cell per warp at a time, lane q handling population q (CLI
+// links of Sec. 2.3, geometry in the population arithmetic, FP64 force
+// partials per CTA), with a cooperative collision.  The level update skips
+// these cells, so this kernel runs beside it.  The block that finishes
+// last sums the partials and runs the particle update of Algorithm 1.
+// Dynamic shared memory: (runs + 1) ints.
 template <typename S>
 __global__ void __launch_bounds__(BNDW_THREADS)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
-                   const uint8_t* __restrict__ mask, BoxDesc B, CollideParams<typename Store<S>::A> P,
-                   ParticleState* ps, int cli, double* partials, int* done, GridDesc G,
-                   double* __restrict__ history, int hist_cap, int* __restrict__ status) {
+                   const uint8_t* __restrict__ mask, const int* __restrict__ run_count, BoxDesc B,
+                   CollideParams<typename Store<S>::A> P, ParticleState* ps, int cli, double* partials, int* done,
+                   GridDesc G, double* __restrict__ history, int hist_cap, int* __restrict__ status) {
     using A = typename Store<S>::A;
+    extern __shared__ int pre[];   // [runs + 1]
     __shared__ LinkFrame<A> Fr;
     __shared__ BoxFrame Bf;
     if (threadIdx.x == 0) {
@@ -333,13 +348,34 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    __shared__ int sl[BND_CHUNK];
-    const long long t0 = (long long)blockIdx.x * BND_CHUNK;
-    const int nm = block_compact_mask(mask, t0, B.cells, BND_CHUNK, sl);
+    const int runs = (int)((B.cells + LINK_THREADS - 1) / LINK_THREADS);
+    const int total = block_prefix<BNDW_THREADS>(run_count, runs, pre);
+    const int W = (int)gridDim.x * (BNDW_THREADS / 32);
     LinkSums acc;
-    for (int i = wib; i < nm; i += BNDW_THREADS / 32) {
+    for (int j = (int)blockIdx.x * (BNDW_THREADS / 32) + wib; j < total; j += W) {
+        // run r holding marked cell j: the largest r with pre[r] <= j
+        int lo = 0, hi = runs;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] <= j) lo = mid;
+            else hi = mid;
+        }
+        const long long r0 = (long long)lo * LINK_THREADS;
+        const bool m0 = r0 + lane < B.cells && mask[r0 + lane] != 0;
+        const bool m1 = r0 + 32 + lane < B.cells && mask[r0 + 32 + lane] != 0;
+        const unsigned b0 = __ballot_sync(0xffffffffu, m0), b1 = __ballot_sync(0xffffffffu, m1);
+        int k = j - pre[lo];
+        unsigned bits = b0;
+        int base = 0;
+        if (k >= __popc(b0)) {
+            k -= __popc(b0);
+            bits = b1;
+            base = 32;
+        }
+        for (; k > 0; --k) bits &= bits - 1u;   // drop the k lowest marked cells
+        const int t = (int)(r0 + base + __ffs((int)bits) - 1);
         int g[3], c;
-        box_cell((int)(t0 + sl[i]), D.n, D.periodic, B, Bf, g);   // marked cells are inside the domain
+        box_cell(t, D.n, D.periodic, B, Bf, g);   // marked cells are inside the domain
         const int b = locate(D, g, &c);
         const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
         A gq = A(0);
@@ -376,7 +412,6 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     if (last_block_done(done, (int)gridDim.x)) particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status);
 }
 
-constexpr int LINK_THREADS = 64;   // remap and compaction blocks: small, so the box spreads over the SMs
 
 // Remap of Sec. 2.3 after the particle moved, over the box of finest cells
 // around the sphere, in one pass: the new solid flag of every cell (the
@@ -779,9 +814,8 @@ struct Level {
     uint8_t* d_refined = nullptr;
     uint8_t* d_host = nullptr;
     uint8_t* d_gkind = nullptr;
-    int* d_glist = nullptr;      // active ghost cells: pool block << 12 | cell
-    int nglist = 0;
-    int* d_xlist = nullptr;      // every ghost cell in use (active or static), same encoding
+    int nglist = 0;              // active ghost cells (host sub-cells)
+    int* d_xlist = nullptr;      // every ghost cell in use, pool block << 12 | cell: the active ones, then the static ones
     int nxlist = 0;
     void* d_pops[2] = {nullptr, nullptr};
     int cur = 0;
@@ -799,7 +833,6 @@ struct AmrEngine {
     std::vector<Level> lv;
     bool have_box = false;
     double box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
-    int substep[MAXL] = {0};
     int boundary_blocks = 1;
     long long coarse_steps = 0;
     // one captured level-0 step per parity of the level-0 buffers; dropped
@@ -1033,7 +1066,6 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_refined);
     handle_free(h, V.d_host);
     handle_free(h, V.d_gkind);
-    handle_free(h, V.d_glist);
     handle_free(h, V.d_xlist);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
@@ -1178,19 +1210,20 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             cudaStreamSynchronize(h->stream) != cudaSuccess)
             return LBMP_ERR_CUDA;
         h->d2h += (long long)kinds.size();
-        std::vector<int> list, used;
+        // used: the active ghost cells (list's order), then the static ones
+        std::vector<int> list, stat;
         for (int gb = 0; gb < F.nghost; ++gb)
             for (int c = 0; c < B3; ++c) {
                 const uint8_t k = kinds[(size_t)gb * B3 + c];
                 if (k == 1) list.push_back(((F.nreal + gb) << 12) | c);
-                if (k != 0) used.push_back(((F.nreal + gb) << 12) | c);
+                if (k == 2) stat.push_back(((F.nreal + gb) << 12) | c);
             }
+        std::vector<int> used(list);
+        used.insert(used.end(), stat.begin(), stat.end());
         F.nglist = (int)list.size();
-        F.d_glist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>(list.size(), 1));
         F.nxlist = (int)used.size();
         F.d_xlist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>(used.size(), 1));
-        if (!F.d_glist || !F.d_xlist) return LBMP_ERR_OOM;
-        if (upload(h, F.d_glist, list.data(), sizeof(int) * list.size())) return LBMP_ERR_CUDA;
+        if (!F.d_xlist) return LBMP_ERR_OOM;
         if (upload(h, F.d_xlist, used.data(), sizeof(int) * used.size())) return LBMP_ERR_CUDA;
     }
     // populations from the old layout
@@ -1290,7 +1323,7 @@ CollideParams<typename Store<S>::A> level_params(const lbmp_handle* h, const Lev
 }
 
 template <typename S>
-void enqueue_advance(lbmp_handle* h, int l) {
+void enqueue_advance(lbmp_handle* h, int l, int sub) {
     using A = typename Store<S>::A;
     AmrEngine* E = h->amr;
     const int L = E->L;
@@ -1302,29 +1335,27 @@ void enqueue_advance(lbmp_handle* h, int l) {
         double kp, km;
         kappa_post(V, F, &kp, &km);
         if (F.nxlist > 0) {
-            k_explode<S><<<(unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS), UPD_THREADS, 0, h->stream>>>(
-                view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[F.cur], (A)kp, (A)km, rescale,
-                P.scale, P.inv_scale, F.d_xlist, F.nxlist, h->status);
+            const unsigned grid = (unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS);
+            auto ex = [&](auto rs) {
+                k_explode<S, decltype(rs)::value><<<grid, UPD_THREADS, 0, h->stream>>>(
+                    view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[F.cur], (A)kp, (A)km, P.scale,
+                    P.inv_scale, F.d_xlist, F.nxlist, h->status);
+            };
+            if (rescale) ex(std::true_type{});
+            else ex(std::false_type{});
             h->launches += 1;
         }
-        E->substep[l + 1] = 0;
-        enqueue_advance<S>(h, l + 1);
-        E->substep[l + 1] = 1;
-        enqueue_advance<S>(h, l + 1);
+        enqueue_advance<S>(h, l + 1, 0);
+        enqueue_advance<S>(h, l + 1, 1);
     }
     UpdateArgs<S> U;
     U.D = view(E, V);
     U.src = (const S*)V.d_pops[V.cur];
     U.dst = (S*)V.d_pops[1 - V.cur];
     U.P = P;
-    U.substep = E->substep[l];
-    U.rescale = rescale;
     U.F = U.D;
     U.fsrc = nullptr;
     U.fkp = U.fkm = (A)1;
-    U.Cc = U.D;
-    U.csrc = nullptr;
-    U.ckp = U.ckm = (A)1;
     U.solid = nullptr;
     U.status = h->status;
     const bool has_fine = l + 1 < L, has_coarse = l > 0;
@@ -1335,15 +1366,6 @@ void enqueue_advance(lbmp_handle* h, int l) {
         // coalescence: averaged finer values are pre-collision values of the coarser cell
         U.fkp = (A)(2.0 * V.taup / F.taup);
         U.fkm = (A)(2.0 * V.taum / F.taum);
-    }
-    if (has_coarse) {
-        Level& C = E->lv[l - 1];
-        U.Cc = view(E, C);
-        U.csrc = (const S*)C.d_pops[C.cur];
-        double kp, km;
-        kappa_post(C, V, &kp, &km);
-        U.ckp = (A)kp;
-        U.ckm = (A)km;
     }
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) {
@@ -1358,28 +1380,31 @@ void enqueue_advance(lbmp_handle* h, int l) {
         G.n = (long long)V.n[0] * V.n[1] * V.n[2];
         cudaEventRecord(E->ev_fork, h->stream);
         cudaStreamWaitEvent(E->side, E->ev_fork, 0);
-        k_amr_boundary<S><<<E->boundary_blocks, BNDW_THREADS, 0, E->side>>>(
-            D, U.src, U.dst, U.solid, h->link_mask, h->box, P, h->d_ps, h->cfg.boundary == LBMP_CLI ? 1 : 0,
+        const size_t pre_bytes = sizeof(int) * (size_t)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS + 1);
+        k_amr_boundary<S><<<E->boundary_blocks, BNDW_THREADS, pre_bytes, E->side>>>(
+            D, U.src, U.dst, U.solid, h->link_mask, h->link_blocks, h->box, P, h->d_ps, h->cfg.boundary == LBMP_CLI ? 1 : 0,
             h->partials, E->d_done, G, h->history, h->cfg.history_capacity, h->status);
         cudaEventRecord(E->ev_join, E->side);
         h->launches += 1;
     }
     const long long ev0 = profile_mark(h);
-    const int ng = has_coarse ? V.nglist : 0;
+    // ghost cells streamed: the active ones, and at the first sub-step also
+    // the static ones (xlist holds both, active first)
+    const int ng = has_coarse ? (sub == 0 ? V.nxlist : V.nglist) : 0;
     const int gblocks = (ng + UPD_THREADS - 1) / UPD_THREADS;
     if (V.nreal > 0 || gblocks > 0) {
         const unsigned grid = (unsigned)(V.nreal * 16 + gblocks);
-        const int* gl = V.d_glist;
+        const int* gl = V.d_xlist;
         cudaStream_t st = h->stream;
         // the rescaling option is a template parameter: without it the kernel carries none of its code
         auto go = [&](auto rs) {
             constexpr bool R = decltype(rs)::value;
-            if (has_fine && has_coarse) k_update<S, true, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-            else if (has_fine) k_update<S, true, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-            else if (has_coarse && coupled) k_update<S, false, true, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-            else if (has_coarse) k_update<S, false, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-            else if (coupled) k_update<S, false, false, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
-            else k_update<S, false, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks);
+            if (has_fine && has_coarse) k_update<S, true, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
+            else if (has_fine) k_update<S, true, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
+            else if (has_coarse && coupled) k_update<S, false, true, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
+            else if (has_coarse) k_update<S, false, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
+            else if (coupled) k_update<S, false, false, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
+            else k_update<S, false, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
         };
         if (rescale) go(std::true_type{});
         else go(std::false_type{});
@@ -1465,6 +1490,15 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
     h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
     h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + LINK_THREADS - 1) / LINK_THREADS));
     if (!h->list || !h->partials || !h->link_mask || !h->link_blocks) return LBMP_ERR_OOM;
+    // the boundary kernel keeps a prefix of the remap's run counts in dynamic shared memory
+    const int pre_bytes = (int)(sizeof(int) * ((B.cells + LINK_THREADS - 1) / LINK_THREADS + 1));
+    bool attr_ok = true;
+    with_storage_amr(h->cfg.precision, [&](auto tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        attr_ok = cudaFuncSetAttribute(k_amr_boundary<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       std::max(pre_bytes, 1024)) == cudaSuccess;
+    });
+    if (!attr_ok) return amr_cuda_error(h, "sphere too large for the boundary kernel's shared memory");
     if (cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
         return LBMP_ERR_CUDA;
     h->h2d += sizeof(ParticleState);
@@ -1605,8 +1639,7 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
     auto enqueue = [&]() {
         with_storage_amr(h->cfg.precision, [&](auto tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
-            E->substep[0] = 0;
-            enqueue_advance<S>(h, 0);
+            enqueue_advance<S>(h, 0, 0);
         });
     };
     for (int i = 0; i < n; ++i) {
