@@ -283,9 +283,10 @@ constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid
 constexpr int LINK_THREADS = 64;   // remap blocks: small, so the box spreads over the SMs; one count per block
 
 // Exclusive prefix of n counts into pre[0..n] (pre[n] = total), computed by
-// the whole CTA (NT threads); every thread must call it.
+// the whole CTA (NT threads); every thread must call it.  first: this
+// thread's count[threadIdx.x] (0 beyond n), loaded by the caller ahead.
 template <int NT>
-__device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n, int* pre) {
+__device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n, int* pre, int first) {
     __shared__ int wsum[NT / 32];
     __shared__ int carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -293,7 +294,7 @@ __device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n
     __syncthreads();
     for (int base = 0; base < n; base += NT) {
         const int i = base + (int)threadIdx.x;
-        int v = i < n ? count[i] : 0;
+        int v = base == 0 ? first : (i < n ? count[i] : 0);
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, v, off);
@@ -342,14 +343,15 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     extern __shared__ int pre[];   // [runs + 1]
     __shared__ LinkFrame<A> Fr;
     __shared__ BoxFrame Bf;
+    const int runs = (int)((B.cells + LINK_THREADS - 1) / LINK_THREADS);
+    const int first = (int)threadIdx.x < runs ? run_count[threadIdx.x] : 0;   // in flight during the set-up
     if (threadIdx.x == 0) {
         Fr.init(*ps);
         box_frame_init(Bf, D.n, D.periodic, B, *ps);
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int runs = (int)((B.cells + LINK_THREADS - 1) / LINK_THREADS);
-    const int total = block_prefix<BNDW_THREADS>(run_count, runs, pre);
+    const int total = block_prefix<BNDW_THREADS>(run_count, runs, pre, first);
     const int W = (int)gridDim.x * (BNDW_THREADS / 32);
     LinkSums acc;
     for (int j = (int)blockIdx.x * (BNDW_THREADS / 32) + wib; j < total; j += W) {
