@@ -153,98 +153,133 @@ struct UpdateArgs {
     const S* src;
     S* dst;
     CollideParams<A> P;
-    // coalescence from the next finer level
-    LevelView F;
-    const S* fsrc;
+    // coalescence: a host cell takes the mean of its eight ghost sub-cells,
+    // which the next finer level's last sub-step left in coal_in (this
+    // level's layout), rescaled by fkp, fkm when rescaling is on
+    const A* coal_in;
     A fkp, fkm;
+    // at this level's last sub-step: the next coarser level C and its coal_in
+    LevelView C;
+    A* coal_out;
     const uint8_t* solid;     // finest level with a sphere: solid flags of real cells
     int* status;
 };
 
-// Update of one cell of pool block b: real cells pull (or, for hosts,
-// coalesce) and collide; ghost cells pull only.  nb27 lists the pool ids of
-// block b's 26 neighbours (and itself at index 13).  rigid (static ghost
-// cells at the first sub-step): the pull carries the exploded field one
-// cell along c_q, so that at the second sub-step a static ghost holds, for
-// each q, the exploded value of the coarse cell one cell further upwind
+// Pull of the 19 populations of cell (b, c) into g.  nb27 lists the pool
+// ids of block b's 26 neighbours (and itself at index 13).  rigid (static
+// ghost cells at the first sub-step): the pull carries the exploded field
+// one cell along c_q, so that at the second sub-step a static ghost holds,
+// for each q, the exploded value of the coarse cell one cell further upwind
 // (coarse content translating rigidly); beyond a wall, or where no block
 // exists (a value no update reads), the cell keeps its own value.
+template <typename S>
+__device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27, bool rigid,
+                                          typename Store<S>::A g[19]) {
+    using A = typename Store<S>::A;
+    const A inv = U.P.inv_scale;
+    const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
+    // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate.
+    // Every population is one load: from the neighbouring cell (real or
+    // ghost), or at a domain wall (-2) the cell's own opposite population
+    // (bounce-back).  No block (-1) is an error: the value is 0 and the
+    // status word says so.
+    const int bsx[3] = {lx == 0 ? -1 : 0, 0, lx == 15 ? 1 : 0};
+    const int bsy[3] = {ly == 0 ? -1 : 0, 0, ly == 15 ? 1 : 0};
+    const int bsz[3] = {lz == 0 ? -1 : 0, 0, lz == 15 ? 1 : 0};
+    const int lsx[3] = {(lx - 1) & 15, lx, (lx + 1) & 15};
+    const int lsy[3] = {((ly - 1) & 15) * BS, ly * BS, ((ly + 1) & 15) * BS};
+    const int lsz[3] = {((lz - 1) & 15) * BS * BS, lz * BS * BS, ((lz + 1) & 15) * BS * BS};
+    bool missing = false;
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int ix = 1 - cx(q), iy = 1 - cy(q), iz = 1 - cz(q);
+        const int nbk = nb27[13 + bsx[ix] + 3 * bsy[iy] + 9 * bsz[iz]];   // entry 13 is b itself
+        const bool own = nbk < 0;
+        const int sb = own ? b : nbk, sq = (own && !rigid) ? opp(q) : q;
+        const int sc = own ? c : lsx[ix] + lsy[iy] + lsz[iz];
+        const A v = Store<S>::load(U.src + (unsigned)((sb * 19 + sq) * B3 + sc), inv);   // pools hold < 2^31 elements
+        const bool lost = nbk == -1 && !rigid;
+        missing |= lost;
+        g[q] = lost ? A(0) : v;
+    }
+    if (missing) atomicOr(U.status, STATUS_AMR_MISSING);
+}
+
+// Update of one cell of pool block b: real cells pull (or, for hosts, take
+// the coalesced mean) and collide; ghost cells pull only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL, bool RESCALE>
 __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
                                             bool rigid = false) {
     using A = typename Store<S>::A;
-    const LevelView& D = U.D;
-    const A scale = U.P.scale, inv = U.P.inv_scale;
-    const bool real = REAL;
-    const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
     A g[19];
-    if (HAS_FINE && real && D.host[(size_t)b * B3 + c] == 1) {
-        // coalescence: mean of the eight ghost sub-cells after the finer level's two steps
-        const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
+    if (HAS_FINE && REAL && U.D.host[(size_t)b * B3 + c] == 1) {
 #pragma unroll
-        for (int q = 0; q < 19; ++q) g[q] = A(0);
-        const int gx = 2 * (bx * BS + lx), gy = 2 * (by * BS + ly), gz = 2 * (bz * BS + lz);
-        for (int s = 0; s < 8; ++s) {
-            const int v[3] = {gx + (s & 1), gy + ((s >> 1) & 1), gz + (s >> 2)};
-            int vc;
-            const int vb = locate(U.F, v, &vc);
-            if (vb < U.F.nreal) {
-                atomicOr(U.status, STATUS_AMR_MISSING);
-                continue;
-            }
-#pragma unroll
-            for (int q = 0; q < 19; ++q) g[q] += Store<S>::load(U.fsrc + paddr(vb, q, vc), inv);
-        }
-#pragma unroll
-        for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
+        for (int q = 0; q < 19; ++q) g[q] = U.coal_in[paddr(b, q, c)];
         if (RESCALE) rescale19<A>(g, U.fkp, U.fkm);
     } else {
-        // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate.
-        // Every population is one load: from the neighbouring cell (real or
-        // ghost), or at a domain wall (-2) the cell's own opposite population
-        // (bounce-back).  No block (-1) is an error: the value is 0 and the
-        // status word says so.
-        const int bsx[3] = {lx == 0 ? -1 : 0, 0, lx == 15 ? 1 : 0};
-        const int bsy[3] = {ly == 0 ? -1 : 0, 0, ly == 15 ? 1 : 0};
-        const int bsz[3] = {lz == 0 ? -1 : 0, 0, lz == 15 ? 1 : 0};
-        const int lsx[3] = {(lx - 1) & 15, lx, (lx + 1) & 15};
-        const int lsy[3] = {((ly - 1) & 15) * BS, ly * BS, ((ly + 1) & 15) * BS};
-        const int lsz[3] = {((lz - 1) & 15) * BS * BS, lz * BS * BS, ((lz + 1) & 15) * BS * BS};
-        bool missing = false;
-#pragma unroll
-        for (int q = 0; q < 19; ++q) {
-            const int ix = 1 - cx(q), iy = 1 - cy(q), iz = 1 - cz(q);
-            const int nbk = nb27[13 + bsx[ix] + 3 * bsy[iy] + 9 * bsz[iz]];   // entry 13 is b itself
-            const bool own = nbk < 0;
-            const int sb = own ? b : nbk, sq = (own && !rigid) ? opp(q) : q;
-            const int sc = own ? c : lsx[ix] + lsy[iy] + lsz[iz];
-            const A v = Store<S>::load(U.src + (unsigned)((sb * 19 + sq) * B3 + sc), inv);   // pools hold < 2^31 elements
-            const bool lost = nbk == -1 && !rigid;
-            missing |= lost;
-            g[q] = lost ? A(0) : v;
-        }
-        if (missing) atomicOr(U.status, STATUS_AMR_MISSING);
+        pull_cell<S>(U, b, c, nb27, rigid, g);
     }
     if (REAL) trt_collide<A, false>(g, U.P, U.status);
 #pragma unroll
-    for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], scale);
+    for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], U.P.scale);
 }
 
 // One launch per level step: the first gblocks CTAs stream ghost cells of
-// the level (a list of pool block << 12 | cell, the active ghost cells
-// first, then at the first sub-step the static ones, which pull rigidly; no
-// collision); the others update the real blocks, one CTA per z-slice of a
-// block (256 cells, full warps).  Both read src and write dst only.
+// the level (a list of pool block << 12 | cell: the active ghost cells,
+// eight consecutive entries per host cell of the coarser level, then the
+// static ones), no collision.  At the first sub-step they stream the active
+// and the static cells (rigidly) into dst.  At the last sub-step they
+// stream the active ones and, instead of storing them, sum each host's
+// eight in a fixed shuffle tree; the first lane of each eight writes the
+// mean into the coarser level's coal_in (coalescence).  The other CTAs
+// update the real blocks, one CTA per z-slice of a block (256 cells, full
+// warps).  All read src; the real-block CTAs write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED, bool RESCALE>
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks) {
+    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks, int coalesce) {
     using A = typename Store<S>::A;
     if (HAS_COARSE && (int)blockIdx.x < gblocks) {   // uniform across the block
         const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
-        if (i < nglist) {
+        if (!coalesce) {
+            if (i < nglist) {
+                const int e = glist[i];
+                const int b = e >> 12, c = e & 4095;
+                update_cell<S, false, true, false, RESCALE>(U, b, c, U.D.nbr + (size_t)b * 27, i >= nactive);
+            }
+            return;
+        }
+        // last sub-step: every lane takes part in the shuffles (nglist is a multiple of 8)
+        const bool valid = i < nglist;
+        A g[19];
+        int b = 0, c = 0;
+        if (valid) {
             const int e = glist[i];
-            const int b = e >> 12, c = e & 4095;
-            update_cell<S, false, true, false, RESCALE>(U, b, c, U.D.nbr + (size_t)b * 27, i >= nactive);
+            b = e >> 12;
+            c = e & 4095;
+            pull_cell<S>(U, b, c, U.D.nbr + (size_t)b * 27, false, g);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 19; ++q) g[q] = A(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            A v = g[q];
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            g[q] = v;
+        }
+        if (valid && (i & 7) == 0) {
+            const int p[3] = {(U.D.bpos[3 * b] * BS + (c & 15)) >> 1, (U.D.bpos[3 * b + 1] * BS + ((c >> 4) & 15)) >> 1,
+                              (U.D.bpos[3 * b + 2] * BS + (c >> 8)) >> 1};
+            int hc;
+            const int hb = locate(U.C, p, &hc);
+            if (hb < 0 || hb >= U.C.nreal) {
+                atomicOr(U.status, STATUS_AMR_MISSING);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 19; ++q) U.coal_out[paddr(hb, q, hc)] = g[q] * A(0.125);
+            }
         }
         return;
     }
@@ -821,6 +856,7 @@ struct Level {
     int nxlist = 0;
     void* d_pops[2] = {nullptr, nullptr};
     int cur = 0;
+    void* d_coal = nullptr;      // levels with a finer level: coalesced host values, arithmetic type, pops layout
     uint8_t* d_flags[2] = {nullptr, nullptr};   // finest level only
     int fcur = 0;
     double taup = 0, taum = 0;
@@ -1071,6 +1107,7 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_xlist);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
+    handle_free(h, V.d_coal);
     handle_free(h, V.d_flags[0]);
     handle_free(h, V.d_flags[1]);
     V = Level();
@@ -1182,6 +1219,11 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         if (!V.d_map || !V.d_refined || !V.d_bpos || !V.d_nbr || !V.d_pops[0] || !V.d_pops[1] || !V.d_host ||
             !V.d_gkind)
             return LBMP_ERR_OOM;
+        if (l + 1 < L) {
+            const size_t as = h->cfg.precision == LBMP_FP64 ? 8 : 4;
+            V.d_coal = handle_alloc(h, as * 19 * B3 * (size_t)std::max(V.nreal, 1));
+            if (!V.d_coal) return LBMP_ERR_OOM;
+        }
         if (l == L - 1) {
             V.d_flags[0] = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
             V.d_flags[1] = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
@@ -1212,14 +1254,32 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             cudaStreamSynchronize(h->stream) != cudaSuccess)
             return LBMP_ERR_CUDA;
         h->d2h += (long long)kinds.size();
-        // used: the active ghost cells (list's order), then the static ones
-        std::vector<int> list, stat;
-        for (int gb = 0; gb < F.nghost; ++gb)
+        // used: the active ghost cells, the eight sub-cells of each host of
+        // the coarser level consecutive (host order, then sub-cell order),
+        // then the static ones
+        const Level& C = E->lv[l - 1];
+        std::vector<std::pair<long long, int>> act;
+        std::vector<int> stat;
+        for (int gb = 0; gb < F.nghost; ++gb) {
+            const int* bp = &F.bpos[3 * (size_t)(F.nreal + gb)];
             for (int c = 0; c < B3; ++c) {
                 const uint8_t k = kinds[(size_t)gb * B3 + c];
-                if (k == 1) list.push_back(((F.nreal + gb) << 12) | c);
-                if (k == 2) stat.push_back(((F.nreal + gb) << 12) | c);
+                const int e = ((F.nreal + gb) << 12) | c;
+                if (k == 2) stat.push_back(e);
+                if (k != 1) continue;
+                const int g[3] = {bp[0] * BS + (c & 15), bp[1] * BS + ((c >> 4) & 15), bp[2] * BS + (c >> 8)};
+                const int p[3] = {g[0] >> 1, g[1] >> 1, g[2] >> 1};
+                const int m = C.map[(p[0] / BS) + C.nb[0] * ((p[1] / BS) + C.nb[1] * (p[2] / BS))];
+                if (m < 0) return LBMP_ERR_CUDA;   // an active ghost cell lies in a real coarser cell by construction
+                const int pc = (p[0] & 15) + BS * ((p[1] & 15) + BS * (p[2] & 15));
+                const int sub = (g[0] & 1) + 2 * (g[1] & 1) + 4 * (g[2] & 1);
+                act.push_back({(((long long)m << 12 | pc) << 3) | sub, e});
             }
+        }
+        std::sort(act.begin(), act.end());
+        if (act.size() % 8 != 0) return LBMP_ERR_CUDA;
+        std::vector<int> list(act.size());
+        for (size_t i = 0; i < act.size(); ++i) list[i] = act[i].second;
         std::vector<int> used(list);
         used.insert(used.end(), stat.begin(), stat.end());
         F.nglist = (int)list.size();
@@ -1355,19 +1415,25 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     U.src = (const S*)V.d_pops[V.cur];
     U.dst = (S*)V.d_pops[1 - V.cur];
     U.P = P;
-    U.F = U.D;
-    U.fsrc = nullptr;
+    U.coal_in = nullptr;
     U.fkp = U.fkm = (A)1;
+    U.C = U.D;
+    U.coal_out = nullptr;
     U.solid = nullptr;
     U.status = h->status;
     const bool has_fine = l + 1 < L, has_coarse = l > 0;
     if (has_fine) {
         Level& F = E->lv[l + 1];
-        U.F = view(E, F);
-        U.fsrc = (const S*)F.d_pops[F.cur];
+        U.coal_in = (const A*)V.d_coal;
         // coalescence: averaged finer values are pre-collision values of the coarser cell
         U.fkp = (A)(2.0 * V.taup / F.taup);
         U.fkm = (A)(2.0 * V.taum / F.taum);
+    }
+    const int coalesce = (has_coarse && sub == 1) ? 1 : 0;   // this sub-step ends the coarser level's step
+    if (coalesce) {
+        Level& C = E->lv[l - 1];
+        U.C = view(E, C);
+        U.coal_out = (A*)C.d_coal;
     }
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) {
@@ -1401,12 +1467,12 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         // the rescaling option is a template parameter: without it the kernel carries none of its code
         auto go = [&](auto rs) {
             constexpr bool R = decltype(rs)::value;
-            if (has_fine && has_coarse) k_update<S, true, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
-            else if (has_fine) k_update<S, true, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
-            else if (has_coarse && coupled) k_update<S, false, true, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
-            else if (has_coarse) k_update<S, false, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
-            else if (coupled) k_update<S, false, false, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
-            else k_update<S, false, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks);
+            if (has_fine && has_coarse) k_update<S, true, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+            else if (has_fine) k_update<S, true, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+            else if (has_coarse && coupled) k_update<S, false, true, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+            else if (has_coarse) k_update<S, false, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+            else if (coupled) k_update<S, false, false, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+            else k_update<S, false, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
         };
         if (rescale) go(std::true_type{});
         else go(std::false_type{});
