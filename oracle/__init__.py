@@ -28,6 +28,7 @@ class OrcParams(ctypes.Structure):
         ("boundary", ctypes.c_int),
         ("force_average", ctypes.c_int),
         ("plain_mem", ctypes.c_int),
+        ("bulk", ctypes.c_double),
     ]
 
 
@@ -53,6 +54,7 @@ class OrcAmrParams(ctypes.Structure):
         ("force_average", ctypes.c_int),
         ("plain_mem", ctypes.c_int),
         ("rescale", ctypes.c_int),
+        ("bulk", ctypes.c_double),
     ]
 
 
@@ -138,7 +140,7 @@ class UniformSim:
     """One uniform-grid simulation held by the C++ oracle."""
 
     def __init__(self, shape, tau, magic=3.0 / 16.0, periodic=(1, 1, 1), body_force=(0.0, 0.0, 0.0),
-                 boundary="cli", force_average=True, plain_mem=False):
+                 boundary="cli", force_average=True, plain_mem=False, bulk=1.0):
         L = lib()
         p = OrcParams()
         p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -149,6 +151,7 @@ class UniformSim:
         p.boundary = {"cli": 0, "sbb": 1}[boundary]
         p.force_average = int(bool(force_average))
         p.plain_mem = int(bool(plain_mem))
+        p.bulk = float(bulk)
         self.shape = tuple(int(v) for v in shape)
         self.ncells = self.shape[0] * self.shape[1] * self.shape[2]
         self._h = L.orc_create(ctypes.byref(p))
@@ -260,7 +263,7 @@ class RefinedSim:
     """Block-structured refined simulation held by the C++ oracle (refined.cpp)."""
 
     def __init__(self, shape, levels, tau, magic=3.0 / 16.0, periodic=(1, 1, 1), boundary="cli",
-                 force_average=True, plain_mem=False, rescale=False):
+                 force_average=True, plain_mem=False, rescale=False, bulk=1.0):
         L = lib()
         p = OrcAmrParams()
         p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -272,6 +275,7 @@ class RefinedSim:
         p.force_average = int(bool(force_average))
         p.plain_mem = int(bool(plain_mem))
         p.rescale = int(bool(rescale))
+        p.bulk = float(bulk)
         self._L = L
         self.levels = int(levels)
         self._h = L.orc_amr_create(ctypes.byref(p))

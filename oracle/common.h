@@ -5,7 +5,9 @@
  */
 #ifndef LBM_ORACLE_COMMON_H
 #define LBM_ORACLE_COMMON_H
+#include <cmath>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 namespace orc {
@@ -49,6 +51,103 @@ inline double geq(int q, double drho, const double u[3]) {
     double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
     double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     return W[q] * (drho + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+// ------------------------------------------------------------ MRT (Sec. 2.1)
+// Moment basis of the D3Q19 MRT model the paper uses (transformation matrix
+// of Duenweg et al. 2007): row k of M is the polynomial e_k evaluated at
+// c_q.  Rows 0-3: density and momentum; 4: |c|^2 - 1 (bulk); 5-9: the five
+// shear components; 10-15: six odd third-order modes; 16: 3|c|^4 - 6|c|^2 + 1
+// (isotropic fourth order); 17-18: two anisotropic fourth-order modes.  The
+// rows are orthogonal under the lattice weights.
+inline double mrt_basis(int k, int q) {
+    const double x = C[q][0], y = C[q][1], z = C[q][2];
+    const double c2 = x * x + y * y + z * z;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return x;
+        case 2: return y;
+        case 3: return z;
+        case 4: return c2 - 1.0;
+        case 5: return 3.0 * x * x - c2;
+        case 6: return y * y - z * z;
+        case 7: return x * y;
+        case 8: return y * z;
+        case 9: return z * x;
+        case 10: return (3.0 * c2 - 5.0) * x;
+        case 11: return (3.0 * c2 - 5.0) * y;
+        case 12: return (3.0 * c2 - 5.0) * z;
+        case 13: return (y * y - z * z) * x;
+        case 14: return (z * z - x * x) * y;
+        case 15: return (x * x - y * y) * z;
+        case 16: return 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+        case 17: return (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+        default: return (2.0 * c2 - 3.0) * (y * y - z * z);
+    }
+}
+
+// Relaxation rate of moment k (Sec. 2.1): 0 for the conserved moments,
+// s_b for the bulk and the isotropic fourth-order mode, s_nu for the shear
+// modes and the two anisotropic fourth-order modes, s_nu^- for the six odd
+// modes (the counts of the paper's relaxation matrix: 4 zeros, 2 s_b, 7
+// s_nu, 6 s_nu^-).
+inline double mrt_rate(int k, double s_nu, double s_minus, double s_b) {
+    if (k < 4) return 0.0;
+    if (k == 4 || k == 16) return s_b;
+    if (k >= 10 && k <= 15) return s_minus;
+    return s_nu;
+}
+
+// M^-1 by Gauss-Jordan elimination with partial pivoting (computed once).
+inline const double* mrt_inverse() {
+    static const std::vector<double> inv = [] {
+        double a[19][38];
+        for (int k = 0; k < 19; ++k)
+            for (int q = 0; q < 38; ++q) a[k][q] = q < 19 ? mrt_basis(k, q) : (q - 19 == k ? 1.0 : 0.0);
+        for (int col = 0; col < 19; ++col) {
+            int piv = col;
+            for (int r = col + 1; r < 19; ++r)
+                if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+            for (int q = 0; q < 38; ++q) std::swap(a[col][q], a[piv][q]);
+            const double d = a[col][col];
+            for (int q = 0; q < 38; ++q) a[col][q] /= d;
+            for (int r = 0; r < 19; ++r) {
+                if (r == col) continue;
+                const double f = a[r][col];
+                if (f != 0.0)
+                    for (int q = 0; q < 38; ++q) a[r][q] -= f * a[col][q];
+            }
+        }
+        std::vector<double> m(19 * 19);
+        for (int r = 0; r < 19; ++r)
+            for (int q = 0; q < 19; ++q) m[(size_t)r * 19 + q] = a[r][19 + q];
+        return m;
+    }();
+    return inv.data();
+}
+
+// MRT collision of one cell's deviations g (Sec. 2.1, C = M^-1 S M):
+// m = M g, m_eq = M g_eq, m' = m - S (m - m_eq) + (I - S/2) M src, g' = M^-1 m'.
+// src (may be NULL): the velocity-space body-force source of the cell.
+inline void mrt_collide(const double g[19], const double geq_dev[19], const double* src, double s_nu,
+                        double s_minus, double s_b, double out[19]) {
+    const double* Minv = mrt_inverse();
+    double m[19];
+    for (int k = 0; k < 19; ++k) {
+        double mk = 0.0, mq = 0.0, ms = 0.0;
+        for (int q = 0; q < 19; ++q) {
+            mk += mrt_basis(k, q) * g[q];
+            mq += mrt_basis(k, q) * geq_dev[q];
+            if (src) ms += mrt_basis(k, q) * src[q];
+        }
+        const double s = mrt_rate(k, s_nu, s_minus, s_b);
+        m[k] = mk - s * (mk - mq) + (1.0 - 0.5 * s) * ms;
+    }
+    for (int q = 0; q < 19; ++q) {
+        double v = 0.0;
+        for (int k = 0; k < 19; ++k) v += Minv[(size_t)q * 19 + k] * m[k];
+        out[q] = v;
+    }
 }
 
 inline void cross(const double a[3], const double b[3], double out[3]) {

@@ -34,6 +34,7 @@ typedef struct {
     int boundary;         /* 0 = CLI (Eq. of Sec. 2.3), 1 = simple bounce-back (delta = 1/2) */
     int force_average;    /* 1 = average hydrodynamic force/torque over two steps (Algorithm 1) */
     int plain_mem;        /* 1 = particle update of Sec. 2.2 without the virtual-mass terms */
+    double bulk;          /* MRT bulk factor Lambda_b (Sec. 2.1); 0 or 1 = TRT */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -114,6 +115,7 @@ typedef struct {
     int force_average;
     int plain_mem;
     int rescale;          /* 1: rescale non-equilibrium parts at level interfaces */
+    double bulk;          /* MRT bulk factor Lambda_b (Sec. 2.1); 0 or 1 = TRT */
 } orc_amr_params;
 typedef struct orc_amr orc_amr;
 orc_amr* orc_amr_create(const orc_amr_params* p);

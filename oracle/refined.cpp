@@ -58,7 +58,7 @@ struct LevelData {
     std::vector<uint8_t> host;        // real cells: 1 host, 2 second ring, 0 otherwise
     std::vector<uint8_t> gkind;       // ghost cells: 1 active (host sub-cell), 2 static, 0 unused
     std::vector<uint8_t> flag;        // real cells of the finest level: 1 = inside the sphere
-    double taup = 0, taum = 0, sp = 0, sm = 0;
+    double taup = 0, taum = 0, sp = 0, sm = 0, sb = 0;
 };
 
 }  // namespace
@@ -120,6 +120,8 @@ void level_rates(orc_amr* a) {
         D.taum = 0.5 + a->p.magic / (D.taup - 0.5);
         D.sp = 1.0 / D.taup;
         D.sm = 1.0 / D.taum;
+        const double bulk = a->p.bulk > 0.0 ? a->p.bulk : 1.0;
+        D.sb = bulk == 1.0 ? D.sp : 1.0 / (0.5 + bulk * (D.taup - 0.5));   // Lambda_b fixed on every level, like Lambda
     }
 }
 
@@ -181,12 +183,20 @@ void rescale_levels(const orc_amr* a, double f[19], int from, int to) {
     }
 }
 
-// TRT collision (Sec. 2.1) of one cell's deviations at level D.
+// TRT collision (Sec. 2.1) of one cell's deviations at level D; the MRT
+// form when the bulk rate differs from s+ (Lambda_b != 1).
 void collide(const LevelData& D, double g[19]) {
     double drho = 0, u[3] = {0, 0, 0};
     for (int q = 0; q < 19; ++q) {
         drho += g[q];
         for (int k = 0; k < 3; ++k) u[k] += g[q] * C[q][k];
+    }
+    if (D.sb != D.sp) {
+        double ge[19], out[19];
+        for (int q = 0; q < 19; ++q) ge[q] = geq(q, drho, u);
+        mrt_collide(g, ge, nullptr, D.sp, D.sm, D.sb, out);
+        std::memcpy(g, out, sizeof(out));
+        return;
     }
     double out[19];
     const double e0 = geq(0, drho, u);

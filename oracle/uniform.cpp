@@ -40,6 +40,8 @@ struct orc_sim {
     Planes planes;
     double gravity[3] = {0, 0, 0};
     double sp = 0, sm = 0;          // s+ and s-
+    double sb = 0;                  // bulk rate s_b of the MRT model (used when bulk != 1)
+    double bulk = 1.0;              // bulk factor Lambda_b (1: TRT)
     std::vector<double> history;    // 15 per step
     double plane_force[3] = {0, 0, 0};
     std::vector<uint8_t> has_link;  // per cell: some source of the pull is solid
@@ -150,6 +152,19 @@ void collide_cell(orc_sim* s, long x) {
     const double* F = s->p.body_force;
     bool forced = (F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0);
     double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    if (s->bulk != 1.0) {   // MRT with the bulk factor Lambda_b (Sec. 2.1)
+        double gi[19], ge[19], src[19], out[19];
+        for (int q = 0; q < 19; ++q) {
+            gi[q] = g[(size_t)q * s->n + x];
+            ge[q] = geq(q, drho, u);
+            const double cu = C[q][0] * u[0] + C[q][1] * u[1] + C[q][2] * u[2];
+            const double cF = C[q][0] * F[0] + C[q][1] * F[1] + C[q][2] * F[2];
+            src[q] = W[q] * (3.0 * cF - 3.0 * uF + 9.0 * cu * cF);   // Guo source (reading in the design notes)
+        }
+        mrt_collide(gi, ge, forced ? src : nullptr, s->sp, s->sm, s->sb, out);
+        for (int q = 0; q < 19; ++q) g[(size_t)q * s->n + x] = out[q];
+        return;
+    }
     double out[19];
     // rest population: purely symmetric
     {
@@ -362,6 +377,8 @@ orc_sim* orc_create(const orc_params* p) {
     // Sec. 2.1: s+ = s_nu = 1/tau; Lambda = (1/s+ - 1/2)(1/s- - 1/2)
     s->sp = 1.0 / p->tau;
     s->sm = 1.0 / (0.5 + p->magic / (p->tau - 0.5));
+    s->bulk = p->bulk > 0.0 ? p->bulk : 1.0;
+    s->sb = 1.0 / (0.5 + s->bulk * (p->tau - 0.5));   // Lambda_b = (1/s_b - 1/2) / (1/s_nu - 1/2)
     return s;
 }
 
