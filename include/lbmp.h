@@ -75,6 +75,9 @@ typedef struct {
     lbmp_alloc_fn alloc;
     lbmp_free_fn free;
     void* alloc_ctx;
+    double bulk_factor;      /* MRT bulk factor Lambda_b (Sec. 2.1): the bulk mode and the isotropic fourth-order
+                                mode relax at s_b with (1/s_b - 1/2) = Lambda_b (1/s_nu - 1/2); 1 (default) is TRT,
+                                the paper's runs use 100.  Must be > 0.  Not with rescale_noneq or the drag adjoint. */
 } lbmp_config;
 
 /* Fills *cfg with defaults: 32^3 periodic, 1 level, FP32, tau 0.6,

@@ -372,7 +372,7 @@ class Simulation:
 
     def __init__(self, shape, precision="fp32", tau=0.6, magic=3.0 / 16.0, bc=("periodic",) * 3, boundary="cli",
                  force_average=True, history_capacity=4096, fp16_scale_log2=11, stream=None,
-                 torch_allocator=True, levels=1, rescale=False, regrid_interval=0):
+                 torch_allocator=True, levels=1, rescale=False, regrid_interval=0, bulk=1.0):
         import torch
         if not torch.cuda.is_available():
             raise LbmpError(3, "no CUDA device: this library has no CPU path")
@@ -385,6 +385,7 @@ class Simulation:
         cfg.precision = PRECISIONS[precision]
         cfg.tau = float(tau)
         cfg.magic = float(magic)
+        cfg.bulk_factor = float(bulk)
         cfg.boundary = BOUNDARY[boundary]
         cfg.force_average = int(bool(force_average))
         cfg.history_capacity = int(history_capacity)
@@ -520,13 +521,14 @@ class BatchSimulation:
     """Many independent uniform periodic simulations advanced together."""
 
     def __init__(self, sims, precision="fp32", magic=3.0 / 16.0, boundary="cli", force_average=True,
-                 history_capacity=4096, stream=None, torch_allocator=True):
+                 history_capacity=4096, stream=None, torch_allocator=True, bulk=1.0):
         import torch
         if not torch.cuda.is_available():
             raise LbmpError(3, "no CUDA device: this library has no CPU path")
         cfg = lbmp_config_default()
         cfg.precision = PRECISIONS[precision]
         cfg.magic = float(magic)
+        cfg.bulk_factor = float(bulk)
         cfg.boundary = BOUNDARY[boundary]
         cfg.force_average = int(bool(force_average))
         cfg.history_capacity = int(history_capacity)

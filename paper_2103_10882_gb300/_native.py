@@ -28,6 +28,7 @@ class LbmpConfig(ctypes.Structure):
         ("alloc", ALLOC_FN),
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
+        ("bulk_factor", ctypes.c_double),
     ]
 
 

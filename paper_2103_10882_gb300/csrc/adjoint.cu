@@ -589,6 +589,7 @@ lbmp_status adjoint_check(const lbmp_handle* h, std::string* why) {
             return *why = "the drag adjoint needs the sphere at rest", LBMP_ERR_UNSUPPORTED;
     }
     if (h->cfg.precision == LBMP_FP16) return *why = "the drag adjoint runs in FP32 or FP64", LBMP_ERR_UNSUPPORTED;
+    if (h->cfg.bulk_factor != 1.0) return *why = "the drag adjoint is the reverse of the TRT step (bulk factor 1)", LBMP_ERR_UNSUPPORTED;
     return LBMP_OK;
 }
 

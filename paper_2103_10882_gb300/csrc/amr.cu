@@ -1372,6 +1372,7 @@ CollideParams<typename Store<S>::A> level_params(const lbmp_handle* h, const Lev
     CollideParams<A> p;
     p.sp = (A)(1.0 / V.taup);
     p.sm = (A)(1.0 / V.taum);
+    p.db = (A)bulk_rate_offset(V.taup, h->cfg.bulk_factor);   // Lambda_b fixed on every level, like Lambda
     p.F[0] = p.F[1] = p.F[2] = (A)0;
     p.forced = 0;
     if (h->cfg.precision == LBMP_FP16) {

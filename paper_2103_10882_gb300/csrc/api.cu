@@ -211,6 +211,7 @@ lbmp_status lbmp_config_default(lbmp_config* c) {
     c->regrid_interval = 0;
     c->history_capacity = 4096;
     c->fp16_scale_log2 = 11;
+    c->bulk_factor = 1.0;
     return LBMP_OK;
 }
 
@@ -234,6 +235,11 @@ lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
         return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown precision");
     if (!(cfg->tau > 0.5)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: tau must exceed 1/2");
     if (!(cfg->magic > 0.0)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: magic parameter must be > 0");
+    if (!(cfg->bulk_factor > 0.0) || !std::isfinite(cfg->bulk_factor))
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: bulk factor must be > 0 (1 = TRT)");
+    if (cfg->bulk_factor != 1.0 && cfg->levels > 1 && cfg->rescale_noneq)
+        return fail(nullptr, LBMP_ERR_UNSUPPORTED,
+                    "lbmp_create: non-equilibrium rescaling is built for TRT only (bulk factor 1)");
     if (cfg->boundary != LBMP_CLI && cfg->boundary != LBMP_SBB)
         return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown boundary scheme");
     for (int a = 0; a < 3; ++a)

@@ -29,7 +29,7 @@ struct SimDev {
     int mask_off;        // boundary mask: one byte per box cell
     int bnd_off, bnd_n;  // boundary-kernel blocks of the simulation (and their force partials)
     BoxDesc box;
-    double sp, sm;
+    double sp, sm, db;
     long long hist_off;  // records
 };
 
@@ -45,6 +45,7 @@ __host__ __device__ __forceinline__ CollideParams<typename Store<S>::A> sim_para
     CollideParams<typename Store<S>::A> p;
     p.sp = (typename Store<S>::A)D.sp;
     p.sm = (typename Store<S>::A)D.sm;
+    p.db = (typename Store<S>::A)D.db;
     p.F[0] = p.F[1] = p.F[2] = 0;
     p.forced = 0;
     p.scale = scale;
@@ -421,6 +422,7 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
         const double sp = 1.0 / in.tau, sm = 1.0 / (0.5 + h->cfg.magic / (in.tau - 0.5));
         D.sp = sp;
         D.sm = sm;
+        D.db = bulk_rate_offset(in.tau, h->cfg.bulk_factor);
         ParticleState& P = B->h_ps[s];
         std::memset(&P, 0, sizeof(P));
         for (int a = 0; a < 3; ++a) {

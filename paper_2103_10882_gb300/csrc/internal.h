@@ -26,6 +26,7 @@ struct GridDesc {
 template <typename A>
 struct CollideParams {
     A sp, sm;          // s+ = 1/tau, s- from the magic parameter
+    A db;              // MRT: s_b - s+ (bulk factor Lambda_b != 1), 0 for TRT
     A F[3];            // fluid body force
     int forced;
     A scale, inv_scale;   // FP16 storage scaling (1 otherwise)
@@ -151,6 +152,13 @@ inline void relaxation_rates(double tau, double magic, double* sp, double* sm) {
     *sm = 1.0 / (0.5 + magic / (tau - 0.5));
 }
 
+// MRT bulk rate from the bulk factor: Lambda_b = (1/s_b - 1/2)/(1/s_nu - 1/2)
+// (Sec. 2.1); returns s_b - s+, exactly 0 for Lambda_b = 1 (TRT).
+inline double bulk_rate_offset(double tau, double bulk) {
+    if (bulk == 1.0) return 0.0;
+    return 1.0 / (0.5 + bulk * (tau - 0.5)) - 1.0 / tau;
+}
+
 template <typename A>
 inline CollideParams<A> collide_params(const lbmp_handle* h) {
     CollideParams<A> p;
@@ -158,6 +166,7 @@ inline CollideParams<A> collide_params(const lbmp_handle* h) {
     relaxation_rates(h->tau, h->magic, &sp, &sm);
     p.sp = (A)sp;
     p.sm = (A)sm;
+    p.db = (A)bulk_rate_offset(h->tau, h->cfg.bulk_factor);
     for (int a = 0; a < 3; ++a) p.F[a] = (A)h->body_force[a];
     p.forced = (h->body_force[0] != 0.0 || h->body_force[1] != 0.0 || h->body_force[2] != 0.0) ? 1 : 0;
     if (h->cfg.precision == LBMP_FP16) {

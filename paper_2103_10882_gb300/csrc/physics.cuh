@@ -54,12 +54,18 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
     const A uu = ux * ux + uy * uy + uz * uz;
     if (!(uu <= A(0.09))) atomicOr(status, STATUS_UNSTABLE_FLUID);
     const A sp = P.sp, sm = P.sm;
+    const bool mrt = P.db != A(0);
+    // MRT bulk correction: sums of (f - f_eq + source/2) over the rest,
+    // face and edge populations (the even modes' inputs)
+    A nR = A(0), nF = A(0), nE = A(0);
     {
         const A e0 = wgt<A>(0) * (drho - A(1.5) * uu);
+        if (mrt) nR = g[0] - e0;
         A o = g[0] - sp * (g[0] - e0);
         if (FORCED) {
             const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
             o += (A(1) - A(0.5) * sp) * wgt<A>(0) * (A(-3) * uF);
+            if (mrt) nR += A(0.5) * wgt<A>(0) * (A(-3) * uF);
         }
         g[0] = o;
     }
@@ -73,6 +79,10 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
         const A gm = A(0.5) * (g[q] - g[q + 1]);
         const A dp = sp * (gp - ep);
         const A dm = sm * (gm - em);
+        if (mrt) {
+            if (q < 7) nF += A(2) * (gp - ep);
+            else nE += A(2) * (gp - ep);
+        }
         A a = g[q] - dp - dm;
         A b = g[q + 1] - dp + dm;
         if (FORCED) {
@@ -82,9 +92,31 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
             const A Sm = (A(1) - A(0.5) * sm) * w * (A(3) * cF);
             a += Sp + Sm;
             b += Sp - Sm;
+            if (mrt) {   // half the symmetric source of the pair
+                const A hs = w * (A(9) * cu * cF - A(3) * uF);
+                if (q < 7) nF += hs;
+                else nE += hs;
+            }
         }
         g[q] = a;
         g[q + 1] = b;
+    }
+    if (mrt) {
+        // MRT of Sec. 2.1 = TRT with the bulk mode e4 = |c|^2 - 1 and the
+        // isotropic fourth-order mode e16 = 3|c|^4 - 6|c|^2 + 1 relaxed at s_b
+        // instead of s+: subtract (s_b - s+) w_q sum_k e_k(q) c_k with
+        // c_k = sum_p e_k(p) (f - f_eq + source/2)_p / sum_p w_p e_k(p)^2
+        // (e4: rest -1, faces 0, edges 1, norm 2/3; e16: rest 1, faces -2,
+        // edges 1, norm 2).
+        const A c4 = A(1.5) * (nE - nR);
+        const A c16 = A(0.5) * (nR - A(2) * nF + nE);
+        g[0] -= P.db * wgt<A>(0) * (c16 - c4);
+        const A df = P.db * wgt<A>(1) * (A(-2) * c16);
+        const A de = P.db * wgt<A>(7) * (c4 + c16);
+#pragma unroll
+        for (int q = 1; q < 7; ++q) g[q] -= df;
+#pragma unroll
+        for (int q = 7; q < 19; ++q) g[q] -= de;
     }
 }
 
@@ -128,10 +160,19 @@ __device__ __forceinline__ A warp_trt_collide(A gq, int lane, const CollideParam
     const A em = w * (A(3) * cu);
     const A gp = A(0.5) * (gq + gb), gm = A(0.5) * (gq - gb);
     A out = gq - P.sp * (gp - ep) - P.sm * (gm - em);
+    A v = gq - ep - em;   // f - f_eq of the lane (the odd part drops out of the even sums below)
     if (FORCED) {
         const A cF = A(c0) * P.F[0] + A(c1) * P.F[1] + A(c2) * P.F[2];
         const A uF = ux * P.F[0] + uy * P.F[1] + uz * P.F[2];
         out += (A(1) - A(0.5) * P.sp) * w * (A(9) * cu * cF - A(3) * uF) + (A(1) - A(0.5) * P.sm) * w * (A(3) * cF);
+        v += A(0.5) * w * (A(9) * cu * cF - A(3) * uF);
+    }
+    if (P.db != A(0)) {   // MRT bulk correction, as in trt_collide (uniform across the warp)
+        const A e4 = lane == 0 ? A(-1) : (lane <= 6 ? A(0) : (lane < 19 ? A(1) : A(0)));
+        const A e16 = lane == 0 ? A(1) : (lane <= 6 ? A(-2) : (lane < 19 ? A(1) : A(0)));
+        const A c4 = A(1.5) * warp_sum<A>(e4 * v);
+        const A c16 = A(0.5) * warp_sum<A>(e16 * v);
+        out -= P.db * w * (e4 * c4 + e16 * c16);
     }
     return lane < 19 ? out : A(0);
 }
