@@ -10,7 +10,8 @@ coupled method (Algorithm 1 on the finest level, sub-cycling, explosion and
 coalescence, regrids when due).  MLUPS counts real cell updates of all levels.
 
 Also reported (key "uniform512"): a periodic 512^3 box with a sphere of 40
-cells, the bandwidth case of the stream-collide kernel.  Both fields are far
+cells, the bandwidth case of the stream-collide kernel; "uniform512_mrt" is
+the same case with the paper's MRT collision (bulk factor 100).  Both fields are far
 larger than L2 (no flush needed).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp16|fp64]
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uniform", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-mrt", action="store_true", help="skip the MRT (bulk factor 100) variant of the uniform case")
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--validate", type=int, default=0,
@@ -456,11 +458,11 @@ def main():
     line["roofline"]["bytes_per_cell_update"] = 38 * bpp
 
     # --------------------------------------------- uniform bandwidth case
-    if not args.no_uniform:
+    def uniform_case(bulk):
         e = args.edge
         uw = UNIFORM
         tau_u, gm_u = ga_tau_g(uw["ga"], uw["u_g"], uw["diameter"], uw["density_ratio"])
-        us = L.Simulation((e, e, e), precision=prec, tau=tau_u)
+        us = L.Simulation((e, e, e), precision=prec, tau=tau_u, bulk=bulk)
         pos = np.array([e / 2, e / 2, e / 4]) + workloads.sub_cell_offset(rank)
         us.add_sphere(pos, uw["diameter"], uw["density_ratio"], cv=uw["cv"])
         us.set_gravity((0.0, 0.0, -gm_u))
@@ -469,15 +471,22 @@ def main():
         with ClockSampler(local) as clk_u:
             ums, uprof, u0, u1 = timed(us, args.uniform_steps, us.stream, torch, profile=True)
         us.close()
-        line["uniform512"] = {
-            "workload": uniform_name(e, prec), "value": (u1[1] - u0[1]) / (ums * 1e-3) / 1e6, "unit": "MLUPS",
+        model = "TRT" if bulk == 1.0 else "MRT, bulk factor %g" % bulk
+        return {
+            "workload": uniform_name(e, prec) + ("" if bulk == 1.0 else ", " + model),
+            "value": (u1[1] - u0[1]) / (ums * 1e-3) / 1e6, "unit": "MLUPS",
             "ms_per_step": ums / args.uniform_steps,
-            "roofline": roofline(uprof, "k_bulk (stream + TRT collide, %s)" % prec,
+            "roofline": roofline(uprof, "k_bulk (stream + %s collide, %s)" % (model, prec),
                                  profiled_traffic("k_bulk_%s_uniform256.md" % prec, "traffic_bytes_per_launch_512")
-                                 if e == 512 else None),
+                                 if e == 512 and bulk == 1.0 else None),
             "roofline_mlups": measured_peak()[0] * 1e9 / (38 * bpp) / 1e6,
             "clocks": clk_u.summary(),
         }
+
+    if not args.no_uniform:
+        line["uniform512"] = uniform_case(1.0)
+        if not args.no_mrt:   # the paper's default collision (Sec. 2.1: Lambda_b = 100)
+            line["uniform512_mrt"] = uniform_case(100.0)
     # --------------------------------------------- batched parameter sweep
     if not args.no_batch:
         sims = []
