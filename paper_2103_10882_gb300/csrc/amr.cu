@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(BNDW_THREADS)
         for (; k > 0; --k) bits &= bits - 1u;   // drop the k lowest marked cells
         const int t = (int)(r0 + base + __ffs((int)bits) - 1);
         int g[3], c;
-        box_cell(t, D.n, D.periodic, B, Bf, g);   // marked cells are inside the domain
+        if (!box_cell(t, D.n, D.periodic, B, Bf, g)) continue;   // marked cells are inside the domain
         const int b = locate(D, g, &c);
         const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
         A gq = A(0);
@@ -560,11 +560,11 @@ __global__ void __launch_bounds__(LINK_THREADS)
     for (int w = 0; w < warp; ++w) wbase += wsum[w];
     if (is_b) {
         int g[3], c;
-        box_cell(t, D.n, D.periodic, B, F, g);
-        const int b = locate(D, g, &c);
+        const bool in = box_cell(t, D.n, D.periodic, B, F, g);
+        const int b = in ? locate(D, g, &c) : -1;
         const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
-        if (pos < capacity) list[pos] = (b << 12) | c;
-        else atomicOr(status, STATUS_LINK_OVERFLOW);
+        if (pos >= capacity) atomicOr(status, STATUS_LINK_OVERFLOW);
+        else if (b >= 0) list[pos] = (b << 12) | c;
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         int tot = base;

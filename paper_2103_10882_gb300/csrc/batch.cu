@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(BW)
     LinkSums acc;
     for (int i = wib; i < nm; i += BW / 32) {
         int xyz[3];
-        box_cell((int)(t0 + sl[i]), n3, per3, D.box, Bf, xyz);
+        if (!box_cell((int)(t0 + sl[i]), n3, per3, D.box, Bf, xyz)) continue;   // marked cells are inside
         const int x = xyz[0], y = xyz[1], z = xyz[2];
         const size_t cell = (size_t)x + (size_t)G.nx * ((size_t)y + (size_t)G.ny * (size_t)z);
         A gq = A(0);
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(BW)
     if (t >= D.box.cells) return;
     const ParticleState& P = ps[sim];
     int p[3];
-    box_cell(t, n3, G.periodic, D.box, F, p);   // periodic: always inside
+    if (!box_cell(t, n3, G.periodic, D.box, F, p)) return;   // periodic: inside unless the centre is corrupt
     const int i = p[0], j = p[1], k = p[2];
     const size_t n = (size_t)G.n;
     const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);

@@ -54,6 +54,7 @@ __device__ __forceinline__ bool na_box_cell(int t, const Box& B, int* c) {
         if (v < 0 || v >= B.n[a]) {
             if (!B.periodic[a]) return false;
             v = v < 0 ? v + B.n[a] : v - B.n[a];
+            if (v < 0 || v >= B.n[a]) return false;
         }
         c[a] = v;
     }

@@ -399,10 +399,13 @@ __device__ __forceinline__ void box_frame_init(BoxFrame& F, const int n[3], cons
     bool wide = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        F.o[a] = (B.E[a] >= n[a]) ? 0 : (int)floor(P.x[a] - 0.5) - B.R;
-        const double f = floor(P.x[a]);
+        // a centre that is not finite or absurdly far (only after an unstable step, which the
+        // status word reports) is replaced so that the integer box arithmetic stays in range
+        const double x = fabs(P.x[a]) < 1e9 ? P.x[a] : 0.0;
+        F.o[a] = (B.E[a] >= n[a]) ? 0 : (int)floor(x - 0.5) - B.R;
+        const double f = floor(x);
         F.Xi[a] = (int)f;
-        F.Xh[a] = (float)(0.5 - (P.x[a] - f));
+        F.Xh[a] = (float)(0.5 - (x - f));
         // a sphere reaching within two cells of half a period: the FP32 tests skip minimum images
         wide |= periodic[a] && (P.r > 0.4 * n[a] || P.r + 2.0 >= 0.5 * n[a]);
     }
@@ -425,6 +428,7 @@ __device__ __forceinline__ bool box_cell(int t, const int n[3], const int period
         if (v < 0 || v >= n[a]) {
             if (!periodic[a]) return false;
             v = v < 0 ? v + n[a] : v - n[a];   // the box is never wider than the domain
+            if (v < 0 || v >= n[a]) return false;   // a centre outside the domain: touch nothing
         }
         p[a] = v;
     }
@@ -535,7 +539,13 @@ __device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, d
         P.a[a] = acc;
         P.b[a] = bet;
     }
-    if (fabs(P.x[a] - xold) > 0.5 || !(fabs(P.u[a]) < 0.5)) atomicOr(status, STATUS_PARTICLE_JUMP);
+    if (!(fabs(P.x[a] - xold) <= 0.5) || !(fabs(P.u[a]) < 0.5) || !(fabs(P.w[a]) < 1e30)) {
+        // a jump or a non-finite state: flag it, and keep the sphere where it was and at rest, so that
+        // the box kernels that follow until the host reads the status stay inside the domain
+        atomicOr(status, STATUS_PARTICLE_JUMP);
+        P.x[a] = xold;
+        P.u[a] = P.w[a] = P.a[a] = P.b[a] = 0.0;
+    }
     const int n = a == 0 ? G.nx : (a == 1 ? G.ny : G.nz);
     if (G.periodic[a]) {   // keep the centre inside the periodic box
         const double L = (double)n;

@@ -345,10 +345,10 @@ __global__ void __launch_bounds__(LINK_THREADS)
     for (int w = 0; w < warp; ++w) wbase += wsum[w];
     if (is_b) {
         int p[3];
-        box_cell(t, n3, G.periodic, B, F, p);
+        const bool in = box_cell(t, n3, G.periodic, B, F, p);
         const int pos = base + wbase + __popc(ballot & ((1u << lane) - 1u));
-        if (pos < capacity) list[pos] = p[0] + G.nx * (p[1] + G.ny * p[2]);
-        else atomicOr(status, STATUS_LINK_OVERFLOW);
+        if (pos >= capacity) atomicOr(status, STATUS_LINK_OVERFLOW);
+        else if (in) list[pos] = p[0] + G.nx * (p[1] + G.ny * p[2]);
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         int tot = base;
