@@ -66,6 +66,9 @@ def parse():
                     help="instead of timing: run the refined workload this many level-0 steps in FP64, FP32 and FP16 "
                          "and report the reduced precisions' errors on the particle's path")
     ap.add_argument("--adjoint-reps", type=int, default=3)
+    ap.add_argument("--stability", action="store_true",
+                    help="instead of timing: the stability-limit study (lowest stable density ratio per diameter at "
+                         "Ga = 100, plain MEM and virtual mass) and one JSON line")
     return ap.parse_args()
 
 
@@ -330,6 +333,30 @@ def validate(args):
     return 0
 
 
+def stability_study(args):
+    """Lowest stable density ratio per sphere diameter at Ga = 100 (Sec. 3.2,
+    Table 1) with the plain momentum exchange method, by bisection in
+    log(pi_p), and the virtual-mass correction (C_v = 0.5) at pi_p = 0.001;
+    the paper's Table 1 alongside as context."""
+    import paper_2103_10882_gb300 as L
+    from paper_2103_10882_gb300 import studies, workloads
+    table = {10: 0.13, 15: 0.09, 20: 0.066, 30: 0.045, 40: 0.034}   # Table 1 of the paper (context)
+    prec = args.precision
+    out = {"study": "stability limit of light rising spheres, Ga=100, u_g=0.01, box (6.4, 6.4, 12.8) d_p, "
+                    "stable = no instability flag until t_n = 10", "precision": prec, "mem": {}, "vm_mem": {}}
+    t0 = time.time()
+    for d in workloads.STABILITY["diameters"]:
+        s, u, runs = studies.density_ratio_limit(L, d, 0.0, table[d] / 4, table[d] * 4, iters=4, precision=prec)
+        out["mem"][str(d)] = {"pi_min": s, "highest_unstable": u, "paper_table1": table[d], "runs": len(runs)}
+        ok, done, uz = studies.rising_sphere_run(L, d, 0.001, 0.5, precision=prec)
+        out["vm_mem"][str(d)] = {"density_ratio": 0.001, "stable": ok, "u_z_over_u_g": uz}
+        print("d %d: MEM pi_min %s (paper %.3f); VM-MEM at 0.001 stable %s" % (d, s, table[d], ok),
+              file=sys.stderr, flush=True)
+    out["seconds"] = time.time() - t0
+    print(json.dumps(out))
+    return 0
+
+
 def adjoint_line(L, workloads, torch, prec, reps):
     """Gradient of the mean drag on the differentiation workload: forward
     (500 steps, checkpoints every 50) and backward (recompute + reverse
@@ -400,6 +427,8 @@ def main():
         return run_reference(args)
     if args.validate > 0:
         return validate(args)
+    if args.stability:
+        return stability_study(args)
     import numpy as np
     import torch
 

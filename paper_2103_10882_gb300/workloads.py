@@ -98,3 +98,10 @@ def fourier_velocity_field(shape, kmax: float, amplitude: float, seed: int) -> n
                 u[d] += a[d] * wave
     speed = np.sqrt((u * u).sum(axis=0)).max()
     return u * (amplitude / speed)
+
+
+# Stability-limit study (Sec. 3.2, Table 1): a rising sphere in a periodic
+# box of (6.4, 6.4, 12.8) d_p, starting at (3.2, 3.2, 0.6) d_p, Ga = 100 at
+# u_g = 0.01, run until t_n = t u_g / d_p = 10.
+STABILITY = dict(box=(6.4, 6.4, 12.8), start=(3.2, 3.2, 0.6), ga=100.0, u_g=0.01, t_n=10.0,
+                 diameters=(10, 15, 20, 30, 40))
