@@ -29,6 +29,7 @@ class OrcParams(ctypes.Structure):
         ("force_average", ctypes.c_int),
         ("plain_mem", ctypes.c_int),
         ("bulk", ctypes.c_double),
+        ("refill", ctypes.c_int),
     ]
 
 
@@ -55,6 +56,7 @@ class OrcAmrParams(ctypes.Structure):
         ("plain_mem", ctypes.c_int),
         ("rescale", ctypes.c_int),
         ("bulk", ctypes.c_double),
+        ("refill", ctypes.c_int),
     ]
 
 
@@ -121,6 +123,7 @@ def lib():
         L.orc_amr_get_particle.argtypes = [vp, dp]
         L.orc_amr_get_history.restype = ctypes.c_int64
         L.orc_amr_get_history.argtypes = [vp, dp, ctypes.c_int64]
+        L.orc_grad_noneq.argtypes = [ctypes.c_double, dp, dp]
         L.orc_drag_tangent.restype = ctypes.c_double
         L.orc_drag_tangent.argtypes = [ctypes.POINTER(OrcDragParams), dp, ip, ctypes.c_double, dp, dp, ip, dp, dp]
         _lib = L
@@ -132,6 +135,14 @@ def _d(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def grad_noneq(tau, S):
+    """Grad's post-collision non-equilibrium part (19 values) for a strain rate S (3x3)."""
+    _, pS = _d(np.asarray(S, dtype=np.float64).reshape(9))
+    out = np.empty(19)
+    lib().orc_grad_noneq(float(tau), pS, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
 def set_threads(n: int) -> int:
     return lib().orc_set_threads(int(n))
 
@@ -140,7 +151,7 @@ class UniformSim:
     """One uniform-grid simulation held by the C++ oracle."""
 
     def __init__(self, shape, tau, magic=3.0 / 16.0, periodic=(1, 1, 1), body_force=(0.0, 0.0, 0.0),
-                 boundary="cli", force_average=True, plain_mem=False, bulk=1.0):
+                 boundary="cli", force_average=True, plain_mem=False, bulk=1.0, refill="equilibrium"):
         L = lib()
         p = OrcParams()
         p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -152,6 +163,7 @@ class UniformSim:
         p.force_average = int(bool(force_average))
         p.plain_mem = int(bool(plain_mem))
         p.bulk = float(bulk)
+        p.refill = {"equilibrium": 0, "grad": 1}[refill]
         self.shape = tuple(int(v) for v in shape)
         self.ncells = self.shape[0] * self.shape[1] * self.shape[2]
         self._h = L.orc_create(ctypes.byref(p))
@@ -263,7 +275,7 @@ class RefinedSim:
     """Block-structured refined simulation held by the C++ oracle (refined.cpp)."""
 
     def __init__(self, shape, levels, tau, magic=3.0 / 16.0, periodic=(1, 1, 1), boundary="cli",
-                 force_average=True, plain_mem=False, rescale=False, bulk=1.0):
+                 force_average=True, plain_mem=False, rescale=False, bulk=1.0, refill="equilibrium"):
         L = lib()
         p = OrcAmrParams()
         p.nx, p.ny, p.nz = (int(v) for v in shape)
@@ -276,6 +288,7 @@ class RefinedSim:
         p.plain_mem = int(bool(plain_mem))
         p.rescale = int(bool(rescale))
         p.bulk = float(bulk)
+        p.refill = {"equilibrium": 0, "grad": 1}[refill]
         self._L = L
         self.levels = int(levels)
         self._h = L.orc_amr_create(ctypes.byref(p))

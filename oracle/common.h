@@ -150,6 +150,39 @@ inline void mrt_collide(const double g[19], const double geq_dev[19], const doub
     }
 }
 
+// ------------------------------------------------ Grad refill (Sec. 2.3)
+// The paper refills uncovered cells with the approach of Dorschner et al.
+// (2015), Grad's approximation using local velocity gradients.  Reading:
+// equilibrium at the mean density of the neighbours and the wall velocity,
+// plus Grad's non-equilibrium part from the strain rate S.  The refilled
+// state is a post-collision state, so the first-order Chapman-Enskog stress
+// enters after one collision: -3 w_q (1 - s+)/s+ Q_q:S, Q_q = c_q c_q - I/3.
+inline double grad_noneq(int q, double sp, const double S[9]) {
+    double qs = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) qs += (C[q][a] * C[q][b] - (a == b ? 1.0 / 3.0 : 0.0)) * S[3 * a + b];
+    return -3.0 * W[q] * (1.0 - sp) / sp * qs;
+}
+
+// Strain rate at an uncovered cell from the velocities of its six face
+// neighbours (up[a]: at x + e_a, um[a]: at x - e_a, each used only where
+// that neighbour is fluid) and the wall velocity uw at the cell: central
+// differences where both are fluid, one-sided against uw where one is,
+// zero where neither is.  S = (grad u + grad u^T) / 2, row major.
+inline void refill_strain(const double up[3][3], const bool okp[3], const double um[3][3], const bool okm[3],
+                          const double uw[3], double S[9]) {
+    double G[3][3];   // G[a][b] = d u_b / d x_a
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            if (okp[a] && okm[a]) G[a][b] = 0.5 * (up[a][b] - um[a][b]);
+            else if (okp[a]) G[a][b] = up[a][b] - uw[b];
+            else if (okm[a]) G[a][b] = uw[b] - um[a][b];
+            else G[a][b] = 0.0;
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) S[3 * a + b] = 0.5 * (G[a][b] + G[b][a]);
+}
+
 inline void cross(const double a[3], const double b[3], double out[3]) {
     out[0] = a[1] * b[2] - a[2] * b[1];
     out[1] = a[2] * b[0] - a[0] * b[2];

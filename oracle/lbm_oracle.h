@@ -35,6 +35,7 @@ typedef struct {
     int force_average;    /* 1 = average hydrodynamic force/torque over two steps (Algorithm 1) */
     int plain_mem;        /* 1 = particle update of Sec. 2.2 without the virtual-mass terms */
     double bulk;          /* MRT bulk factor Lambda_b (Sec. 2.1); 0 or 1 = TRT */
+    int refill;           /* uncovered cells: 0 = equilibrium, 1 = Grad's approximation (Sec. 2.3) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -116,7 +117,11 @@ typedef struct {
     int plain_mem;
     int rescale;          /* 1: rescale non-equilibrium parts at level interfaces */
     double bulk;          /* MRT bulk factor Lambda_b (Sec. 2.1); 0 or 1 = TRT */
+    int refill;           /* uncovered cells: 0 = equilibrium, 1 = Grad's approximation (Sec. 2.3) */
 } orc_amr_params;
+/* Grad's post-collision non-equilibrium part for relaxation time tau and
+ * strain rate S (row major) into out[19] (test helper). */
+void orc_grad_noneq(double tau, const double S[9], double out[19]);
 typedef struct orc_amr orc_amr;
 orc_amr* orc_amr_create(const orc_amr_params* p);
 void orc_amr_destroy(orc_amr* a);

@@ -823,7 +823,28 @@ void remap(orc_amr* a) {
                 min_image(a, D, xc, d);
                 cross(P.w, d, wr);
                 const double u[3] = {P.u[0] + wr[0], P.u[1] + wr[1], P.u[2] + wr[2]};
-                for (int q = 0; q < 19; ++q) D.rg[pidx((int)b, q, c)] = geq(q, rho - 1.0, u);
+                double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                if (a->p.refill == 1) {   // face neighbours fluid before and after the move
+                    double up[3][3], um[3][3];
+                    bool okp[3], okm[3];
+                    for (int ax = 0; ax < 3; ++ax)
+                        for (int sgn = 0; sgn < 2; ++sgn) {
+                            int v[3] = {g[0], g[1], g[2]};
+                            v[ax] += sgn == 0 ? 1 : -1;
+                            int nb_, nc_;
+                            bool ok = wrap(a, D, v) && locate(D, v, &nb_, &nc_) == LOC_REAL;
+                            if (ok) ok = D.flag[(size_t)nb_ * B3 + nc_] == 0 && nf[(size_t)nb_ * B3 + nc_] == 0;
+                            double* uu = sgn == 0 ? up[ax] : um[ax];
+                            uu[0] = uu[1] = uu[2] = 0.0;
+                            if (ok)
+                                for (int p = 0; p < 19; ++p)
+                                    for (int k = 0; k < 3; ++k) uu[k] += D.rg[pidx(nb_, p, nc_)] * C[p][k];
+                            (sgn == 0 ? okp : okm)[ax] = ok;
+                        }
+                    refill_strain(up, okp, um, okm, u, S);
+                }
+                for (int q = 0; q < 19; ++q)
+                    D.rg[pidx((int)b, q, c)] = geq(q, rho - 1.0, u) + (a->p.refill == 1 ? grad_noneq(q, D.sp, S) : 0.0);
             } else if (was && !is) {
                 for (int q = 0; q < 19; ++q) D.rg[pidx((int)b, q, c)] = 0.0;
             }

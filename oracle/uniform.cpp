@@ -344,7 +344,26 @@ void remap(orc_sim* s) {
                     double wr[3];
                     cross(P.w, d, wr);
                     double u[3] = {P.u[0] + wr[0], P.u[1] + wr[1], P.u[2] + wr[2]};
-                    for (int q = 0; q < 19; ++q) s->g[(size_t)q * n + x] = geq(q, rho - 1.0, u);
+                    double S[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                    if (s->p.refill == 1) {   // face neighbours fluid before and after the move
+                        double up[3][3], um[3][3];
+                        bool okp[3], okm[3];
+                        for (int a = 0; a < 3; ++a)
+                            for (int sgn = 0; sgn < 2; ++sgn) {
+                                const int q = 1 + 2 * a + sgn;   // +e_a, then -e_a
+                                long y;
+                                bool ok = neighbour(s, i, j, k, q, +1, &y) && s->flag[y] == FLUID && nf[y] == FLUID;
+                                double* uu = sgn == 0 ? up[a] : um[a];
+                                uu[0] = uu[1] = uu[2] = 0.0;
+                                if (ok)
+                                    for (int p = 0; p < 19; ++p)
+                                        for (int b = 0; b < 3; ++b) uu[b] += s->g[(size_t)p * n + y] * C[p][b];
+                                (sgn == 0 ? okp : okm)[a] = ok;
+                            }
+                        refill_strain(up, okp, um, okm, u, S);
+                    }
+                    for (int q = 0; q < 19; ++q)
+                        s->g[(size_t)q * n + x] = geq(q, rho - 1.0, u) + (s->p.refill == 1 ? grad_noneq(q, s->sp, S) : 0.0);
                 } else if (was_fluid && !is_fluid) {
                     for (int q = 0; q < 19; ++q) s->g[(size_t)q * n + x] = 0.0;
                 }
@@ -380,6 +399,10 @@ orc_sim* orc_create(const orc_params* p) {
     s->bulk = p->bulk > 0.0 ? p->bulk : 1.0;
     s->sb = 1.0 / (0.5 + s->bulk * (p->tau - 0.5));   // Lambda_b = (1/s_b - 1/2) / (1/s_nu - 1/2)
     return s;
+}
+
+void orc_grad_noneq(double tau, const double S[9], double out[19]) {
+    for (int q = 0; q < 19; ++q) out[q] = grad_noneq(q, 1.0 / tau, S);
 }
 
 void orc_destroy(orc_sim* s) { delete s; }
