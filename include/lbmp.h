@@ -52,6 +52,7 @@ typedef enum {
 enum { LBMP_PERIODIC = 0, LBMP_NOSLIP = 1 };
 enum { LBMP_FP64 = 0, LBMP_FP32 = 1, LBMP_FP16 = 2 };
 enum { LBMP_CLI = 0, LBMP_SBB = 1 };
+enum { LBMP_REFILL_EQUILIBRIUM = 0, LBMP_REFILL_GRAD = 1 };
 
 /* Optional device allocator (e.g. a framework's caching allocator). Both
  * NULL: cudaMalloc / cudaFree.  alloc returns NULL on failure. */
@@ -78,6 +79,12 @@ typedef struct {
     double bulk_factor;      /* MRT bulk factor Lambda_b (Sec. 2.1): the bulk mode and the isotropic fourth-order
                                 mode relax at s_b with (1/s_b - 1/2) = Lambda_b (1/s_nu - 1/2); 1 (default) is TRT,
                                 the paper's runs use 100.  Must be > 0.  Not with rescale_noneq or the drag adjoint. */
+    int refill;              /* cells the sphere uncovers (Sec. 2.3): LBMP_REFILL_EQUILIBRIUM (default) sets the
+                                equilibrium at the mean density of the neighbours that stay fluid and the rigid-body
+                                velocity; LBMP_REFILL_GRAD adds Grad's non-equilibrium part, -3 w_q (1 - s+)/s+ Q_q:S
+                                with Q_q = c_q c_q - I/3 and the strain rate S from the velocities of the six face
+                                neighbours (central differences, one-sided against the wall velocity) - the paper's
+                                choice (Dorschner et al.'s approach, read as Grad's approximation) */
 } lbmp_config;
 
 /* Fills *cfg with defaults: 32^3 periodic, 1 level, FP32, tau 0.6,

@@ -29,6 +29,7 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2}
 BC = {"periodic": 0, "noslip": 1}
+REFILL = {"equilibrium": 0, "grad": 1}
 BOUNDARY = {"cli": 0, "sbb": 1}
 STATUS = {0: "LBMP_OK", 1: "LBMP_ERR_INVALID_ARG", 2: "LBMP_ERR_OOM", 3: "LBMP_ERR_CUDA", 4: "LBMP_ERR_UNSTABLE",
           5: "LBMP_ERR_PARTICLE_NOT_FINEST", 6: "LBMP_ERR_TIMEOUT", 7: "LBMP_ERR_UNSUPPORTED"}
@@ -372,7 +373,8 @@ class Simulation:
 
     def __init__(self, shape, precision="fp32", tau=0.6, magic=3.0 / 16.0, bc=("periodic",) * 3, boundary="cli",
                  force_average=True, history_capacity=4096, fp16_scale_log2=11, stream=None,
-                 torch_allocator=True, levels=1, rescale=False, regrid_interval=0, bulk=1.0):
+                 torch_allocator=True, levels=1, rescale=False, regrid_interval=0, bulk=1.0,
+                 refill="equilibrium"):
         import torch
         if not torch.cuda.is_available():
             raise LbmpError(3, "no CUDA device: this library has no CPU path")
@@ -386,6 +388,7 @@ class Simulation:
         cfg.tau = float(tau)
         cfg.magic = float(magic)
         cfg.bulk_factor = float(bulk)
+        cfg.refill = REFILL[refill]
         cfg.boundary = BOUNDARY[boundary]
         cfg.force_average = int(bool(force_average))
         cfg.history_capacity = int(history_capacity)
@@ -521,7 +524,8 @@ class BatchSimulation:
     """Many independent uniform periodic simulations advanced together."""
 
     def __init__(self, sims, precision="fp32", magic=3.0 / 16.0, boundary="cli", force_average=True,
-                 history_capacity=4096, stream=None, torch_allocator=True, bulk=1.0):
+                 history_capacity=4096, stream=None, torch_allocator=True, bulk=1.0,
+                 refill="equilibrium"):
         import torch
         if not torch.cuda.is_available():
             raise LbmpError(3, "no CUDA device: this library has no CPU path")
@@ -529,6 +533,7 @@ class BatchSimulation:
         cfg.precision = PRECISIONS[precision]
         cfg.magic = float(magic)
         cfg.bulk_factor = float(bulk)
+        cfg.refill = REFILL[refill]
         cfg.boundary = BOUNDARY[boundary]
         cfg.force_average = int(bool(force_average))
         cfg.history_capacity = int(history_capacity)

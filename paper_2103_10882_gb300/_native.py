@@ -29,6 +29,7 @@ class LbmpConfig(ctypes.Structure):
         ("free", FREE_FN),
         ("alloc_ctx", ctypes.c_void_p),
         ("bulk_factor", ctypes.c_double),
+        ("refill", ctypes.c_int),
     ]
 
 

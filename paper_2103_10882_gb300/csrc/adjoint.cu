@@ -501,7 +501,7 @@ void forward_step(lbmp_handle* h, const S* src, S* dst, double* force_out) {
     int nb = 0;
     launch_boundary<S>(src, dst, h->flags[h->fcur], h->list, h->count, h->list_cap, h->G, p, h->d_ps,
                        h->cfg.boundary == LBMP_CLI ? 1 : 0, h->partials, &nb, h->status, h->stream);
-    launch_refill<S>(dst, h->flags[h->fcur], h->flags[h->fcur], h->G, h->box, h->d_ps, A(1), A(1), h->stream);
+    launch_refill<S>(dst, h->flags[h->fcur], h->flags[h->fcur], h->G, h->box, h->d_ps, A(1), A(1), A(0), h->stream);
     if (force_out) k_adj_force<<<1, 32, 0, h->stream>>>(h->partials, nb, force_out);
 }
 

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(LINK_THREADS)
     k_amr_remap(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
                 BoxDesc B, const ParticleState* __restrict__ ps, typename Store<S>::A scale,
                 typename Store<S>::A inv_scale, uint8_t* __restrict__ mask, int* __restrict__ block_count,
-                int* __restrict__ status) {
+                int* __restrict__ status, typename Store<S>::A gcoef) {
     using A = typename Store<S>::A;
     __shared__ BoxFrame F;
     if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
@@ -514,8 +514,32 @@ __global__ void __launch_bounds__(LINK_THREADS)
                                         A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
                                         A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
                         const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                        for (int q = 0; q < 19; ++q)
-                            Store<S>::store(pops + paddr(b, q, c), geq_dev<A>(q, rho - A(1), u, uu), scale);
+                        A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+                        if (gcoef != A(0)) {   // Grad refill: face neighbours fluid before and after the move
+                            auto nb = [&](int a, int sgn, A uo[3]) {
+                                int v[3] = {g[0], g[1], g[2]};
+                                v[a] += sgn;
+                                if (!wrap3(v, D)) return false;
+                                if (ball_flag(v, D.n, D.periodic, F, P)) return false;
+                                int vc;
+                                const int vb = locate(D, v, &vc);
+                                if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] == FLAG_SOLID) return false;
+                                uo[0] = uo[1] = uo[2] = A(0);
+                                for (int q = 1; q < 19; ++q) {
+                                    const A gq = Store<S>::load(pops + paddr(vb, q, vc), inv_scale);
+                                    uo[0] += A(cx(q)) * gq;
+                                    uo[1] += A(cy(q)) * gq;
+                                    uo[2] += A(cz(q)) * gq;
+                                }
+                                return true;
+                            };
+                            refill_strain<A>(nb, u, Sr);
+                        }
+                        for (int q = 0; q < 19; ++q) {
+                            A e = geq_dev<A>(q, rho - A(1), u, uu);
+                            if (gcoef != A(0)) e += grad_term<A>(q, Sr, gcoef);
+                            Store<S>::store(pops + paddr(b, q, c), e, scale);
+                        }
                     }
                 }
             }
@@ -1337,7 +1361,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             using A = typename Store<S>::A;
             k_amr_remap<S><<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), (S*)Ff.d_pops[Ff.cur], Ff.d_flags[1],
                                                                Ff.d_flags[0], h->box, h->d_ps, (A)1, (A)1,
-                                                               h->link_mask, h->link_blocks, h->status);
+                                                               h->link_mask, h->link_blocks, h->status, (A)0);
         });
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
@@ -1487,7 +1511,8 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         uint8_t* fnext = V.d_flags[1 - V.fcur];
         const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
         k_amr_remap<S><<<nl, LINK_THREADS, 0, h->stream>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
-                                                           P.inv_scale, h->link_mask, h->link_blocks, h->status);
+                                                           P.inv_scale, h->link_mask, h->link_blocks, h->status,
+                                                           (A)grad_refill_coef(h->cfg.refill, V.taup));
         V.fcur = 1 - V.fcur;
         h->launches += 1;
     }

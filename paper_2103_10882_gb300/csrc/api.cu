@@ -106,7 +106,7 @@ void enqueue_step(lbmp_handle* h) {
             uint8_t* fnext = h->flags[1 - h->fcur];
             launch_flags_box(fnext, h->G, h->box, h->d_ps, h->stream);
             launch_refill<S>(dst, h->flags[h->fcur], fnext, h->G, h->box, h->d_ps, (A)fp16_scale(h, false),
-                             (A)fp16_scale(h, true), h->stream);
+                             (A)fp16_scale(h, true), (A)grad_refill_coef(h->cfg.refill, h->tau), h->stream);
             launch_build_links(fnext, h->G, h->box, h->d_ps, h->link_mask, h->link_blocks, h->list, h->count,
                                h->list_cap, h->status, h->stream);
             h->fcur = 1 - h->fcur;
@@ -212,6 +212,7 @@ lbmp_status lbmp_config_default(lbmp_config* c) {
     c->history_capacity = 4096;
     c->fp16_scale_log2 = 11;
     c->bulk_factor = 1.0;
+    c->refill = LBMP_REFILL_EQUILIBRIUM;
     return LBMP_OK;
 }
 
@@ -237,6 +238,8 @@ lbmp_status lbmp_create(const lbmp_config* cfg, lbmp_handle** out) {
     if (!(cfg->magic > 0.0)) return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: magic parameter must be > 0");
     if (!(cfg->bulk_factor > 0.0) || !std::isfinite(cfg->bulk_factor))
         return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: bulk factor must be > 0 (1 = TRT)");
+    if (cfg->refill != LBMP_REFILL_EQUILIBRIUM && cfg->refill != LBMP_REFILL_GRAD)
+        return fail(nullptr, LBMP_ERR_INVALID_ARG, "lbmp_create: unknown refill");
     if (cfg->bulk_factor != 1.0 && cfg->levels > 1 && cfg->rescale_noneq)
         return fail(nullptr, LBMP_ERR_UNSUPPORTED,
                     "lbmp_create: non-equilibrium rescaling is built for TRT only (bulk factor 1)");

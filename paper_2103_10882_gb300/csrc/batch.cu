@@ -183,7 +183,7 @@ template <typename S>
 __global__ void __launch_bounds__(BW)
     k_batch_remap(S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
                   const SimDev* __restrict__ sims, const ParticleState* __restrict__ ps,
-                  typename Store<S>::A scale, typename Store<S>::A inv, uint8_t* __restrict__ mask) {
+                  typename Store<S>::A scale, typename Store<S>::A inv, uint8_t* __restrict__ mask, int grad) {
     using A = typename Store<S>::A;
     __shared__ BoxFrame F;
     const int sim = blockIdx.y;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(BW)
             cnt += 1;
         }
         fn[c] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
-        if (uncovered) {   // equilibrium refill
+        if (uncovered) {   // equilibrium refill, plus Grad's term when asked for
             const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
             const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, 1), wrap_diff((j + 0.5) - P.x[1], G.ny, 1),
                                  wrap_diff((k + 0.5) - P.x[2], G.nz, 1)};
@@ -234,10 +234,32 @@ __global__ void __launch_bounds__(BW)
                             A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
                             A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
             const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            const A gcoef = grad ? A(-3.0 * (1.0 - D.sp) / D.sp) : A(0);
+            A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+            if (grad) {   // face neighbours fluid before and after the move
+                auto nb = [&](int a, int sgn, A uo[3]) {
+                    int v[3] = {i, j, k};
+                    v[a] += sgn;
+                    v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
+                    if (ball_flag(v, n3, G.periodic, F, P)) return false;
+                    const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+                    if (fc[y] == FLAG_SOLID) return false;
+                    uo[0] = uo[1] = uo[2] = A(0);
+                    for (int q2 = 1; q2 < 19; ++q2) {
+                        const A gq = Store<S>::load(p0 + (size_t)q2 * n + y, inv);
+                        uo[0] += A(cx(q2)) * gq;
+                        uo[1] += A(cy(q2)) * gq;
+                        uo[2] += A(cz(q2)) * gq;
+                    }
+                    return true;
+                };
+                refill_strain<A>(nb, u, Sr);
+            }
             for (int q = 0; q < 19; ++q) {
                 const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
-                Store<S>::store(p0 + (size_t)q * n + c,
-                                wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu), scale);
+                A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+                if (grad) e += grad_term<A>(q, Sr, gcoef);
+                Store<S>::store(p0 + (size_t)q * n + c, e, scale);
             }
         }
     }
@@ -376,7 +398,8 @@ void enqueue_batch_step(lbmp_handle* h) {
     cudaStreamWaitEvent(h->stream, B->ev_join, 0);
     uint8_t* fnext = B->flags[1 - B->fcur];
     const dim3 gr(B->max_box_blocks, B->nsims);
-    k_batch_remap<S><<<gr, BW, 0, h->stream>>>(dst, B->flags[B->fcur], fnext, B->d_sims, B->d_ps, scale, inv, B->mask);
+    k_batch_remap<S><<<gr, BW, 0, h->stream>>>(dst, B->flags[B->fcur], fnext, B->d_sims, B->d_ps, scale, inv, B->mask,
+                                               h->cfg.refill == LBMP_REFILL_GRAD ? 1 : 0);
     B->cur = 1 - B->cur;
     B->fcur = 1 - B->fcur;
     h->launches += 3;
@@ -512,7 +535,7 @@ lbmp_status batch_create(lbmp_handle* h, const lbmp_batch_sim* sims, int n) {
         // boundary flags and mask of the start position (both flag buffers hold its solid cells)
         const dim3 gr(B->max_box_blocks, B->nsims);
         k_batch_remap<S><<<gr, BW, 0, h->stream>>>((S*)B->pops[0], B->flags[1], B->flags[0], B->d_sims, B->d_ps,
-                                                   scale, inv, B->mask);
+                                                   scale, inv, B->mask, 0);   // nothing is uncovered here
     });
     h->h2d += (long long)(sizeof(SimDev) + sizeof(ParticleState) + sizeof(long long)) * n +
               (long long)(sizeof(int) * bnd_sim.size());

@@ -67,7 +67,7 @@ void launch_flags_box(uint8_t* flags_next, const GridDesc& g, const BoxDesc& b, 
 template <typename S>
 void launch_refill(S* pops, const uint8_t* flags_cur, const uint8_t* flags_next, const GridDesc& g,
                    const BoxDesc& b, const ParticleState* ps, typename Store<S>::A scale,
-                   typename Store<S>::A inv_scale, cudaStream_t stream);
+                   typename Store<S>::A inv_scale, typename Store<S>::A gcoef, cudaStream_t stream);
 // Boundary-cell list of the box; mask (b.cells bytes) and block_count
 // (ceil(b.cells / 256) ints) are scratch.
 void launch_build_links(const uint8_t* flags, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
@@ -150,6 +150,14 @@ namespace lbmp {
 inline void relaxation_rates(double tau, double magic, double* sp, double* sm) {
     *sp = 1.0 / tau;
     *sm = 1.0 / (0.5 + magic / (tau - 0.5));
+}
+
+// Coefficient of Grad's refill term for relaxation time tau (-3 (1 - s+)/s+,
+// see refill_strain and grad_term), or 0 for the equilibrium refill.
+inline double grad_refill_coef(int refill, double tau) {
+    if (refill != LBMP_REFILL_GRAD) return 0.0;
+    const double sp = 1.0 / tau;
+    return -3.0 * (1.0 - sp) / sp;
 }
 
 // MRT bulk rate from the bulk factor: Lambda_b = (1/s_b - 1/2)/(1/s_nu - 1/2)

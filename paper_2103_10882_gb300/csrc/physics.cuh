@@ -615,6 +615,44 @@ __device__ __forceinline__ void particle_block_update(ParticleState* __restrict_
     }
 }
 
+
+// Grad refill of an uncovered cell (Sec. 2.3: the paper uses Dorschner et
+// al.'s approach, read as Grad's approximation from the local strain rate).
+// Strain rate S (xx, yy, zz, xy, yz, xz) from the six face neighbours'
+// velocities: central differences where both are fluid, one-sided against
+// the wall velocity uw where one is, zero where neither is.  nb(a, sgn, u)
+// returns whether the face neighbour x + sgn e_a is fluid (before and after
+// the move) and, if so, its velocity in u.
+template <typename A, typename NB>
+__device__ __forceinline__ void refill_strain(NB&& nb, const A uw[3], A S[6]) {
+    A G[3][3];   // G[a][b] = d u_b / d x_a
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        A up[3], um[3];
+        const bool okp = nb(a, 1, up), okm = nb(a, -1, um);
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            G[a][b] = (okp && okm) ? A(0.5) * (up[b] - um[b]) : (okp ? up[b] - uw[b] : (okm ? uw[b] - um[b] : A(0)));
+    }
+    S[0] = G[0][0];
+    S[1] = G[1][1];
+    S[2] = G[2][2];
+    S[3] = A(0.5) * (G[0][1] + G[1][0]);
+    S[4] = A(0.5) * (G[1][2] + G[2][1]);
+    S[5] = A(0.5) * (G[0][2] + G[2][0]);
+}
+
+// Grad's non-equilibrium part of population q of a refilled post-collision
+// state: gcoef w_q Q_q:S with Q_q = c_q c_q - I/3 and gcoef = -3 (1 - s+)/s+
+// (the first-order Chapman-Enskog stress after one collision).
+template <typename A>
+__device__ __forceinline__ A grad_term(int q, const A S[6], A gcoef) {
+    const A x = A(cx(q)), y = A(cy(q)), z = A(cz(q));
+    const A qs = x * x * S[0] + y * y * S[1] + z * z * S[2] + A(2) * (x * y * S[3] + y * z * S[4] + x * z * S[5]) -
+                 (S[0] + S[1] + S[2]) / A(3);
+    return gcoef * wgt<A>(q) * qs;
+}
+
 // Last-block-done hand-off: each of nblocks blocks calls it after writing
 // its partials; the block that finishes last (a device counter, reset by
 // that block) gets true.  No block waits for another.

@@ -212,7 +212,7 @@ __global__ void k_flags_box(uint8_t* __restrict__ flags_next, GridDesc G, BoxDes
 template <typename S>
 __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur, const uint8_t* __restrict__ fnext,
                          GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
-                         typename Store<S>::A scale, typename Store<S>::A inv_scale) {
+                         typename Store<S>::A scale, typename Store<S>::A inv_scale, typename Store<S>::A gcoef) {
     using A = typename Store<S>::A;
     __shared__ BoxFrame F;
     const int n3[3] = {G.nx, G.ny, G.nz};
@@ -259,10 +259,33 @@ __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
     const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
                     A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
     const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+    if (gcoef != A(0)) {   // Grad refill: face neighbours fluid before and after the move
+        auto nb = [&](int a, int sgn, A uo[3]) {
+            int v[3] = {i, j, k};
+            v[a] += sgn;
+            if (v[a] < 0 || v[a] >= n3[a]) {
+                if (!G.periodic[a]) return false;
+                v[a] = (v[a] + n3[a]) % n3[a];
+            }
+            const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+            if (fcur[y] != 0 || fnext[y] != 0) return false;
+            uo[0] = uo[1] = uo[2] = A(0);
+            for (int q = 1; q < 19; ++q) {
+                const A gq = Store<S>::load(pops + (size_t)q * n + y, inv_scale);
+                uo[0] += A(cx(q)) * gq;
+                uo[1] += A(cy(q)) * gq;
+                uo[2] += A(cz(q)) * gq;
+            }
+            return true;
+        };
+        refill_strain<A>(nb, u, Sr);
+    }
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
-        const A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+        A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+        if (gcoef != A(0)) e += grad_term<A>(q, Sr, gcoef);
         Store<S>::store(pops + (size_t)q * n + c, e, scale);
     }
 }
@@ -501,9 +524,9 @@ void launch_flags_box(uint8_t* flags_next, const GridDesc& g, const BoxDesc& b, 
 template <typename S>
 void launch_refill(S* pops, const uint8_t* flags_cur, const uint8_t* flags_next, const GridDesc& g,
                    const BoxDesc& b, const ParticleState* ps, typename Store<S>::A scale,
-                   typename Store<S>::A inv_scale, cudaStream_t stream) {
+                   typename Store<S>::A inv_scale, typename Store<S>::A gcoef, cudaStream_t stream) {
     k_refill<S><<<blocks_for(b.cells, 128), 128, 0, stream>>>(pops, flags_cur, flags_next, g, b, ps, scale,
-                                                               inv_scale);
+                                                               inv_scale, gcoef);
 }
 
 void launch_build_links(const uint8_t* flags, const GridDesc& g, const BoxDesc& b, const ParticleState* ps,
@@ -557,7 +580,7 @@ void launch_zero_solid(S* pops, const uint8_t* flags, const GridDesc& g, cudaStr
                                      const CollideParams<Store<S>::A>&, const ParticleState*, int, double*, int*,  \
                                      int*, cudaStream_t);                                                          \
     template void launch_refill<S>(S*, const uint8_t*, const uint8_t*, const GridDesc&, const BoxDesc&,            \
-                                   const ParticleState*, Store<S>::A, Store<S>::A, cudaStream_t);                  \
+                                   const ParticleState*, Store<S>::A, Store<S>::A, Store<S>::A, cudaStream_t);     \
     template void launch_init_equilibrium<S>(S*, const uint8_t*, const GridDesc&, double, const double*,           \
                                              const double*, Store<S>::A, cudaStream_t);                            \
     template void launch_to_f64<S>(const S*, double*, long long, Store<S>::A, cudaStream_t);                       \
