@@ -42,6 +42,10 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math"}
 REFINED = dict(shape=(64, 64, 256), levels=3, diameter=20.0, density_ratio=0.5, ga=200.0, u_g=0.01, cv=0.5,
                bc=("noslip", "noslip", "periodic"), regrid=50, sensor=(1e-3, 0.2))
 UNIFORM = dict(shape=(512, 512, 512), diameter=40.0, density_ratio=0.5, ga=200.0, u_g=0.01, cv=0.5)
+# the large refined case: FP16 storage against FP64 on terminal velocity and lateral drift (seeded start offset
+# and a lateral velocity perturbation of 1e-3 u_g in a seeded direction)
+LARGE = dict(shape=(128, 128, 512), levels=4, diameter=40.0, density_ratio=0.1, ga=300.0, u_g=0.01, cv=0.5,
+             bc=("noslip", "noslip", "periodic"), regrid=50, sensor=(1e-3, 0.2), perturbation=1e-3, seed=1)
 
 
 def parse():
@@ -66,6 +70,8 @@ def parse():
                     help="instead of timing: run the refined workload this many level-0 steps in FP64, FP32 and FP16 "
                          "and report the reduced precisions' errors on the particle's path")
     ap.add_argument("--adjoint-reps", type=int, default=3)
+    ap.add_argument("--validate-workload", default="refined", choices=["refined", "large"],
+                    help="workload of --validate: the headline refined case or the large FP16 case")
     ap.add_argument("--stability", action="store_true",
                     help="instead of timing: the stability-limit study (lowest stable density ratio per diameter at "
                          "Ga = 100, plain MEM and virtual mass) and one JSON line")
@@ -172,25 +178,33 @@ def ga_tau_g(ga, u_g, d, pi):
     return 3 * nu + 0.5, u_g ** 2 / (abs(pi - 1) * d)
 
 
-def refined_start(shape, levels, d):
+def refined_start(shape, levels, d, seed=0):
     f = 1 << (levels - 1)
     from paper_2103_10882_gb300 import workloads
-    off = workloads.sub_cell_offset(0)
+    off = workloads.sub_cell_offset(seed)
     # lateral centre, 0.6 d above the bottom (finest units)
     return (shape[0] * f / 2 + off[0], shape[1] * f / 2 + off[1], 0.6 * d + off[2])
 
 
-def refined_sim(L, prec, history_capacity=1 << 16):
-    """The headline workload through the public API: hierarchy, sphere,
-    gravity from Ga, refinement sensor, fluid at rest."""
-    w = REFINED
+def refined_sim(L, prec, history_capacity=1 << 16, w=None):
+    """A refined rising-sphere workload (the headline one unless w is given)
+    through the public API: hierarchy, sphere, gravity from Ga, refinement
+    sensor, fluid at rest, and the sphere's seeded lateral perturbation."""
+    import math
+    from paper_2103_10882_gb300 import workloads
+    w = REFINED if w is None else w
+    seed = w.get("seed", 0)
     tau, _ = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
     sim = L.Simulation(w["shape"], precision=prec, tau=tau, bc=w["bc"], levels=w["levels"],
                        regrid_interval=w["regrid"], history_capacity=history_capacity)
-    sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+    sim.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"], seed), w["diameter"], w["density_ratio"],
                    cv=w["cv"])
     sim.set_ga(w["ga"], w["u_g"], (0.0, 0.0, -1.0))
     sim.set_refinement_sensor(*w["sensor"])
+    if w.get("perturbation"):
+        theta = 2.0 * math.pi * float(workloads.uniform01(seed + 1000, 1)[0])
+        v = w["perturbation"] * w["u_g"]
+        sim.set_particle_velocity((v * math.cos(theta), v * math.sin(theta), 0.0))
     sim.init_fluid()
     return sim
 
@@ -296,11 +310,10 @@ def validate(args):
     import numpy as np
     import torch
     import paper_2103_10882_gb300 as L
-    w = REFINED
-    tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    w = LARGE if args.validate_workload == "large" else REFINED
     runs = {}
     for prec in ("fp64", "fp32", "fp16"):
-        sim = refined_sim(L, prec, history_capacity=1 << 17)
+        sim = refined_sim(L, prec, history_capacity=1 << 19, w=w)
         c0 = sim.counters()
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -315,8 +328,9 @@ def validate(args):
         sim.close()
     ref = runs["fp64"]["hist"]
     d = w["diameter"]
-    out = {"validate": "refined rising sphere (headline workload), %d level-0 steps = %d finest steps"
-                       % (args.validate, len(ref)),
+    name = ("large refined case: level-0 128x128x512, 4 levels, d=40, pi_p=0.1, Ga=300, seeded offset and 1e-3 u_g "
+            "lateral perturbation" if w is LARGE else "refined rising sphere (headline workload)")
+    out = {"validate": "%s, %d level-0 steps = %d finest steps" % (name, args.validate, len(ref)),
            "fp64": {"u_z_end": ref[-1, 11], "z_end": ref[-1, 8], "mlups": runs["fp64"]["mlups"]}}
     for prec in ("fp32", "fp16"):
         h = runs[prec]["hist"]
