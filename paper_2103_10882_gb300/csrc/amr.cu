@@ -42,6 +42,7 @@ constexpr int BS = 16;
 constexpr int B3 = BS * BS * BS;
 constexpr int MAXL = 6;
 constexpr int UPD_THREADS = 256;
+constexpr int UPD_MIN_CTAS = 6;      // resident level-update CTAs per SM asked of the compiler (FP32/FP16 arithmetic): 40 registers
 constexpr int STATUS_AMR_MISSING = 8;    // a pull found no source cell
 // Finest-level cell flags: fluid, solid (centre inside the sphere), and
 // fluid with a solid D3Q19 neighbour (updated by k_amr_boundary).
@@ -235,7 +236,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 // update the real blocks, one CTA per z-slice of a block (256 cells, full
 // warps).  All read src; the real-block CTAs write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED, bool RESCALE>
-__global__ void __launch_bounds__(UPD_THREADS)
+__global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS)
     k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks, int coalesce) {
     using A = typename Store<S>::A;
     if (HAS_COARSE && (int)blockIdx.x < gblocks) {   // uniform across the block
