@@ -37,6 +37,7 @@ namespace lbmp {
 namespace {
 
 constexpr int AT = 256;   // threads per block of the cell kernels
+constexpr int ADJ_MIN_CTAS = 4;   // resident reverse-step CTAs per SM asked of the compiler (FP32): 64 registers
 
 enum : uint8_t { KIND_PLAIN = 0, KIND_SOLID = 1, KIND_NEAR = 2 };
 
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(AT)
 // lambda_q = nu_q(x + c_q).  Solid cells get nu = 0; near cells are left to
 // k_adj_near.
 template <typename S>
-__global__ void __launch_bounds__(AT)
+__global__ void __launch_bounds__(AT, sizeof(S) == 8 ? 1 : ADJ_MIN_CTAS)
     k_adj_plain(const S* __restrict__ gprev, const typename Store<S>::A* __restrict__ nu_next,
                 typename Store<S>::A* __restrict__ nu_out, const uint8_t* __restrict__ kind, GridDesc G,
                 AdjParams<typename Store<S>::A> P, double* __restrict__ acc) {
