@@ -56,7 +56,7 @@ __host__ __device__ __forceinline__ CollideParams<typename Store<S>::A> sim_para
 // ------------------------------------------------------------ stream-collide
 // tile = (simulation, x0, y0, z0); block (16, TY); each thread ZC cells along z.
 template <typename S, int ZC>
-__global__ void __launch_bounds__(512) k_batch_bulk(const S* __restrict__ src, S* __restrict__ dst,
+__global__ void __launch_bounds__(512, sizeof(S) == 8 ? 1 : 3) k_batch_bulk(const S* __restrict__ src, S* __restrict__ dst,
                                                     const uint8_t* __restrict__ flags,
                                                     const int4* __restrict__ tiles, const SimDev* __restrict__ sims,
                                                     typename Store<S>::A scale, typename Store<S>::A inv,
