@@ -291,6 +291,22 @@ lbmp_status lbmp_boundary_cells_noalloc(const uint8_t* flags, int nx, int ny, in
                                         const double center[3], double diameter, int* list, int capacity,
                                         int* count, uintptr_t cuda_stream);
 
+/* Checkpoint and resume (the paper describes none; long refined runs need
+ * them).  lbmp_save writes the handle's state to the file `path`: the grid
+ * description, tau, the body force, the step count, the sphere's record and
+ * history, the populations (storage type, as held) and flags, and on refined
+ * grids the block coverage of every level, the level-0 step count, the
+ * refinement sensor and the refined box.  The byte order is the host's.
+ * lbmp_load restores such a file into a handle created with the same grid,
+ * levels, precision and boundary conditions (other config fields come from
+ * the handle); a handle without a sphere gets the saved one.  Stepping on
+ * after a load continues the saved run bit for bit.  Errors:
+ * LBMP_ERR_INVALID_ARG for a missing file, another format or a different
+ * grid (or a handle with a sphere of another diameter);
+ * LBMP_ERR_UNSUPPORTED for batched handles.  Both synchronise the stream. */
+lbmp_status lbmp_save(lbmp_handle* h, const char* path);
+lbmp_status lbmp_load(lbmp_handle* h, const char* path);
+
 /* Message of the last failure on this handle (or of the last failed create
  * when h is NULL).  Never NULL. */
 const char* lbmp_last_error(const lbmp_handle* h);

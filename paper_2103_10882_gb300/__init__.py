@@ -9,6 +9,7 @@ PyTorch supplies device memory (its caching allocator) and the CUDA stream.
 There is no CPU fallback: without the library or a GPU every call raises.
 """
 import ctypes
+import os
 
 import numpy as np
 
@@ -21,7 +22,7 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_get_populations", "lbmp_gather_populations", "lbmp_step", "lbmp_step_async", "lbmp_check_status", "lbmp_synchronize",
            "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
            "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error",
-           "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_set_refinement_sensor", "lbmp_get_block_sensor",
+           "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_save", "lbmp_load", "lbmp_set_refinement_sensor", "lbmp_get_block_sensor",
            "lbmp_level_shape", "lbmp_get_block_map",
            "lbmp_get_level_cells", "lbmp_updates_per_step", "lbmp_batch_create", "lbmp_batch_autotune",
            "lbmp_batch_info", "lbmp_batch_get_populations", "BatchSimulation", "PRECISIONS", "lbmp_drag_forward",
@@ -251,6 +252,14 @@ def lbmp_level_shape(h, level):
     out = (ctypes.c_int * 3)()
     _check(h, _lib().lbmp_level_shape(h, int(level), out))
     return tuple(out)
+
+
+def lbmp_save(h, path):
+    _check(h, _lib().lbmp_save(h, os.fsencode(path)))
+
+
+def lbmp_load(h, path):
+    _check(h, _lib().lbmp_load(h, os.fsencode(path)))
 
 
 def lbmp_set_refinement_sensor(h, sigma_c, c):
@@ -486,6 +495,14 @@ class Simulation:
 
     def regrid(self):
         lbmp_regrid(self.h)
+
+    def save(self, path):
+        """Checkpoint of the whole state into the file `path`."""
+        lbmp_save(self.h, path)
+
+    def load(self, path):
+        """Restores a checkpoint written by save() on a handle of the same grid."""
+        lbmp_load(self.h, path)
 
     def set_refinement_sensor(self, sigma_c=1e-3, c=0.2):
         """Flow-based refinement sensor of Sec. 4.2.2 (sigma_c = 0 turns it off)."""

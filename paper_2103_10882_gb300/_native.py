@@ -88,6 +88,8 @@ SIGNATURES = {
                                             ctypes.c_int, ctypes.c_int]),
     "lbmp_refine_box": (ctypes.c_int, [ctypes.c_void_p, c_double_p, c_double_p]),
     "lbmp_regrid": (ctypes.c_int, [ctypes.c_void_p]),
+    "lbmp_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "lbmp_load": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "lbmp_set_refinement_sensor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double]),
     "lbmp_get_block_sensor": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, ctypes.c_size_t,
                                              ctypes.POINTER(ctypes.c_size_t)]),

@@ -28,6 +28,7 @@
 #include <type_traits>
 #include <array>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -1793,6 +1794,82 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
         }
     }
     return LBMP_OK;
+}
+
+// ------------------------------------------------------------ checkpoint
+namespace {
+bool ck_put(FILE* f, const void* p, size_t n) { return n == 0 || std::fwrite(p, 1, n, f) == n; }
+bool ck_get(FILE* f, void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f) == n; }
+}  // namespace
+
+// Refined part of a checkpoint: the block coverage of every level, every
+// level's real-block populations (current buffer, storage type), then the
+// level-0 step count, the sensor and the refined box.
+lbmp_status amr_save(lbmp_handle* h, FILE* f) {
+    AmrEngine* E = h->amr;
+    const int32_t L = E->L;
+    bool ok = ck_put(f, &L, sizeof(L));
+    for (int l = 0; l < L && ok; ++l) {
+        const int64_t n = (int64_t)E->cover[l].size();
+        ok = ck_put(f, &n, sizeof(n)) && ck_put(f, E->cover[l].data(), (size_t)n);
+    }
+    const size_t es = esize(h);
+    for (int l = 0; l < L && ok; ++l) {
+        const Level& V = E->lv[l];
+        const int32_t nr = V.nreal;
+        const size_t bytes = es * 19 * B3 * (size_t)V.nreal;
+        std::vector<unsigned char> buf(bytes);
+        ok = ck_put(f, &nr, sizeof(nr)) &&
+             (bytes == 0 || cudaMemcpy(buf.data(), V.d_pops[V.cur], bytes, cudaMemcpyDeviceToHost) == cudaSuccess) &&
+             ck_put(f, buf.data(), bytes);
+    }
+    const int64_t cs = E->coarse_steps;
+    const int32_t hb = E->have_box ? 1 : 0;
+    ok = ok && ck_put(f, &cs, sizeof(cs)) && ck_put(f, &E->sensor_sigma, sizeof(double)) &&
+         ck_put(f, &E->sensor_c, sizeof(double)) && ck_put(f, &hb, sizeof(hb)) && ck_put(f, E->box_lo, sizeof(E->box_lo)) &&
+         ck_put(f, E->box_hi, sizeof(E->box_hi));
+    return ok ? LBMP_OK : LBMP_ERR_CUDA;
+}
+
+// Rebuilds the saved hierarchy (the finest flags follow from the restored
+// sphere position) and restores every level's populations.
+lbmp_status amr_load(lbmp_handle* h, FILE* f) {
+    AmrEngine* E = h->amr;
+    int32_t L = 0;
+    if (!ck_get(f, &L, sizeof(L)) || L != E->L) return LBMP_ERR_INVALID_ARG;
+    std::vector<Mask> R(L);
+    for (int l = 0; l < L; ++l) {
+        int nb[3];
+        lattice_of(E, l, nb);
+        int64_t n = 0;
+        if (!ck_get(f, &n, sizeof(n)) || n != (int64_t)nb[0] * nb[1] * nb[2]) return LBMP_ERR_INVALID_ARG;
+        R[l].resize((size_t)n);
+        if (!ck_get(f, R[l].data(), (size_t)n)) return LBMP_ERR_INVALID_ARG;
+    }
+    const lbmp_status s = build_layout(h, R);
+    if (s != LBMP_OK) return s;
+    E->cover = R;
+    const size_t es = esize(h);
+    for (int l = 0; l < L; ++l) {
+        Level& V = E->lv[l];
+        int32_t nr = 0;
+        if (!ck_get(f, &nr, sizeof(nr)) || nr != V.nreal) return LBMP_ERR_INVALID_ARG;
+        const size_t bytes = es * 19 * B3 * (size_t)V.nreal;
+        std::vector<unsigned char> buf(bytes);
+        if (!ck_get(f, buf.data(), bytes)) return LBMP_ERR_INVALID_ARG;
+        if (bytes && cudaMemcpy(V.d_pops[V.cur], buf.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+            return LBMP_ERR_CUDA;
+        h->h2d += (long long)bytes;
+    }
+    int64_t cs = 0;
+    int32_t hb = 0;
+    if (!ck_get(f, &cs, sizeof(cs)) || !ck_get(f, &E->sensor_sigma, sizeof(double)) ||
+        !ck_get(f, &E->sensor_c, sizeof(double)) || !ck_get(f, &hb, sizeof(hb)) || !ck_get(f, E->box_lo, sizeof(E->box_lo)) ||
+        !ck_get(f, E->box_hi, sizeof(E->box_hi)))
+        return LBMP_ERR_INVALID_ARG;
+    E->coarse_steps = cs;
+    E->have_box = hb != 0;
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? LBMP_OK : LBMP_ERR_CUDA;
 }
 
 lbmp_status amr_level_shape(lbmp_handle* h, int level, int out[3]) {

@@ -4,6 +4,8 @@
 // Algorithm 1 on the finest level.  Used by the C ABI when levels > 1.
 #pragma once
 
+#include <cstdio>
+
 #include "internal.h"
 
 namespace lbmp {
@@ -22,6 +24,8 @@ lbmp_status amr_level_shape(lbmp_handle* h, int level, int out[3]);
 lbmp_status amr_block_map(lbmp_handle* h, int level, int32_t* out, size_t cap, size_t* n);
 lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n);
 lbmp_status amr_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n);
+lbmp_status amr_save(lbmp_handle* h, FILE* f);   // refined part of a checkpoint
+lbmp_status amr_load(lbmp_handle* h, FILE* f);   // after the particle record is on the device
 long long amr_cell_updates_per_coarse_step(const lbmp_handle* h);
 int amr_launches_per_coarse_step(const lbmp_handle* h);
 

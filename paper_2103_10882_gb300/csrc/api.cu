@@ -933,6 +933,136 @@ lbmp_status lbmp_batch_get_populations(lbmp_handle* h, int sim, double* out, siz
     return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_batch_get_populations: bad simulation index or capacity");
 }
 
+// ------------------------------------------------------------ checkpoint
+namespace {
+
+struct CkptHeader {
+    char tag[8];              // "LBMPCKPT"
+    int32_t version;          // 1
+    int32_t nx, ny, nz, levels, precision, bc[3];
+    int32_t has_particle, history_capacity, particle_bytes, kind;   // kind: 0 uniform, 1 refined
+    double tau, magic, bulk_factor;
+    double body_force[3];
+    int64_t steps;
+};
+
+bool put(FILE* f, const void* p, size_t n) { return n == 0 || fwrite(p, 1, n, f) == n; }
+bool get(FILE* f, void* p, size_t n) { return n == 0 || fread(p, 1, n, f) == n; }
+
+}  // namespace
+
+lbmp_status lbmp_save(lbmp_handle* h, const char* path) {
+    if (!h || !path) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_save: NULL argument");
+    if (h->batch) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_save: batched handles are not checkpointed");
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_fail(h, cudaGetLastError(), "lbmp_save");
+    if (h->has_particle) {
+        const lbmp_status s = download_particle(h);
+        if (s != LBMP_OK) return s;
+    }
+    CkptHeader H;
+    std::memset(&H, 0, sizeof(H));
+    std::memcpy(H.tag, "LBMPCKPT", 8);
+    H.version = 1;
+    H.nx = h->cfg.nx;
+    H.ny = h->cfg.ny;
+    H.nz = h->cfg.nz;
+    H.levels = h->cfg.levels;
+    H.precision = h->cfg.precision;
+    for (int a = 0; a < 3; ++a) H.bc[a] = h->cfg.bc[a];
+    H.has_particle = h->has_particle ? 1 : 0;
+    H.history_capacity = h->history ? h->cfg.history_capacity : 0;
+    H.particle_bytes = (int32_t)sizeof(ParticleState);
+    H.kind = h->amr ? 1 : 0;
+    H.tau = h->tau;
+    H.magic = h->magic;
+    H.bulk_factor = h->cfg.bulk_factor;
+    for (int a = 0; a < 3; ++a) H.body_force[a] = h->body_force[a];
+    H.steps = h->steps;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(h, LBMP_ERR_INVALID_ARG, std::string("lbmp_save: cannot open ") + path);
+    bool ok = put(f, &H, sizeof(H)) && put(f, &h->h_ps, sizeof(ParticleState));
+    if (ok && H.history_capacity > 0) {
+        std::vector<double> hist((size_t)H.history_capacity * 15);
+        ok = cudaMemcpy(hist.data(), h->history, hist.size() * sizeof(double), cudaMemcpyDeviceToHost) == cudaSuccess &&
+             put(f, hist.data(), hist.size() * sizeof(double));
+    }
+    if (ok && h->amr) {
+        ok = amr_save(h, f) == LBMP_OK;
+    } else if (ok) {
+        const size_t pb = (size_t)19 * (size_t)h->G.n * elem_size(h->cfg.precision);
+        std::vector<unsigned char> buf(pb);
+        ok = cudaMemcpy(buf.data(), h->pops[h->cur], pb, cudaMemcpyDeviceToHost) == cudaSuccess && put(f, buf.data(), pb);
+        buf.resize((size_t)h->G.n);
+        ok = ok && cudaMemcpy(buf.data(), h->flags[h->fcur], (size_t)h->G.n, cudaMemcpyDeviceToHost) == cudaSuccess &&
+             put(f, buf.data(), (size_t)h->G.n);
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(h, LBMP_ERR_CUDA, std::string("lbmp_save: writing ") + path + " failed");
+    return LBMP_OK;
+}
+
+lbmp_status lbmp_load(lbmp_handle* h, const char* path) {
+    if (!h || !path) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: NULL argument");
+    if (h->batch) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_load: batched handles are not checkpointed");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(h, LBMP_ERR_INVALID_ARG, std::string("lbmp_load: cannot open ") + path);
+    struct Closer {
+        FILE* f;
+        ~Closer() { std::fclose(f); }
+    } closer{f};
+    CkptHeader H;
+    ParticleState P;
+    if (!get(f, &H, sizeof(H)) || std::memcmp(H.tag, "LBMPCKPT", 8) != 0 || H.version != 1 ||
+        H.particle_bytes != (int32_t)sizeof(ParticleState) || !get(f, &P, sizeof(P)))
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: not a checkpoint of this library version");
+    bool same = H.nx == h->cfg.nx && H.ny == h->cfg.ny && H.nz == h->cfg.nz && H.levels == h->cfg.levels &&
+                H.precision == h->cfg.precision && H.kind == (h->amr ? 1 : 0);
+    for (int a = 0; a < 3; ++a) same = same && H.bc[a] == h->cfg.bc[a];
+    if (!same)
+        return fail(h, LBMP_ERR_INVALID_ARG,
+                    "lbmp_load: the checkpoint's grid, levels, precision or boundary conditions differ from the handle's");
+    if (h->has_particle && !H.has_particle)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: the handle has a sphere, the checkpoint none");
+    if (h->has_particle && h->h_ps.D != P.D)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: the handle's sphere has another diameter");
+    if (H.has_particle && !h->has_particle) {   // buffers and hierarchy for the saved sphere
+        const lbmp_status s = lbmp_add_sphere(h, P.x, P.D, P.rho_p, P.cv, P.cvw, nullptr);
+        if (s != LBMP_OK) return s;
+    }
+    std::vector<double> hist((size_t)std::max(H.history_capacity, 0) * 15);
+    if (!get(f, hist.data(), hist.size() * sizeof(double)))
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: truncated checkpoint");
+    h->tau = H.tau;
+    for (int a = 0; a < 3; ++a) h->body_force[a] = H.body_force[a];
+    h->steps = H.steps;
+    if (H.has_particle) {
+        h->h_ps = P;
+        const lbmp_status s = upload_particle(h);
+        if (s != LBMP_OK) return s;
+    }
+    if (H.history_capacity > 0 && h->history && H.history_capacity == h->cfg.history_capacity)
+        LBMP_CK(h, cudaMemcpy(h->history, hist.data(), hist.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (h->amr) {
+        const lbmp_status s = amr_load(h, f);
+        if (s != LBMP_OK) return fail(h, s, "lbmp_load: restoring the refined hierarchy failed");
+        return read_status(h);
+    }
+    const size_t pb = (size_t)19 * (size_t)h->G.n * elem_size(h->cfg.precision);
+    std::vector<unsigned char> buf(pb);
+    if (!get(f, buf.data(), pb)) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: truncated checkpoint");
+    LBMP_CK(h, cudaMemcpy(h->pops[h->cur], buf.data(), pb, cudaMemcpyHostToDevice));
+    buf.resize((size_t)h->G.n);
+    if (!get(f, buf.data(), (size_t)h->G.n)) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: truncated checkpoint");
+    LBMP_CK(h, cudaMemcpy(h->flags[h->fcur], buf.data(), (size_t)h->G.n, cudaMemcpyHostToDevice));
+    LBMP_CK(h, cudaMemcpy(h->flags[1 - h->fcur], buf.data(), (size_t)h->G.n, cudaMemcpyHostToDevice));
+    h->h2d += (long long)(pb + 2 * (size_t)h->G.n);
+    if (h->has_particle)
+        launch_build_links(h->flags[h->fcur], h->G, h->box, h->d_ps, h->link_mask, h->link_blocks, h->list, h->count,
+                           h->list_cap, h->status, h->stream);
+    LBMP_CK(h, cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
 lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int checkpoint_interval, int axis,
                               double* J, double* forces) {
     if (!h) return LBMP_ERR_INVALID_ARG;
