@@ -435,6 +435,36 @@ def adjoint_line(L, workloads, torch, prec, reps):
     return out
 
 
+def replica_context(backend="nccl"):
+    """(world, rank, local rank, torch.distributed or None) from the torchrun
+    environment; with more than one rank the process group is joined (NCCL
+    between GPUs).  Every rank runs an independent replica of the workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def max_over_ranks(value, dist, device):
+    """The largest of the ranks' values (every rank gets it): the job's time."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, updates_per_rank, ms_max):
+    """Whole-job throughput of weak-scaled replicas: all ranks' cell updates
+    over the slowest rank's time."""
+    return world * updates_per_rank / (ms_max * 1e-3) / 1e6
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -449,14 +479,8 @@ def main():
     import paper_2103_10882_gb300 as L
     from paper_2103_10882_gb300 import workloads
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))   # before the NCCL group is joined
+    world, rank, local, dist = replica_context("nccl")
     prec = args.precision
     bpp = BYTES_PER_POP[prec]
     line = {}
@@ -473,12 +497,9 @@ def main():
         ms, _, c0, c1 = timed(sim, args.steps, sim.stream, torch, profile=False)
         # second timed pass: events around every stream-collide launch (roofline of k_update)
         pms, prof, _, _ = timed(sim, max(10, args.steps // 5), sim.stream, torch, profile=True)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     updates = c1[1] - c0[1]
-    value = world * updates / (ms_max * 1e-3) / 1e6
+    value = job_mlups(world, updates, ms_max)
     e2e_line = e2e(sim, args.e2e_steps, np.array([0.0, 0.0, -gm]))
     part = sim.particle()
     sim.close()
