@@ -209,10 +209,11 @@ def refined_sim(L, prec, history_capacity=1 << 16, w=None):
     return sim
 
 
-def cpu_baseline(seconds):
+def cpu_baseline(seconds, max_steps=None, warmup=0):
     """The FP64 refined oracle on the host cores, on a bounded sample of the
-    same workload: the same hierarchy and sphere for as many level-0 steps as
-    fit in `seconds` (at least one)."""
+    same workload: the same hierarchy and sphere, `warmup` untimed level-0
+    steps (at most one), then timed level-0 steps until `seconds` have passed
+    or `max_steps` are done (at least one)."""
     import oracle
     w = REFINED
     tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
@@ -223,13 +224,15 @@ def cpu_baseline(seconds):
     o.set_sensor(*w["sensor"])
     o.init_equilibrium()
     upd = sum((o.block_map(l) >= 0).sum() * 4096 * (1 << l) for l in range(w["levels"]))
+    if warmup > 0:
+        o.step(1)
     t0 = time.perf_counter()
     steps = 0
     while True:
         o.step(1)
         steps += 1
         dt = time.perf_counter() - t0
-        if dt >= seconds:
+        if dt >= seconds or (max_steps is not None and steps >= max_steps):
             break
     o.close()
     return {"value": upd * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
@@ -240,7 +243,7 @@ def cpu_baseline(seconds):
 def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
-    cb = cpu_baseline(max(args.cpu_seconds, 1.0))
+    cb = cpu_baseline(max(args.cpu_seconds, 1.0), max_steps=max(args.steps, 1), warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
             "data": "synthetic", "config": {"workload": refined_name("fp64 oracle")}, "cpu_baseline": cb,
