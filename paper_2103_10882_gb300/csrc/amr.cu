@@ -320,18 +320,21 @@ constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid
 constexpr int LINK_THREADS = 64;   // remap blocks: small, so the box spreads over the SMs; one count per block
 
 // Exclusive prefix of n counts into pre[0..n] (pre[n] = total), computed by
-// the whole CTA (NT threads); every thread must call it.  first: this
-// thread's count[threadIdx.x] (0 beyond n), loaded by the caller ahead.
+// the whole CTA (NT threads, two consecutive counts per thread and pass);
+// every thread must call it.  first0, first1: counts 2 threadIdx.x and
+// 2 threadIdx.x + 1 (0 beyond n), loaded by the caller ahead.
 template <int NT>
-__device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n, int* pre, int first) {
+__device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n, int* pre, int first0, int first1) {
     __shared__ int wsum[NT / 32];
     __shared__ int carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int base = 0; base < n; base += NT) {
-        const int i = base + (int)threadIdx.x;
-        int v = base == 0 ? first : (i < n ? count[i] : 0);
+    for (int base = 0; base < n; base += 2 * NT) {
+        const int i = base + 2 * (int)threadIdx.x;
+        const int c0 = base == 0 ? first0 : (i < n ? count[i] : 0);
+        const int c1 = base == 0 ? first1 : (i + 1 < n ? count[i + 1] : 0);
+        int v = c0 + c1;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, v, off);
@@ -349,7 +352,9 @@ __device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n
             if (lane < NT / 32) wsum[lane] = w;
         }
         __syncthreads();
-        if (i < n) pre[i + 1] = carry + (wid > 0 ? wsum[wid - 1] : 0) + v;
+        const int incl = carry + (wid > 0 ? wsum[wid - 1] : 0) + v;   // through count i + 1
+        if (i < n) pre[i + 1] = incl - c1;
+        if (i + 1 < n) pre[i + 2] = incl;
         __syncthreads();
         if (threadIdx.x == 0) carry += wsum[NT / 32 - 1];
         __syncthreads();
@@ -381,16 +386,15 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     __shared__ LinkFrame<A> Fr;
     __shared__ BoxFrame Bf;
     const int runs = (int)((B.cells + LINK_THREADS - 1) / LINK_THREADS);
-    const int first = (int)threadIdx.x < runs ? run_count[threadIdx.x] : 0;   // in flight during the set-up
-    if (threadIdx.x == 0) {
-        Fr.init(*ps);
-        box_frame_init(Bf, D.n, D.periodic, B, *ps);
-    }
+    const int i2 = 2 * (int)threadIdx.x;   // this thread's first two counts, in flight during the set-up
+    const int first0 = i2 < runs ? run_count[i2] : 0, first1 = i2 + 1 < runs ? run_count[i2 + 1] : 0;
+    if (threadIdx.x == 0) Fr.init(*ps);   // the two FP64 set-ups on two warps
+    if (threadIdx.x == 32) box_frame_init(Bf, D.n, D.periodic, B, *ps);
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int total = block_prefix<BNDW_THREADS>(run_count, runs, pre, first);
+    const int total = block_prefix<BNDW_THREADS>(run_count, runs, pre, first0, first1);
     const int W = (int)gridDim.x * (BNDW_THREADS / 32);
-    LinkSums acc;
+    LinkSums<A> acc;
     for (int j = (int)blockIdx.x * (BNDW_THREADS / 32) + wib; j < total; j += W) {
         // run r holding marked cell j: the largest r with pre[r] <= j
         int lo = 0, hi = runs;

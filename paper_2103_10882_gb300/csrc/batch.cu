@@ -116,10 +116,8 @@ __global__ void __launch_bounds__(BW)
     const GridDesc& G = D.G;
     const int n3[3] = {G.nx, G.ny, G.nz};
     const int per3[3] = {1, 1, 1};
-    if (threadIdx.x == 0) {
-        Fr.init(ps[sim]);
-        box_frame_init(Bf, n3, per3, D.box, ps[sim]);
-    }
+    if (threadIdx.x == 0) Fr.init(ps[sim]);   // the two FP64 set-ups on two warps
+    if (threadIdx.x == 32) box_frame_init(Bf, n3, per3, D.box, ps[sim]);
     __syncthreads();
     const CollideParams<A> P = sim_params<S>(D, scale, inv);
     const S* s0 = src + D.pop_off;
@@ -130,7 +128,7 @@ __global__ void __launch_bounds__(BW)
     __shared__ int sl[BND_CHUNK];
     const long long t0 = (long long)(blockIdx.x - D.bnd_off) * BND_CHUNK;
     const int nm = block_compact_mask(mask + D.mask_off, t0, D.box.cells, BND_CHUNK, sl);
-    LinkSums acc;
+    LinkSums<A> acc;
     for (int i = wib; i < nm; i += BW / 32) {
         int xyz[3];
         if (!box_cell((int)(t0 + sl[i]), n3, per3, D.box, Bf, xyz)) continue;   // marked cells are inside

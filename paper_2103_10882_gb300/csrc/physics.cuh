@@ -268,56 +268,78 @@ __device__ __forceinline__ A cli_link(int q, const A d[3], bool use_delta, A gt_
 }
 
 // Per-lane sums of the link forces and torques of one particle.  fl and tl
-// of every link are added in FP64.  The lattice-weight part 2 w_k c_k is
-// summed in integers: 36 * 2 w_k is 4 on faces and 2 on edges, and its
-// torque (pu + 1/2 - X) x 2 w_k c_k is carried as (2 pu + 1) x (36 * 2 w_k c_k)
-// over 72 minus X x (the force part), so it cancels exactly wherever the
-// links close around the body.
+// of every link are added in the arithmetic type A; in FP32 each running
+// sum carries its rounding error (Knuth's TwoSum, exact for every
+// addition), so a lane's sum is exact to far below FP32 resolution without
+// the slow FP64 pipe.  The block sum is formed in FP64.  The lattice-weight part
+// 2 w_k c_k is summed in integers: 36 * 2 w_k is 4 on faces and 2 on edges,
+// and its torque (pu + 1/2 - X) x 2 w_k c_k is carried as
+// (2 pu + 1) x (36 * 2 w_k c_k) over 72 minus X x (the force part), so it
+// cancels exactly wherever the links close around the body.
+template <typename A>
 struct LinkSums {
-    double F[3] = {0.0, 0.0, 0.0}, T[3] = {0.0, 0.0, 0.0};
+    A F[3] = {A(0), A(0), A(0)}, T[3] = {A(0), A(0), A(0)};
+    A eF[3] = {A(0), A(0), A(0)}, eT[3] = {A(0), A(0), A(0)};   // FP32: rounding errors of F and T
     int iF[3] = {0, 0, 0};
     long long iT[3] = {0, 0, 0};
 
-    template <typename A>
+    __device__ static __forceinline__ void sum2(A& s, A& e, A x) {
+        if constexpr (sizeof(A) == 8) {
+            s += x;
+        } else {
+            const A t = s + x, xv = t - s;
+            e += (s - (t - xv)) + (x - xv);
+            s = t;
+        }
+    }
+    // lane total of component a of F (T) in FP64
+    __device__ __forceinline__ double force(int a) const {
+        if constexpr (sizeof(A) == 8) return F[a];
+        else return (double)F[a] + (double)eF[a];
+    }
+    __device__ __forceinline__ double torque(int a) const {
+        if constexpr (sizeof(A) == 8) return T[a];
+        else return (double)T[a] + (double)eT[a];
+    }
+
     __device__ __forceinline__ void add(int k, const int pu[3], const A fl[3], const A tl[3]) {
         const int m = k <= 6 ? 4 : 2;
         const int mc[3] = {m * cx(k), m * cy(k), m * cz(k)};
         const long long p2[3] = {2LL * pu[0] + 1, 2LL * pu[1] + 1, 2LL * pu[2] + 1};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            F[a] += (double)fl[a];
-            T[a] += (double)tl[a];
+            sum2(F[a], eF[a], fl[a]);
+            sum2(T[a], eT[a], tl[a]);
             iF[a] += mc[a];
         }
         iT[0] += p2[1] * mc[2] - p2[2] * mc[1];
         iT[1] += p2[2] * mc[0] - p2[0] * mc[2];
         iT[2] += p2[0] * mc[1] - p2[1] * mc[0];
     }
-    // force (v[0..2]) and torque about X (v[3..5]) of this lane's links
-    __device__ __forceinline__ void total(const double X[3], double v[6]) const {
-        const double fr[3] = {iF[0] / 36.0, iF[1] / 36.0, iF[2] / 36.0};
-        v[0] = F[0] + fr[0];
-        v[1] = F[1] + fr[1];
-        v[2] = F[2] + fr[2];
-        v[3] = T[0] + ((double)iT[0] / 72.0 - (X[1] * fr[2] - X[2] * fr[1]));
-        v[4] = T[1] + ((double)iT[1] / 72.0 - (X[2] * fr[0] - X[0] * fr[2]));
-        v[5] = T[2] + ((double)iT[2] / 72.0 - (X[0] * fr[1] - X[1] * fr[0]));
-    }
 };
 
-// Deterministic block sum of the threads' link sums: the FP64 parts go
-// through a shared-memory tree in a fixed order, the integer parts through
-// warp shuffles; thread 0 writes force and torque about X to out[0..5].
-// Every thread of the block must call it.
-template <int NT>
-__device__ __forceinline__ void block_link_sums(const LinkSums& acc, const double X[3], double* __restrict__ out) {
+__device__ __forceinline__ double pick3(const double v[3], int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); }
+
+// Deterministic block sum of the threads' link sums into out[0..5]: force,
+// and torque about X.  Every thread of the block must call it.  The six
+// FP64 components are staged in shared memory and summed by warps 0..5,
+// one component each: lane l adds column l of the NT / 32 warp rows
+// pairwise, then a butterfly runs across the lanes.  The integer parts are
+// summed exactly by shuffles.  FP64 additions are slow and narrow on this
+// GPU, so the chain is one barrier and eight additions deep, spread over
+// the four schedulers, and the constant divisions are multiplications by
+// the reciprocals.  Each writer fences its output for a last-block hand-off.
+template <int NT, typename A>
+__device__ __forceinline__ void block_link_sums(const LinkSums<A>& acc, const double X[3], double* __restrict__ out) {
+    static_assert(NT % 32 == 0 && NT >= 192, "six warps take the six components");
+    constexpr int NW = NT / 32;
     __shared__ double sd[6][NT];
-    __shared__ long long si[6][NT / 32];
+    __shared__ long long si[6][NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        sd[c][tid] = acc.F[c];
-        sd[3 + c][tid] = acc.T[c];
+        sd[c][tid] = acc.force(c);
+        sd[3 + c][tid] = acc.torque(c);
     }
     long long iv[6] = {acc.iF[0], acc.iF[1], acc.iF[2], acc.iT[0], acc.iT[1], acc.iT[2]};
 #pragma unroll
@@ -328,30 +350,36 @@ __device__ __forceinline__ void block_link_sums(const LinkSums& acc, const doubl
 #pragma unroll
         for (int c = 0; c < 6; ++c) si[c][wid] = iv[c];
     __syncthreads();
-    for (int h = NT / 2; h > 0; h >>= 1) {
-        for (int idx = tid; idx < 6 * h; idx += NT) {
-            const int c = idx / h, i = idx - c * h;
-            sd[c][i] += sd[c][i + h];
-        }
-        __syncthreads();
+    if (wid >= 6) return;
+    const int c = wid;
+    double v[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) v[w] = sd[c][lane + 32 * w];
+#pragma unroll
+    for (int st = 1; st < NW; st <<= 1)
+#pragma unroll
+        for (int w = 0; w + st < NW; w += 2 * st) v[w] += v[w + st];
+    double t = v[0];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane != 0) return;
+    long long iF[3] = {0, 0, 0}, iT = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        iF[0] += si[0][w];
+        iF[1] += si[1][w];
+        iF[2] += si[2][w];
+        iT += si[c][w];
     }
-    if (tid == 0) {
-        LinkSums t;
-        for (int c = 0; c < 3; ++c) {
-            t.F[c] = sd[c][0];
-            t.T[c] = sd[3 + c][0];
-            long long a = 0, b = 0;
-            for (int w = 0; w < NT / 32; ++w) {
-                a += si[c][w];
-                b += si[3 + c][w];
-            }
-            t.iF[c] = (int)a;
-            t.iT[c] = b;
-        }
-        double v[6];
-        t.total(X, v);
-        for (int c = 0; c < 6; ++c) out[c] = v[c];
+    const double r36 = 1.0 / 36.0, r72 = 1.0 / 72.0;
+    const double fr[3] = {(double)iF[0] * r36, (double)iF[1] * r36, (double)iF[2] * r36};
+    if (c < 3) {
+        out[c] = t + pick3(fr, c);
+    } else {
+        const int a1 = c == 3 ? 1 : (c == 4 ? 2 : 0), a2 = c == 3 ? 2 : (c == 4 ? 0 : 1);
+        out[c] = t + ((double)iT * r72 - (X[a1] * pick3(fr, a2) - X[a2] * pick3(fr, a1)));
     }
+    __threadfence();
 }
 
 __device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
@@ -498,18 +526,22 @@ __device__ __forceinline__ bool ball_flag_and_neighbours(const int p[3], const i
     return own;
 }
 
+// m = (rho_p + C_v) V and I = 2/5 (rho_p + C_vw) V r^2 (Sec. 2.2: virtual mass and moment of inertia).
+__device__ __forceinline__ double particle_mass(const ParticleState& P) { return (P.rho_p + P.cv) * P.V; }
+__device__ __forceinline__ double particle_inertia(const ParticleState& P) {
+    return 0.4 * (P.rho_p + P.cvw) * P.V * P.r * P.r;
+}
+
 // One axis a of Algorithm 1's particle update: average of the hydrodynamic
 // force and torque over two steps, gravity/buoyancy, the virtual force and
 // torque from the previous accelerations, and the kick-drift-kick update
-// with the virtually increased mass and moment of inertia.  The axes are
+// with the virtually increased mass and moment of inertia, whose inverses
+// the caller passes (particle_mass, particle_inertia).  The axes are
 // independent; P.steps is advanced once afterwards.
-__device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, double Fh, double Th, const GridDesc& G,
-                                                      double* __restrict__ history, int hist_cap,
-                                                      int* __restrict__ status) {
+__device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, double Fh, double Th, double inv_m,
+                                                      double inv_I, const GridDesc& G, double* __restrict__ history,
+                                                      int hist_cap, int* __restrict__ status) {
     const double V = P.V, r = P.r;
-    const double m = (P.rho_p + P.cv) * V;
-    const double I = 0.4 * (P.rho_p + P.cvw) * V * r * r;
-    const double inv_m = 1.0 / m, inv_I = 1.0 / I;
     const bool avg = P.force_average && P.steps > 0;
     const double Fbar = avg ? 0.5 * (Fh + P.Fh_old[a]) : Fh;
     const double Tbar = avg ? 0.5 * (Th + P.Th_old[a]) : Th;
@@ -562,53 +594,51 @@ __device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, d
     }
 }
 
-// Algorithm 1 after the LBM step, on the staged particle record (one thread).
-__device__ __forceinline__ void particle_advance(ParticleState& P, const double FT[6], const GridDesc& G,
-                                                 double* __restrict__ history, int hist_cap,
-                                                 int* __restrict__ status) {
-    for (int a = 0; a < 3; ++a) particle_advance_axis(P, a, FT[a], FT[3 + a], G, history, hist_cap, status);
-    P.steps += 1;
-}
-
-// Particle update by one thread block of NT threads: sums the nblocks
-// force partials in a fixed order, stages the record in shared memory,
-// advances its three axes on threads 0..2 and writes it back.  The
-// partials may come from other blocks of the same launch: they are read
-// through L2.
+// Particle update by one block of NT >= 256 threads once the nblocks force
+// partials are complete: warps 0..5 sum one component each in a fixed
+// order (lane l takes partials l, l + 32, ... in two alternating sums, then
+// a butterfly runs across the lanes), warp 6 forms 1/m and 1/I, warp 7
+// stages the record in shared memory; threads 0..2 then advance the three
+// axes and the block writes the record back.  The partials may come from
+// other blocks of the same launch: they are read through L2.  Every thread
+// of the block must call it.
 template <int NT>
 __device__ __forceinline__ void particle_block_update(ParticleState* __restrict__ ps, const double* partials,
                                                       int nblocks, const GridDesc& G, double* __restrict__ history,
                                                       int hist_cap, int* __restrict__ status) {
-    __shared__ double red[6][NT];
+    static_assert(NT % 32 == 0 && NT >= 256, "eight warps share the work");
+    constexpr int words = (int)(sizeof(ParticleState) / sizeof(int));
+    __shared__ double sFT[6], sinv[2];
     __shared__ ParticleState sP;
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += NT)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (wid < 6) {
+        double s0 = 0.0, s1 = 0.0;
+        int b = lane;
+        for (; b + 32 < nblocks; b += 64) {
+            s0 += __ldcg(partials + (size_t)b * 6 + wid);
+            s1 += __ldcg(partials + (size_t)(b + 32) * 6 + wid);
+        }
+        if (b < nblocks) s0 += __ldcg(partials + (size_t)b * 6 + wid);
+        double t = s0 + s1;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) v[c] += __ldcg(partials + (size_t)b * 6 + c);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) red[c][threadIdx.x] = v[c];
-    {
-        const int words = (int)(sizeof(ParticleState) / sizeof(int));
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) sFT[wid] = t;
+    } else if (wid == 6) {
+        if (lane < 2) sinv[lane] = 1.0 / (lane == 0 ? particle_mass(*ps) : particle_inertia(*ps));
+    } else if (wid == 7) {
         const int* srcw = reinterpret_cast<const int*>(ps);
         int* dstw = reinterpret_cast<int*>(&sP);
-        for (int i = threadIdx.x; i < words; i += NT) dstw[i] = __ldcg(srcw + i);
+#pragma unroll 4
+        for (int i = lane; i < words; i += 32) dstw[i] = __ldcg(srcw + i);
     }
     __syncthreads();
-    for (int h = NT / 2; h > 0; h >>= 1) {
-        for (int idx = threadIdx.x; idx < 6 * h; idx += NT) {
-            const int c = idx / h, i = idx - c * h;
-            red[c][i] += red[c][i + h];
-        }
-        __syncthreads();
-    }
     if (threadIdx.x < 3)   // the three axes in parallel
-        particle_advance_axis(sP, threadIdx.x, red[threadIdx.x][0], red[3 + threadIdx.x][0], G, history, hist_cap,
-                              status);
+        particle_advance_axis(sP, threadIdx.x, sFT[threadIdx.x], sFT[3 + threadIdx.x], sinv[0], sinv[1], G, history,
+                              hist_cap, status);
     __syncthreads();
     if (threadIdx.x == 0) sP.steps += 1;
     __syncthreads();
     {
-        const int words = (int)(sizeof(ParticleState) / sizeof(int));
         const int* srcw = reinterpret_cast<const int*>(&sP);
         int* dstw = reinterpret_cast<int*>(ps);
         for (int i = threadIdx.x; i < words; i += NT) dstw[i] = srcw[i];

@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(BNDW_THREADS)
     __syncthreads();
     const size_t n = (size_t)G.n;
     const int n3[3] = {G.nx, G.ny, G.nz};
-    LinkSums acc;
+    LinkSums<A> acc;
     for (int w = blockIdx.x * (BNDW_THREADS / 32) + wib; w < cnt; w += nwarps) {
         const int cell = list[w];
         const int x = cell % G.nx, y = (cell / G.nx) % G.ny, z = cell / (G.nx * G.ny);
@@ -146,41 +146,7 @@ constexpr int PART_THREADS = 256;
 __global__ void __launch_bounds__(PART_THREADS)
     k_particle(ParticleState* __restrict__ ps, const double* __restrict__ partials, int nblocks, GridDesc G,
                double* __restrict__ history, int hist_cap, int* __restrict__ status) {
-    __shared__ double red[6][PART_THREADS];
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += PART_THREADS)
-#pragma unroll
-        for (int c = 0; c < 6; ++c) v[c] += partials[(size_t)b * 6 + c];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) red[c][threadIdx.x] = v[c];
-    __syncthreads();
-    for (int s = PART_THREADS / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-#pragma unroll
-            for (int c = 0; c < 6; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
-        __syncthreads();
-    }
-    // stage the particle record in shared memory (one coalesced read and write
-    // instead of dependent global accesses by a single thread)
-    __shared__ ParticleState sP;
-    {
-        const int words = (int)(sizeof(ParticleState) / sizeof(int));
-        const int* srcw = reinterpret_cast<const int*>(ps);
-        int* dstw = reinterpret_cast<int*>(&sP);
-        for (int i = threadIdx.x; i < words; i += PART_THREADS) dstw[i] = srcw[i];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double FT[6] = {red[0][0], red[1][0], red[2][0], red[3][0], red[4][0], red[5][0]};
-        particle_advance(sP, FT, G, history, hist_cap, status);
-    }
-    __syncthreads();
-    {
-        const int words = (int)(sizeof(ParticleState) / sizeof(int));
-        const int* srcw = reinterpret_cast<const int*>(&sP);
-        int* dstw = reinterpret_cast<int*>(ps);
-        for (int i = threadIdx.x; i < words; i += PART_THREADS) dstw[i] = srcw[i];
-    }
+    particle_block_update<PART_THREADS>(ps, partials, nblocks, G, history, hist_cap, status);
 }
 
 // ------------------------------------------------------------------ remap
