@@ -456,13 +456,81 @@ __global__ void __launch_bounds__(BNDW_THREADS)
 }
 
 
+// Refill of the uncovered cell (b, c) at g by the whole warp (Sec. 2.3).
+// Lane q = 1..18 takes the neighbour g + c_q, counted when it is fluid
+// before (fcur) and after (the ball predicate) the move, with its density
+// 1 + sum_p g_p and its momentum sum_p c_p g_p (used for the six face
+// neighbours by Grad's strain rate).  The mean density of the counted
+// neighbours and the rigid-body velocity u_p + omega_p x (x - x_p) give the
+// equilibrium, plus Grad's non-equilibrium term when gcoef != 0; lane
+// q < 19 writes population q.  Every lane calls it with the same cell.
+template <typename S>
+__device__ __forceinline__ void refill_cell_warp(const LevelView& D, S* __restrict__ pops,
+                                                 const uint8_t* __restrict__ fcur, const BoxFrame& F,
+                                                 const ParticleState& P, int b, int c, const int g[3],
+                                                 typename Store<S>::A scale, typename Store<S>::A inv_scale,
+                                                 typename Store<S>::A gcoef) {
+    using A = typename Store<S>::A;
+    const int lane = threadIdx.x & 31;
+    bool ok = false;
+    A r = A(0), mo[3] = {A(0), A(0), A(0)};
+    if (lane >= 1 && lane < 19) {
+        int v[3] = {g[0] + cx(lane), g[1] + cy(lane), g[2] + cz(lane)};
+        if (wrap3(v, D) && !ball_flag(v, D.n, D.periodic, F, P)) {
+            int vc;
+            const int vb = locate(D, v, &vc);
+            if (vb >= 0 && vb < D.nreal && fcur[(size_t)vb * B3 + vc] != FLAG_SOLID) {
+                ok = true;
+                A gp[19];
+#pragma unroll
+                for (int p = 0; p < 19; ++p) gp[p] = Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
+                r = A(1);
+#pragma unroll
+                for (int p = 0; p < 19; ++p) r += gp[p];
+#pragma unroll
+                for (int p = 1; p < 19; ++p) {
+                    mo[0] += A(cx(p)) * gp[p];
+                    mo[1] += A(cy(p)) * gp[p];
+                    mo[2] += A(cz(p)) * gp[p];
+                }
+            }
+        }
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    A rs = ok ? r : A(0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
+    const int cnt = __popc(okm);
+    const A rho = cnt > 0 ? rs / A(cnt) : A(1);
+    const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
+                         wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
+                         wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
+    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+    if (gcoef != A(0)) {   // Grad refill: face neighbour q = 1 + 2 a (+1 for -e_a), fluid before and after
+        auto nb = [&](int a, int sgn, A uo[3]) {
+            const int q = 1 + 2 * a + (sgn > 0 ? 0 : 1);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) uo[k] = __shfl_sync(0xffffffffu, mo[k], q);
+            return ((okm >> q) & 1u) != 0;
+        };
+        refill_strain<A>(nb, u, Sr);
+    }
+    if (lane < 19) {
+        A e = geq_dev<A>(lane, rho - A(1), u, uu);
+        if (gcoef != A(0)) e += grad_term<A>(lane, Sr, gcoef);
+        Store<S>::store(pops + paddr(b, lane, c), e, scale);
+    }
+}
+
 // Remap of Sec. 2.3 after the particle moved, over the box of finest cells
 // around the sphere, in one pass: the new solid flag of every cell (the
 // exact ball predicate); covered cells drop their populations; uncovered
-// cells are refilled with the equilibrium at the mean density of the
-// neighbours that are fluid before and after and the rigid-body velocity
-// u_p + omega_p x (x - x_p); fluid cells with a solid neighbour are marked
-// for the boundary list (counts per block for the ordered compaction).
+// cells are refilled afterwards, one at a time by their whole warp
+// (refill_cell_warp); fluid cells with a solid neighbour are marked for the
+// boundary list (counts per block for the ordered compaction).
 // Neighbour flags are evaluated from the same predicate instead of being
 // read back, so no second pass is needed.
 template <typename S>
@@ -478,6 +546,8 @@ __global__ void __launch_bounds__(LINK_THREADS)
     const ParticleState& P = *ps;
     const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
     int is_b = 0;
+    bool uncovered = false;   // fluid after the move, solid before: refilled below by the warp
+    int ub = 0, uc = 0, ug[3] = {0, 0, 0};
     if (t < B.cells) {
         int g[3];
         if (box_cell(t, D.n, D.periodic, B, F, g)) {
@@ -494,63 +564,25 @@ __global__ void __launch_bounds__(LINK_THREADS)
 #pragma unroll
                     for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
                 } else {
-                    const bool uncovered = fcur[x] == FLAG_SOLID;
+                    uncovered = fcur[x] == FLAG_SOLID;
                     is_b = any_nb ? 1 : 0;
-                    A rsum = A(0);
-                    int cnt = 0;
-                    for (int q = 1; uncovered && q < 19; ++q) {
-                        int v[3] = {g[0] + cx(q), g[1] + cy(q), g[2] + cz(q)};
-                        if (!wrap3(v, D)) continue;
-                        if (ball_flag(v, D.n, D.periodic, F, P)) continue;
-                        int vc;
-                        const int vb = locate(D, v, &vc);
-                        if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] == FLAG_SOLID) continue;
-                        A r = A(1);
-                        for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
-                        rsum += r;
-                        cnt += 1;
-                    }
                     fnext[x] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
-                    if (uncovered) {
-                        const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
-                        const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
-                                             wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
-                                             wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
-                        const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])),
-                                        A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
-                                        A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
-                        const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                        A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
-                        if (gcoef != A(0)) {   // Grad refill: face neighbours fluid before and after the move
-                            auto nb = [&](int a, int sgn, A uo[3]) {
-                                int v[3] = {g[0], g[1], g[2]};
-                                v[a] += sgn;
-                                if (!wrap3(v, D)) return false;
-                                if (ball_flag(v, D.n, D.periodic, F, P)) return false;
-                                int vc;
-                                const int vb = locate(D, v, &vc);
-                                if (vb < 0 || vb >= D.nreal || fcur[(size_t)vb * B3 + vc] == FLAG_SOLID) return false;
-                                uo[0] = uo[1] = uo[2] = A(0);
-                                for (int q = 1; q < 19; ++q) {
-                                    const A gq = Store<S>::load(pops + paddr(vb, q, vc), inv_scale);
-                                    uo[0] += A(cx(q)) * gq;
-                                    uo[1] += A(cy(q)) * gq;
-                                    uo[2] += A(cz(q)) * gq;
-                                }
-                                return true;
-                            };
-                            refill_strain<A>(nb, u, Sr);
-                        }
-                        for (int q = 0; q < 19; ++q) {
-                            A e = geq_dev<A>(q, rho - A(1), u, uu);
-                            if (gcoef != A(0)) e += grad_term<A>(q, Sr, gcoef);
-                            Store<S>::store(pops + paddr(b, q, c), e, scale);
-                        }
-                    }
+                    ub = b;
+                    uc = c;
+                    ug[0] = g[0];
+                    ug[1] = g[1];
+                    ug[2] = g[2];
                 }
             }
         }
         mask[t] = (uint8_t)is_b;
+    }
+    for (unsigned todo = __ballot_sync(0xffffffffu, uncovered); todo != 0u; todo &= todo - 1u) {
+        const int src = __ffs((int)todo) - 1;
+        const int g3[3] = {__shfl_sync(0xffffffffu, ug[0], src), __shfl_sync(0xffffffffu, ug[1], src),
+                           __shfl_sync(0xffffffffu, ug[2], src)};
+        refill_cell_warp<S>(D, pops, fcur, F, P, __shfl_sync(0xffffffffu, ub, src),
+                            __shfl_sync(0xffffffffu, uc, src), g3, scale, inv_scale, gcoef);
     }
     const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
     __shared__ int wsum[LINK_THREADS / 32];

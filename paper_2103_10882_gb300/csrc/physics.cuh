@@ -292,16 +292,6 @@ struct LinkSums {
             s = t;
         }
     }
-    // lane total of component a of F (T) in FP64
-    __device__ __forceinline__ double force(int a) const {
-        if constexpr (sizeof(A) == 8) return F[a];
-        else return (double)F[a] + (double)eF[a];
-    }
-    __device__ __forceinline__ double torque(int a) const {
-        if constexpr (sizeof(A) == 8) return T[a];
-        else return (double)T[a] + (double)eT[a];
-    }
-
     __device__ __forceinline__ void add(int k, const int pu[3], const A fl[3], const A tl[3]) {
         const int m = k <= 6 ? 4 : 2;
         const int mc[3] = {m * cx(k), m * cy(k), m * cz(k)};
@@ -320,27 +310,35 @@ struct LinkSums {
 
 __device__ __forceinline__ double pick3(const double v[3], int i) { return i == 0 ? v[0] : (i == 1 ? v[1] : v[2]); }
 
+// Double-float addition (h, l) += (bh, bl): Knuth's TwoSum of the leading
+// parts, the trailing parts added to its error, renormalised (Fast2Sum).
+// About 44 significant bits, in FP32 arithmetic.
+__device__ __forceinline__ void df_add(float& h, float& l, float bh, float bl) {
+    const float s = h + bh, v = s - h;
+    const float e = ((h - (s - v)) + (bh - v)) + (l + bl);
+    h = s + e;
+    l = e - (h - s);
+}
+
 // Deterministic block sum of the threads' link sums into out[0..5]: force,
-// and torque about X.  Every thread of the block must call it.  The six
-// FP64 components are staged in shared memory and summed by warps 0..5,
-// one component each: lane l adds column l of the NT / 32 warp rows
-// pairwise, then a butterfly runs across the lanes.  The integer parts are
-// summed exactly by shuffles.  FP64 additions are slow and narrow on this
-// GPU, so the chain is one barrier and eight additions deep, spread over
-// the four schedulers, and the constant divisions are multiplications by
-// the reciprocals.  Each writer fences its output for a last-block hand-off.
+// and torque about X.  Every thread of the block must call it.  FP64
+// additions, and conversions to FP64, are slow and narrow on this GPU, so
+// in FP32 the lanes' sums (each with its TwoSum error) are reduced as
+// double-float pairs, a butterfly within each warp and, after one barrier,
+// one across the warps' results by warps 0..5 (one component each); only
+// lane 0 of those warps converts to FP64.  In FP64 the six components are
+// staged in shared memory and warp c adds column l of the warp rows
+// pairwise in lane l, then across the lanes.  The integer parts are summed
+// exactly by shuffles, and the constant divisions are multiplications by
+// the reciprocals.  A last-block hand-off after this call is ordered by its
+// barrier and release (the writers need no fence of their own).
 template <int NT, typename A>
 __device__ __forceinline__ void block_link_sums(const LinkSums<A>& acc, const double X[3], double* __restrict__ out) {
-    static_assert(NT % 32 == 0 && NT >= 192, "six warps take the six components");
+    static_assert(NT % 32 == 0 && NT >= 192 && NT <= 1024, "six warps take the six components");
     constexpr int NW = NT / 32;
-    __shared__ double sd[6][NT];
+    constexpr int SPAN = NW <= 8 ? 8 : (NW <= 16 ? 16 : 32);   // lanes of the cross-warp butterfly
     __shared__ long long si[6][NW];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        sd[c][tid] = acc.force(c);
-        sd[3 + c][tid] = acc.torque(c);
-    }
     long long iv[6] = {acc.iF[0], acc.iF[1], acc.iF[2], acc.iT[0], acc.iT[1], acc.iT[2]};
 #pragma unroll
     for (int c = 0; c < 6; ++c)
@@ -349,20 +347,64 @@ __device__ __forceinline__ void block_link_sums(const LinkSums<A>& acc, const do
     if (lane == 0)
 #pragma unroll
         for (int c = 0; c < 6; ++c) si[c][wid] = iv[c];
-    __syncthreads();
-    if (wid >= 6) return;
-    const int c = wid;
-    double v[NW];
+    double t;
+    int c;
+    if constexpr (sizeof(A) == 4) {
+        __shared__ float sh[6][NW], sl[6][NW];
+        float h[6], l[6];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) v[w] = sd[c][lane + 32 * w];
+        for (int a = 0; a < 3; ++a) {
+            h[a] = acc.F[a] + acc.eF[a];
+            l[a] = acc.eF[a] - (h[a] - acc.F[a]);
+            h[3 + a] = acc.T[a] + acc.eT[a];
+            l[3 + a] = acc.eT[a] - (h[3 + a] - acc.T[a]);
+        }
 #pragma unroll
-    for (int st = 1; st < NW; st <<= 1)
+        for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-        for (int w = 0; w + st < NW; w += 2 * st) v[w] += v[w + st];
-    double t = v[0];
+            for (int k = 0; k < 6; ++k) {
+                const float oh = __shfl_xor_sync(0xffffffffu, h[k], off), ol = __shfl_xor_sync(0xffffffffu, l[k], off);
+                df_add(h[k], l[k], oh, ol);
+            }
+        if (lane == 0)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if (lane != 0) return;
+            for (int k = 0; k < 6; ++k) {
+                sh[k][wid] = h[k];
+                sl[k][wid] = l[k];
+            }
+        __syncthreads();
+        if (wid >= 6) return;
+        c = wid;
+        float th = lane < NW ? sh[c][lane] : 0.0f, tl = lane < NW ? sl[c][lane] : 0.0f;
+#pragma unroll
+        for (int off = SPAN / 2; off > 0; off >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, th, off), ol = __shfl_xor_sync(0xffffffffu, tl, off);
+            df_add(th, tl, oh, ol);
+        }
+        if (lane != 0) return;
+        t = (double)th + (double)tl;
+    } else {
+        __shared__ double sd[6][NT];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            sd[a][tid] = acc.F[a];
+            sd[3 + a][tid] = acc.T[a];
+        }
+        __syncthreads();
+        if (wid >= 6) return;
+        c = wid;
+        double v[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v[w] = sd[c][lane + 32 * w];
+#pragma unroll
+        for (int st = 1; st < NW; st <<= 1)
+#pragma unroll
+            for (int w = 0; w + st < NW; w += 2 * st) v[w] += v[w + st];
+        t = v[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane != 0) return;
+    }
     long long iF[3] = {0, 0, 0}, iT = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -379,7 +421,6 @@ __device__ __forceinline__ void block_link_sums(const LinkSums<A>& acc, const do
         const int a1 = c == 3 ? 1 : (c == 4 ? 2 : 0), a2 = c == 3 ? 2 : (c == 4 ? 0 : 1);
         out[c] = t + ((double)iT * r72 - (X[a1] * pick3(fr, a2) - X[a2] * pick3(fr, a1)));
     }
-    __threadfence();
 }
 
 __device__ __forceinline__ int src_coord(int x, int c, int n, int periodic) {
@@ -685,15 +726,18 @@ __device__ __forceinline__ A grad_term(int q, const A S[6], A gcoef) {
 
 // Last-block-done hand-off: each of nblocks blocks calls it after writing
 // its partials; the block that finishes last (a device counter, reset by
-// that block) gets true.  No block waits for another.
+// that block) gets true.  No block waits for another.  The block barrier
+// followed by thread 0's acquire-release atomic at GPU scope publishes the
+// partials of all the block's threads and, in the last block, makes the
+// other blocks' partials visible (read them through L2).
 __device__ __forceinline__ bool last_block_done(int* counter, int nblocks) {
     __shared__ int last;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(counter, 1) == nblocks - 1;
+        int old;
+        asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(counter) : "memory");
+        last = old == nblocks - 1;
         if (last) *counter = 0;
-        __threadfence();
     }
     __syncthreads();
     return last != 0;
