@@ -945,6 +945,8 @@ struct AmrEngine {
     std::vector<std::vector<uint8_t>> cover;      // block coverage per level of the current layout
     cudaStream_t side = nullptr;                  // k_amr_boundary runs here, beside the finest update
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_remap = nullptr;   // a finest remap left on the side stream (remap_pending) ends here
+    bool remap_pending = false;
     double sensor_sigma = 0.0, sensor_c = 0.0;   // flow sensor (sigma_c = 0: off)
     double* d_sensor = nullptr;                   // per real block of all levels
     size_t sensor_cap = 0;
@@ -1509,6 +1511,10 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         G.nz = V.n[2];
         for (int a = 0; a < 3; ++a) G.periodic[a] = E->periodic[a];
         G.n = (long long)V.n[0] * V.n[1] * V.n[2];
+        if (E->remap_pending) {   // the previous remap (side stream) before this update
+            cudaStreamWaitEvent(h->stream, E->ev_remap, 0);
+            E->remap_pending = false;
+        }
         cudaEventRecord(E->ev_fork, h->stream);
         cudaStreamWaitEvent(E->side, E->ev_fork, 0);
         const size_t pre_bytes = sizeof(int) * (size_t)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS + 1);
@@ -1544,13 +1550,30 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
     h->updates += (long long)V.nreal * B3;
     if (coupled) {
-        cudaStreamWaitEvent(h->stream, E->ev_join, 0);
         const LevelView D = view(E, V);
         uint8_t* fnext = V.d_flags[1 - V.fcur];
         const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
-        k_amr_remap<S><<<nl, LINK_THREADS, 0, h->stream>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
-                                                           P.inv_scale, h->link_mask, h->link_blocks, h->status,
-                                                           (A)grad_refill_coef(h->cfg.refill, V.taup));
+        // After the second sub-step the coarser levels' update and explosion come next; they touch
+        // neither the finest real cells, their flags nor the particle, so the remap runs beside them
+        // on the side stream (after the boundary kernel there) and the next finest update, or the end
+        // of the level-0 step, waits for it.  After the first sub-step the next finest update follows
+        // at once.
+        const bool beside = has_coarse && sub == 1;
+        cudaStream_t rs = h->stream;
+        if (beside) {
+            cudaEventRecord(E->ev_fork, h->stream);
+            cudaStreamWaitEvent(E->side, E->ev_fork, 0);
+            rs = E->side;
+        } else {
+            cudaStreamWaitEvent(h->stream, E->ev_join, 0);
+        }
+        k_amr_remap<S><<<nl, LINK_THREADS, 0, rs>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
+                                                    P.inv_scale, h->link_mask, h->link_blocks, h->status,
+                                                    (A)grad_refill_coef(h->cfg.refill, V.taup));
+        if (beside) {
+            cudaEventRecord(E->ev_remap, E->side);
+            E->remap_pending = true;
+        }
         V.fcur = 1 - V.fcur;
         h->launches += 1;
     }
@@ -1579,7 +1602,8 @@ lbmp_status amr_create(lbmp_handle* h) {
     if (!E->d_done) return LBMP_ERR_OOM;
     if (cudaStreamCreateWithFlags(&E->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&E->ev_remap, cudaEventDisableTiming) != cudaSuccess)
         return LBMP_ERR_CUDA;
 
     if (cudaMemsetAsync(E->d_done, 0, sizeof(int), h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
@@ -1593,6 +1617,7 @@ void amr_destroy(lbmp_handle* h) {
     if (h->amr->side) cudaStreamDestroy(h->amr->side);
     if (h->amr->ev_fork) cudaEventDestroy(h->amr->ev_fork);
     if (h->amr->ev_join) cudaEventDestroy(h->amr->ev_join);
+    if (h->amr->ev_remap) cudaEventDestroy(h->amr->ev_remap);
 
     for (auto& V : h->amr->lv) free_level(h, V);
     handle_free(h, h->amr->d_sensor);
@@ -1773,6 +1798,10 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
             using S = std::remove_pointer_t<decltype(tag)>;
             enqueue_advance<S>(h, 0, 0);
         });
+        if (E->remap_pending) {   // the step ends with everything on the caller's stream
+            cudaStreamWaitEvent(h->stream, E->ev_remap, 0);
+            E->remap_pending = false;
+        }
     };
     for (int i = 0; i < n; ++i) {
         if (h->profiling) {   // per-kernel events: plain launches
