@@ -947,6 +947,12 @@ struct AmrEngine {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_remap = nullptr;   // a finest remap left on the side stream (remap_pending) ends here
     bool remap_pending = false;
+    // explosions into a level that has a finer level of its own run on aux, beside that finer
+    // level's sub-steps; the level's first update waits for ev_x[level]
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_aux_fork = nullptr;
+    cudaEvent_t ev_x[MAXL] = {};
+    bool x_pending[MAXL] = {};
     double sensor_sigma = 0.0, sensor_c = 0.0;   // flow sensor (sigma_c = 0: off)
     double* d_sensor = nullptr;                   // per real block of all levels
     size_t sensor_cap = 0;
@@ -1463,13 +1469,27 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         kappa_post(V, F, &kp, &km);
         if (F.nxlist > 0) {
             const unsigned grid = (unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS);
+            // Only level l+1's own update reads the exploded ghost cells.  When level l+1 has a finer
+            // level, that level's sub-steps come first and touch neither level l+1's ghost cells nor
+            // level l's populations, so the explosion runs beside them on aux.
+            const bool beside = l + 2 < L;
+            cudaStream_t xs = h->stream;
+            if (beside) {
+                cudaEventRecord(E->ev_aux_fork, h->stream);
+                cudaStreamWaitEvent(E->aux, E->ev_aux_fork, 0);
+                xs = E->aux;
+            }
             auto ex = [&](auto rs) {
-                k_explode<S, decltype(rs)::value><<<grid, UPD_THREADS, 0, h->stream>>>(
+                k_explode<S, decltype(rs)::value><<<grid, UPD_THREADS, 0, xs>>>(
                     view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[F.cur], (A)kp, (A)km, P.scale,
                     P.inv_scale, F.d_xlist, F.nxlist, h->status);
             };
             if (rescale) ex(std::true_type{});
             else ex(std::false_type{});
+            if (beside) {
+                cudaEventRecord(E->ev_x[l + 1], E->aux);
+                E->x_pending[l + 1] = true;
+            }
             h->launches += 1;
         }
         enqueue_advance<S>(h, l + 1, 0);
@@ -1523,6 +1543,10 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
             h->partials, E->d_done, G, h->history, h->cfg.history_capacity, h->status);
         cudaEventRecord(E->ev_join, E->side);
         h->launches += 1;
+    }
+    if (E->x_pending[l]) {   // this level's ghost cells, exploded on aux
+        cudaStreamWaitEvent(h->stream, E->ev_x[l], 0);
+        E->x_pending[l] = false;
     }
     const long long ev0 = profile_mark(h);
     // ghost cells streamed: the active ones, and at the first sub-step also
@@ -1603,8 +1627,12 @@ lbmp_status amr_create(lbmp_handle* h) {
     if (cudaStreamCreateWithFlags(&E->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&E->ev_remap, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&E->ev_remap, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&E->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&E->ev_aux_fork, cudaEventDisableTiming) != cudaSuccess)
         return LBMP_ERR_CUDA;
+    for (int l = 0; l < MAXL; ++l)
+        if (cudaEventCreateWithFlags(&E->ev_x[l], cudaEventDisableTiming) != cudaSuccess) return LBMP_ERR_CUDA;
 
     if (cudaMemsetAsync(E->d_done, 0, sizeof(int), h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return regrid_now(h);
@@ -1618,6 +1646,10 @@ void amr_destroy(lbmp_handle* h) {
     if (h->amr->ev_fork) cudaEventDestroy(h->amr->ev_fork);
     if (h->amr->ev_join) cudaEventDestroy(h->amr->ev_join);
     if (h->amr->ev_remap) cudaEventDestroy(h->amr->ev_remap);
+    if (h->amr->aux) cudaStreamDestroy(h->amr->aux);
+    if (h->amr->ev_aux_fork) cudaEventDestroy(h->amr->ev_aux_fork);
+    for (int l = 0; l < MAXL; ++l)
+        if (h->amr->ev_x[l]) cudaEventDestroy(h->amr->ev_x[l]);
 
     for (auto& V : h->amr->lv) free_level(h, V);
     handle_free(h, h->amr->d_sensor);
@@ -1802,6 +1834,11 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
             cudaStreamWaitEvent(h->stream, E->ev_remap, 0);
             E->remap_pending = false;
         }
+        for (int l = 0; l < E->L; ++l)
+            if (E->x_pending[l]) {
+                cudaStreamWaitEvent(h->stream, E->ev_x[l], 0);
+                E->x_pending[l] = false;
+            }
     };
     for (int i = 0; i < n; ++i) {
         if (h->profiling) {   // per-kernel events: plain launches
