@@ -317,6 +317,12 @@ __device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int l
 
 constexpr int BNDW_THREADS = 256;
 constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid)
+// Register cap of the boundary kernel (BNDW_THREADS threads).  It runs beside the finest level's
+// update for most of that update, so every register it holds is taken from the update's CTAs: at
+// 56 in FP32 a boundary CTA (14,336 registers) leaves room for five update CTAs of 40 registers
+// instead of four.
+template <typename S>
+constexpr int BND_MAXREG = sizeof(S) == 8 ? 128 : (sizeof(S) == 4 ? 56 : 64);
 constexpr int LINK_THREADS = 64;   // remap blocks: small, so the box spreads over the SMs; one count per block
 
 // Exclusive prefix of n counts into pre[0..n] (pre[n] = total), computed by
@@ -376,7 +382,7 @@ __device__ __forceinline__ int block_prefix(const int* __restrict__ count, int n
 // last sums the partials and runs the particle update of Algorithm 1.
 // Dynamic shared memory: (runs + 1) ints.
 template <typename S>
-__global__ void __launch_bounds__(BNDW_THREADS)
+__global__ void __maxnreg__(BND_MAXREG<S>)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
                    const uint8_t* __restrict__ mask, const int* __restrict__ run_count, BoxDesc B,
                    CollideParams<typename Store<S>::A> P, ParticleState* ps, int cli, double* partials, int* done,
