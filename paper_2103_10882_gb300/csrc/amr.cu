@@ -42,8 +42,10 @@ namespace {
 constexpr int BS = 16;
 constexpr int B3 = BS * BS * BS;
 constexpr int MAXL = 6;
-constexpr int UPD_THREADS = 256;
-constexpr int UPD_MIN_CTAS = 6;      // resident level-update CTAs per SM asked of the compiler (FP32/FP16 arithmetic): 40 registers
+// Level update CTAs: half a z-slice of a block each (128 cells); at 12 resident CTAs per SM (40
+// registers) the short launches of the finer levels end in smaller waves than with whole slices.
+constexpr int UPD_THREADS = 128;
+constexpr int UPD_MIN_CTAS = 12;     // resident level-update CTAs per SM asked of the compiler (FP32/FP16 arithmetic)
 constexpr int STATUS_AMR_MISSING = 8;    // a pull found no source cell
 // Finest-level cell flags: fluid, solid (centre inside the sphere), and
 // fluid with a solid D3Q19 neighbour (updated by k_amr_boundary).
@@ -234,8 +236,9 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 // stream the active ones and, instead of storing them, sum each host's
 // eight in a fixed shuffle tree; the first lane of each eight writes the
 // mean into the coarser level's coal_in (coalescence).  The other CTAs
-// update the real blocks, one CTA per z-slice of a block (256 cells, full
-// warps).  All read src; the real-block CTAs write dst only.
+// update the real blocks, B3 / UPD_THREADS CTAs per block, each a run of
+// UPD_THREADS cells in block order (full warps).  All read src; the
+// real-block CTAs write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED, bool RESCALE>
 __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS)
     k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks, int coalesce) {
@@ -286,10 +289,11 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         return;
     }
     __shared__ int nb27[27];
-    const int b = (blockIdx.x - gblocks) >> 4;
+    constexpr int SPB = B3 / UPD_THREADS;   // CTAs per block
+    const int b = (blockIdx.x - gblocks) / SPB;
     if (threadIdx.x < 27) nb27[threadIdx.x] = U.D.nbr[b * 27 + threadIdx.x];
     __syncthreads();
-    const int c = (((blockIdx.x - gblocks) & 15) << 8) + threadIdx.x;
+    const int c = ((blockIdx.x - gblocks) % SPB) * UPD_THREADS + threadIdx.x;
     if (COUPLED) {   // finest level flags: 1 solid, 2 fluid next to the sphere (k_amr_boundary's cells)
         const uint8_t f = U.solid[(size_t)b * B3 + c];
         if (f == FLAG_SOLID) {
@@ -319,8 +323,8 @@ constexpr int BNDW_THREADS = 256;
 constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid)
 // Register cap of the boundary kernel (BNDW_THREADS threads).  It runs beside the finest level's
 // update for most of that update, so every register it holds is taken from the update's CTAs: at
-// 56 in FP32 a boundary CTA (14,336 registers) leaves room for five update CTAs of 40 registers
-// instead of four.
+// 56 in FP32 a boundary CTA (14,336 registers) leaves room for 1,280 update threads of 40 registers
+// instead of 1,024.
 template <typename S>
 constexpr int BND_MAXREG = sizeof(S) == 8 ? 128 : (sizeof(S) == 4 ? 56 : 64);
 constexpr int LINK_THREADS = 64;   // remap blocks: small, so the box spreads over the SMs; one count per block
@@ -1560,7 +1564,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     const int ng = has_coarse ? (sub == 0 ? V.nxlist : V.nglist) : 0;
     const int gblocks = (ng + UPD_THREADS - 1) / UPD_THREADS;
     if (V.nreal > 0 || gblocks > 0) {
-        const unsigned grid = (unsigned)(V.nreal * 16 + gblocks);
+        const unsigned grid = (unsigned)(V.nreal * (B3 / UPD_THREADS) + gblocks);
         const int* gl = V.d_xlist;
         cudaStream_t st = h->stream;
         // the rescaling option is a template parameter: without it the kernel carries none of its code
