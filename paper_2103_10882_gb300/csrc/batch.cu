@@ -101,8 +101,13 @@ __global__ void __launch_bounds__(512, sizeof(S) == 8 ? 1 : 3) k_batch_bulk(cons
 // partials; the last of them to finish runs that simulation's particle
 // update (Algorithm 1).  The bulk kernel skips these cells, so this kernel
 // runs beside it.
+// Register cap of the boundary kernel (BW threads): it runs beside the bulk kernel (three CTAs of 512 threads
+// at 40 registers per SM), and at its natural 122 registers a resident boundary CTA left room for one bulk CTA.
 template <typename S>
-__global__ void __launch_bounds__(BW)
+constexpr int BND_MAXREG = sizeof(S) == 8 ? 128 : 64;
+
+template <typename S>
+__global__ void __maxnreg__(BND_MAXREG<S>)
     k_batch_boundary(const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ flags,
                      const uint8_t* __restrict__ mask, const SimDev* __restrict__ sims,
                      const int* __restrict__ bnd_sim, ParticleState* ps, int cli, typename Store<S>::A scale,
@@ -171,12 +176,85 @@ __global__ void __launch_bounds__(BW)
 }
 
 // -------------------------------------------------------------------- remap
+// Refill of the uncovered cell (i, j, k) = flat index c of one simulation by
+// the whole warp (Sec. 2.3): lane q = 1..18 takes the periodic neighbour
+// (i, j, k) + c_q, counted when it is fluid before (fc) and after (the ball
+// predicate) the move, with its density 1 + sum_p g_p and momentum
+// sum_p c_p g_p (for Grad's strain rate from the face neighbours).  The mean
+// density and the rigid-body velocity give the equilibrium, plus Grad's
+// term when grad is set; lane q < 19 writes population q.  Every lane calls
+// it with the same cell.
+template <typename S>
+__device__ __forceinline__ void batch_refill_warp(S* __restrict__ p0, const uint8_t* __restrict__ fc, const GridDesc& G,
+                                                  const int n3[3], const BoxFrame& F, const ParticleState& P, int i,
+                                                  int j, int k, size_t c, typename Store<S>::A scale,
+                                                  typename Store<S>::A inv, int grad, double sp) {
+    using A = typename Store<S>::A;
+    const int lane = threadIdx.x & 31;
+    const size_t n = (size_t)G.n;
+    bool ok = false;
+    A r = A(0), mo[3] = {A(0), A(0), A(0)};
+    if (lane >= 1 && lane < 19) {
+        int v[3] = {i + cx(lane), j + cy(lane), k + cz(lane)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
+        if (!ball_flag(v, n3, G.periodic, F, P)) {
+            const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+            if (fc[y] != FLAG_SOLID) {
+                ok = true;
+                A gp[19];
+#pragma unroll
+                for (int q2 = 0; q2 < 19; ++q2) gp[q2] = Store<S>::load(p0 + (size_t)q2 * n + y, inv);
+                r = A(1);
+#pragma unroll
+                for (int q2 = 0; q2 < 19; ++q2) r += gp[q2];
+#pragma unroll
+                for (int q2 = 1; q2 < 19; ++q2) {
+                    mo[0] += A(cx(q2)) * gp[q2];
+                    mo[1] += A(cy(q2)) * gp[q2];
+                    mo[2] += A(cz(q2)) * gp[q2];
+                }
+            }
+        }
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    A rs = ok ? r : A(0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
+    const int cnt = __popc(okm);
+    const A rho = cnt > 0 ? rs / A(cnt) : A(1);
+    const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, 1), wrap_diff((j + 0.5) - P.x[1], G.ny, 1),
+                         wrap_diff((k + 0.5) - P.x[2], G.nz, 1)};
+    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+    A gcoef = A(0);
+    if (grad) {   // face neighbour q = 1 + 2 a (+1 for -e_a), fluid before and after the move
+        gcoef = A(-3.0 * (1.0 - sp) / sp);
+        auto nb = [&](int a, int sgn, A uo[3]) {
+            const int q = 1 + 2 * a + (sgn > 0 ? 0 : 1);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) uo[m] = __shfl_sync(0xffffffffu, mo[m], q);
+            return ((okm >> q) & 1u) != 0;
+        };
+        refill_strain<A>(nb, u, Sr);
+    }
+    if (lane < 19) {
+        const int q = lane;
+        const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
+        A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+        if (grad) e += grad_term<A>(q, Sr, gcoef);
+        Store<S>::store(p0 + (size_t)q * n + c, e, scale);
+    }
+}
+
 // Remap of Sec. 2.3 in one pass over each simulation's box: the new flag of
 // every cell (the exact ball predicate; 2 for fluid cells with a solid
 // neighbour, evaluated from the same predicate), covered cells zeroed,
-// uncovered cells refilled with the equilibrium at the mean density of the
-// neighbours fluid before and after and the rigid-body velocity, and the
-// mask of boundary cells in box order for the next step's k_batch_boundary.
+// uncovered cells refilled afterwards, one at a time by their whole warp
+// (batch_refill_warp), and the mask of boundary cells in box order for the
+// next step's k_batch_boundary.
 template <typename S>
 __global__ void __launch_bounds__(BW)
     k_batch_remap(S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
@@ -192,76 +270,36 @@ __global__ void __launch_bounds__(BW)
     if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, D.box, ps[sim]);
     __syncthreads();
     const int t = blockIdx.x * BW + threadIdx.x;
-    if (t >= D.box.cells) return;
     const ParticleState& P = ps[sim];
-    int p[3];
-    if (!box_cell(t, n3, G.periodic, D.box, F, p)) return;   // periodic: inside unless the centre is corrupt
-    const int i = p[0], j = p[1], k = p[2];
-    const size_t n = (size_t)G.n;
-    const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
     const uint8_t* fc = fcur + D.flag_off;
     uint8_t* fn = fnext + D.flag_off;
     S* p0 = pops + D.pop_off;
-    int is_b = 0;
-    bool any_nb = false;
-    if (ball_flag_and_neighbours(p, n3, G.periodic, F, P, &any_nb)) {
-        fn[c] = FLAG_SOLID;
-        for (int q = 0; q < 19; ++q) Store<S>::store(p0 + (size_t)q * n + c, A(0), scale);
-    } else {
-        const bool uncovered = fc[c] == FLAG_SOLID;
-        is_b = any_nb ? 1 : 0;
-        A rsum = A(0);
-        int cnt = 0;
-        for (int q = 1; uncovered && q < 19; ++q) {
-            int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
-            for (int a = 0; a < 3; ++a) v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
-            if (ball_flag(v, n3, G.periodic, F, P)) continue;
-            const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
-            if (fc[y] == FLAG_SOLID) continue;
-            A r = A(1);
-            for (int q2 = 0; q2 < 19; ++q2) r += Store<S>::load(p0 + (size_t)q2 * n + y, inv);
-            rsum += r;
-            cnt += 1;
+    const size_t n = (size_t)G.n;
+    bool uncovered = false;   // fluid after the move, solid before: refilled below by the warp
+    int p[3] = {0, 0, 0};
+    size_t c = 0;
+    // periodic: box_cell fails only for a corrupt centre
+    if (t < D.box.cells && box_cell(t, n3, G.periodic, D.box, F, p)) {
+        c = (size_t)p[0] + (size_t)G.nx * ((size_t)p[1] + (size_t)G.ny * (size_t)p[2]);
+        int is_b = 0;
+        bool any_nb = false;
+        if (ball_flag_and_neighbours(p, n3, G.periodic, F, P, &any_nb)) {
+            fn[c] = FLAG_SOLID;
+            for (int q = 0; q < 19; ++q) Store<S>::store(p0 + (size_t)q * n + c, A(0), scale);
+        } else {
+            uncovered = fc[c] == FLAG_SOLID;
+            is_b = any_nb ? 1 : 0;
+            fn[c] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
         }
-        fn[c] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
-        if (uncovered) {   // equilibrium refill, plus Grad's term when asked for
-            const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
-            const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, 1), wrap_diff((j + 0.5) - P.x[1], G.ny, 1),
-                                 wrap_diff((k + 0.5) - P.x[2], G.nz, 1)};
-            const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])),
-                            A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
-                            A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
-            const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-            const A gcoef = grad ? A(-3.0 * (1.0 - D.sp) / D.sp) : A(0);
-            A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
-            if (grad) {   // face neighbours fluid before and after the move
-                auto nb = [&](int a, int sgn, A uo[3]) {
-                    int v[3] = {i, j, k};
-                    v[a] += sgn;
-                    v[a] = v[a] < 0 ? v[a] + n3[a] : (v[a] >= n3[a] ? v[a] - n3[a] : v[a]);
-                    if (ball_flag(v, n3, G.periodic, F, P)) return false;
-                    const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
-                    if (fc[y] == FLAG_SOLID) return false;
-                    uo[0] = uo[1] = uo[2] = A(0);
-                    for (int q2 = 1; q2 < 19; ++q2) {
-                        const A gq = Store<S>::load(p0 + (size_t)q2 * n + y, inv);
-                        uo[0] += A(cx(q2)) * gq;
-                        uo[1] += A(cy(q2)) * gq;
-                        uo[2] += A(cz(q2)) * gq;
-                    }
-                    return true;
-                };
-                refill_strain<A>(nb, u, Sr);
-            }
-            for (int q = 0; q < 19; ++q) {
-                const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
-                A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
-                if (grad) e += grad_term<A>(q, Sr, gcoef);
-                Store<S>::store(p0 + (size_t)q * n + c, e, scale);
-            }
-        }
+        mask[D.mask_off + t] = (uint8_t)is_b;
     }
-    mask[D.mask_off + t] = (uint8_t)is_b;
+    for (unsigned todo = __ballot_sync(0xffffffffu, uncovered); todo != 0u; todo &= todo - 1u) {
+        const int src = __ffs((int)todo) - 1;
+        const int i = __shfl_sync(0xffffffffu, p[0], src), j = __shfl_sync(0xffffffffu, p[1], src),
+                  k = __shfl_sync(0xffffffffu, p[2], src);
+        const size_t cc = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+        batch_refill_warp<S>(p0, fc, G, n3, F, P, i, j, k, cc, scale, inv, grad, D.sp);
+    }
 }
 
 template <typename S>
