@@ -109,3 +109,47 @@ def test_mrt_conserves_mass_and_momentum(orc):
     g1 = s.populations()
     assert abs(g1.sum() - m0) < 1e-12
     assert np.abs(g1.sum(axis=1) @ C.astype(float) - p0).max() < 1e-12
+
+
+def _mode(name):
+    """Per-direction values of one D3Q19 moment (Duenweg's orthogonal basis,
+    built here from the lattice velocities)."""
+    cx, cy, cz = (C[:, a].astype(float) for a in range(3))
+    c2 = cx * cx + cy * cy + cz * cz
+    return {
+        "bulk": c2 - 1.0,                                        # |c|^2 - 1
+        "quartic": 3.0 * c2 * c2 - 6.0 * c2 + 1.0,               # isotropic fourth order
+        "shear": cx * cy,                                        # a shear mode
+        "normal_stress": cy * cy - cz * cz,                      # a shear mode
+        "third_order": (cy * cy - cz * cz) * cx,                 # an odd third-order mode
+        "third_order_iso": (3.0 * c2 - 5.0) * cx,                # the other kind of odd third-order mode
+        "aniso_quartic": (2.0 * c2 - 3.0) * (cy * cy - cz * cz),  # an anisotropic fourth-order mode
+    }[name]
+
+
+@pytest.mark.parametrize("bulk", [10.0, 100.0])
+def test_each_moment_relaxes_at_its_class_rate(orc, bulk):
+    """A spatially uniform state does not change under streaming, so only the
+    collision acts.  A deviation along one non-conserved moment, with weights
+    (g_q = a w_q e_q: orthogonal to density and momentum, zero equilibrium at
+    rest), stays along it and shrinks by (1 - s) per step.  The reading of
+    Sec. 2.1's relaxation counts: s_b for the bulk and the isotropic
+    fourth-order moments, s_nu for the shear and the anisotropic fourth-order
+    ones, s_minus (TRT's odd rate) for the third-order ones; this pins the
+    isotropic fourth-order rate, which the hydrodynamic tests cannot see."""
+    s_nu = 1.0 / TAU
+    s_minus = 1.0 / (0.5 + (3.0 / 16.0) / (1.0 / s_nu - 0.5))
+    s_b = 1.0 / (0.5 + bulk * (1.0 / s_nu - 0.5))
+    rates = {"bulk": s_b, "quartic": s_b, "shear": s_nu, "normal_stress": s_nu, "aniso_quartic": s_nu,
+             "third_order": s_minus, "third_order_iso": s_minus}
+    for name, s in rates.items():
+        e = _mode(name)
+        assert abs(W @ e) < 1e-15 and np.abs(W @ (e[:, None] * C)).max() < 1e-15   # not density, not momentum
+        sim = orc.UniformSim((4, 4, 4), tau=TAU, bulk=bulk)
+        g0 = 1e-4 * np.tile((W * e)[:, None], (1, 64))
+        sim.set_populations(g0)
+        for n in (1, 2, 5):
+            sim.step(1 if n != 5 else 3)
+            g = sim.populations()
+            want = (1.0 - s) ** n * g0
+            assert np.abs(g - want).max() <= 1e-13 * np.abs(g0).max(), (name, n)
