@@ -172,9 +172,88 @@ __global__ void k_flags_box(uint8_t* __restrict__ flags_next, GridDesc G, BoxDes
     flags_next[c] = ball_flag(p, n3, G.periodic, F, *ps) ? 1 : 0;
 }
 
-// Cells now solid are zeroed; cells the sphere uncovered are refilled with
-// the equilibrium at the mean density of neighbours fluid before and after,
-// and the rigid-body velocity u_p + omega_p x (x - x_p).
+// Refill of the uncovered cell (i, j, k) = index c by the whole warp
+// (Sec. 2.3): lane q = 1..18 takes the neighbour (i, j, k) + c_q (wrapped on
+// periodic axes; none beyond a wall), counted when it is fluid before (fcur)
+// and after (fnext) the move, with its density 1 + sum_p g_p and momentum
+// sum_p c_p g_p (for Grad's strain rate from the face neighbours).  The mean
+// density and the rigid-body velocity u_p + omega_p x (x - x_p) give the
+// equilibrium, plus Grad's term when gcoef != 0; lane q < 19 writes
+// population q.  Every lane calls it with the same cell.
+template <typename S>
+__device__ __forceinline__ void refill_warp(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
+                                            const uint8_t* __restrict__ fnext, const GridDesc& G, const int n3[3],
+                                            const ParticleState& P, int i, int j, int k, size_t c,
+                                            typename Store<S>::A scale, typename Store<S>::A inv_scale,
+                                            typename Store<S>::A gcoef) {
+    using A = typename Store<S>::A;
+    const int lane = threadIdx.x & 31;
+    const size_t n = (size_t)G.n;
+    bool ok = false;
+    A r = A(0), mo[3] = {A(0), A(0), A(0)};
+    if (lane >= 1 && lane < 19) {
+        int v[3] = {i + cx(lane), j + cy(lane), k + cz(lane)};
+        bool in = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (v[a] < 0 || v[a] >= n3[a]) {
+                if (!G.periodic[a]) in = false;
+                v[a] = (v[a] + n3[a]) % n3[a];
+            }
+        }
+        if (in) {
+            const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
+            if (fcur[y] == 0 && fnext[y] == 0) {
+                ok = true;
+                A gp[19];
+#pragma unroll
+                for (int q = 0; q < 19; ++q) gp[q] = Store<S>::load(pops + (size_t)q * n + y, inv_scale);
+                r = A(1);
+#pragma unroll
+                for (int q = 0; q < 19; ++q) r += gp[q];
+#pragma unroll
+                for (int q = 1; q < 19; ++q) {
+                    mo[0] += A(cx(q)) * gp[q];
+                    mo[1] += A(cy(q)) * gp[q];
+                    mo[2] += A(cz(q)) * gp[q];
+                }
+            }
+        }
+    }
+    const unsigned okm = __ballot_sync(0xffffffffu, ok);
+    A rs = ok ? r : A(0);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
+    const int cnt = __popc(okm);
+    const A rho = cnt > 0 ? rs / A(cnt) : A(1);
+    const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, G.periodic[0]),
+                         wrap_diff((j + 0.5) - P.x[1], G.ny, G.periodic[1]),
+                         wrap_diff((k + 0.5) - P.x[2], G.nz, G.periodic[2])};
+    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
+                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
+    if (gcoef != A(0)) {   // Grad refill: face neighbour q = 1 + 2 a (+1 for -e_a), fluid before and after the move
+        auto nb = [&](int a, int sgn, A uo[3]) {
+            const int q = 1 + 2 * a + (sgn > 0 ? 0 : 1);
+#pragma unroll
+            for (int m = 0; m < 3; ++m) uo[m] = __shfl_sync(0xffffffffu, mo[m], q);
+            return ((okm >> q) & 1u) != 0;
+        };
+        refill_strain<A>(nb, u, Sr);
+    }
+    if (lane < 19) {
+        const int q = lane;
+        const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
+        A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
+        if (gcoef != A(0)) e += grad_term<A>(q, Sr, gcoef);
+        Store<S>::store(pops + (size_t)q * n + c, e, scale);
+    }
+}
+
+// Cells now solid are zeroed; cells the sphere uncovered are refilled
+// afterwards, one at a time by their whole warp (refill_warp).  blockDim.x
+// is a multiple of 32.
 template <typename S>
 __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur, const uint8_t* __restrict__ fnext,
                          GridDesc G, BoxDesc B, const ParticleState* __restrict__ ps,
@@ -185,74 +264,24 @@ __global__ void k_refill(S* __restrict__ pops, const uint8_t* __restrict__ fcur,
     if (threadIdx.x == 0) box_frame_init(F, n3, G.periodic, B, *ps);
     __syncthreads();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= B.cells) return;
-    int p[3];
-    if (!box_cell(t, n3, G.periodic, B, F, p)) return;
-    const int i = p[0], j = p[1], k = p[2];
     const size_t n = (size_t)G.n;
-    const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
-    if (fnext[c] != 0) {
+    bool uncovered = false;
+    int p[3] = {0, 0, 0};
+    if (t < B.cells && box_cell(t, n3, G.periodic, B, F, p)) {
+        const size_t c = (size_t)p[0] + (size_t)G.nx * ((size_t)p[1] + (size_t)G.ny * (size_t)p[2]);
+        if (fnext[c] != 0) {
 #pragma unroll
-        for (int q = 0; q < 19; ++q) Store<S>::store(pops + (size_t)q * n + c, A(0), scale);
-        return;
-    }
-    if (fcur[c] == 0) return;
-    // uncovered cell
-    const ParticleState& P = *ps;
-    A rsum = A(0);
-    int cnt = 0;
-    for (int q = 1; q < 19; ++q) {
-        int v[3] = {i + cx(q), j + cy(q), k + cz(q)};
-        bool ok = true;
-        for (int a = 0; a < 3; ++a) {
-            if (v[a] < 0 || v[a] >= n3[a]) {
-                if (!G.periodic[a]) ok = false;
-                v[a] = (v[a] + n3[a]) % n3[a];
-            }
+            for (int q = 0; q < 19; ++q) Store<S>::store(pops + (size_t)q * n + c, A(0), scale);
+        } else {
+            uncovered = fcur[c] != 0;
         }
-        if (!ok) continue;
-        const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
-        if (fcur[y] != 0 || fnext[y] != 0) continue;
-        A r = A(1);
-        for (int p = 0; p < 19; ++p) r += Store<S>::load(pops + (size_t)p * n + y, inv_scale);
-        rsum += r;
-        cnt += 1;
     }
-    const A rho = cnt > 0 ? rsum / A(cnt) : A(1);
-    const double d[3] = {wrap_diff((i + 0.5) - P.x[0], G.nx, G.periodic[0]),
-                         wrap_diff((j + 0.5) - P.x[1], G.ny, G.periodic[1]),
-                         wrap_diff((k + 0.5) - P.x[2], G.nz, G.periodic[2])};
-    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
-                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
-    const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
-    if (gcoef != A(0)) {   // Grad refill: face neighbours fluid before and after the move
-        auto nb = [&](int a, int sgn, A uo[3]) {
-            int v[3] = {i, j, k};
-            v[a] += sgn;
-            if (v[a] < 0 || v[a] >= n3[a]) {
-                if (!G.periodic[a]) return false;
-                v[a] = (v[a] + n3[a]) % n3[a];
-            }
-            const size_t y = (size_t)v[0] + (size_t)G.nx * ((size_t)v[1] + (size_t)G.ny * (size_t)v[2]);
-            if (fcur[y] != 0 || fnext[y] != 0) return false;
-            uo[0] = uo[1] = uo[2] = A(0);
-            for (int q = 1; q < 19; ++q) {
-                const A gq = Store<S>::load(pops + (size_t)q * n + y, inv_scale);
-                uo[0] += A(cx(q)) * gq;
-                uo[1] += A(cy(q)) * gq;
-                uo[2] += A(cz(q)) * gq;
-            }
-            return true;
-        };
-        refill_strain<A>(nb, u, Sr);
-    }
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        const A cu = A(cx(q)) * u[0] + A(cy(q)) * u[1] + A(cz(q)) * u[2];
-        A e = wgt<A>(q) * ((rho - A(1)) + A(3) * cu + A(4.5) * cu * cu - A(1.5) * uu);
-        if (gcoef != A(0)) e += grad_term<A>(q, Sr, gcoef);
-        Store<S>::store(pops + (size_t)q * n + c, e, scale);
+    for (unsigned todo = __ballot_sync(0xffffffffu, uncovered); todo != 0u; todo &= todo - 1u) {
+        const int src = __ffs((int)todo) - 1;
+        const int i = __shfl_sync(0xffffffffu, p[0], src), j = __shfl_sync(0xffffffffu, p[1], src),
+                  k = __shfl_sync(0xffffffffu, p[2], src);
+        const size_t c = (size_t)i + (size_t)G.nx * ((size_t)j + (size_t)G.ny * (size_t)k);
+        refill_warp<S>(pops, fcur, fnext, G, n3, *ps, i, j, k, c, scale, inv_scale, gcoef);
     }
 }
 
