@@ -115,7 +115,7 @@ typedef struct {
     int boundary;
     int force_average;
     int plain_mem;
-    int rescale;          /* 1: rescale non-equilibrium parts at level interfaces */
+    int rescale;          /* 1: rescale non-equilibrium parts of cells that change level in a regrid */
     double bulk;          /* MRT bulk factor Lambda_b (Sec. 2.1); 0 or 1 = TRT */
     int refill;           /* uncovered cells: 0 = equilibrium, 1 = Grad's approximation (Sec. 2.3) */
 } orc_amr_params;

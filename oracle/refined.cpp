@@ -10,14 +10,31 @@
  * Time stepping (Rohde's non-uniform scheme named in Sec. 4.1), read as:
  *   advance(l):
  *     explosion: every ghost cell of level l+1 takes the post-collision
- *       populations of the level-l cell containing it (optionally with the
- *       non-equilibrium part rescaled);
+ *       populations of the level-l cell containing it;
  *     advance(l+1) twice (finer levels take two steps per coarser step);
  *     update(l): each real level-l cell either pulls its populations from
  *       its neighbours (real or ghost cells of level l) or, if it is a host
  *       (a neighbour of the finer region), takes the average of its eight
- *       ghost sub-cells (coalescence, optionally rescaled); then collides.
+ *       ghost sub-cells (coalescence); then collides.
  *       Active ghost cells of level l stream but do not collide.
+ *
+ * Non-equilibrium rescaling.  To first order in Chapman-Enskog a level-l
+ * post-collision population carries f_neq = -(tau_l - 1) 3 w Q:grad u dx_l,
+ * and one step of streaming over a distance d (in cells of that level)
+ * adds -d 3 w Q:grad u dx.  In fine units a coarse post-collision value is
+ * -(2 tau_c - 2) = -(tau_f - 3/2) (acoustic scaling: 2 tau_c = tau_f + 1/2).
+ * The interface transfers above move populations between cell centres
+ * that are 1.5 fine cells apart along the interface normal, so an exploded
+ * value reaching the first fine cell arrives with -(tau_f - 3/2) - 3/2 =
+ * -tau_f, the fine pre-collision value, and the coalesced mean of the
+ * values streamed out of the fine region arrives at the host with
+ * -(tau_f - 1) - 3/2 = -2 tau_c, the coarse pre-collision value.  The
+ * transfers are therefore consistent without rescaling; rescaling them as
+ * well would count the level change twice.  Populations that change level
+ * in place, without streaming, are those of a regrid: a refined block's
+ * cells take their parent's post-collision state and a coarsened cell the
+ * mean of its eight children's.  Those are rescaled (rescale option) by
+ * kappa = (tau_f - 1) / (2 (tau_c - 1)) per TRT part, or 1/kappa.
  *   On the finest level every step also runs the coupling of Algorithm 1.
  * Hosts are real level-l cells with a level-(l+1)-covered cell among their 26
  * neighbours; their sub-cells are the active ghost cells of level l+1.  Cells
@@ -153,20 +170,8 @@ void rescale(double f[19], double kp, double km) {
     std::memcpy(f, out, sizeof(out));
 }
 
-// Coalescence rescaling: the averaged ghost values have streamed after the
-// finer collision, so they are pre-collision values of the finer level and
-// become pre-collision values of the coarser cell (which collides next):
-// f_neq,c = (2 tau_c / tau_f) f_neq,f for each TRT part (first-order
-// Chapman-Enskog, f_neq ~ -tau dx grad f_eq, dx_c = 2 dx_f).
-void rescale_coalesce(const orc_amr* a, double f[19], int coarse) {
-    if (!a->p.rescale) return;
-    const LevelData& Cc = a->lv[coarse];
-    const LevelData& Ff = a->lv[coarse + 1];
-    rescale(f, 2.0 * Cc.taup / Ff.taup, 2.0 * Cc.taum / Ff.taum);
-}
-
 // Rescaling of post-collision states from level `from` to level `to` (one
-// level at a time): explosion, and refinement or coarsening in a regrid.
+// level at a time): refinement or coarsening of cells in a regrid.
 void rescale_levels(const orc_amr* a, double f[19], int from, int to) {
     if (!a->p.rescale) return;
     while (from < to) {
@@ -633,17 +638,14 @@ void explode(orc_amr* a, int l) {
                 a->error = 1;
                 continue;
             }
-            double f[19];
-            for (int q = 0; q < 19; ++q) f[q] = D.rg[pidx(pb, q, pc)];
-            rescale_levels(a, f, l, l + 1);
             for (int q = 0; q < 19; ++q) {
-                F.gg[pidx((int)gb, q, c)] = f[q];
-                F.gg_new[pidx((int)gb, q, c)] = f[q];
+                F.gg[pidx((int)gb, q, c)] = D.rg[pidx(pb, q, pc)];
+                F.gg_new[pidx((int)gb, q, c)] = D.rg[pidx(pb, q, pc)];
             }
         }
 }
 
-// Exploded value of population q at level-l+1 position p: the rescaled
+// Exploded value of population q at level-l+1 position p: the
 // post-collision population of the level-l cell containing p.
 double exploded(orc_amr* a, int l, const int p[3], int q) {
     const LevelData& D = a->lv[l];
@@ -653,10 +655,7 @@ double exploded(orc_amr* a, int l, const int p[3], int q) {
         a->error = 1;
         return 0.0;
     }
-    double f[19];
-    for (int k = 0; k < 19; ++k) f[k] = D.rg[pidx(b, k, c)];
-    rescale_levels(a, f, l, l + 1);
-    return f[q];
+    return D.rg[pidx(b, q, c)];
 }
 
 // Value of population q pulled into cell g (level l) from g - c_q: the
@@ -757,7 +756,6 @@ void update(orc_amr* a, int l, double F[3], double T[3]) {
                     for (int q = 0; q < 19; ++q) f[q] += Fl.gg[pidx(gb, q, gc)];
                 }
                 for (int q = 0; q < 19; ++q) f[q] /= 8.0;
-                rescale_coalesce(a, f, l);
             } else {
                 for (int q = 0; q < 19; ++q) {
                     if (coupled && q > 0) {

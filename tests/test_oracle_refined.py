@@ -8,7 +8,14 @@
   are conserved to rounding, also at edges and corners of the refined
   region and across a regrid;
 - the viscosity per level follows acoustic scaling: a shear wave crossing a
-  refined slab decays at the rate of the finest-level viscosity;
+  refined slab decays at the rate of the finest-level viscosity, with the
+  rescaling option on or off;
+- the non-equilibrium parts carried across the level interfaces are the
+  ones Chapman-Enskog fixes at each level: in a developed shear wave every
+  real cell's stored stress (and, away from the interfaces, its odd third
+  moment) is the first-order value of its own level; right after a regrid
+  that refines one slab and coarsens another, the cells that changed level
+  in place hold their new level's values only with the rescaling on;
 - the block forest is 2:1 balanced, complete (all eight children) and keeps
   the sphere's block and its neighbours on the finest level;
 - before the disturbance of a sphere reaches the interface, the refined run
@@ -98,15 +105,19 @@ def test_mass_momentum_conserved_rescale_off(orc, levels):
     assert np.abs(p1 - p0).max() < 1e-14 * scale
 
 
-def test_shear_wave_decay_across_refined_slab(orc):
+@pytest.mark.parametrize("rescale", [False, True])
+def test_shear_wave_decay_across_refined_slab(orc, rescale):
     """u_x = A sin(2 pi z / L) with the middle third of z refined (planar
     interfaces): the mode decays with the finest-level viscosity
     nu = (tau_f - 1/2)/3 (finest units), since each level's tau follows
     acoustic scaling.  A wrong per-level tau makes the coarse region decay at
-    a different rate and the mode amplitude is off by far more than 1%."""
+    a different rate and the mode amplitude is off by far more than 1%.  The
+    rescaling option changes only regrids, so it leaves this unchanged; the
+    earlier reading that rescaled the interface transfers too was off by
+    1.5e-2 here."""
     shape = (16, 16, 96)
     tau_f = 0.8
-    s = orc.RefinedSim(shape, 2, tau=tau_f, rescale=False)
+    s = orc.RefinedSim(shape, 2, tau=tau_f, rescale=rescale)
     s.refine_box((0, 0, 64), (32, 32, 128))
     A = 1e-3
     s.init_equilibrium(shear=A, shear_dir=0, shear_axis=2)
@@ -237,3 +248,101 @@ def test_regrid_keeps_uniform_flow_and_mass(orc):
         else:
             assert abs(m1 - m0) < 1e-14 * scale
             assert np.abs(p1 - p0).max() < 1e-14 * scale
+
+
+CXZ = (C[:, 0] * C[:, 2]).astype(float)
+CXXZ = (C[:, 0] ** 2 * C[:, 2]).astype(float)
+
+
+def _ce_deviation(s, levels, tau_f, U, A, k, t, planes, magic=3.0 / 16.0):
+    """Largest deviation, per level, of the stored post-collision moments
+    Pi_xz = sum_q c_x c_z g_q and Pi_xxz = sum_q c_x^2 c_z g_q from their
+    first-order Chapman-Enskog values for u_x = U + a sin(k z), a = A
+    exp(-nu k^2 t) (finest units), each relative to the largest value of its
+    closed form on that level.  On a level of cell size h (finest cells) the
+    velocity gradient in that level's lattice units is h du_x/dz, and with
+    tau+ and tau- of that level:
+      Pi_xz  = -(tau+ - 1)/3 h du_x/dz          (pre-collision: -tau+ c_s^2 (grad u + grad u^T)),
+      Pi_xxz = -(tau- - 1) 2/3 u_x h du_x/dz    (pre-collision: -tau- d/dz sum c_x^2 c_z^2 f_eq);
+    the equilibrium parts of both vanish (u_z = 0).  Pi_xxz is compared only
+    on cells at least two cells of their level from an interface plane
+    (`planes`, finest units): next to an interface the odd moments carry
+    the scheme's own first-order interface error."""
+    nu = (tau_f - 0.5) / 3
+    out = []
+    for l in range(levels):
+        xyz, g = s.real_cells(l)
+        h = 2 ** (levels - 1 - l)
+        tp = 0.5 + (tau_f - 0.5) / h
+        tm = 0.5 + magic / (tp - 0.5)
+        z = (xyz[:, 2] + 0.5) * h
+        a = A * np.exp(-nu * k * k * t)
+        ux = U + a * np.sin(k * z)
+        dudz = h * a * k * np.cos(k * z)
+        e_s = -(tp - 1) / 3 * dudz
+        e_a = -(tm - 1) * (2.0 / 3.0) * ux * dudz
+        away = np.ones(len(z), dtype=bool)
+        for zp in planes:
+            away &= np.abs(z - zp) > 2 * h
+        ds = np.abs(g @ CXZ - e_s).max() / (abs(tp - 1) / 3 * h * a * k)
+        da = np.abs((g @ CXXZ - e_a)[away]).max() / (abs(tm - 1) * (2.0 / 3.0) * U * h * a * k)
+        out.append((ds, da))
+    return out
+
+
+@pytest.mark.parametrize("tau_f", [0.56, 0.8])
+@pytest.mark.parametrize("rescale", [False, True])
+def test_interface_transfers_carry_each_levels_stress(orc, tau_f, rescale):
+    """A shear wave u_x = U + A sin(k z) on a grid whose slab z in [96, 160)
+    (finest units) is refined, after 40 level-0 steps: every real cell of
+    both levels, including the hosts and the fine cells next to the
+    interfaces, holds the Chapman-Enskog stress of its own level to within
+    4% of its amplitude (the odd moment to within 5% away from the planes).
+    This holds because the interface transfers move populations 1.5 fine
+    cells between cell centres, which supplies the level change of the
+    non-equilibrium part (oracle header).  Catches any rescaling of the
+    interface transfers: the reading that scaled the explosion by
+    (tau_f - 1)/(2 (tau_c - 1)) and the coalescence by 2 tau_c/tau_f was
+    off by 0.68-7.2 here."""
+    U, A = 0.05, 1e-3
+    s = orc.RefinedSim((16, 16, 96), 2, tau=tau_f, rescale=rescale)
+    s.refine_box((0, 0, 96), (32, 32, 160))
+    s.init_equilibrium(u=(U, 0.0, 0.0), shear=A, shear_dir=0, shear_axis=2)
+    s.step(40)
+    k = 2 * np.pi / 192
+    for ds, da in _ce_deviation(s, 2, tau_f, U, A, k, 80, planes=(96, 160)):
+        assert ds < 0.04
+        assert da < 0.05
+
+
+@pytest.mark.parametrize("tau_f", [0.56, 0.8])
+def test_regrid_rescaling_gives_new_levels_stress(orc, tau_f):
+    """The same developed shear wave, then a regrid that refines z in
+    [32, 96) and coarsens [96, 160): the cells that changed level hold
+    their parent's state (refined) or their children's mean (coarsened)
+    without streaming, so only the rescaling by kappa = (tau_f - 1) /
+    (2 (tau_c - 1)) per TRT part (1/kappa when coarsening) turns them into
+    the new level's Chapman-Enskog state: within 4% (stress) and 5% (odd
+    moment, away from the new planes and from the old one at z = 160, whose
+    interface error the coarsened cells inherit).  Without the rescaling the stress is
+    off by more than 40% on one of the levels (70-250% at these tau), and a
+    kappa twice too large gave 50-100%; a kappa- of 1 gave 0.9-11 on the
+    odd moment."""
+    U, A = 0.05, 1e-3
+    k = 2 * np.pi / 192
+    dev = {}
+    for rescale in (True, False):
+        s = orc.RefinedSim((16, 16, 96), 2, tau=tau_f, rescale=rescale)
+        s.refine_box((0, 0, 96), (32, 32, 160))
+        s.init_equilibrium(u=(U, 0.0, 0.0), shear=A, shear_dir=0, shear_axis=2)
+        s.step(40)
+        before = [s.block_map(l).copy() for l in range(2)]
+        s.refine_box((0, 0, 32), (32, 32, 96))
+        after = [s.block_map(l) for l in range(2)]
+        assert np.any((before[1] >= 0) & (after[1] < 0)) and np.any((before[1] < 0) & (after[1] >= 0))
+        dev[rescale] = _ce_deviation(s, 2, tau_f, U, A, k, 80, planes=(32, 96, 160))
+    for ds, da in dev[True]:
+        assert ds < 0.04
+        assert da < 0.05
+    assert max(ds for ds, _ in dev[False]) > 0.4
+    assert max(da for _, da in dev[False]) > 0.4
