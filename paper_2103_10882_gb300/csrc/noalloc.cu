@@ -1,19 +1,30 @@
 // Boundary-cell list of one sphere computed without allocating anything.
 //
-// Some callers cannot call cudaMalloc: a host function enqueued on a stream
-// (which must not call CUDA runtime routines), a time-critical loop in which
+// Some callers cannot call cudaMalloc: a time-critical loop in which
 // cudaMalloc's possible device-wide synchronisation is not acceptable, or a
 // process whose device memory is entirely handed out by another allocator.
 // lbmp_boundary_cells_noalloc serves them: the caller passes the flags and
 // the output buffers, and the two kernels below keep their scratch (a mask
 // byte per box cell and a count per thread block) in one file-scope device
-// array of fixed size instead of memory from an allocator.
+// array of fixed size instead of memory from an allocator.  The call itself
+// uses the CUDA runtime (it launches kernels), so it must not be made from a
+// host function enqueued on a stream (cudaLaunchHostFunc), where CUDA
+// forbids runtime calls.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents; every entry a call reads has been written earlier in the same
 // call, so nothing needs clearing.  Calls that overlap on the GPU (two
 // streams, or two host threads) race on it and must be serialised by the
 // caller.
+//
+// The first call on a device looks up the array's device address and
+// launches the two kernels for the first time; with lazy module loading
+// that loads this file's module, which backs the array and may synchronise
+// the device.  A caller that needs every call free of such work makes one
+// warm-up call outside its critical loop (and before any stream capture).
+// The address is kept for the life of the process: after cudaDeviceReset
+// (or any other teardown of the device's primary context) the call must not
+// be used again in that process.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -204,7 +215,7 @@ extern "C" lbmp_status lbmp_boundary_cells_noalloc(const uint8_t* flags, int nx,
         B.periodic[a] = periodic[a] ? 1 : 0;
         B.E[a] = 2 * R + 2;
         B.o[a] = (int)std::floor(center[a] - 0.5) - R;
-        if (B.periodic[a] && B.E[a] >= n3[a]) {
+        if (B.E[a] >= n3[a]) {   // the box spans the axis, periodic or not: the coupled step starts it at 0
             B.E[a] = n3[a];
             B.o[a] = 0;
         }
