@@ -68,7 +68,7 @@ typedef struct {
     double magic;            /* TRT magic parameter Lambda (Sec. 2.1); 3/16 by default */
     int boundary;            /* LBMP_CLI (Sec. 2.3) or LBMP_SBB (delta = 1/2 on every link) */
     int force_average;       /* 1: average F/T over two steps (Algorithm 1) */
-    int rescale_noneq;       /* refined grids: rescale non-equilibrium parts at level interfaces (default 0) */
+    int rescale_noneq;       /* refined grids: rescale the non-equilibrium parts of cells that change level in a regrid (default 0) */
     int regrid_interval;     /* refined grids: coarse steps between regrids, 0 = manual */
     int history_capacity;    /* particle history records kept on the device (ring) */
     int fp16_scale_log2;     /* LBMP_FP16: deviations are stored times 2^fp16_scale_log2 */
@@ -168,8 +168,14 @@ lbmp_status lbmp_get_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* de
  * tau are those of the finest level; lbmp_step advances level-0 steps, each
  * made of 2^l steps of level l.  Interface transfer: explosion into ghost
  * cells and coalescence of ghost cells into the coarser cells next to the
- * finer region (Rohde's scheme named in Sec. 4.1), optionally with the
- * non-equilibrium part rescaled (config.rescale_noneq).  The sphere and the
+ * finer region (Rohde's scheme named in Sec. 4.1).  These transfers move
+ * populations between cell centres 1.5 fine cells apart, which to first
+ * order in Chapman-Enskog carries the non-equilibrium part from one
+ * level's form to the other's, so they are not rescaled.  Cells that change
+ * level in place in a regrid are: with config.rescale_noneq, each TRT part
+ * of a refined cell's non-equilibrium part is scaled by
+ * (tau_f - 1) / (2 (tau_c - 1)) and a coarsened cell's by the inverse
+ * (otherwise they are copied, which conserves mass exactly).  The sphere and the
  * blocks around it stay on the finest level: its blocks and their 26
  * neighbours are finest, every coarser level adds the 26 neighbours of the
  * next finer level's parents (2:1 balance), and the hierarchy is rebuilt
@@ -216,6 +222,14 @@ lbmp_status lbmp_get_block_map(lbmp_handle* h, int level, int32_t* out, size_t c
  * level coordinates xyz[n][3] and FP64 deviations g[n][19].  *n = cells;
  * pass cap = 0 to query. */
 lbmp_status lbmp_get_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n);
+/* Cell flags of a level's real cells, in lbmp_get_level_cells order (the
+ * remap of Sec. 2.3 on the finest level): 1 centre inside the sphere, 2
+ * fluid with a D3Q19 neighbour inside it (the cells whose links take the
+ * boundary rule), 0 other fluid; every cell of the coarser levels, and of
+ * a grid without a sphere, is 0.  out: host array of cap bytes (caller
+ * owned); *n receives the number of cells (nothing is written when cap is
+ * smaller).  Refined grids only (uniform grids: lbmp_get_flags). */
+lbmp_status lbmp_get_level_flags(lbmp_handle* h, int level, uint8_t* out, size_t cap, size_t* n);
 /* Cell updates and kernel launches of one (level-0) step. */
 lbmp_status lbmp_updates_per_step(lbmp_handle* h, int64_t* updates, int32_t* launches);
 
@@ -267,9 +281,11 @@ lbmp_status lbmp_profile(lbmp_handle* h, int enable);
 lbmp_status lbmp_get_profile(lbmp_handle* h, double out[6]);
 /* Boundary cells of one sphere, computed without allocating any memory.
  * (No counterpart in the paper: this is a service for callers that cannot
- * call cudaMalloc, such as a host function enqueued on a stream, a loop
- * that must not risk the device synchronisation an allocation may cause,
- * or a process whose device memory belongs to another allocator.)
+ * call cudaMalloc, such as a loop that must not risk the device
+ * synchronisation an allocation may cause, or a process whose device
+ * memory belongs to another allocator.  The call launches kernels through
+ * the CUDA runtime, so it must not be made from a host function enqueued
+ * on a stream, where CUDA forbids runtime calls.)
  *   flags       device array of nx*ny*nz bytes, 0 = fluid, nonzero = solid
  *   periodic    per axis, nonzero for a periodic axis
  *   center      sphere centre (host), diameter in cells
@@ -284,9 +300,13 @@ lbmp_status lbmp_get_profile(lbmp_handle* h, double out[6]);
  * Scratch lives in one fixed device array of 266240 bytes per device, held
  * until the process exits: boxes larger than 64^3 cells (diameters above 56
  * cells) are rejected with LBMP_ERR_INVALID_ARG.  The first call on a
- * device looks up that array's address; make it before any stream capture.
- * All calls share the array, so calls that overlap on the GPU race: the
- * caller serialises them.  Errors are reported by lbmp_last_error(NULL). */
+ * device looks up that array's address and launches the kernels for the
+ * first time, which may load the library's module and synchronise the
+ * device: make one warm-up call before any stream capture and outside any
+ * loop that must not synchronise.  The address is kept for the life of the
+ * process, so the call must not be used after cudaDeviceReset.  All calls
+ * share the array, so calls that overlap on the GPU race: the caller
+ * serialises them.  Errors are reported by lbmp_last_error(NULL). */
 lbmp_status lbmp_boundary_cells_noalloc(const uint8_t* flags, int nx, int ny, int nz, const int periodic[3],
                                         const double center[3], double diameter, int* list, int capacity,
                                         int* count, uintptr_t cuda_stream);

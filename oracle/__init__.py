@@ -120,6 +120,11 @@ def lib():
         L.orc_amr_mass.argtypes = [vp, dp]
         L.orc_amr_real_cells.restype = ctypes.c_int64
         L.orc_amr_real_cells.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int32), dp, ctypes.c_int64]
+        L.orc_amr_get_flags.restype = ctypes.c_int64
+        L.orc_amr_get_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8), ctypes.c_int64]
+        L.orc_amr_get_links.restype = ctypes.c_int64
+        L.orc_amr_get_links.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), dp,
+                                        ctypes.c_int64]
         L.orc_amr_get_particle.argtypes = [vp, dp]
         L.orc_amr_get_history.restype = ctypes.c_int64
         L.orc_amr_get_history.argtypes = [vp, dp, ctypes.c_int64]
@@ -384,6 +389,24 @@ class RefinedSim:
         self._L.orc_amr_real_cells(self._h, int(level), xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                                    g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
         return xyz, g
+
+    def flags(self):
+        """Finest-level flags in real_cells order: 1 solid, 2 fluid next to the sphere, 0 fluid."""
+        n = self._L.orc_amr_get_flags(self._h, None, 0)
+        out = np.empty(n, dtype=np.uint8)
+        self._L.orc_amr_get_flags(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), n)
+        return out
+
+    def links(self):
+        """Finest-level boundary links: (cell [n] int64, q [n] int32, delta [n])."""
+        n = self._L.orc_amr_get_links(self._h, None, None, None, 0)
+        cell = np.empty(n, dtype=np.int64)
+        q = np.empty(n, dtype=np.int32)
+        d = np.empty(n)
+        self._L.orc_amr_get_links(self._h, cell.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                  d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+        return cell, q, d
 
     def mass(self):
         out = np.empty(4)

@@ -156,6 +156,15 @@ void orc_amr_level_populations(const orc_amr* a, int level, double* out);
 /* Real cells of a level in block-position order then local (x fastest)
  * order: coordinates [n][3] and deviations [n][19].  Returns n. */
 int64_t orc_amr_real_cells(const orc_amr* a, int level, int32_t* xyz, double* g, int64_t cap);
+/* Flags of the finest level's real cells in orc_amr_real_cells order: 1
+ * inside the sphere, 2 fluid with a D3Q19 neighbour inside it, 0 otherwise.
+ * Returns the number of cells (nothing written if cap is too small). */
+int64_t orc_amr_get_flags(const orc_amr* a, uint8_t* out, int64_t cap);
+/* Boundary links of the finest level: fluid cell (linear index over the
+ * whole finest level, x fastest), direction q with x + c_q inside the
+ * sphere, and the wall distance delta in [0, 1] (Sec. 2.3), cells in
+ * orc_amr_real_cells order and q ascending.  Returns the number of links. */
+int64_t orc_amr_get_links(const orc_amr* a, int64_t* cell, int32_t* q, double* delta, int64_t cap);
 /* sum over real cells of (rho, rho u) times the cell volume in finest units. */
 void orc_amr_mass(const orc_amr* a, double out[4]);
 void orc_amr_get_particle(const orc_amr* a, double out[24]);

@@ -1034,6 +1034,69 @@ int64_t orc_amr_real_cells(const orc_amr* a, int level, int32_t* xyz, double* g,
     return (int64_t)D.rpos.size() * B3;
 }
 
+int64_t orc_amr_get_flags(const orc_amr* a, uint8_t* out, int64_t cap) {
+    const LevelData& D = a->lv[a->L - 1];
+    const int64_t n = (int64_t)D.rpos.size() * B3;
+    if (!out || cap < n) return n;
+    for (size_t b = 0; b < D.rpos.size(); ++b)
+        for (int c = 0; c < B3; ++c) {
+            const size_t x = b * B3 + c;
+            if (D.flag[x]) {
+                out[x] = 1;
+                continue;
+            }
+            out[x] = 0;
+            if (!a->part.present) continue;
+            const int g[3] = {D.rpos[b][0] * BS + c % BS, D.rpos[b][1] * BS + (c / BS) % BS,
+                              D.rpos[b][2] * BS + c / (BS * BS)};
+            for (int q = 1; q < 19; ++q) {
+                int v[3] = {g[0] + C[q][0], g[1] + C[q][1], g[2] + C[q][2]};
+                int vb, vc;
+                if (wrap(a, D, v) && locate(D, v, &vb, &vc) == LOC_REAL && D.flag[(size_t)vb * B3 + vc]) {
+                    out[x] = 2;
+                    break;
+                }
+            }
+        }
+    return n;
+}
+
+int64_t orc_amr_get_links(const orc_amr* a, int64_t* cell, int32_t* qout, double* delta, int64_t cap) {
+    const LevelData& D = a->lv[a->L - 1];
+    int64_t cnt = 0;
+    if (!a->part.present) return 0;
+    for (size_t b = 0; b < D.rpos.size(); ++b)
+        for (int c = 0; c < B3; ++c) {
+            if (D.flag[b * B3 + c]) continue;
+            const int g[3] = {D.rpos[b][0] * BS + c % BS, D.rpos[b][1] * BS + (c / BS) % BS,
+                              D.rpos[b][2] * BS + c / (BS * BS)};
+            for (int q = 1; q < 19; ++q) {
+                int v[3] = {g[0] + C[q][0], g[1] + C[q][1], g[2] + C[q][2]};
+                int vb, vc;
+                if (!wrap(a, D, v) || locate(D, v, &vb, &vc) != LOC_REAL || !D.flag[(size_t)vb * B3 + vc]) continue;
+                if (cnt < cap) {
+                    // smallest root s in [0, 1] of |x + s c_q - x_p| = r (Sec. 2.3), x the cell centre
+                    const double xc[3] = {g[0] + 0.5, g[1] + 0.5, g[2] + 0.5};
+                    double d[3];
+                    min_image(a, D, xc, d);
+                    double cc = 0, dc = 0, dd = 0;
+                    for (int k = 0; k < 3; ++k) {
+                        cc += (double)(C[q][k] * C[q][k]);
+                        dc += d[k] * C[q][k];
+                        dd += d[k] * d[k];
+                    }
+                    double disc = dc * dc - cc * (dd - a->part.r * a->part.r);
+                    if (disc < 0) disc = 0;
+                    cell[cnt] = (int64_t)g[0] + (int64_t)D.n[0] * ((int64_t)g[1] + (int64_t)D.n[1] * g[2]);
+                    qout[cnt] = q;
+                    delta[cnt] = std::min(1.0, std::max(0.0, (-dc - std::sqrt(disc)) / cc));
+                }
+                ++cnt;
+            }
+        }
+    return cnt;
+}
+
 void orc_amr_mass(const orc_amr* a, double out[4]) {
     for (int k = 0; k < 4; ++k) out[k] = 0.0;
     for (int l = 0; l < a->L; ++l) {

@@ -24,7 +24,7 @@ __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbm
            "lbmp_profile", "lbmp_get_profile", "lbmp_boundary_cells_noalloc", "lbmp_last_error",
            "lbmp_init_fluid_wave", "lbmp_refine_box", "lbmp_regrid", "lbmp_save", "lbmp_load", "lbmp_set_refinement_sensor", "lbmp_get_block_sensor",
            "lbmp_level_shape", "lbmp_get_block_map",
-           "lbmp_get_level_cells", "lbmp_updates_per_step", "lbmp_batch_create", "lbmp_batch_autotune",
+           "lbmp_get_level_cells", "lbmp_get_level_flags", "lbmp_updates_per_step", "lbmp_batch_create", "lbmp_batch_autotune",
            "lbmp_batch_info", "lbmp_batch_get_populations", "BatchSimulation", "PRECISIONS", "lbmp_drag_forward",
            "lbmp_drag_backward", "mean_drag"]
 
@@ -294,6 +294,16 @@ def lbmp_get_level_cells(h, level):
     return xyz, g
 
 
+def lbmp_get_level_flags(h, level):
+    n = ctypes.c_size_t(0)
+    _check(h, _lib().lbmp_get_level_flags(h, int(level), None, 0, ctypes.byref(n)))
+    out = np.empty(n.value, dtype=np.uint8)
+    if n.value:
+        _check(h, _lib().lbmp_get_level_flags(h, int(level), out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                              n.value, ctypes.byref(n)))
+    return out
+
+
 def lbmp_updates_per_step(h):
     u, l = ctypes.c_int64(0), ctypes.c_int32(0)
     _check(h, _lib().lbmp_updates_per_step(h, ctypes.byref(u), ctypes.byref(l)))
@@ -520,6 +530,10 @@ class Simulation:
 
     def level_cells(self, level):
         return lbmp_get_level_cells(self.h, level)
+
+    def level_flags(self, level):
+        """Flags of a level's real cells in level_cells order (finest level: 1 solid, 2 next to the sphere)."""
+        return lbmp_get_level_flags(self.h, level)
 
     def updates_per_step(self):
         """(cell updates, kernel launches) of one level-0 step."""

@@ -98,6 +98,8 @@ SIGNATURES = {
                                           ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "lbmp_get_level_cells": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                             c_double_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "lbmp_get_level_flags": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint8),
+                                            ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "lbmp_updates_per_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int32)]),
     "lbmp_batch_create": (ctypes.c_int, [ctypes.POINTER(LbmpConfig), ctypes.POINTER(LbmpBatchSim), ctypes.c_int,

@@ -120,13 +120,16 @@ __device__ __forceinline__ void rescale19(A f[19], A kp, A km) {
 
 // --------------------------------------------------------------- explosion
 // Explosion for one coarse step of level l: every ghost cell of level l+1
-// in use takes the (optionally rescaled) post-collision populations of the
-// level-l cell that contains it, into f0, the source of the first sub-step.
-template <typename S, bool RESCALE>
+// in use takes the post-collision populations of the level-l cell that
+// contains it, into f0, the source of the first sub-step.  No rescaling: the
+// 1.5-fine-cell offset between the coarse centre and the first fine cell
+// supplies the level change of the non-equilibrium part (Chapman-Enskog;
+// only cells that change level in a regrid are rescaled, in k_migrate).
+template <typename S>
 __global__ void __launch_bounds__(UPD_THREADS)
     k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0,
-              typename Store<S>::A kp, typename Store<S>::A km, typename Store<S>::A scale,
-              typename Store<S>::A inv_scale, const int* __restrict__ list, int n, int* __restrict__ status) {
+              typename Store<S>::A scale, typename Store<S>::A inv_scale, const int* __restrict__ list, int n,
+              int* __restrict__ status) {
     using A = typename Store<S>::A;
     const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
     if (i >= n) return;
@@ -144,7 +147,6 @@ __global__ void __launch_bounds__(UPD_THREADS)
     A f[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(csrc + paddr(pb, q, pc), inv_scale);
-    if (RESCALE) rescale19<A>(f, kp, km);
 #pragma unroll
     for (int q = 0; q < 19; ++q) Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
 }
@@ -159,9 +161,8 @@ struct UpdateArgs {
     CollideParams<A> P;
     // coalescence: a host cell takes the mean of its eight ghost sub-cells,
     // which the next finer level's last sub-step left in coal_in (this
-    // level's layout), rescaled by fkp, fkm when rescaling is on
+    // level's layout)
     const A* coal_in;
-    A fkp, fkm;
     // at this level's last sub-step: the next coarser level C and its coal_in
     LevelView C;
     A* coal_out;
@@ -211,7 +212,7 @@ __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, 
 
 // Update of one cell of pool block b: real cells pull (or, for hosts, take
 // the coalesced mean) and collide; ghost cells pull only.
-template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL, bool RESCALE>
+template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL>
 __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
                                             bool rigid = false) {
     using A = typename Store<S>::A;
@@ -219,7 +220,6 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
     if (HAS_FINE && REAL && U.D.host[(size_t)b * B3 + c] == 1) {
 #pragma unroll
         for (int q = 0; q < 19; ++q) g[q] = U.coal_in[paddr(b, q, c)];
-        if (RESCALE) rescale19<A>(g, U.fkp, U.fkm);
     } else {
         pull_cell<S>(U, b, c, nb27, rigid, g);
     }
@@ -239,7 +239,7 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 // update the real blocks, B3 / UPD_THREADS CTAs per block, each a run of
 // UPD_THREADS cells in block order (full warps).  All read src; the
 // real-block CTAs write dst only.
-template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED, bool RESCALE>
+template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
 __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS)
     k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks, int coalesce) {
     using A = typename Store<S>::A;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
             if (i < nglist) {
                 const int e = glist[i];
                 const int b = e >> 12, c = e & 4095;
-                update_cell<S, false, true, false, RESCALE>(U, b, c, U.D.nbr + (size_t)b * 27, i >= nactive);
+                update_cell<S, false, true, false>(U, b, c, U.D.nbr + (size_t)b * 27, i >= nactive);
             }
             return;
         }
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         }
         if (f == FLAG_BOUNDARY) return;
     }
-    update_cell<S, HAS_FINE, HAS_COARSE, true, RESCALE>(U, b, c, nb27);
+    update_cell<S, HAS_FINE, HAS_COARSE, true>(U, b, c, nb27);
 }
 
 // ---------------------------------------------------------------- coupling
@@ -1472,11 +1472,8 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     const int L = E->L;
     Level& V = E->lv[l];
     const CollideParams<A> P = level_params<S>(h, V);
-    const int rescale = h->cfg.rescale_noneq ? 1 : 0;
     if (l + 1 < L) {
         Level& F = E->lv[l + 1];
-        double kp, km;
-        kappa_post(V, F, &kp, &km);
         if (F.nxlist > 0) {
             const unsigned grid = (unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS);
             // Only level l+1's own update reads the exploded ghost cells.  When level l+1 has a finer
@@ -1489,13 +1486,9 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
                 cudaStreamWaitEvent(E->aux, E->ev_aux_fork, 0);
                 xs = E->aux;
             }
-            auto ex = [&](auto rs) {
-                k_explode<S, decltype(rs)::value><<<grid, UPD_THREADS, 0, xs>>>(
-                    view(E, V), (const S*)V.d_pops[V.cur], view(E, F), (S*)F.d_pops[F.cur], (A)kp, (A)km, P.scale,
-                    P.inv_scale, F.d_xlist, F.nxlist, h->status);
-            };
-            if (rescale) ex(std::true_type{});
-            else ex(std::false_type{});
+            k_explode<S><<<grid, UPD_THREADS, 0, xs>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
+                                                       (S*)F.d_pops[F.cur], P.scale, P.inv_scale, F.d_xlist,
+                                                       F.nxlist, h->status);
             if (beside) {
                 cudaEventRecord(E->ev_x[l + 1], E->aux);
                 E->x_pending[l + 1] = true;
@@ -1511,19 +1504,12 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     U.dst = (S*)V.d_pops[1 - V.cur];
     U.P = P;
     U.coal_in = nullptr;
-    U.fkp = U.fkm = (A)1;
     U.C = U.D;
     U.coal_out = nullptr;
     U.solid = nullptr;
     U.status = h->status;
     const bool has_fine = l + 1 < L, has_coarse = l > 0;
-    if (has_fine) {
-        Level& F = E->lv[l + 1];
-        U.coal_in = (const A*)V.d_coal;
-        // coalescence: averaged finer values are pre-collision values of the coarser cell
-        U.fkp = (A)(2.0 * V.taup / F.taup);
-        U.fkm = (A)(2.0 * V.taum / F.taum);
-    }
+    if (has_fine) U.coal_in = (const A*)V.d_coal;   // coalescence: the finer level's eight-cell means
     const int coalesce = (has_coarse && sub == 1) ? 1 : 0;   // this sub-step ends the coarser level's step
     if (coalesce) {
         Level& C = E->lv[l - 1];
@@ -1567,18 +1553,12 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         const unsigned grid = (unsigned)(V.nreal * (B3 / UPD_THREADS) + gblocks);
         const int* gl = V.d_xlist;
         cudaStream_t st = h->stream;
-        // the rescaling option is a template parameter: without it the kernel carries none of its code
-        auto go = [&](auto rs) {
-            constexpr bool R = decltype(rs)::value;
-            if (has_fine && has_coarse) k_update<S, true, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-            else if (has_fine) k_update<S, true, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-            else if (has_coarse && coupled) k_update<S, false, true, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-            else if (has_coarse) k_update<S, false, true, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-            else if (coupled) k_update<S, false, false, true, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-            else k_update<S, false, false, false, R><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-        };
-        if (rescale) go(std::true_type{});
-        else go(std::false_type{});
+        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
         h->launches += 1;
     }
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
@@ -2028,6 +2008,23 @@ lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, 
     h->d2h += (long long)(sizeof(int32_t) * 3 + sizeof(double) * 19) * (long long)cells;
     handle_free(h, dx);
     handle_free(h, dg);
+    return e == cudaSuccess ? LBMP_OK : LBMP_ERR_CUDA;
+}
+
+lbmp_status amr_level_flags(lbmp_handle* h, int level, uint8_t* out, size_t cap, size_t* n) {
+    AmrEngine* E = h->amr;
+    if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
+    Level& V = E->lv[level];
+    const size_t cells = (size_t)V.nreal * B3;
+    *n = cells;
+    if (!out || cap < cells || cells == 0) return LBMP_OK;
+    if (level != E->L - 1 || !h->has_particle) {
+        std::memset(out, 0, cells);
+        return LBMP_OK;
+    }
+    cudaError_t e = cudaMemcpyAsync(out, V.d_flags[V.fcur], cells, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    h->d2h += (long long)cells;
     return e == cudaSuccess ? LBMP_OK : LBMP_ERR_CUDA;
 }
 

@@ -23,6 +23,7 @@ lbmp_status amr_step(lbmp_handle* h, int n_coarse);   // enqueues; status read b
 lbmp_status amr_level_shape(lbmp_handle* h, int level, int out[3]);
 lbmp_status amr_block_map(lbmp_handle* h, int level, int32_t* out, size_t cap, size_t* n);
 lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n);
+lbmp_status amr_level_flags(lbmp_handle* h, int level, uint8_t* out, size_t cap, size_t* n);
 lbmp_status amr_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n);
 lbmp_status amr_save(lbmp_handle* h, FILE* f);   // refined part of a checkpoint
 lbmp_status amr_load(lbmp_handle* h, FILE* f);   // after the particle record is on the device

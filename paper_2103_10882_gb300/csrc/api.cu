@@ -870,6 +870,13 @@ lbmp_status lbmp_get_level_cells(lbmp_handle* h, int level, int32_t* xyz, double
     return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_get_level_cells: failed");
 }
 
+lbmp_status lbmp_get_level_flags(lbmp_handle* h, int level, uint8_t* out, size_t cap, size_t* n) {
+    if (!h || !n) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_level_flags: NULL argument");
+    if (!h->amr) return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_get_level_flags: the grid has one level (lbmp_get_flags)");
+    const lbmp_status st = amr_level_flags(h, level, out, cap, n);
+    return st == LBMP_OK ? LBMP_OK : fail(h, st, "lbmp_get_level_flags: failed");
+}
+
 lbmp_status lbmp_updates_per_step(lbmp_handle* h, int64_t* updates, int32_t* launches) {
     if (!h) return LBMP_ERR_INVALID_ARG;
     if (h->amr) {

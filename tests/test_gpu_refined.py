@@ -46,6 +46,20 @@ def same_maps(o, g, levels):
         assert np.array_equal(o.block_map(l), g.block_map(l)), "block map of level %d differs" % l
 
 
+def same_integer_work(o, g, levels):
+    """Block maps, finest-level flags (solid, next to the sphere, fluid) and
+    the boundary links bit-exact; link wall distances within 1e-12."""
+    same_maps(o, g, levels)
+    f = levels - 1
+    assert np.array_equal(o.flags(), g.level_flags(f)), "finest-level flags differ"
+    oc, oq, od = o.links()
+    gc, gq, gd = g.links()
+    a, b = np.lexsort((oq, oc)), np.lexsort((gq, gc))
+    assert np.array_equal(oc[a], gc[b]) and np.array_equal(oq[a], gq[b]), "boundary links differ"
+    if len(od):
+        assert np.abs(od[a] - gd[b]).max() < 1e-12
+
+
 def cells_close(o, g, levels, rel):
     for l in range(levels):
         xo, fo = o.real_cells(l)
@@ -112,14 +126,31 @@ def test_uniform_flow_and_conservation_gpu(lib):
     assert np.abs(p1 - p0).max() < 1e-14 * scale
 
 
-def test_rescaled_transfer_parity(orc, lib):
-    """The optional non-equilibrium rescaling follows the oracle too."""
-    o, g = pair(orc, lib, (32, 32, 48), 2, tau=0.8, rescale=True, box=((18, 26, 30), (42, 38, 58)))
+@pytest.mark.parametrize("levels,shape,box0,box1", [
+    (2, (32, 32, 48), ((18, 26, 30), (42, 38, 58)), ((40, 10, 50), (60, 40, 90))),
+    (3, (32, 32, 64), ((36, 44, 40), (84, 76, 92)), ((20, 24, 150), (60, 56, 200))),
+])
+def test_rescaled_regrid_parity(orc, lib, levels, shape, box0, box1):
+    """The non-equilibrium rescaling of cells that change level in a regrid
+    (kappa per TRT part when refined, 1/kappa when coarsened) follows the
+    oracle: a shear wave with drift, three steps, a regrid that both refines
+    and coarsens, then two more steps."""
+    o, g = pair(orc, lib, shape, levels, tau=0.8, rescale=True, box=box0)
     o.init_equilibrium(u=(0.01, 0.0, 0.0), shear=0.01, shear_dir=0, shear_axis=2)
     g.init_fluid_wave(1.0, (0.01, 0.0, 0.0), 0.01, 0, 2)
     o.step(3)
     g.step(3)
-    cells_close(o, g, 2, 1e-10)
+    before = [o.block_map(l).copy() for l in range(levels)]
+    o.refine_box(*box1)
+    g.refine_box(*box1)
+    after = [o.block_map(l) for l in range(levels)]
+    f = levels - 1
+    assert np.any((before[f] >= 0) & (after[f] < 0)) and np.any((before[f] < 0) & (after[f] >= 0))
+    same_maps(o, g, levels)
+    cells_close(o, g, levels, 1e-12)
+    o.step(2)
+    g.step(2)
+    cells_close(o, g, levels, 1e-10)
 
 
 def test_refined_sphere_fp64(orc, lib):
@@ -139,9 +170,8 @@ def test_refined_sphere_fp64(orc, lib):
     Fs = 0.7 * 2e-4 * math.pi * 1000 / 6
     np.testing.assert_allclose(hg[:, 0:6], ho[:, 0:6], rtol=0, atol=1e-10 * Fs)
     np.testing.assert_allclose(hg[:, 6:9], ho[:, 6:9], rtol=1e-10, atol=1e-10)
-    gc, gq, gd = g.links()
-    # oracle links in global finest coordinates are those of the boundary cells of the finest level
-    assert len(gc) > 0 and np.all((gd > 0) & (gd <= 1))
+    same_integer_work(o, g, 3)
+    assert len(g.links()[0]) > 0
 
 
 def test_moving_sphere_with_regrids(orc, lib):
@@ -157,7 +187,7 @@ def test_moving_sphere_with_regrids(orc, lib):
         g.step(1)
         o.regrid()
         g.regrid()
-        same_maps(o, g, 2)
+        same_integer_work(o, g, 2)
     cells_close(o, g, 2, 1e-10)
     ho, hg = o.history(), g.history()
     np.testing.assert_allclose(hg[:, 6:9], ho[:, 6:9], rtol=1e-10, atol=1e-10)
@@ -237,3 +267,44 @@ def test_long_rising_sphere_run_stays_sane(lib):
     assert abs(h[-1, 6] - start[0]) < 10.0 and abs(h[-1, 7] - start[1]) < 10.0
     assert grew
     sim.close()
+
+
+def test_sensor_regrids_walls_100_finest_steps_fp64(orc, lib):
+    """Three levels, no-slip walls on x and y, a light sphere (d = 10) and
+    the curl sensor (sigma_c = 1e-5, c = 0.2): 25 level-0 steps (100
+    finest steps) with a regrid every 5, three of which change the forest
+    through the sensor and the sphere.  After every regrid the maps, the
+    finest-level flags and the boundary links are bit-exact; at the end the
+    populations of every level are within 1e-10 and the force history within
+    1e-10 of the buoyancy scale.  Before each regrid the oracle's block
+    values are checked to stay clear of the thresholds, so the FP64 maps are
+    decided the same way on both sides."""
+    sigma, cfac = 1e-5, 0.2
+    pos, D, pi, gz = (62.3, 65.6, 90.2), 10.0, 0.3, 1e-3
+    o, g = pair(orc, lib, (32, 32, 96), 3, tau=0.7, bc=("noslip", "noslip", "periodic"), sphere=(pos, D, pi, 0.5),
+                gravity=(0, 0, gz))
+    o.set_sensor(sigma, cfac)
+    g.set_refinement_sensor(sigma, cfac)
+    o.init_equilibrium()
+    g.init_fluid()
+    same_integer_work(o, g, 3)
+    changed = 0
+    for k in range(5):
+        o.step(5)
+        g.step(5)
+        vals = np.concatenate([o.block_sensor(l) for l in range(3)])
+        for thr in (sigma, cfac * sigma):
+            assert np.abs(vals / thr - 1).min() > 1e-6
+        before = [o.block_map(l).copy() for l in range(3)]
+        o.regrid()
+        g.regrid()
+        changed += any(not np.array_equal(before[l], o.block_map(l)) for l in range(3))
+        same_integer_work(o, g, 3)
+    assert changed >= 3
+    assert all(len(o.real_cells(l)[0]) > 0 for l in range(3))
+    cells_close(o, g, 3, 1e-10)
+    ho, hg = o.history(), g.history()
+    assert ho.shape == hg.shape == (100, 15)
+    Fs = (1 - pi) * gz * math.pi * D ** 3 / 6
+    np.testing.assert_allclose(hg[:, 0:6], ho[:, 0:6], rtol=0, atol=1e-10 * Fs)
+    np.testing.assert_allclose(hg[:, 6:9], ho[:, 6:9], rtol=1e-10, atol=1e-10)

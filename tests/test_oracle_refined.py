@@ -346,3 +346,32 @@ def test_regrid_rescaling_gives_new_levels_stress(orc, tau_f):
         assert da < 0.05
     assert max(ds for ds, _ in dev[False]) > 0.4
     assert max(da for _, da in dev[False]) > 0.4
+
+
+@pytest.mark.parametrize("pos", [(30.7, 33.2, 31.6), (2.3, 61.6, 33.1)])
+def test_refined_flags_and_links_match_uniform_oracle(orc, pos):
+    """The refined oracle's finest-level flags (inside the closed ball, and
+    fluid cells with a D3Q19 neighbour inside it) and boundary links with
+    their wall distances are those of the uniform oracle on the finest
+    resolution (whose links are pinned by brute force in test_oracle_pins),
+    also for a sphere across a periodic face.  Catches a wrong neighbour
+    direction, an off-by-one cell centre or a wrong root of the delta
+    quadratic in the refined accessors."""
+    r = orc.RefinedSim((16, 16, 16), 3, tau=0.7)
+    r.add_sphere(pos, 10.0, 0.3, cv=0.5)
+    u = orc.UniformSim((64, 64, 64), tau=0.7)
+    u.add_sphere(pos, 10.0, 0.3, cv=0.5)
+    xyz, _ = r.real_cells(2)
+    lin = xyz[:, 0] + 64 * (xyz[:, 1] + 64 * xyz[:, 2])
+    f = r.flags()
+    uf = u.flags()
+    assert np.array_equal(f == 1, uf[lin] != 0)
+    rc, rq, rd = r.links()
+    uc, uq, ud = u.links()
+    assert len(rc) > 0
+    assert np.array_equal(np.unique(rc), np.unique(uc))
+    assert np.array_equal(np.sort(np.unique(lin[f == 2])), np.unique(uc))
+    a = np.lexsort((rq, rc))
+    b = np.lexsort((uq, uc))
+    assert np.array_equal(rc[a], uc[b]) and np.array_equal(rq[a], uq[b])
+    assert np.abs(rd[a] - ud[b]).max() < 1e-15
