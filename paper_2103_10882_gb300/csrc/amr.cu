@@ -62,7 +62,6 @@ struct LevelView {
     const int* bpos;       // [npool][3]
     const int* nbr;        // [npool][27] pool ids of neighbour blocks, -1 none, -2 wall
     const uint8_t* host;   // [nreal][B3] 1 host, 2 second ring (levels below the finest)
-    const uint8_t* gkind;  // [npool - nreal][B3] 1 active, 2 static, 0 unused
     const uint8_t* refined;  // block positions covered by the next finer level
 };
 
@@ -647,39 +646,92 @@ __global__ void __launch_bounds__(LINK_THREADS)
 
 // ------------------------------------------------------ classification
 // Host flag of every real cell: 1 when a cell covered by the next finer
-// level lies within Chebyshev distance 1, 2 when the nearest is at 2.
-__global__ void k_host_flags(LevelView D, uint8_t* __restrict__ host) {
+// level lies within Chebyshev distance 1, 2 when the nearest is at 2.  Each
+// CTA (a run of 256 cells) also counts its cells of either kind into
+// run_counts[2 * run], run_counts[2 * run + 1].
+__global__ void __launch_bounds__(256) k_host_flags(LevelView D, uint8_t* __restrict__ host, int* __restrict__ run_counts) {
     const int b = blockIdx.x >> 4;
     const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
-    {
-        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
-        const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
-        int dist = 3;
-        for (int dz = -2; dz <= 2; ++dz)
-            for (int dy = -2; dy <= 2; ++dy)
-                for (int dx = -2; dx <= 2; ++dx) {
-                    int v[3] = {g[0] + dx, g[1] + dy, g[2] + dz};
-                    if (!wrap3(v, D)) continue;
-                    if (D.refined[(v[0] >> 4) + D.nb[0] * ((v[1] >> 4) + D.nb[1] * (v[2] >> 4))]) {
-                        const int m = max(abs(dx), max(abs(dy), abs(dz)));
-                        dist = min(dist, m);
-                    }
+    const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
+    const int g[3] = {bx * BS + (c & 15), by * BS + ((c >> 4) & 15), bz * BS + (c >> 8)};
+    int dist = 3;
+    for (int dz = -2; dz <= 2; ++dz)
+        for (int dy = -2; dy <= 2; ++dy)
+            for (int dx = -2; dx <= 2; ++dx) {
+                int v[3] = {g[0] + dx, g[1] + dy, g[2] + dz};
+                if (!wrap3(v, D)) continue;
+                if (D.refined[(v[0] >> 4) + D.nb[0] * ((v[1] >> 4) + D.nb[1] * (v[2] >> 4))]) {
+                    const int m = max(abs(dx), max(abs(dy), abs(dz)));
+                    dist = min(dist, m);
                 }
-        host[(size_t)b * B3 + c] = dist <= 1 ? 1 : (dist == 2 ? 2 : 0);
+            }
+    const int kind = dist <= 1 ? 1 : (dist == 2 ? 2 : 0);
+    host[(size_t)b * B3 + c] = (uint8_t)kind;
+    __shared__ int wc[2][8];
+    const unsigned b1 = __ballot_sync(0xffffffffu, kind == 1), b2 = __ballot_sync(0xffffffffu, kind == 2);
+    if ((threadIdx.x & 31) == 0) {
+        wc[0][threadIdx.x >> 5] = __popc(b1);
+        wc[1][threadIdx.x >> 5] = __popc(b2);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        int t = 0;
+        for (int w = 0; w < 8; ++w) t += wc[threadIdx.x][w];
+        run_counts[2 * blockIdx.x + threadIdx.x] = t;
     }
 }
 
-// Kind of every ghost cell of level l+1: the host flag of its parent.
-__global__ void k_ghost_kind(LevelView C, const uint8_t* __restrict__ chost, LevelView F, uint8_t* __restrict__ gkind) {
-    const int gb = blockIdx.x >> 4;
-    const int b = F.nreal + gb;
-    const int bx = F.bpos[3 * b], by = F.bpos[3 * b + 1], bz = F.bpos[3 * b + 2];
-    {
-        const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
-        const int p[3] = {(bx * BS + (c & 15)) >> 1, (by * BS + ((c >> 4) & 15)) >> 1, (bz * BS + (c >> 8)) >> 1};
-        int pc;
-        const int pb = locate(C, p, &pc);
-        gkind[(size_t)gb * B3 + c] = (pb >= 0 && pb < C.nreal) ? chost[(size_t)pb * B3 + pc] : 0;
+// Ghost-cell list of level l+1 from the host flags of level l (same runs as
+// k_host_flags): the eight sub-cells of every host (flag 1) in host order
+// (real block, then cell) and sub-cell order, then those of every
+// second-ring cell (flag 2), the static ghost cells.  An entry is the
+// sub-cell's pool block << 12 | cell.  n1: hosts of the whole level.
+__global__ void __launch_bounds__(256)
+    k_ghost_lists(LevelView C, const uint8_t* __restrict__ host, const int* __restrict__ run_counts, int n1,
+                  LevelView F, int* __restrict__ list, int* __restrict__ status) {
+    __shared__ int red[2][256];
+    __shared__ int wc[2][8];
+    int s1 = 0, s2 = 0;
+    for (int r = threadIdx.x; r < (int)blockIdx.x; r += 256) {
+        s1 += run_counts[2 * r];
+        s2 += run_counts[2 * r + 1];
+    }
+    red[0][threadIdx.x] = s1;
+    red[1][threadIdx.x] = s2;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    const int b = blockIdx.x >> 4;
+    const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
+    const int kind = host[(size_t)b * B3 + c];
+    const unsigned b1 = __ballot_sync(0xffffffffu, kind == 1), b2 = __ballot_sync(0xffffffffu, kind == 2);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        wc[0][warp] = __popc(b1);
+        wc[1][warp] = __popc(b2);
+    }
+    __syncthreads();
+    if (kind == 0) return;
+    int pos = red[kind - 1][0];
+    for (int w = 0; w < warp; ++w) pos += wc[kind - 1][w];
+    pos += __popc((kind == 1 ? b1 : b2) & ((1u << lane) - 1u));
+    int* out = list + 8 * (kind == 1 ? pos : n1 + pos);
+    const int p[3] = {C.bpos[3 * b] * BS + (c & 15), C.bpos[3 * b + 1] * BS + ((c >> 4) & 15), C.bpos[3 * b + 2] * BS + (c >> 8)};
+    for (int sub = 0; sub < 8; ++sub) {
+        const int g[3] = {2 * p[0] + (sub & 1), 2 * p[1] + ((sub >> 1) & 1), 2 * p[2] + (sub >> 2)};
+        int gc;
+        const int gb = locate(F, g, &gc);
+        if (gb < F.nreal) {   // by construction every sub-cell of a host or second-ring cell is a ghost cell
+            atomicOr(status, STATUS_AMR_MISSING);
+            out[sub] = 0;
+            continue;
+        }
+        out[sub] = (gb << 12) | gc;
     }
 }
 
@@ -922,7 +974,6 @@ struct Level {
     int* d_nbr = nullptr;
     uint8_t* d_refined = nullptr;
     uint8_t* d_host = nullptr;
-    uint8_t* d_gkind = nullptr;
     int nglist = 0;              // active ghost cells (host sub-cells)
     int* d_xlist = nullptr;      // every ghost cell in use, pool block << 12 | cell: the active ones, then the static ones
     int nxlist = 0;
@@ -1003,7 +1054,6 @@ LevelView view(const AmrEngine* E, const Level& V) {
     w.bpos = V.d_bpos;
     w.nbr = V.d_nbr;
     w.host = V.d_host;
-    w.gkind = V.d_gkind;
     w.refined = V.d_refined;
     return w;
 }
@@ -1183,7 +1233,6 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_nbr);
     handle_free(h, V.d_refined);
     handle_free(h, V.d_host);
-    handle_free(h, V.d_gkind);
     handle_free(h, V.d_xlist);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
@@ -1295,9 +1344,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         V.d_pops[0] = handle_alloc(h, es * 19 * B3 * (size_t)std::max(np, 1));
         V.d_pops[1] = handle_alloc(h, es * 19 * B3 * (size_t)std::max(np, 1));
         V.d_host = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
-        V.d_gkind = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nghost, 1));
-        if (!V.d_map || !V.d_refined || !V.d_bpos || !V.d_nbr || !V.d_pops[0] || !V.d_pops[1] || !V.d_host ||
-            !V.d_gkind)
+        if (!V.d_map || !V.d_refined || !V.d_bpos || !V.d_nbr || !V.d_pops[0] || !V.d_pops[1] || !V.d_host)
             return LBMP_ERR_OOM;
         if (l + 1 < L) {
             const size_t as = h->cfg.precision == LBMP_FP64 ? 8 : 4;
@@ -1316,58 +1363,51 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         cudaMemsetAsync(V.d_pops[0], 0, es * 19 * B3 * (size_t)std::max(np, 1), h->stream);
         cudaMemsetAsync(V.d_pops[1], 0, es * 19 * B3 * (size_t)std::max(np, 1), h->stream);
         cudaMemsetAsync(V.d_host, 0, (size_t)B3 * std::max(V.nreal, 1), h->stream);
-        cudaMemsetAsync(V.d_gkind, 0, (size_t)B3 * std::max(V.nghost, 1), h->stream);
     }
-    // classification
-    for (int l = 0; l + 1 < L; ++l) {
+    // classification and the ghost-cell lists of every finer level, built on
+    // the device from the coarser level's host flags (one copy of the per-run
+    // counts back to size the lists)
+    std::vector<int*> d_runs(L, nullptr);
+    std::vector<std::vector<int>> runs(L);
+    bool ok = true;
+    for (int l = 0; l + 1 < L && ok; ++l) {
+        Level& C = E->lv[l];
+        if (C.nreal == 0) continue;
+        const size_t nr = (size_t)C.nreal * 16;
+        d_runs[l] = (int*)handle_alloc(h, sizeof(int) * 2 * nr);
+        if (!d_runs[l]) {
+            ok = false;
+            break;
+        }
+        runs[l].resize(2 * nr);
+        k_host_flags<<<(unsigned)nr, 256, 0, h->stream>>>(view(E, C), C.d_host, d_runs[l]);
+        if (cudaMemcpyAsync(runs[l].data(), d_runs[l], sizeof(int) * 2 * nr, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+            ok = false;
+        h->d2h += (long long)(sizeof(int) * 2 * nr);
+    }
+    if (ok && cudaStreamSynchronize(h->stream) != cudaSuccess) ok = false;
+    for (int l = 0; l + 1 < L && ok; ++l) {
         Level& C = E->lv[l];
         Level& F = E->lv[l + 1];
-        if (C.nreal > 0) k_host_flags<<<(unsigned)C.nreal * 16, 256, 0, h->stream>>>(view(E, C), C.d_host);
-        if (F.nghost > 0) k_ghost_kind<<<(unsigned)F.nghost * 16, 256, 0, h->stream>>>(view(E, C), C.d_host, view(E, F), F.d_gkind);
-    }
-    // compact lists of the active ghost cells of every level
-    for (int l = 1; l < L; ++l) {
-        Level& F = E->lv[l];
-        if (F.nghost == 0) continue;
-        std::vector<uint8_t> kinds((size_t)F.nghost * B3);
-        if (cudaMemcpyAsync(kinds.data(), F.d_gkind, kinds.size(), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
-            cudaStreamSynchronize(h->stream) != cudaSuccess)
-            return LBMP_ERR_CUDA;
-        h->d2h += (long long)kinds.size();
-        // used: the active ghost cells, the eight sub-cells of each host of
-        // the coarser level consecutive (host order, then sub-cell order),
-        // then the static ones
-        const Level& C = E->lv[l - 1];
-        std::vector<std::pair<long long, int>> act;
-        std::vector<int> stat;
-        for (int gb = 0; gb < F.nghost; ++gb) {
-            const int* bp = &F.bpos[3 * (size_t)(F.nreal + gb)];
-            for (int c = 0; c < B3; ++c) {
-                const uint8_t k = kinds[(size_t)gb * B3 + c];
-                const int e = ((F.nreal + gb) << 12) | c;
-                if (k == 2) stat.push_back(e);
-                if (k != 1) continue;
-                const int g[3] = {bp[0] * BS + (c & 15), bp[1] * BS + ((c >> 4) & 15), bp[2] * BS + (c >> 8)};
-                const int p[3] = {g[0] >> 1, g[1] >> 1, g[2] >> 1};
-                const int m = C.map[(p[0] / BS) + C.nb[0] * ((p[1] / BS) + C.nb[1] * (p[2] / BS))];
-                if (m < 0) return LBMP_ERR_CUDA;   // an active ghost cell lies in a real coarser cell by construction
-                const int pc = (p[0] & 15) + BS * ((p[1] & 15) + BS * (p[2] & 15));
-                const int sub = (g[0] & 1) + 2 * (g[1] & 1) + 4 * (g[2] & 1);
-                act.push_back({(((long long)m << 12 | pc) << 3) | sub, e});
-            }
+        long long n1 = 0, n2 = 0;
+        for (size_t r = 0; r < runs[l].size(); r += 2) {
+            n1 += runs[l][r];
+            n2 += runs[l][r + 1];
         }
-        std::sort(act.begin(), act.end());
-        if (act.size() % 8 != 0) return LBMP_ERR_CUDA;
-        std::vector<int> list(act.size());
-        for (size_t i = 0; i < act.size(); ++i) list[i] = act[i].second;
-        std::vector<int> used(list);
-        used.insert(used.end(), stat.begin(), stat.end());
-        F.nglist = (int)list.size();
-        F.nxlist = (int)used.size();
-        F.d_xlist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>(used.size(), 1));
-        if (!F.d_xlist) return LBMP_ERR_OOM;
-        if (upload(h, F.d_xlist, used.data(), sizeof(int) * used.size())) return LBMP_ERR_CUDA;
+        F.nglist = (int)(8 * n1);
+        F.nxlist = (int)(8 * (n1 + n2));
+        F.d_xlist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>((size_t)F.nxlist, 1));
+        if (!F.d_xlist) {
+            ok = false;
+            break;
+        }
+        if (F.nxlist > 0)
+            k_ghost_lists<<<(unsigned)C.nreal * 16, 256, 0, h->stream>>>(view(E, C), C.d_host, d_runs[l], (int)n1,
+                                                                           view(E, F), F.d_xlist, h->status);
     }
+    if (ok && cudaStreamSynchronize(h->stream) != cudaSuccess) ok = false;
+    for (int l = 0; l < L; ++l) handle_free(h, d_runs[l]);
+    if (!ok) return LBMP_ERR_OOM;
     // populations from the old layout
     if (!old.empty()) {
         with_storage_amr(h->cfg.precision, [&](auto tag) {
