@@ -8,6 +8,11 @@ steps with the particle criterion and the flow-based curl sensor (Sec.
 4.2.2: sigma_c = 1e-3, c = 0.2), FP32 deviation storage.  A timed step is one level-0 step of the full
 coupled method (Algorithm 1 on the finest level, sub-cycling, explosion and
 coalescence, regrids when due).  MLUPS counts real cell updates of all levels.
+The headline value is a window of --steps level-0 steps of the developed run
+(from level-0 step 2000 on, the wake has grown the finest level) placed so
+that it holds one regrid; the line also carries the first steps from rest
+(cold_start), a long developed window (developed_long, one regrid per 50
+steps) and the same developed window in FP16 storage and FP64.
 
 Also reported (key "uniform512"): a periodic 512^3 box with a sphere of 40
 cells, the bandwidth case of the stream-collide kernel; "uniform512_mrt" is
@@ -59,6 +64,10 @@ def parse():
     ap.add_argument("--edge", type=int, default=512, help="edge of the uniform bandwidth case")
     ap.add_argument("--uniform-steps", type=int, default=30)
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--long-steps", type=int, default=1000,
+                    help="level-0 steps of the long developed window of the headline workload (FP32 line)")
+    ap.add_argument("--no-other-precisions", action="store_true",
+                    help="skip the FP16-storage and FP64 windows of the headline workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uniform", action="store_true")
@@ -78,10 +87,12 @@ def parse():
     return ap.parse_args()
 
 
-def refined_name(prec):
-    return ("refined rising sphere: level-0 64x64x256 (16^3 blocks), 3 levels, d=20 finest, pi_p=0.5, Ga=200, "
-            "C_v=0.5, walls x/y, periodic z, regrid every 50 level-0 steps (particle + curl sensor sigma_c=1e-3, "
-            "c=0.2), %s" % prec)
+REFINED_NAME = ("refined rising sphere: level-0 64x64x256 (16^3 blocks), 3 levels, d=20 finest, pi_p=0.5, Ga=200, "
+                "C_v=0.5, walls x/y, periodic z, regrid every 50 level-0 steps (particle + curl sensor sigma_c=1e-3, "
+                "c=0.2)")
+# level-0 step from which the run counts as developed: the wake has grown the finest level (3.3 -> 4-5 M
+# cell updates per level-0 step) and regrids change the hierarchy
+DEVELOPED_STEP = 2000
 
 
 def uniform_name(edge, prec):
@@ -246,7 +257,7 @@ def run_reference(args):
     cb = cpu_baseline(max(args.cpu_seconds, 1.0), max_steps=max(args.steps, 1), warmup=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "MLUPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": refined_name("fp64 oracle")}, "cpu_baseline": cb,
+            "data": "synthetic", "config": {"workload": REFINED_NAME}, "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -468,6 +479,68 @@ def job_mlups(world, updates_per_rank, ms_max):
     return world * updates_per_rank / (ms_max * 1e-3) / 1e6
 
 
+def refined_runs(L, prec, args, torch, local, dist, world, full):
+    """The headline workload in one precision.  After the warm-up: a cold-start
+    window (the first steps from rest); the run is then advanced untimed to
+    the developed state and a window of args.steps level-0 steps is timed that
+    holds one regrid (value); with full=True also a long developed window
+    (args.long_steps, one regrid per 50 steps), the per-launch profile of the
+    level update (roofline) and the end-to-end measurement through the C ABI."""
+    import numpy as np
+    w = REFINED
+    bpp = BYTES_PER_POP[prec]
+    tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    sim = refined_sim(L, prec)
+    sim.step(args.warmup)
+    out = {}
+    with ClockSampler(local) as clk:
+        cms, _, c0, c1 = timed(sim, args.steps, sim.stream, torch, profile=False)
+        out["cold_start"] = {"value": job_mlups(world, c1[1] - c0[1], max_over_ranks(cms, dist, "cuda")),
+                             "unit": "MLUPS", "ms_per_step": cms / args.steps, "start_step": int(c0[0]),
+                             "steps": args.steps, "cell_updates_per_step": (c1[1] - c0[1]) / args.steps,
+                             "note": "first steps from rest after the warm-up (the initial hierarchy)"}
+        # developed state: the window (start, start + K] holds the regrid after level-0 step DEVELOPED_STEP + 50
+        interval = w["regrid"]
+        regrid_at = DEVELOPED_STEP + interval
+        start = regrid_at - (args.steps + 1) // 2
+        sim.step(max(start - int(sim.counters()[0]), 0))
+        start = int(sim.counters()[0])
+        maps0 = [sim.block_map(l).copy() for l in range(w["levels"])]
+        ms, _, d0, d1 = timed(sim, args.steps, sim.stream, torch, profile=False)
+        maps1 = [sim.block_map(l) for l in range(w["levels"])]
+        ms_max = max_over_ranks(ms, dist, "cuda")
+        regrids = sum(1 for s_ in range(start + 1, start + args.steps + 1) if s_ % interval == 0)
+        out["value"] = job_mlups(world, d1[1] - d0[1], ms_max)
+        out["ms_per_step"] = ms_max / args.steps
+        out["gpu_launches"] = int(d1[2] - d0[2])
+        out["config"] = {"start_step": start, "steps": args.steps, "regrids_in_window": regrids,
+                         "hierarchy_changed_in_window": any(not np.array_equal(a, b) for a, b in zip(maps0, maps1)),
+                         "cell_updates_per_step": (d1[1] - d0[1]) / args.steps,
+                         "real_blocks_per_level": [int((m >= 0).sum()) for m in maps1],
+                         "launches_per_step": int(sim.updates_per_step()[1]),
+                         "l2": "inputs larger than L2 (no flush)"}
+        if full:
+            lms, _, e0, e1 = timed(sim, args.long_steps, sim.stream, torch, profile=False)
+            out["developed_long"] = {
+                "value": job_mlups(world, e1[1] - e0[1], max_over_ranks(lms, dist, "cuda")), "unit": "MLUPS",
+                "ms_per_step": lms / args.long_steps, "start_step": int(e0[0]), "steps": args.long_steps,
+                "regrids": args.long_steps // interval, "cell_updates_per_step": (e1[1] - e0[1]) / args.long_steps}
+        # per-launch events around every level update (no CUDA graph): the roofline of k_update
+        pms, prof, _, _ = timed(sim, max(10, args.steps // 2), sim.stream, torch, profile=True)
+    out["clocks"] = clk.summary()
+    out["roofline"] = roofline(prof, "k_update (refined stream + collide / coalescence, %s)" % prec,
+                               profiled_traffic("k_update_%s_refined.md" % prec, "traffic_bytes_per_launch"))
+    out["roofline"]["bytes_per_cell_update"] = 38 * bpp
+    out["profiled_pass"] = {"steps": int(prof[3]), "ms_per_step": prof[2] / max(prof[3], 1),
+                            "start_step": int(sim.counters()[0] - prof[3]), "note": "per-launch events, no CUDA graph"}
+    if full:
+        out["e2e"] = e2e(sim, args.e2e_steps, np.array([0.0, 0.0, -gm]))
+        part = sim.particle()
+        out["particle_after"] = {"step": int(sim.counters()[0]), "z": part[8], "u_z": part[11]}
+    sim.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -489,40 +562,31 @@ def main():
     line = {}
 
     # ------------------------------------------------- refined (headline)
-    w = REFINED
-    tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
-    sim = refined_sim(L, prec)
-    upd_step, launches_step = sim.updates_per_step()
-    sim.step(args.warmup)
-    if dist:
-        dist.barrier()
-    with ClockSampler(local) as clk:
-        ms, _, c0, c1 = timed(sim, args.steps, sim.stream, torch, profile=False)
-        # second timed pass: events around every stream-collide launch (roofline of k_update)
-        pms, prof, _, _ = timed(sim, max(10, args.steps // 5), sim.stream, torch, profile=True)
-    ms_max = max_over_ranks(ms, dist, "cuda")
-    updates = c1[1] - c0[1]
-    value = job_mlups(world, updates, ms_max)
-    e2e_line = e2e(sim, args.e2e_steps, np.array([0.0, 0.0, -gm]))
-    part = sim.particle()
-    sim.close()
+    ref = refined_runs(L, prec, args, torch, local, dist, world, full=True)
     line.update({
-        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": ref["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ref["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
-        "config": {"workload": refined_name(prec), "cell_updates_per_step": updates / args.steps,
-                   "launches_per_step": launches_step, "l2": "inputs larger than L2 (no flush)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": roofline(prof, "k_update (refined stream + collide / coalescence, %s)" % prec,
-                             profiled_traffic("k_update_%s_refined.md" % prec, "traffic_bytes_per_launch")),
-        "profiled_pass": {"steps": int(prof[3]), "ms_per_step": prof[2] / max(prof[3], 1),
-                          "note": "per-launch events, no CUDA graph"},
-        "e2e": e2e_line,
-        "gpu_launches": int(c1[2] - c0[2]),
-        "clocks": clk.summary(),
-        "particle_after": {"z": part[8], "u_z": part[11]},
+        "config": dict(ref["config"], workload=REFINED_NAME, precision=prec,
+                       parallelism="replicas" if world > 1 else "single GPU"),
     })
-    line["roofline"]["bytes_per_cell_update"] = 38 * bpp
+    for k in ("roofline", "profiled_pass", "e2e", "gpu_launches", "clocks", "cold_start", "developed_long",
+              "particle_after"):
+        if k in ref:
+            line[k] = ref[k]
+    # the same windows in the other two precisions (FP16 deviation storage with FP32 arithmetic; FP64)
+    if not args.no_other_precisions:
+        others = {}
+        for p2 in ("fp16", "fp64", "fp32"):
+            if p2 != prec:
+                r2 = refined_runs(L, p2, args, torch, local, dist, world, full=False)
+                others[p2] = {"value": r2["value"], "unit": "MLUPS", "ms_per_step": r2["ms_per_step"], "dtype": DTYPE[p2],
+                              "config": r2["config"], "roofline": r2["roofline"], "clocks": r2["clocks"]}
+        f64 = others["fp64"]["value"] if "fp64" in others else ref["value"]
+        line["speedup_over_fp64"] = ref["value"] / f64
+        for p2, r2 in others.items():
+            r2["speedup_over_fp64"] = r2["value"] / f64
+            line["refined_" + p2] = r2
 
     # --------------------------------------------- uniform bandwidth case
     def uniform_case(bulk):
