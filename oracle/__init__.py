@@ -90,6 +90,10 @@ def lib():
         L.orc_get_history.argtypes = [vp, dp, ctypes.c_int64]
         L.orc_get_plane_force.argtypes = [vp, dp]
         L.orc_particle_only_step.argtypes = [vp, dp, dp]
+        L.orc_set_particle_fixed.restype = ip
+        L.orc_set_particle_fixed.argtypes = [vp, ip]
+        L.orc_set_wall_velocity.restype = ip
+        L.orc_set_wall_velocity.argtypes = [vp, ip, ip, dp]
         L.orc_set_threads.restype = ip
         L.orc_set_threads.argtypes = [ip]
         L.orc_amr_create.restype = vp
@@ -148,6 +152,14 @@ def grad_noneq(tau, S):
     return out
 
 
+def _fixed_mode(fixed):
+    if fixed == "translation":
+        return 2
+    if fixed is True or fixed is False:
+        return int(fixed)
+    return int(fixed)
+
+
 def set_threads(n: int) -> int:
     return lib().orc_set_threads(int(n))
 
@@ -192,9 +204,20 @@ class UniformSim:
             cv_omega = cv
         a, pa = _d(pos)
         rc = self._L.orc_add_sphere(self._h, pa, float(diameter), float(density_ratio), float(cv),
-                                    float(cv_omega), int(bool(fixed)))
+                                    float(cv_omega), _fixed_mode(fixed))
         if rc != 0:
             raise ValueError("add_sphere rejected")
+
+    def set_fixed(self, fixed):
+        """Held degrees of freedom: False/0 none, True/1 all, 2 or "translation" translation only."""
+        if self._L.orc_set_particle_fixed(self._h, _fixed_mode(fixed)) != 0:
+            raise ValueError("set_fixed rejected")
+
+    def set_wall_velocity(self, axis, side, u):
+        """Velocity of the domain wall on the low (0) or high (1) face of a non-periodic axis."""
+        a, pa = _d(u)
+        if self._L.orc_set_wall_velocity(self._h, int(axis), int(side), pa) != 0:
+            raise ValueError("set_wall_velocity rejected")
 
     def set_particle_velocity(self, u, w=(0.0, 0.0, 0.0)):
         a, pa = _d(u)
@@ -325,7 +348,7 @@ class RefinedSim:
             cv_omega = cv
         a, pa = _d(pos)
         self._rc(self._L.orc_amr_add_sphere(self._h, pa, float(diameter), float(density_ratio), float(cv),
-                                            float(cv_omega), int(bool(fixed))))
+                                            float(cv_omega), _fixed_mode(fixed)))
 
     def set_gravity(self, g):
         a, pa = _d(g)

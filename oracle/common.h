@@ -32,7 +32,8 @@ enum : uint8_t { FLUID = 0, SOLID_PARTICLE = 1, SOLID_PLANE = 2 };
 
 struct Particle {
     bool present = false;
-    bool fixed = false;
+    int fixed = 0;        // held degrees of freedom: 0 none, 1 translation and rotation, 2 translation only
+    int prev_fixed = 0;   // the value of fixed in the previous step
     double x[3] = {0, 0, 0};
     double u[3] = {0, 0, 0};   // wall velocity seen by the fluid (u at t + 1/2)
     double w[3] = {0, 0, 0};
@@ -237,31 +238,35 @@ inline void particle_advance(Particle& P, const double Fh[3], const double Th[3]
         }
     }
     for (int a = 0; a < 3; ++a) P.Fp[a] = Fp[a];
-    if (!P.fixed) {
-        for (int a = 0; a < 3; ++a) {
-            // second half kick of the previous step completes u(t)
-            if (P.steps > 0) {
-                P.u[a] += Fp[a] / (2.0 * m);
-                P.w[a] += Tp[a] / (2.0 * I);
-            }
+    // A held group (translation, rotation) keeps its velocity and has zero
+    // acceleration, so the virtual force or torque of the next step is zero;
+    // a group released in this step starts its kick-drift-kick afresh (no
+    // half kick completing a previous step).
+    const bool tfree = P.fixed == 0, rfree = P.fixed != 1;
+    const bool tprev = P.steps > 0 && P.prev_fixed == 0, rprev = P.steps > 0 && P.prev_fixed != 1;
+    for (int a = 0; a < 3; ++a) {
+        if (tfree) {
+            if (tprev) P.u[a] += Fp[a] / (2.0 * m);   // second half kick of the previous step completes u(t)
             P.a[a] = Fp[a] / m;
-            P.b[a] = Tp[a] / I;
-            // first half kick, then drift with u(t + 1/2)
-            P.u[a] += Fp[a] / (2.0 * m);
-            P.w[a] += Tp[a] / (2.0 * I);
+            P.u[a] += Fp[a] / (2.0 * m);              // first half kick, then drift with u(t + 1/2)
             P.x[a] += P.u[a];
             if (periodic[a]) {
                 double L = extent[a];
                 if (P.x[a] >= L) P.x[a] -= L;
                 else if (P.x[a] < 0.0) P.x[a] += L;
             }
+        } else {
+            P.a[a] = 0.0;
         }
-    } else {
-        for (int a = 0; a < 3; ++a) {
-            P.a[a] = Fp[a] / m;
+        if (rfree) {
+            if (rprev) P.w[a] += Tp[a] / (2.0 * I);
             P.b[a] = Tp[a] / I;
+            P.w[a] += Tp[a] / (2.0 * I);
+        } else {
+            P.b[a] = 0.0;
         }
     }
+    P.prev_fixed = P.fixed;
     P.steps += 1;
     double rec[15];
     for (int a = 0; a < 3; ++a) {

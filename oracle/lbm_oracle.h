@@ -48,6 +48,17 @@ int orc_add_sphere(orc_sim* s, const double pos[3], double diameter, double dens
                    double cv, double cv_omega, int fixed);
 void orc_set_particle_velocity(orc_sim* s, const double u[3], const double w[3]);
 void orc_set_gravity(orc_sim* s, const double g[3]);
+/* Held degrees of freedom of the sphere from the next step on: 0 none, 1
+ * translation and rotation, 2 translation only (rotation free).  A held
+ * group keeps its velocity and has zero acceleration; a released group
+ * starts its kick-drift-kick afresh.  -1 without a sphere or for another
+ * value.  (orc_add_sphere's `fixed` takes the same values.) */
+int orc_set_particle_fixed(orc_sim* s, int fixed);
+/* Velocity of the no-slip domain wall on the low (side 0) or high (side 1)
+ * face of a non-periodic axis (bounce-back with Ladd's moving-wall term,
+ * the CLI rule at delta = 1/2); -1 for a periodic axis. */
+int orc_set_wall_velocity(orc_sim* s, int axis, int side, const double u[3]);
+
 /* Test geometry: two moving plane walls normal to `axis` at coordinates lo < hi.
  * Cells whose centre lies outside [lo, hi] are solid; links use CLI with the
  * exact sub-grid distance. */

@@ -905,7 +905,8 @@ int orc_amr_add_sphere(orc_amr* a, const double pos[3], double diameter, double 
     Particle& P = a->part;
     P = Particle();
     P.present = true;
-    P.fixed = fixed != 0;
+    if (fixed < 0 || fixed > 2) return -1;
+    P.fixed = P.prev_fixed = fixed;
     for (int k = 0; k < 3; ++k) P.x[k] = pos[k];
     P.D = diameter;
     P.r = 0.5 * diameter;

@@ -45,6 +45,7 @@ struct orc_sim {
     std::vector<double> history;    // 15 per step
     double plane_force[3] = {0, 0, 0};
     std::vector<uint8_t> has_link;  // per cell: some source of the pull is solid
+    double wall_u[3][2][3] = {};    // velocity of the domain wall [axis][0 low, 1 high] (non-periodic axes)
 };
 
 namespace {
@@ -219,8 +220,19 @@ void stream_and_boundaries(orc_sim* s, double F[3], double T[3]) {
                 for (int q = 0; q < 19; ++q) {
                     long src;
                     if (!neighbour(s, i, j, k, q, -1, &src)) {
-                        // stationary no-slip domain wall: simple bounce-back
-                        gn[(size_t)q * n + x] = gt[(size_t)opposite(q) * n + x];
+                        // no-slip domain wall half-way between cells: bounce-back with
+                        // Ladd's moving-wall term 2 w_q rho_0 c_q.u_w / c_s^2 (the CLI
+                        // rule of Sec. 2.3 at delta = 1/2), summed over the faces the
+                        // link crosses
+                        double mw = 0.0;
+                        const int ijk[3] = {i, j, k};
+                        for (int a = 0; a < 3; ++a) {
+                            const int c = ijk[a] - C[q][a];
+                            if (s->p.periodic[a] || (c >= 0 && c < extent(s, a))) continue;
+                            const double* uw = s->wall_u[a][c < 0 ? 0 : 1];
+                            mw += 2.0 * W[q] * (C[q][0] * uw[0] + C[q][1] * uw[1] + C[q][2] * uw[2]) / CS2;
+                        }
+                        gn[(size_t)q * n + x] = gt[(size_t)opposite(q) * n + x] + mw;
                     } else if (s->flag[src] == FLUID) {
                         gn[(size_t)q * n + x] = gt[(size_t)q * n + src];
                     } else {
@@ -413,7 +425,8 @@ int orc_add_sphere(orc_sim* s, const double pos[3], double diameter, double dens
     Particle& P = s->part;
     P = Particle();
     P.present = true;
-    P.fixed = fixed != 0;
+    if (fixed < 0 || fixed > 2) return -1;
+    P.fixed = P.prev_fixed = fixed;
     for (int a = 0; a < 3; ++a) P.x[a] = pos[a];
     P.D = diameter;
     P.r = 0.5 * diameter;
@@ -553,6 +566,18 @@ int orc_set_threads(int n) {
     (void)n;
     return 1;
 #endif
+}
+
+int orc_set_particle_fixed(orc_sim* s, int fixed) {
+    if (!s->part.present || fixed < 0 || fixed > 2) return -1;
+    s->part.fixed = fixed;
+    return 0;
+}
+
+int orc_set_wall_velocity(orc_sim* s, int axis, int side, const double u[3]) {
+    if (axis < 0 || axis > 2 || side < 0 || side > 1 || s->p.periodic[axis]) return -1;
+    for (int a = 0; a < 3; ++a) s->wall_u[axis][side][a] = u[a];
+    return 0;
 }
 
 void orc_particle_only_step(orc_sim* s, const double F_hyd[3], const double T_hyd[3]) {
