@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--adjoint-reps", type=int, default=3)
     ap.add_argument("--validate-workload", default="refined", choices=["refined", "large"],
                     help="workload of --validate: the headline refined case or the large FP16 case")
+    ap.add_argument("--rotation", action="store_true",
+                    help="instead of timing: the rotating virtual-mass test (Sec. 3.4, Table 3) and one JSON line")
     ap.add_argument("--stability", action="store_true",
                     help="instead of timing: the stability-limit study (lowest stable density ratio per diameter at "
                          "Ga = 100, plain MEM and virtual mass) and one JSON line")
@@ -364,22 +366,70 @@ def validate(args):
 def stability_study(args):
     """Lowest stable density ratio per sphere diameter at Ga = 100 (Sec. 3.2,
     Table 1) with the plain momentum exchange method, by bisection in
-    log(pi_p), and the virtual-mass correction (C_v = 0.5) at pi_p = 0.001;
-    the paper's Table 1 alongside as context."""
+    log(pi_p), with the paper's collision (MRT, bulk factor 100) and its
+    force-oscillation criterion next to the status word; the same with TRT;
+    and the virtual-mass correction (C_v = 0.5) at pi_p = 0.001.  The
+    paper's Table 1 alongside as context."""
     import paper_2103_10882_gb300 as L
     from paper_2103_10882_gb300 import studies, workloads
     table = {10: 0.13, 15: 0.09, 20: 0.066, 30: 0.045, 40: 0.034}   # Table 1 of the paper (context)
     prec = args.precision
     out = {"study": "stability limit of light rising spheres, Ga=100, u_g=0.01, box (6.4, 6.4, 12.8) d_p, "
-                    "stable = no instability flag until t_n = 10", "precision": prec, "mem": {}, "vm_mem": {}}
+                    "stable = neither the force-oscillation criterion (step-to-step change of the hydrodynamic force "
+                    "above 100 |F_g|) nor the status word trips before t_n = 10", "precision": prec,
+           "mem_mrt100": {}, "mem_trt": {}, "vm_mem": {}}
     t0 = time.time()
     for d in workloads.STABILITY["diameters"]:
-        s, u, runs = studies.density_ratio_limit(L, d, 0.0, table[d] / 4, table[d] * 4, iters=4, precision=prec)
-        out["mem"][str(d)] = {"pi_min": s, "highest_unstable": u, "paper_table1": table[d], "runs": len(runs)}
-        ok, done, uz = studies.rising_sphere_run(L, d, 0.001, 0.5, precision=prec)
-        out["vm_mem"][str(d)] = {"density_ratio": 0.001, "stable": ok, "u_z_over_u_g": uz}
-        print("d %d: MEM pi_min %s (paper %.3f); VM-MEM at 0.001 stable %s" % (d, s, table[d], ok),
+        for key, bulk in (("mem_mrt100", 100.0), ("mem_trt", 1.0)):
+            s, u, runs = studies.density_ratio_limit(L, d, 0.0, table[d] / 4, table[d] * 4, iters=4, precision=prec,
+                                                     bulk=bulk)
+            trip = [dict(pi=r["density_ratio"], t_n_force=r["t_n_force"], t_n_status=r["t_n_status"]) for r in runs
+                    if not r["stable"]]
+            out[key][str(d)] = {"pi_min": s, "highest_unstable": u, "paper_table1": table[d], "runs": len(runs),
+                                "unstable_runs": trip}
+        r = studies.rising_sphere_run(L, d, 0.001, 0.5, precision=prec)
+        out["vm_mem"][str(d)] = {"density_ratio": 0.001, "stable": r["stable"], "u_z_over_u_g": r["u_z_over_u_g"]}
+        print("d %d: MEM (MRT 100) pi_min %s, MEM (TRT) %s (paper %.3f); VM-MEM at 0.001 stable %s"
+              % (d, out["mem_mrt100"][str(d)]["pi_min"], out["mem_trt"][str(d)]["pi_min"], table[d], r["stable"]),
               file=sys.stderr, flush=True)
+    out["seconds"] = time.time() - t0
+    print(json.dumps(out))
+    return 0
+
+
+def rotation_study(args):
+    """The rotating virtual-mass test (Sec. 3.4, Table 3): omega_n over t_n
+    for pi_p = 0.1 and 1.1 with MEM and VM-MEM (C_v = 0.5), and pi_p = 0.001
+    with both; the mean and terminal relative errors of VM-MEM against MEM
+    (Table 3's measures) and the paper's values alongside as context."""
+    import numpy as np
+    import paper_2103_10882_gb300 as L
+    from paper_2103_10882_gb300 import studies, workloads
+    w = workloads.ROTATION
+    table3 = {0.1: (0.46e-3, 0.01e-3), 1.1: (0.15e-3, 0.0)}   # Table 3 of the paper (context)
+    out = {"study": "rotating sphere with virtual mass: (12.8, 6.4, 4.8) d_p, walls on z, upper wall u_w=0.1, "
+                    "Couette start, d_p=%d, Re_p=110, translation held, rotation released after %g t_c, monitored "
+                    "for %g t_c" % (w["diameter"], w["develop_tc"], w["monitor_tc"]), "precision": args.precision,
+           "runs": {}}
+    t0 = time.time()
+    runs = {}
+    for pi in w["density_ratios"]:
+        for name, cv in (("mem", 0.0), ("vm_mem", 0.5)):
+            r = studies.rotating_sphere_run(L, pi, cv, precision=args.precision)
+            runs[(pi, name)] = r
+            om = np.asarray(r["omega_n"])
+            out["runs"]["%s_%g" % (name, pi)] = {
+                "stable": r["stable"], "samples": len(om), "omega_n_end": float(om[-1]) if len(om) else None,
+                "omega_n_at": {str(t): float(om[int(round(t * r["t_c"] / 10)) - 1]) for t in (0.5, 1, 2, 4, 8)
+                               if len(om) >= int(round(t * r["t_c"] / 10))}}
+            print("pi_p %g %s: stable %s, omega_n end %s" % (pi, name, r["stable"], out["runs"]["%s_%g" % (name, pi)]["omega_n_end"]),
+                  file=sys.stderr, flush=True)
+    out["errors_vm_vs_mem"] = {}
+    for pi in (0.1, 1.1):
+        if runs[(pi, "mem")]["stable"] and runs[(pi, "vm_mem")]["stable"]:
+            mean, term = studies.rotation_errors(runs[(pi, "vm_mem")], runs[(pi, "mem")])
+            out["errors_vm_vs_mem"][str(pi)] = {"mean_rel": mean, "terminal_rel": term,
+                                                "paper_table3": {"mean_rel": table3[pi][0], "terminal_rel": table3[pi][1]}}
     out["seconds"] = time.time() - t0
     print(json.dumps(out))
     return 0
@@ -549,6 +599,8 @@ def main():
         return validate(args)
     if args.stability:
         return stability_study(args)
+    if args.rotation:
+        return rotation_study(args)
     import numpy as np
     import torch
 

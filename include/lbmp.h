@@ -107,8 +107,23 @@ lbmp_status lbmp_add_sphere(lbmp_handle* h, const double pos[3], double diameter
 /* Translational and angular velocity of the sphere (the wall velocity the
  * fluid sees in the next step). */
 lbmp_status lbmp_set_particle_velocity(lbmp_handle* h, int id, const double u[3], const double omega[3]);
-/* fixed != 0 keeps the sphere in place (forces are still computed). */
+/* Held degrees of freedom of the sphere (forces are still computed):
+ * fixed = 0 none, 1 translation and rotation (the sphere keeps its place
+ * and velocities), 2 translation only, the rotation free (the rotating
+ * virtual-mass test of Sec. 3.4).  A held group keeps its velocity and
+ * records zero acceleration, so the virtual force or torque of Sec. 3.3
+ * after it is zero; a group released at a step starts its kick-drift-kick
+ * there (no half kick completing an earlier step).  Other values:
+ * LBMP_ERR_INVALID_ARG. */
 lbmp_status lbmp_set_particle_fixed(lbmp_handle* h, int id, int fixed);
+/* Velocity u (lattice units, |u_i| < 0.3) of the no-slip domain wall on the
+ * low (side 0) or high (side 1) face of a non-periodic axis: the wall sits
+ * half-way between cells and a link crossing it takes bounce-back plus
+ * Ladd's term 2 w_q rho_0 c_q.u / c_s^2, the CLI rule of Sec. 2.3 at
+ * delta = 1/2 (the moving upper wall of the Couette flow in Sec. 3.4).
+ * Uniform grids only (refined and batched: LBMP_ERR_UNSUPPORTED); a
+ * periodic axis: LBMP_ERR_INVALID_ARG.  Walls start at rest. */
+lbmp_status lbmp_set_wall_velocity(lbmp_handle* h, int axis, int side, const double u[3]);
 
 /* Galileo number relation (Sec. 3.1, Eq. Ga): u_g = sqrt(|pi_p - 1| g d_p),
  * Ga = u_g d_p / nu.  Pure host arithmetic: returns nu, |g| and tau. */

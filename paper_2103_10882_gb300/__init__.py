@@ -17,7 +17,7 @@ from . import _native
 from ._native import LbmpConfig
 
 __all__ = ["LbmpError", "Simulation", "lbmp_config_default", "lbmp_create", "lbmp_destroy", "lbmp_add_sphere",
-           "lbmp_set_particle_velocity", "lbmp_set_particle_fixed", "lbmp_ga_parameters", "lbmp_set_ga",
+           "lbmp_set_particle_velocity", "lbmp_set_particle_fixed", "lbmp_set_wall_velocity", "lbmp_ga_parameters", "lbmp_set_ga",
            "lbmp_set_tau", "lbmp_set_gravity", "lbmp_set_body_force", "lbmp_init_fluid", "lbmp_set_populations",
            "lbmp_get_populations", "lbmp_gather_populations", "lbmp_step", "lbmp_step_async", "lbmp_check_status", "lbmp_synchronize",
            "lbmp_get_particle", "lbmp_get_history", "lbmp_get_flags", "lbmp_get_links", "lbmp_get_counters",
@@ -92,7 +92,14 @@ def lbmp_set_particle_velocity(h, pid, u, omega=(0.0, 0.0, 0.0)):
 
 
 def lbmp_set_particle_fixed(h, pid, fixed=True):
-    _check(h, _lib().lbmp_set_particle_fixed(h, int(pid), int(bool(fixed))))
+    """fixed: False/0 free, True/1 translation and rotation held, 2 or "translation" translation held."""
+    mode = 2 if fixed == "translation" else int(fixed)
+    _check(h, _lib().lbmp_set_particle_fixed(h, int(pid), mode))
+
+
+def lbmp_set_wall_velocity(h, axis, side, u):
+    a = np.ascontiguousarray(u, dtype=np.float64)
+    _check(h, _lib().lbmp_set_wall_velocity(h, int(axis), int(side), _dp(a)))
 
 
 def lbmp_ga_parameters(ga, u_g, diameter, density_ratio):
@@ -442,7 +449,12 @@ class Simulation:
         lbmp_set_particle_velocity(self.h, 0, u, omega)
 
     def set_fixed(self, fixed=True):
+        """True: translation and rotation held; "translation": translation held, rotation free."""
         lbmp_set_particle_fixed(self.h, 0, fixed)
+
+    def set_wall_velocity(self, axis, side, u):
+        """Velocity of the domain wall on the low (0) or high (1) face of a non-periodic axis."""
+        lbmp_set_wall_velocity(self.h, axis, side, u)
 
     def mean_drag(self, tau, force, u0, nsteps, checkpoint_interval=50, axis=0):
         """Differentiable mean drag on the fixed sphere; see mean_drag()."""

@@ -55,6 +55,7 @@ SIGNATURES = {
                                        ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
     "lbmp_set_particle_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, c_double_p, c_double_p]),
     "lbmp_set_particle_fixed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
+    "lbmp_set_wall_velocity": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, c_double_p]),
     "lbmp_ga_parameters": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                           c_double_p, c_double_p, c_double_p]),
     "lbmp_set_ga": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, c_double_p]),

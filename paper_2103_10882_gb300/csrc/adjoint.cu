@@ -583,7 +583,7 @@ void adjoint_destroy(lbmp_handle* h) {
 lbmp_status adjoint_check(const lbmp_handle* h, std::string* why) {
     if (h->amr || h->batch) return *why = "the drag adjoint runs on a single uniform grid", LBMP_ERR_UNSUPPORTED;
     if (!h->has_particle) return *why = "the drag adjoint needs a sphere", LBMP_ERR_INVALID_ARG;
-    if (!h->h_ps.fixed) return *why = "the drag adjoint needs the sphere held fixed", LBMP_ERR_UNSUPPORTED;
+    if (h->h_ps.fixed != 1) return *why = "the drag adjoint needs the sphere held fixed", LBMP_ERR_UNSUPPORTED;
     for (int a = 0; a < 3; ++a) {
         if (!h->G.periodic[a]) return *why = "the drag adjoint needs a periodic box", LBMP_ERR_UNSUPPORTED;
         if (h->h_ps.u[a] != 0.0 || h->h_ps.w[a] != 0.0)

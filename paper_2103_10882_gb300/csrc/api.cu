@@ -417,10 +417,31 @@ lbmp_status lbmp_set_particle_velocity(lbmp_handle* h, int id, const double u[3]
 lbmp_status lbmp_set_particle_fixed(lbmp_handle* h, int id, int fixed) {
     if (!h) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_fixed: NULL handle");
     if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_fixed: no such sphere");
+    if (fixed < 0 || fixed > 2) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_particle_fixed: fixed must be 0, 1 or 2");
     lbmp_status s = download_particle(h);
     if (s != LBMP_OK) return s;
-    h->h_ps.fixed = fixed ? 1 : 0;
+    h->h_ps.fixed = fixed;
     return upload_particle(h);
+}
+
+lbmp_status lbmp_set_wall_velocity(lbmp_handle* h, int axis, int side, const double u[3]) {
+    if (!h || !u) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_wall_velocity: NULL argument");
+    if (h->amr || h->batch)
+        return fail(h, LBMP_ERR_UNSUPPORTED, "lbmp_set_wall_velocity: uniform grids only (refined walls are at rest)");
+    if (axis < 0 || axis > 2 || side < 0 || side > 1)
+        return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_wall_velocity: axis must be 0..2 and side 0 or 1");
+    if (h->G.periodic[axis]) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_wall_velocity: the axis is periodic");
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(u[a]) || std::fabs(u[a]) >= 0.3)
+            return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_set_wall_velocity: need finite |u| < 0.3 (lattice units)");
+        h->G.uw[axis][side][a] = u[a];
+    }
+    int moving = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int s = 0; s < 2; ++s)
+            for (int k = 0; k < 3; ++k) moving |= h->G.uw[a][s][k] != 0.0;
+    h->G.moving = moving;
+    return LBMP_OK;
 }
 
 lbmp_status lbmp_ga_parameters(double ga, double u_g, double diameter, double density_ratio, double* nu, double* g,
@@ -945,12 +966,13 @@ namespace {
 
 struct CkptHeader {
     char tag[8];              // "LBMPCKPT"
-    int32_t version;          // 1
+    int32_t version;          // 2
     int32_t nx, ny, nz, levels, precision, bc[3];
     int32_t has_particle, history_capacity, particle_bytes, kind;   // kind: 0 uniform, 1 refined
     double tau, magic, bulk_factor;
     double body_force[3];
     int64_t steps;
+    double wall_u[3][2][3];   // domain wall velocities (uniform grids)
 };
 
 bool put(FILE* f, const void* p, size_t n) { return n == 0 || fwrite(p, 1, n, f) == n; }
@@ -969,7 +991,7 @@ lbmp_status lbmp_save(lbmp_handle* h, const char* path) {
     CkptHeader H;
     std::memset(&H, 0, sizeof(H));
     std::memcpy(H.tag, "LBMPCKPT", 8);
-    H.version = 1;
+    H.version = 2;
     H.nx = h->cfg.nx;
     H.ny = h->cfg.ny;
     H.nz = h->cfg.nz;
@@ -985,6 +1007,7 @@ lbmp_status lbmp_save(lbmp_handle* h, const char* path) {
     H.bulk_factor = h->cfg.bulk_factor;
     for (int a = 0; a < 3; ++a) H.body_force[a] = h->body_force[a];
     H.steps = h->steps;
+    std::memcpy(H.wall_u, h->G.uw, sizeof(H.wall_u));
     FILE* f = std::fopen(path, "wb");
     if (!f) return fail(h, LBMP_ERR_INVALID_ARG, std::string("lbmp_save: cannot open ") + path);
     bool ok = put(f, &H, sizeof(H)) && put(f, &h->h_ps, sizeof(ParticleState));
@@ -1019,7 +1042,7 @@ lbmp_status lbmp_load(lbmp_handle* h, const char* path) {
     } closer{f};
     CkptHeader H;
     ParticleState P;
-    if (!get(f, &H, sizeof(H)) || std::memcmp(H.tag, "LBMPCKPT", 8) != 0 || H.version != 1 ||
+    if (!get(f, &H, sizeof(H)) || std::memcmp(H.tag, "LBMPCKPT", 8) != 0 || H.version != 2 ||
         H.particle_bytes != (int32_t)sizeof(ParticleState) || !get(f, &P, sizeof(P)))
         return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_load: not a checkpoint of this library version");
     bool same = H.nx == h->cfg.nx && H.ny == h->cfg.ny && H.nz == h->cfg.nz && H.levels == h->cfg.levels &&
@@ -1042,6 +1065,12 @@ lbmp_status lbmp_load(lbmp_handle* h, const char* path) {
     h->tau = H.tau;
     for (int a = 0; a < 3; ++a) h->body_force[a] = H.body_force[a];
     h->steps = H.steps;
+    if (!h->amr) {
+        std::memcpy(h->G.uw, H.wall_u, sizeof(H.wall_u));
+        int moving = 0;
+        for (const double* v = &H.wall_u[0][0][0]; v < &H.wall_u[0][0][0] + 18; ++v) moving |= *v != 0.0;
+        h->G.moving = moving;
+    }
     if (H.has_particle) {
         h->h_ps = P;
         const lbmp_status s = upload_particle(h);

@@ -20,7 +20,31 @@ struct GridDesc {
     int nx, ny, nz;
     int periodic[3];
     long long n;   // nx * ny * nz
+    // velocities of the no-slip domain walls [axis][0 low face, 1 high face] (uniform grids);
+    // moving != 0 when any is nonzero
+    double uw[3][2][3] = {};
+    int moving = 0;
 };
+
+// Moving-wall term of a pull from beyond a no-slip domain wall half-way
+// between cells: bounce-back plus Ladd's 2 w_q rho_0 c_q.u_w / c_s^2 = 6 w_q
+// c_q.u_w (the CLI rule of Sec. 2.3 at delta = 1/2), summed over the faces
+// the link from the cell xyz against c_q crosses.
+template <typename A>
+__device__ __forceinline__ A wall_term(const GridDesc& G, int q, const int xyz[3]) {
+    if (!G.moving) return A(0);
+    const int n3[3] = {G.nx, G.ny, G.nz};
+    const int c3[3] = {cx(q), cy(q), cz(q)};
+    A t = A(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int s = xyz[a] - c3[a];
+        if (G.periodic[a] || (s >= 0 && s < n3[a])) continue;
+        const double* u = G.uw[a][s < 0 ? 0 : 1];
+        t += A(6) * wgt<A>(q) * (A(c3[0]) * A(u[0]) + A(c3[1]) * A(u[1]) + A(c3[2]) * A(u[2]));
+    }
+    return t;
+}
 
 // Collision parameters in the arithmetic precision A of the storage type.
 template <typename A>

@@ -76,9 +76,9 @@ struct ParticleState {
     double D, r, rho_p, cv, cvw, V;
     long long steps;
     int present;
-    int fixed;
+    int fixed;         // held degrees of freedom: 0 none, 1 translation and rotation, 2 translation only
     int force_average;
-    int pad;
+    int prev_fixed;    // the value of fixed in the previous step
 };
 
 static_assert(sizeof(ParticleState) % sizeof(int) == 0, "particle record is copied as ints");

@@ -598,19 +598,25 @@ __device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, d
     P.Fp[a] = Fp;
     const double xold = P.x[a];
     const double acc = Fp * inv_m, bet = Tp * inv_I;
-    if (!P.fixed) {
-        if (P.steps > 0) {   // second half kick of the previous step completes u(t)
-            P.u[a] += 0.5 * acc;
-            P.w[a] += 0.5 * bet;
-        }
+    // A held group (translation; rotation) keeps its velocity and records zero acceleration, so the
+    // virtual force or torque after it is zero; a group released in this step starts afresh, with
+    // no half kick completing a previous step.
+    const bool tfree = P.fixed == 0, rfree = P.fixed != 1;
+    const bool tprev = P.steps > 0 && P.prev_fixed == 0, rprev = P.steps > 0 && P.prev_fixed != 1;
+    if (tfree) {
+        if (tprev) P.u[a] += 0.5 * acc;   // second half kick of the previous step completes u(t)
         P.a[a] = acc;
-        P.b[a] = bet;
         P.u[a] += 0.5 * acc;   // first half kick, then drift with u(t + 1/2)
-        P.w[a] += 0.5 * bet;
         P.x[a] += P.u[a];
     } else {
-        P.a[a] = acc;
+        P.a[a] = 0.0;
+    }
+    if (rfree) {
+        if (rprev) P.w[a] += 0.5 * bet;
         P.b[a] = bet;
+        P.w[a] += 0.5 * bet;
+    } else {
+        P.b[a] = 0.0;
     }
     if (!(fabs(P.x[a] - xold) <= 0.5) || !(fabs(P.u[a]) < 0.5) || !(fabs(P.w[a]) < 1e30)) {
         // a jump or a non-finite state: flag it, and keep the sphere where it was and at rest, so that
@@ -677,7 +683,10 @@ __device__ __forceinline__ void particle_block_update(ParticleState* __restrict_
         particle_advance_axis(sP, threadIdx.x, sFT[threadIdx.x], sFT[3 + threadIdx.x], sinv[0], sinv[1], G, history,
                               hist_cap, status);
     __syncthreads();
-    if (threadIdx.x == 0) sP.steps += 1;
+    if (threadIdx.x == 0) {
+        sP.steps += 1;
+        sP.prev_fixed = sP.fixed;
+    }
     __syncthreads();
     {
         const int* srcw = reinterpret_cast<const int*>(&sP);

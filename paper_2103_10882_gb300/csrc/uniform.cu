@@ -49,8 +49,9 @@ __global__ void __launch_bounds__(BULK_THREADS)
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const int sx = xs[cx(q) + 1], sy = ys[cy(q) + 1], sz = zs[cz(q) + 1];
-        if (WALLS && (sx < 0 || sy < 0 || sz < 0)) {   // stationary no-slip wall: bounce-back
-            g[q] = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
+        if (WALLS && (sx < 0 || sy < 0 || sz < 0)) {   // no-slip wall: bounce-back (moving: Ladd's term)
+            const int xyz[3] = {x, y, z};
+            g[q] = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale) + wall_term<A>(G, q, xyz);
         } else {
             const int off = sx + nx * (sy + ny * sz);
             g[q] = Store<S>::load(src + (size_t)q * n + off, P.inv_scale);
@@ -107,7 +108,7 @@ __global__ void __launch_bounds__(BNDW_THREADS)
                 far_ok &= f3[a] >= 0;
             }
             if (wall) {
-                gq = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale);
+                gq = Store<S>::load(src + (size_t)opp(q) * n + cell, P.inv_scale) + wall_term<A>(G, q, xyz);
             } else {
                 const size_t sidx = (size_t)s3[0] + (size_t)G.nx * ((size_t)s3[1] + (size_t)G.ny * (size_t)s3[2]);
                 if (q == 0 || flags[sidx] == 0) {

@@ -105,3 +105,10 @@ def fourier_velocity_field(shape, kmax: float, amplitude: float, seed: int) -> n
 # u_g = 0.01, run until t_n = t u_g / d_p = 10.
 STABILITY = dict(box=(6.4, 6.4, 12.8), start=(3.2, 3.2, 0.6), ga=100.0, u_g=0.01, t_n=10.0,
                  diameters=(10, 15, 20, 30, 40))
+# The rotating virtual-mass test (Sec. 3.4): a (12.8, 6.4, 4.8) d_p box with no-slip walls on z (the upper one
+# moving with u_w in x, the fluid starting from the Couette profile), the sphere at the centre with its
+# translation held and its rotation released after the flow around it has developed; Re_p = u_p d_p / nu
+# with u_p = u_w / 2 the undisturbed velocity at the centre.
+ROTATION = dict(box=(12.8, 6.4, 4.8), diameter=40, u_w=0.1, re_p=110.0, develop_tc=4.0, monitor_tc=8.0,
+                density_ratios=(0.1, 1.1, 0.001))
+
