@@ -226,31 +226,43 @@ def cpu_baseline(seconds, max_steps=None, warmup=0):
     """The FP64 refined oracle on the host cores, on a bounded sample of the
     same workload: the same hierarchy and sphere, `warmup` untimed level-0
     steps (at most one), then timed level-0 steps until `seconds` have passed
-    or `max_steps` are done (at least one)."""
+    or `max_steps` are done (at least one), first on all host cores (the
+    oracle's OpenMP loops, bit-identical results), then on one core for
+    half as long."""
     import oracle
     w = REFINED
     tau, gm = ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
-    o = oracle.RefinedSim(w["shape"], w["levels"], tau=tau, periodic=(0, 0, 1))
-    o.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
-                 cv=w["cv"])
-    o.set_gravity((0, 0, -gm))
-    o.set_sensor(*w["sensor"])
-    o.init_equilibrium()
-    upd = sum((o.block_map(l) >= 0).sum() * 4096 * (1 << l) for l in range(w["levels"]))
-    if warmup > 0:
-        o.step(1)
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        o.step(1)
-        steps += 1
-        dt = time.perf_counter() - t0
-        if dt >= seconds or (max_steps is not None and steps >= max_steps):
-            break
-    o.close()
-    return {"value": upd * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "refined workload (same hierarchy and sphere), %d level-0 steps in %.1f s, single thread"
-                      % (steps, dt)}
+    cores = os.cpu_count() or 1
+
+    def sample(threads, budget):
+        oracle.set_threads(threads)
+        o = oracle.RefinedSim(w["shape"], w["levels"], tau=tau, periodic=(0, 0, 1))
+        o.add_sphere(refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+                     cv=w["cv"])
+        o.set_gravity((0, 0, -gm))
+        o.set_sensor(*w["sensor"])
+        o.init_equilibrium()
+        upd = sum((o.block_map(l) >= 0).sum() * 4096 * (1 << l) for l in range(w["levels"]))
+        if warmup > 0:
+            o.step(1)
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            o.step(1)
+            steps += 1
+            dt = time.perf_counter() - t0
+            if dt >= budget or (max_steps is not None and steps >= max_steps):
+                break
+        o.close()
+        return upd * steps / dt / 1e6, steps, dt
+
+    v_all, n_all, t_all = sample(cores, seconds)
+    v_one, n_one, t_one = sample(1, 0.5 * seconds)
+    oracle.set_threads(cores)
+    return {"value": v_all, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "value_1_core": v_one,
+            "sample": "refined workload (same hierarchy and sphere): %d level-0 steps in %.1f s on %d threads, "
+                      "%d in %.1f s on one" % (n_all, t_all, cores, n_one, t_one)}
 
 
 def run_reference(args):

@@ -49,6 +49,7 @@
  */
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -87,7 +88,7 @@ struct orc_amr {
     Particle part;
     double gravity[3] = {0, 0, 0};
     std::vector<double> history;
-    int error = 0;                      // 1: a pull found no source, 2: sphere left the finest level
+    std::atomic<int> error{0};          // 1: a pull found no source, 2: sphere left the finest level
     std::vector<int> substep;           // per level: index (0 or 1) of the current step within the coarser step
     bool have_box = false;
     double box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
@@ -627,7 +628,9 @@ void regrid_now(orc_amr* a, bool use_sensor = false) {
 void explode(orc_amr* a, int l) {
     LevelData& D = a->lv[l];
     LevelData& F = a->lv[l + 1];
-    for (size_t gb = 0; gb < F.gpos.size(); ++gb)
+    const long ngb = (long)F.gpos.size();
+#pragma omp parallel for schedule(static)
+    for (long gb = 0; gb < ngb; ++gb)
         for (int c = 0; c < B3; ++c) {
             if (!F.gkind[gb * B3 + c]) continue;
             const int g[3] = {F.gpos[gb][0] * BS + c % BS, F.gpos[gb][1] * BS + (c / BS) % BS,
@@ -733,8 +736,16 @@ void update(orc_amr* a, int l, double F[3], double T[3]) {
     const bool finest = (l == a->L - 1);
     const bool coupled = finest && a->part.present;
     for (int k = 0; k < 3; ++k) F[k] = T[k] = 0.0;
-    for (size_t b = 0; b < D.rpos.size(); ++b)
+    // blocks are independent (each writes its own cells); the link forces
+    // and torques are summed per block in cell and q order and the block
+    // sums in block order, so the result does not depend on the threads
+    const long nrb = (long)D.rpos.size();
+    std::vector<double> FT((size_t)nrb * 6, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long b = 0; b < nrb; ++b)
         for (int c = 0; c < B3; ++c) {
+            double* Fb = &FT[(size_t)b * 6];
+            double* Tb = Fb + 3;
             const int g[3] = {D.rpos[b][0] * BS + c % BS, D.rpos[b][1] * BS + (c / BS) % BS,
                               D.rpos[b][2] * BS + c / (BS * BS)};
             double f[19];
@@ -762,7 +773,7 @@ void update(orc_amr* a, int l, double F[3], double T[3]) {
                         int s[3] = {g[0] - C[q][0], g[1] - C[q][1], g[2] - C[q][2]};
                         int sb, sc;
                         if (wrap(a, D, s) && locate(D, s, &sb, &sc) == LOC_REAL && D.flag[(size_t)sb * B3 + sc]) {
-                            f[q] = cli_link(a, D, g, q, (int)b, c, F, T);
+                            f[q] = cli_link(a, D, g, q, (int)b, c, Fb, Tb);
                             continue;
                         }
                     }
@@ -772,7 +783,14 @@ void update(orc_amr* a, int l, double F[3], double T[3]) {
             collide(D, f);
             for (int q = 0; q < 19; ++q) D.rg_new[pidx((int)b, q, c)] = f[q];
         }
-    for (size_t b = 0; b < D.gpos.size(); ++b)
+    for (long b = 0; b < nrb; ++b)
+        for (int k = 0; k < 3; ++k) {
+            F[k] += FT[(size_t)b * 6 + k];
+            T[k] += FT[(size_t)b * 6 + 3 + k];
+        }
+    const long ngb = (long)D.gpos.size();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long b = 0; b < ngb; ++b)
         for (int c = 0; c < B3; ++c) {
             const uint8_t k = D.gkind[b * B3 + c];
             if (k == 0) continue;

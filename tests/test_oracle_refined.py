@@ -375,3 +375,24 @@ def test_refined_flags_and_links_match_uniform_oracle(orc, pos):
     b = np.lexsort((uq, uc))
     assert np.array_equal(rc[a], uc[b]) and np.array_equal(rq[a], uq[b])
     assert np.abs(rd[a] - ud[b]).max() < 1e-15
+
+
+def test_refined_oracle_threads_bit_identical(orc):
+    """The refined oracle's parallel loops (blocks of a level, ghost blocks,
+    explosion) write disjoint cells and sum the link forces per block in a
+    fixed order, so one thread and several give the same bits."""
+    res = []
+    for threads in (1, 4):
+        orc.set_threads(threads)
+        s = orc.RefinedSim((16, 16, 16), 3, tau=0.7)
+        s.add_sphere((30.7, 33.2, 31.6), 10.0, 0.3, cv=0.5)
+        s.set_gravity((0, 0, -2e-4))
+        s.init_equilibrium()
+        s.step(2)
+        res.append(([s.real_cells(l)[1] for l in range(3)], s.history()))
+        s.close()
+    import os
+    orc.set_threads(os.cpu_count() or 1)
+    for a, b in zip(res[0][0], res[1][0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(res[0][1], res[1][1])
