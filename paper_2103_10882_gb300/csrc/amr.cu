@@ -1017,6 +1017,9 @@ struct AmrEngine {
     double sensor_sigma = 0.0, sensor_c = 0.0;   // flow sensor (sigma_c = 0: off)
     double* d_sensor = nullptr;                   // per real block of all levels
     size_t sensor_cap = 0;
+    // a layout rebuild failed part way (an allocation or a CUDA call): the levels are incomplete and
+    // every call but destroy refuses
+    bool broken = false;
 
 };
 
@@ -1263,6 +1266,15 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
     amr_drop_graphs(E);
     std::vector<Level> old;
     old.swap(E->lv);
+    // the old layout is freed on every way out (after the migration on success)
+    struct OldLevels {
+        lbmp_handle* h;
+        std::vector<Level>& v;
+        ~OldLevels() {
+            for (auto& V : v) free_level(h, V);
+        }
+    } old_guard{h, old};
+    E->broken = true;   // until the new layout is complete
     E->lv.assign(L, Level());
     for (int l = 0; l < L; ++l) {
         Level& V = E->lv[l];
@@ -1437,7 +1449,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         });
     }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
-    for (auto& V : old) free_level(h, V);
+    for (auto& V : old) free_level(h, V);   // (the migration above has finished reading them)
     // finest-level flags and boundary cells
     Level& Ff = E->lv[L - 1];
     if (h->has_particle || h->h_ps.present) {
@@ -1461,6 +1473,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         });
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
+    E->broken = false;
     return LBMP_OK;
 }
 
@@ -1688,6 +1701,7 @@ void amr_destroy(lbmp_handle* h) {
 }
 
 lbmp_status amr_add_sphere(lbmp_handle* h) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     const Level& F = E->lv[E->L - 1];
     // box around the sphere at the finest level (as in the uniform engine)
@@ -1726,6 +1740,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
 }
 
 lbmp_status amr_refine_box(lbmp_handle* h, const double lo[3], const double hi[3]) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     E->have_box = true;
     for (int a = 0; a < 3; ++a) {
@@ -1792,6 +1807,7 @@ lbmp_status sensor_values(lbmp_handle* h, std::vector<std::vector<double>>& phi)
 }  // namespace
 
 lbmp_status amr_regrid(lbmp_handle* h) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     if (h->has_particle) {
         if (cudaMemcpyAsync(&h->h_ps, h->d_ps, sizeof(ParticleState), cudaMemcpyDeviceToHost, h->stream) !=
@@ -1818,6 +1834,7 @@ lbmp_status amr_set_sensor(lbmp_handle* h, double sigma, double c) {
 }
 
 lbmp_status amr_block_sensor(lbmp_handle* h, int level, double* out, size_t cap, size_t* n) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
     *n = (size_t)E->lv[level].nreal;
@@ -1830,6 +1847,7 @@ lbmp_status amr_block_sensor(lbmp_handle* h, int level, double* out, size_t cap,
 }
 
 lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     const double Lax = (double)E->lv[E->L - 1].n[axis];
     with_storage_amr(h->cfg.precision, [&](auto tag) {
@@ -1849,6 +1867,7 @@ lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double
 }
 
 lbmp_status amr_step(lbmp_handle* h, int n) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     level_rates(E, h->tau, h->magic);
     if (E->graph_tau != h->tau) {
@@ -1938,6 +1957,7 @@ bool ck_get(FILE* f, void* p, size_t n) { return n == 0 || std::fread(p, 1, n, f
 // level's real-block populations (current buffer, storage type), then the
 // level-0 step count, the sensor and the refined box.
 lbmp_status amr_save(lbmp_handle* h, FILE* f) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     const int32_t L = E->L;
     bool ok = ck_put(f, &L, sizeof(L));
@@ -1966,6 +1986,7 @@ lbmp_status amr_save(lbmp_handle* h, FILE* f) {
 // Rebuilds the saved hierarchy (the finest flags follow from the restored
 // sphere position) and restores every level's populations.
 lbmp_status amr_load(lbmp_handle* h, FILE* f) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     int32_t L = 0;
     if (!ck_get(f, &L, sizeof(L)) || L != E->L) return LBMP_ERR_INVALID_ARG;
@@ -2023,6 +2044,7 @@ lbmp_status amr_block_map(lbmp_handle* h, int level, int32_t* out, size_t cap, s
 }
 
 lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, size_t cap, size_t* n) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
     Level& V = E->lv[level];
@@ -2052,6 +2074,7 @@ lbmp_status amr_level_cells(lbmp_handle* h, int level, int32_t* xyz, double* g, 
 }
 
 lbmp_status amr_level_flags(lbmp_handle* h, int level, uint8_t* out, size_t cap, size_t* n) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     if (level < 0 || level >= E->L) return LBMP_ERR_INVALID_ARG;
     Level& V = E->lv[level];
@@ -2069,6 +2092,7 @@ lbmp_status amr_level_flags(lbmp_handle* h, int level, uint8_t* out, size_t cap,
 }
 
 lbmp_status amr_links(lbmp_handle* h, int64_t* cell, int32_t* q, double* delta, size_t cap, size_t* n) {
+    if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
     *n = 0;
     if (!h->has_particle) return LBMP_OK;
