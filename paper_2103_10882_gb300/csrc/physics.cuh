@@ -32,8 +32,15 @@ __device__ __forceinline__ double link_delta(const double d[3], int q, double r)
 // TRT collision on deviations (Sec. 2.1, Lambda_b = 1): the symmetric part of
 // each pair relaxes with s+, the antisymmetric part with s-; incompressible
 // equilibrium with rho_0 = 1; optional Guo-type source split the same way.
-template <typename A, bool FORCED>
+// SCALED: g holds the deviations times 2^s (FP16 storage kept in its scaled
+// form); the collision is linear in g except for the equilibrium's two
+// quadratic terms, which then take one factor 2^-s (P.inv_scale).
+// MRT_MODE: -1 decides TRT or MRT from P.db at run time, 0 is TRT only, 1
+// MRT only (kernels that know which one runs carry no code of the other).
+template <typename A, bool FORCED, bool SCALED = false, int MRT_MODE = -1>
 __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& P, int* status) {
+    static_assert(!(FORCED && SCALED), "the scaled form is for the unforced collision");
+    const A q2 = SCALED ? P.inv_scale : A(1);
     A drho = A(0), jx = A(0), jy = A(0), jz = A(0);
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
@@ -51,10 +58,10 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
         uy += A(0.5) * P.F[1];
         uz += A(0.5) * P.F[2];
     }
-    const A uu = ux * ux + uy * uy + uz * uz;
-    if (!(uu <= A(0.09))) atomicOr(status, STATUS_UNSTABLE_FLUID);
+    const A uu = (ux * ux + uy * uy + uz * uz) * q2;
+    if (!(uu * q2 <= A(0.09))) atomicOr(status, STATUS_UNSTABLE_FLUID);
     const A sp = P.sp, sm = P.sm;
-    const bool mrt = P.db != A(0);
+    const bool mrt = MRT_MODE < 0 ? P.db != A(0) : MRT_MODE == 1;
     // MRT bulk correction: sums of (f - f_eq + source/2) over the rest,
     // face and edge populations (the even modes' inputs)
     A nR = A(0), nF = A(0), nE = A(0);
@@ -73,7 +80,7 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
     for (int q = 1; q < 19; q += 2) {
         const A cu = A(cx(q)) * ux + A(cy(q)) * uy + A(cz(q)) * uz;
         const A w = wgt<A>(q);
-        const A ep = w * (drho + A(4.5) * cu * cu - A(1.5) * uu);
+        const A ep = w * (drho + A(4.5) * q2 * cu * cu - A(1.5) * uu);
         const A em = w * (A(3) * cu);
         const A gp = A(0.5) * (g[q] + g[q + 1]);
         const A gm = A(0.5) * (g[q] - g[q + 1]);

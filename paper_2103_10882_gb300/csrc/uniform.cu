@@ -7,6 +7,8 @@
 // Populations are stored as deviations g = f - w in SoA layout [q][z][y][x].
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "internal.h"
 #include "physics.cuh"
 
@@ -60,6 +62,96 @@ __global__ void __launch_bounds__(BULK_THREADS)
     trt_collide<A, FORCED>(g, P, status);
 #pragma unroll
     for (int q = 0; q < 19; ++q) Store<S>::store(dst + (size_t)q * n + cell, g[q], P.scale);
+}
+
+// FP16 storage, unforced: the same update as k_bulk, two cells (x, x + 1,
+// x even) per thread.  Every population is read as the aligned pair of
+// halves of its source row; the populations shifted along x take their
+// outer half from the neighbouring lane (a shuffle); the first lane of a
+// warp (rows start there) and the last pair of a warp or of a row load that
+// one half themselves.  The collision runs on the stored, scaled values
+// (trt_collide's SCALED form), so neither the loads nor the stores multiply
+// by the scale, and TRT or MRT is chosen at compile time.  nx is even; rows
+// hold whole pairs.
+constexpr int BULK2_THREADS = 256;
+template <bool WALLS, bool MRT>
+__global__ void __launch_bounds__(BULK2_THREADS)
+    k_bulk_h2(const __half* __restrict__ src, __half* __restrict__ dst, GridDesc G, CollideParams<float> P,
+              int* __restrict__ status) {
+    const int xp = blockIdx.x * blockDim.x + threadIdx.x;   // pair index
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const int lane = threadIdx.x & 31;   // blockDim.x is a multiple of 32: a warp is one run of a row
+    const bool valid = 2 * xp < nx && y < ny;
+    const int x = valid ? 2 * xp : 0;
+    const int yy = valid ? y : 0;
+    const size_t n = (size_t)G.n;
+    const int cell = x + nx * (yy + ny * z);
+    int ys[3], zs[3];
+    ys[1] = yy;
+    zs[1] = z;
+    ys[0] = yy + 1 < ny ? yy + 1 : (WALLS && !G.periodic[1] ? -1 : 0);
+    ys[2] = yy > 0 ? yy - 1 : (WALLS && !G.periodic[1] ? -1 : ny - 1);
+    zs[0] = z + 1 < nz ? z + 1 : (WALLS && !G.periodic[2] ? -1 : 0);
+    zs[2] = z > 0 ? z - 1 : (WALLS && !G.periodic[2] ? -1 : nz - 1);
+    // x - 1 of the pair's first cell and x + 2 of its second (-1: beyond a wall)
+    const int xm = x > 0 ? x - 1 : (WALLS && !G.periodic[0] ? -1 : nx - 1);
+    const int xq = x + 2 < nx ? x + 2 : (WALLS && !G.periodic[0] ? -1 : 0);
+    // all loads first (the pairs, then the outer halves of the shifted populations, every lane
+    // loading one: the lanes that need none read their own pair's first half), then the shuffles
+    __half2 pr[19];
+    __half ex[19];
+    bool yw[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const int sy = ys[cy(q) + 1], sz = zs[cz(q) + 1];
+        yw[q] = WALLS && (sy < 0 || sz < 0);
+        const int row = nx * ((yw[q] ? yy : sy) + ny * (yw[q] ? z : sz));
+        const __half* pq = src + (size_t)q * n;
+        pr[q] = __ldg(reinterpret_cast<const __half2*>(pq + row + x));
+        if (cx(q) != 0) {
+            const int xe = cx(q) == 1 ? xm : xq;
+            const bool need = cx(q) == 1 ? lane == 0 : (lane == 31 || x + 2 >= nx);   // warp or row end
+            ex[q] = __ldg(pq + row + ((need && xe >= 0) ? xe : x));
+        }
+    }
+    float g0[19], g1[19];
+#pragma unroll
+    for (int q = 0; q < 19; ++q) {
+        const __half2 p = pr[q];
+        float a, b;
+        if (cx(q) == 0) {
+            a = __low2float(p);
+            b = __high2float(p);
+        } else if (cx(q) == 1) {   // sources x - 1 and x
+            const float prev = __shfl_up_sync(0xffffffffu, __high2float(p), 1);
+            a = lane == 0 ? __half2float(ex[q]) : prev;
+            b = __low2float(p);
+        } else {                   // sources x + 1 and x + 2
+            const float next = __shfl_down_sync(0xffffffffu, __low2float(p), 1);
+            a = __high2float(p);
+            b = (lane == 31 || x + 2 >= nx) ? __half2float(ex[q]) : next;
+        }
+        if (WALLS) {   // bounce-back (moving walls: Ladd's term, scaled like the stored values)
+            const bool wa = yw[q] || (cx(q) == 1 && xm < 0);
+            const bool wb = yw[q] || (cx(q) == -1 && xq < 0);
+            if (wa || wb) {
+                const __half2 o = *reinterpret_cast<const __half2*>(src + (size_t)opp(q) * n + cell);
+                const int xyz0[3] = {x, yy, z}, xyz1[3] = {x + 1, yy, z};
+                if (wa) a = __low2float(o) + wall_term<float>(G, q, xyz0) * P.scale;
+                if (wb) b = __high2float(o) + wall_term<float>(G, q, xyz1) * P.scale;
+            }
+        }
+        g0[q] = a;
+        g1[q] = b;
+    }
+    if (!valid) return;
+    trt_collide<float, false, true, MRT ? 1 : 0>(g0, P, status);
+    trt_collide<float, false, true, MRT ? 1 : 0>(g1, P, status);
+#pragma unroll
+    for (int q = 0; q < 19; ++q)
+        __stcs(reinterpret_cast<__half2*>(dst + (size_t)q * n + cell), __floats2half2_rn(g0[q], g1[q]));
 }
 
 // -------------------------------------------------------------- boundary
@@ -482,6 +574,21 @@ void launch_bulk(const S* src, S* dst, const GridDesc& g, const CollideParams<ty
     dim3 block(bx, by, 1);
     dim3 grid((g.nx + bx - 1) / bx, (g.ny + by - 1) / by, g.nz);
     const bool walls = !(g.periodic[0] && g.periodic[1] && g.periodic[2]);
+    if constexpr (std::is_same<S, __half>::value) {   // FP16, unforced, whole pairs: two cells per thread
+        if (!p.forced && g.nx % 2 == 0) {
+            const int pairs = g.nx / 2;
+            int px = 32;
+            while (px < pairs && px < 128) px *= 2;
+            dim3 b2(px, BULK2_THREADS / px, 1);
+            dim3 g2((pairs + px - 1) / px, (g.ny + b2.y - 1) / b2.y, g.nz);
+            const bool mrt = p.db != 0.0f;
+            if (walls && mrt) k_bulk_h2<true, true><<<g2, b2, 0, stream>>>(src, dst, g, p, status);
+            else if (walls) k_bulk_h2<true, false><<<g2, b2, 0, stream>>>(src, dst, g, p, status);
+            else if (mrt) k_bulk_h2<false, true><<<g2, b2, 0, stream>>>(src, dst, g, p, status);
+            else k_bulk_h2<false, false><<<g2, b2, 0, stream>>>(src, dst, g, p, status);
+            return;
+        }
+    }
     if (walls) {
         if (p.forced) k_bulk<S, true, true><<<grid, block, 0, stream>>>(src, dst, g, p, status);
         else k_bulk<S, true, false><<<grid, block, 0, stream>>>(src, dst, g, p, status);

@@ -248,3 +248,28 @@ def test_uniform_flow_invariant_large(lib):
     cu = C @ np.asarray(u)
     eq = W * (3 * cu + 4.5 * cu ** 2 - 1.5 * uu)
     assert np.abs(g - eq[:, None]).max() < 1e-7
+
+
+@pytest.mark.parametrize("shape,bc,wall", [
+    ((38, 29, 41), ("noslip", "noslip", "periodic"), None),      # even nx: two cells per thread, walls on x and y
+    ((37, 29, 41), ("noslip", "noslip", "periodic"), None),      # odd nx: one cell per thread
+    ((70, 24, 20), ("periodic", "periodic", "noslip"), (0.03, 0.01, 0.0)),   # a row longer than a warp's pairs, moving wall
+])
+def test_fp16_pairs_walls_against_oracle(orc, lib, shape, bc, wall):
+    """FP16 storage on grids with walls and rows of any length: the update
+    that reads aligned pairs of halves (even nx, shuffles across lanes, the
+    last pair of each row and each warp loading its outer half) and the one
+    cell per thread form (odd nx) both stay within the FP16 tolerance of the
+    FP64 oracle, with a light sphere moving and, in the last case, the upper
+    z wall moving."""
+    pos = np.array(shape, dtype=float) / 2 + np.array([0.3, -0.4, 0.2])
+    o, g = make_pair(orc, lib, shape, precision="fp16", tau=0.62, bc=bc, sphere=(pos, 8.0, 0.5, 0.5),
+                     gravity=(0, 0, -5e-5))
+    if wall is not None:
+        o.set_wall_velocity(2, 1, wall)
+        g.set_wall_velocity(2, 1, wall)
+    o.step(120)
+    g.step(120)
+    assert_pops_close(o, g, 5e-3)
+    Fscale = 0.5 * 5e-5 * np.pi * 8.0 ** 3 / 6
+    assert np.abs(g.history()[:, 0:3] - o.history()[:, 0:3]).max() <= 2e-2 * Fscale * (10 if wall else 1)
