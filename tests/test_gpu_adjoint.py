@@ -194,3 +194,42 @@ def test_full_workload_fp32_against_fp64(orc, lib):
     s64.close()
     assert gt == pytest.approx(fd_tau, rel=1e-4)
     assert gf[0] == pytest.approx(fd_f, rel=1e-4)
+
+
+def test_fp64_gradient_u0_element_by_element(orc, lib):
+    """dJ/du0 entry by entry against the tangent-linear oracle (one tangent
+    run per unit direction): every component of every fluid cell next to the
+    sphere (where the reverse step takes the link rules, k_adj_near), of 64
+    seeded fluid cells elsewhere, and of 8 cells inside the sphere (zero: the
+    fluid there is dropped).  16^3, d = 5, 20 steps, checkpoints every 7."""
+    shape, pos, D, tau, steps = (16, 16, 16), (8.3, 7.6, 8.2), 5.0, 0.7, 20
+    F = (1e-5, 2e-6, 0.0)
+    u0 = workloads.fourier_velocity_field(shape, 2, 1e-2, 31)
+    sim = make_sim(lib, shape, pos, D, tau, "fp64")
+    J, _, _, gu = run(lib, sim, tau, F, u0, steps, 7)
+    flags = sim.flags().reshape(tuple(reversed(shape)))
+    sim.close()
+    from lattice_ref import C
+    solid = flags != 0
+    near = np.zeros_like(solid)
+    for c in C[1:]:
+        near |= np.roll(solid, shift=(-c[2], -c[1], -c[0]), axis=(0, 1, 2))
+    near &= ~solid
+    rng = np.random.default_rng(7)
+    far = np.argwhere(~solid & ~near)
+    cells = [tuple(v) for v in np.argwhere(near)]
+    cells += [tuple(v) for v in far[rng.choice(len(far), 64, replace=False)]]
+    inside = np.argwhere(solid)
+    cells += [tuple(v) for v in inside[rng.choice(len(inside), 8, replace=False)]]
+    assert np.count_nonzero(near) >= 50
+    scale = np.abs(gu).max()
+    worst = 0.0
+    for (z, y, x) in cells:
+        for a in range(3):
+            du = np.zeros_like(u0)
+            du[a, z, y, x] = 1.0
+            _, d, _ = orc.drag_tangent(shape, tau, pos, D, steps, u0=u0, body_force=F, du0=du)
+            worst = max(worst, abs(gu[a, z, y, x] - d))
+            if solid[z, y, x]:
+                assert gu[a, z, y, x] == 0.0 and d == 0.0
+    assert worst <= 1e-9 * scale, worst / scale
