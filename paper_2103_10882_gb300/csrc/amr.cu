@@ -126,10 +126,8 @@ __device__ __forceinline__ void rescale19(A f[19], A kp, A km) {
 // only cells that change level in a regrid are rescaled, in k_migrate).
 template <typename S>
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0,
-              typename Store<S>::A scale, typename Store<S>::A inv_scale, const int* __restrict__ list, int n,
-              int* __restrict__ status) {
-    using A = typename Store<S>::A;
+    k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0, const int* __restrict__ list,
+              int n, int* __restrict__ status) {
     const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
     if (i >= n) return;
     const int e = list[i];   // ghost cell in use: pool block << 12 | cell
@@ -143,11 +141,11 @@ __global__ void __launch_bounds__(UPD_THREADS)
         atomicOr(status, STATUS_AMR_MISSING);
         return;
     }
-    A f[19];
+    S f[19];   // a copy of the stored values
 #pragma unroll
-    for (int q = 0; q < 19; ++q) f[q] = Store<S>::load(csrc + paddr(pb, q, pc), inv_scale);
+    for (int q = 0; q < 19; ++q) f[q] = csrc[paddr(pb, q, pc)];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) Store<S>::store(f0 + paddr(b, q, c), f[q], scale);
+    for (int q = 0; q < 19; ++q) f0[paddr(b, q, c)] = f[q];
 }
 
 // ----------------------------------------------------------------- update
@@ -169,7 +167,8 @@ struct UpdateArgs {
     int* status;
 };
 
-// Pull of the 19 populations of cell (b, c) into g.  nb27 lists the pool
+// Pull of the 19 populations of cell (b, c) into g, as stored (FP16: the
+// scaled values g * 2^s, which the collision takes in its SCALED form).  nb27 lists the pool
 // ids of block b's 26 neighbours (and itself at index 13).  rigid (static
 // ghost cells at the first sub-step): the pull carries the exploded field
 // one cell along c_q, so that at the second sub-step a static ghost holds,
@@ -180,7 +179,6 @@ template <typename S>
 __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27, bool rigid,
                                           typename Store<S>::A g[19]) {
     using A = typename Store<S>::A;
-    const A inv = U.P.inv_scale;
     const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
     // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate.
     // Every population is one load: from the neighbouring cell (real or
@@ -201,7 +199,7 @@ __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, 
         const bool own = nbk < 0;
         const int sb = own ? b : nbk, sq = (own && !rigid) ? opp(q) : q;
         const int sc = own ? c : lsx[ix] + lsy[iy] + lsz[iz];
-        const A v = Store<S>::load(U.src + (unsigned)((sb * 19 + sq) * B3 + sc), inv);   // pools hold < 2^31 elements
+        const A v = Store<S>::load_raw(U.src + (unsigned)((sb * 19 + sq) * B3 + sc));   // pools hold < 2^31 elements
         const bool lost = nbk == -1 && !rigid;
         missing |= lost;
         g[q] = lost ? A(0) : v;
@@ -222,9 +220,9 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
     } else {
         pull_cell<S>(U, b, c, nb27, rigid, g);
     }
-    if (REAL) trt_collide<A, false>(g, U.P, U.status);
+    if (REAL) trt_collide<A, false, sizeof(S) == 2>(g, U.P, U.status);
 #pragma unroll
-    for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), g[q], U.P.scale);
+    for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
 }
 
 // One launch per level step: the first gblocks CTAs stream ghost cells of
@@ -297,7 +295,7 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         const uint8_t f = U.solid[(size_t)b * B3 + c];
         if (f == FLAG_SOLID) {
 #pragma unroll
-            for (int q = 0; q < 19; ++q) Store<S>::store(U.dst + paddr(b, q, c), A(0), U.P.scale);
+            for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), A(0));
             return;
         }
         if (f == FLAG_BOUNDARY) return;
@@ -1540,8 +1538,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
                 xs = E->aux;
             }
             k_explode<S><<<grid, UPD_THREADS, 0, xs>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
-                                                       (S*)F.d_pops[F.cur], P.scale, P.inv_scale, F.d_xlist,
-                                                       F.nxlist, h->status);
+                                                       (S*)F.d_pops[F.cur], F.d_xlist, F.nxlist, h->status);
             if (beside) {
                 cudaEventRecord(E->ev_x[l + 1], E->aux);
                 E->x_pending[l + 1] = true;

@@ -45,12 +45,16 @@ struct Store<double> {
     using A = double;
     __device__ static __forceinline__ A load(const double* p, A) { return __ldg(p); }
     __device__ static __forceinline__ void store(double* p, A v, A) { __stcs(p, v); }
+    __device__ static __forceinline__ A load_raw(const double* p) { return __ldg(p); }
+    __device__ static __forceinline__ void store_raw(double* p, A v) { __stcs(p, v); }
 };
 template <>
 struct Store<float> {
     using A = float;
     __device__ static __forceinline__ A load(const float* p, A) { return __ldg(p); }
     __device__ static __forceinline__ void store(float* p, A v, A) { __stcs(p, v); }
+    __device__ static __forceinline__ A load_raw(const float* p) { return __ldg(p); }
+    __device__ static __forceinline__ void store_raw(float* p, A v) { __stcs(p, v); }
 };
 template <>
 struct Store<__half> {
@@ -60,6 +64,9 @@ struct Store<__half> {
         return __half2float(__ldg(p)) * inv_scale;
     }
     __device__ static __forceinline__ void store(__half* p, A v, A scale) { *p = __float2half_rn(v * scale); }
+    // the stored value g * 2^s itself (kernels that work on the scaled values)
+    __device__ static __forceinline__ A load_raw(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ static __forceinline__ void store_raw(__half* p, A v) { *p = __float2half_rn(v); }
 };
 
 // Device-resident state of the sphere, FP64 throughout (Sec. 2.2, 3.3).
