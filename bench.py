@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--long-steps", type=int, default=1000,
                     help="level-0 steps of the long developed window of the headline workload (FP32 line)")
+    ap.add_argument("--cuda-profiler-window", action="store_true",
+                    help="bracket the developed window of the headline precision with cudaProfilerStart/Stop (for "
+                         "ncu --profile-from-start off)")
     ap.add_argument("--no-other-precisions", action="store_true",
                     help="skip the FP16-storage and FP64 windows of the headline workload")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -568,7 +571,13 @@ def refined_runs(L, prec, args, torch, local, dist, world, full):
         sim.step(max(start - int(sim.counters()[0]), 0))
         start = int(sim.counters()[0])
         maps0 = [sim.block_map(l).copy() for l in range(w["levels"])]
+        window = full and args.cuda_profiler_window
+        if window:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
         ms, _, d0, d1 = timed(sim, args.steps, sim.stream, torch, profile=False)
+        if window:
+            torch.cuda.profiler.stop()
         maps1 = [sim.block_map(l) for l in range(w["levels"])]
         ms_max = max_over_ranks(ms, dist, "cuda")
         regrids = sum(1 for s_ in range(start + 1, start + args.steps + 1) if s_ % interval == 0)
