@@ -95,6 +95,14 @@ def parse():
 REFINED_NAME = ("refined rising sphere: level-0 64x64x256 (16^3 blocks), 3 levels, d=20 finest, pi_p=0.5, Ga=200, "
                 "C_v=0.5, walls x/y, periodic z, regrid every 50 level-0 steps (particle + curl sensor sigma_c=1e-3, "
                 "c=0.2)")
+# The paper's only performance figures (Table 4, CPU, context only: another machine, method, workload and metric):
+# the uniform-grid rising sphere at d_p = 100 on SuperMUC-NG took 10.27 h on 36,864 processes for about 3.6e5 finest
+# steps of 3.06e9 cells (derived: about 29.8 GLUPS in total, 0.81 MLUPS per process); the adaptive run took 6.58 h
+# on 768 processes with 3.78e7 cells on average.
+PAPER_CONTEXT = {"source": "Table 4 (SuperMUC-NG, MPI CPU processes)",
+                 "uniform_grid": {"processes": 36864, "cells": 3.06e9, "hours": 10.27,
+                                  "derived_glups_total": 29.8, "derived_mlups_per_process": 0.81},
+                 "adaptive_grid": {"processes": 768, "mean_cells": 3.78e7, "hours": 6.58}}
 # level-0 step from which the run counts as developed: the wake has grown the finest level (3.3 -> 4-5 M
 # cell updates per level-0 step) and regrids change the hierarchy
 DEVELOPED_STEP = 2000
@@ -640,6 +648,7 @@ def main():
         "metric": METRIC, "value": ref["value"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ref["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE[prec], "data": "synthetic",
+        "paper_context": PAPER_CONTEXT,
         "config": dict(ref["config"], workload=REFINED_NAME, precision=prec,
                        parallelism="replicas" if world > 1 else "single GPU"),
     })
