@@ -8,14 +8,15 @@
 // resolution) in one pool, real blocks first, both in block-position order.
 // One level-l step (recursive, finer levels sub-cycled twice, Rohde's scheme
 // named in Sec. 4.1):
-//   k_explode   ghost cells of level l+1 in use <- post-collision level-l cell
-//               containing them (into the buffer of the first sub-step)
+//   k_explode   active ghost cells of level l+1 <- post-collision level-l
+//               cell containing them (into the buffer of the first sub-step)
 //   (two level-(l+1) steps)
 //   k_update    real level-l cells: pull from real/ghost neighbours, or, for
 //               hosts (neighbours of the finer region), the mean of their
 //               eight ghost sub-cells (coalescence); then TRT collide.  Active
-//               ghost cells stream without colliding; static ghost cells stand
-//               for coarse content translating rigidly.
+//               ghost cells stream without colliding; the static ghost cells
+//               beyond them stand for coarse content translating rigidly and
+//               are read from the coarse level, not stored.
 //   finest level: k_amr_boundary (CLI links + momentum-exchange partials),
 //               particle update, remap (flags, refill, boundary cells).
 // The layout (which blocks exist at which level) is integer work done on the
@@ -117,30 +118,38 @@ __device__ __forceinline__ void rescale19(A f[19], A kp, A km) {
     }
 }
 
+// Pool block of the neighbour of (b, local l) displaced by d (|d| <= 1 per
+// axis), with the local index; -2 wall, -1 none.
+__device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int ly, int lz, int dx, int dy, int dz,
+                                        int* cell) {
+    const int sx = lx + dx, sy = ly + dy, sz = lz + dz;
+    const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
+    const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
+    const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
+    *cell = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
+    return (ox | oy | oz) == 0 ? b : D.nbr[b * 27 + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
+}
+
 // --------------------------------------------------------------- explosion
-// Explosion for one coarse step of level l: every ghost cell of level l+1
-// in use takes the post-collision populations of the level-l cell that
-// contains it, into f0, the source of the first sub-step.  No rescaling: the
-// 1.5-fine-cell offset between the coarse centre and the first fine cell
-// supplies the level change of the non-equilibrium part (Chapman-Enskog;
-// only cells that change level in a regrid are rescaled, in k_migrate).
+// Explosion for one coarse step of level l: every active ghost cell of level
+// l+1 (list: pool block << 12 | cell, eight consecutive entries per host)
+// takes the post-collision populations of its host, the level-l cell that
+// contains it (hosts: real block << 12 | cell, one per eight entries), into
+// f0, the source of the first sub-step.  No rescaling: the 1.5-fine-cell
+// offset between the coarse centre and the first fine cell supplies the
+// level change of the non-equilibrium part (Chapman-Enskog; only cells that
+// change level in a regrid are rescaled, in k_migrate).
 template <typename S>
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_explode(LevelView C, const S* __restrict__ csrc, LevelView F, S* __restrict__ f0, const int* __restrict__ list,
-              int n, int* __restrict__ status) {
+    k_explode(const S* __restrict__ csrc, S* __restrict__ f0, const int* __restrict__ list,
+              const int* __restrict__ hosts, int n) {
     const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
     if (i >= n) return;
-    const int e = list[i];   // ghost cell in use: pool block << 12 | cell
+    const int e = list[i];
     const int b = e >> 12;
     const int c = e & 4095;
-    const int p[3] = {(F.bpos[3 * b] * BS + (c & 15)) >> 1, (F.bpos[3 * b + 1] * BS + ((c >> 4) & 15)) >> 1,
-                      (F.bpos[3 * b + 2] * BS + (c >> 8)) >> 1};
-    int pc;
-    const int pb = locate(C, p, &pc);
-    if (pb < 0 || pb >= C.nreal) {
-        atomicOr(status, STATUS_AMR_MISSING);
-        return;
-    }
+    const int hp = hosts[i >> 3];
+    const int pb = hp >> 12, pc = hp & 4095;
     S f[19];   // a copy of the stored values
 #pragma unroll
     for (int q = 0; q < 19; ++q) f[q] = csrc[paddr(pb, q, pc)];
@@ -160,24 +169,44 @@ struct UpdateArgs {
     // which the next finer level's last sub-step left in coal_in (this
     // level's layout)
     const A* coal_in;
-    // at this level's last sub-step: the next coarser level C and its coal_in
+    // levels with a coarser level C: its post-collision populations of the
+    // current coarse step (csrc, read for static ghost neighbours), per group
+    // of eight active ghost cells their host (real block << 12 | cell of C),
+    // per active ghost cell the mask of populations whose upwind neighbour is
+    // a static ghost cell; at the last sub-step also C's coal_in
     LevelView C;
+    const S* csrc;
+    const int* ghost_host;
+    const uint32_t* smask;
     A* coal_out;
     const uint8_t* solid;     // finest level with a sphere: solid flags of real cells
     int* status;
 };
 
+// Where an active ghost cell finds a static ghost cell upwind.  Static ghost
+// cells (the sub-cells of the second ring of coarse cells) hold the exploded
+// coarse values at the first sub-step and stream rigidly, without
+// colliding, into the second, so each of their values is that of a coarse
+// cell, which the pull reads directly: with P the host of the active cell x
+// and s in {0,1}^3 its sub-cell offset, the coarse cell containing x - c_q
+// is P + o, o_a = s_a - 1 for c_a = 1, s_a for c_a = -1, 0 for c_a = 0
+// (first sub-step); at the second sub-step the static cell has carried the
+// content of the coarse cell containing x - 2 c_q, which is P - c_q, or
+// kept its own (P + o) where that lies beyond a wall.
+struct GhostPull {
+    uint32_t smask;   // bit q: the upwind neighbour x - c_q is a static ghost cell
+    int hb, hc;       // the host P: real block and cell of the coarser level
+    int sub;          // sub-cell offset s = (sub & 1, (sub >> 1) & 1, sub >> 2)
+    bool second;      // the level's second sub-step
+};
+
 // Pull of the 19 populations of cell (b, c) into g, as stored (FP16: the
 // scaled values g * 2^s, which the collision takes in its SCALED form).  nb27 lists the pool
-// ids of block b's 26 neighbours (and itself at index 13).  rigid (static
-// ghost cells at the first sub-step): the pull carries the exploded field
-// one cell along c_q, so that at the second sub-step a static ghost holds,
-// for each q, the exploded value of the coarse cell one cell further upwind
-// (coarse content translating rigidly); beyond a wall, or where no block
-// exists (a value no update reads), the cell keeps its own value.
-template <typename S>
-__device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27, bool rigid,
-                                          typename Store<S>::A g[19]) {
+// ids of block b's 26 neighbours (and itself at index 13).  GHOST: (b, c) is
+// an active ghost cell and gp says where static ghost cells lie upwind.
+template <typename S, bool GHOST = false>
+__device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
+                                          typename Store<S>::A g[19], GhostPull gp = GhostPull{}) {
     using A = typename Store<S>::A;
     const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
     // source x - c_q per axis, indexed by 1 - c: block shift and local coordinate.
@@ -197,10 +226,22 @@ __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, 
         const int ix = 1 - cx(q), iy = 1 - cy(q), iz = 1 - cz(q);
         const int nbk = nb27[13 + bsx[ix] + 3 * bsy[iy] + 9 * bsz[iz]];   // entry 13 is b itself
         const bool own = nbk < 0;
-        const int sb = own ? b : nbk, sq = (own && !rigid) ? opp(q) : q;
+        const int sb = own ? b : nbk, sq = own ? opp(q) : q;
         const int sc = own ? c : lsx[ix] + lsy[iy] + lsz[iz];
-        const A v = Store<S>::load_raw(U.src + (unsigned)((sb * 19 + sq) * B3 + sc));   // pools hold < 2^31 elements
-        const bool lost = nbk == -1 && !rigid;
+        const S* src = U.src + (unsigned)((sb * 19 + sq) * B3 + sc);   // pools hold < 2^31 elements
+        bool lost = nbk == -1;
+        if (GHOST && q > 0 && ((gp.smask >> q) & 1u)) {   // static ghost upwind: its coarse cell
+            const int hx = gp.hc & 15, hy = (gp.hc >> 4) & 15, hz = gp.hc >> 8;
+            const int ox = cx(q) == 1 ? (gp.sub & 1) - 1 : (cx(q) == -1 ? (gp.sub & 1) : 0);
+            const int oy = cy(q) == 1 ? ((gp.sub >> 1) & 1) - 1 : (cy(q) == -1 ? ((gp.sub >> 1) & 1) : 0);
+            const int oz = cz(q) == 1 ? (gp.sub >> 2) - 1 : (cz(q) == -1 ? (gp.sub >> 2) : 0);
+            int cc;
+            int cb = gp.second ? nbr_cell(U.C, gp.hb, hx, hy, hz, -cx(q), -cy(q), -cz(q), &cc) : -2;
+            if (cb == -2) cb = nbr_cell(U.C, gp.hb, hx, hy, hz, ox, oy, oz, &cc);
+            lost = cb < 0;
+            src = U.csrc + (unsigned)(((lost ? 0 : cb) * 19 + q) * B3 + cc);
+        }
+        const A v = Store<S>::load_raw(src);
         missing |= lost;
         g[q] = lost ? A(0) : v;
     }
@@ -210,55 +251,52 @@ __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, 
 // Update of one cell of pool block b: real cells pull (or, for hosts, take
 // the coalesced mean) and collide; ghost cells pull only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL>
-__device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
-                                            bool rigid = false) {
+__device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27) {
     using A = typename Store<S>::A;
     A g[19];
     if (HAS_FINE && REAL && U.D.host[(size_t)b * B3 + c] == 1) {
 #pragma unroll
         for (int q = 0; q < 19; ++q) g[q] = U.coal_in[paddr(b, q, c)];
     } else {
-        pull_cell<S>(U, b, c, nb27, rigid, g);
+        pull_cell<S>(U, b, c, nb27, g);
     }
     if (REAL) trt_collide<A, false, sizeof(S) == 2>(g, U.P, U.status);
 #pragma unroll
     for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
 }
 
-// One launch per level step: the first gblocks CTAs stream ghost cells of
-// the level (a list of pool block << 12 | cell: the active ghost cells,
-// eight consecutive entries per host cell of the coarser level, then the
-// static ones), no collision.  At the first sub-step they stream the active
-// and the static cells (rigidly) into dst.  At the last sub-step they
-// stream the active ones and, instead of storing them, sum each host's
-// eight in a fixed shuffle tree; the first lane of each eight writes the
-// mean into the coarser level's coal_in (coalescence).  The other CTAs
-// update the real blocks, B3 / UPD_THREADS CTAs per block, each a run of
-// UPD_THREADS cells in block order (full warps).  All read src; the
-// real-block CTAs write dst only.
+// One launch per level step: the first gblocks CTAs stream the active ghost
+// cells of the level (glist: pool block << 12 | cell, eight consecutive
+// entries per host cell of the coarser level), no collision.  At the first
+// sub-step they store them into dst.  At the last sub-step they sum each
+// host's eight in a fixed shuffle tree instead, and the first lane of each
+// eight writes the mean into the coarser level's coal_in (coalescence).
+// The other CTAs update the real blocks, B3 / UPD_THREADS CTAs per block,
+// each a run of UPD_THREADS cells in block order (full warps).  All read
+// src (and the ghost lanes the coarser level's csrc); the real-block CTAs
+// write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
 __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS)
-    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int nactive, int gblocks, int coalesce) {
+    k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int gblocks, int coalesce) {
     using A = typename Store<S>::A;
     if (HAS_COARSE && (int)blockIdx.x < gblocks) {   // uniform across the block
         const int i = blockIdx.x * UPD_THREADS + threadIdx.x;
-        if (!coalesce) {
-            if (i < nglist) {
-                const int e = glist[i];
-                const int b = e >> 12, c = e & 4095;
-                update_cell<S, false, true, false>(U, b, c, U.D.nbr + (size_t)b * 27, i >= nactive);
-            }
-            return;
-        }
-        // last sub-step: every lane takes part in the shuffles (nglist is a multiple of 8)
+        // every lane of the last sub-step takes part in the shuffles (nglist is a multiple of 8)
         const bool valid = i < nglist;
+        if (!coalesce && !valid) return;
         A g[19];
-        int b = 0, c = 0;
+        int hp = 0;
         if (valid) {
             const int e = glist[i];
-            b = e >> 12;
-            c = e & 4095;
-            pull_cell<S>(U, b, c, U.D.nbr + (size_t)b * 27, false, g);
+            const int b = e >> 12, c = e & 4095;
+            hp = U.ghost_host[i >> 3];
+            const GhostPull gp{U.smask[i], hp >> 12, hp & 4095, i & 7, coalesce != 0};
+            pull_cell<S, true>(U, b, c, U.D.nbr + (size_t)b * 27, g, gp);
+            if (!coalesce) {
+#pragma unroll
+                for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
+                return;
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < 19; ++q) g[q] = A(0);
@@ -272,16 +310,9 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
             g[q] = v;
         }
         if (valid && (i & 7) == 0) {
-            const int p[3] = {(U.D.bpos[3 * b] * BS + (c & 15)) >> 1, (U.D.bpos[3 * b + 1] * BS + ((c >> 4) & 15)) >> 1,
-                              (U.D.bpos[3 * b + 2] * BS + (c >> 8)) >> 1};
-            int hc;
-            const int hb = locate(U.C, p, &hc);
-            if (hb < 0 || hb >= U.C.nreal) {
-                atomicOr(U.status, STATUS_AMR_MISSING);
-            } else {
+            const int hb = hp >> 12, hc = hp & 4095;
 #pragma unroll
-                for (int q = 0; q < 19; ++q) U.coal_out[paddr(hb, q, hc)] = g[q] * A(0.125);
-            }
+            for (int q = 0; q < 19; ++q) U.coal_out[paddr(hb, q, hc)] = g[q] * A(0.125);
         }
         return;
     }
@@ -304,18 +335,6 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
 }
 
 // ---------------------------------------------------------------- coupling
-// Pool block of the neighbour of (b, local l) displaced by d (|d| <= 1 per
-// axis), with the local index; -2 wall, -1 none.
-__device__ __forceinline__ int nbr_cell(const LevelView& D, int b, int lx, int ly, int lz, int dx, int dy, int dz,
-                                        int* cell) {
-    const int sx = lx + dx, sy = ly + dy, sz = lz + dz;
-    const int ox = sx < 0 ? -1 : (sx > 15 ? 1 : 0);
-    const int oy = sy < 0 ? -1 : (sy > 15 ? 1 : 0);
-    const int oz = sz < 0 ? -1 : (sz > 15 ? 1 : 0);
-    *cell = (sx & 15) + BS * ((sy & 15) + BS * (sz & 15));
-    return (ox | oy | oz) == 0 ? b : D.nbr[b * 27 + (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)];
-}
-
 constexpr int BNDW_THREADS = 256;
 constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid)
 // Register cap of the boundary kernel (BNDW_THREADS threads).  It runs beside the finest level's
@@ -644,9 +663,9 @@ __global__ void __launch_bounds__(LINK_THREADS)
 
 // ------------------------------------------------------ classification
 // Host flag of every real cell: 1 when a cell covered by the next finer
-// level lies within Chebyshev distance 1, 2 when the nearest is at 2.  Each
-// CTA (a run of 256 cells) also counts its cells of either kind into
-// run_counts[2 * run], run_counts[2 * run + 1].
+// level lies within Chebyshev distance 1, 2 when the nearest is at 2 (the
+// second ring).  Each CTA (a run of 256 cells) also counts its hosts into
+// run_counts[run].
 __global__ void __launch_bounds__(256) k_host_flags(LevelView D, uint8_t* __restrict__ host, int* __restrict__ run_counts) {
     const int b = blockIdx.x >> 4;
     const int bx = D.bpos[3 * b], by = D.bpos[3 * b + 1], bz = D.bpos[3 * b + 2];
@@ -665,72 +684,91 @@ __global__ void __launch_bounds__(256) k_host_flags(LevelView D, uint8_t* __rest
             }
     const int kind = dist <= 1 ? 1 : (dist == 2 ? 2 : 0);
     host[(size_t)b * B3 + c] = (uint8_t)kind;
-    __shared__ int wc[2][8];
-    const unsigned b1 = __ballot_sync(0xffffffffu, kind == 1), b2 = __ballot_sync(0xffffffffu, kind == 2);
-    if ((threadIdx.x & 31) == 0) {
-        wc[0][threadIdx.x >> 5] = __popc(b1);
-        wc[1][threadIdx.x >> 5] = __popc(b2);
-    }
+    __shared__ int wc[8];
+    const unsigned b1 = __ballot_sync(0xffffffffu, kind == 1);
+    if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = __popc(b1);
     __syncthreads();
-    if (threadIdx.x < 2) {
+    if (threadIdx.x == 0) {
         int t = 0;
-        for (int w = 0; w < 8; ++w) t += wc[threadIdx.x][w];
-        run_counts[2 * blockIdx.x + threadIdx.x] = t;
+        for (int w = 0; w < 8; ++w) t += wc[w];
+        run_counts[blockIdx.x] = t;
     }
 }
 
-// Ghost-cell list of level l+1 from the host flags of level l (same runs as
-// k_host_flags): the eight sub-cells of every host (flag 1) in host order
-// (real block, then cell) and sub-cell order, then those of every
-// second-ring cell (flag 2), the static ghost cells.  An entry is the
-// sub-cell's pool block << 12 | cell.  n1: hosts of the whole level.
+// Active ghost-cell list of level l+1 from the host flags of level l (same
+// runs as k_host_flags): the eight sub-cells of every host (flag 1) in host
+// order (real block, then cell) and sub-cell order, each entry the
+// sub-cell's pool block << 12 | cell, and per host its real block << 12 |
+// cell in hosts.
 __global__ void __launch_bounds__(256)
-    k_ghost_lists(LevelView C, const uint8_t* __restrict__ host, const int* __restrict__ run_counts, int n1,
-                  LevelView F, int* __restrict__ list, int* __restrict__ status) {
-    __shared__ int red[2][256];
-    __shared__ int wc[2][8];
-    int s1 = 0, s2 = 0;
-    for (int r = threadIdx.x; r < (int)blockIdx.x; r += 256) {
-        s1 += run_counts[2 * r];
-        s2 += run_counts[2 * r + 1];
-    }
-    red[0][threadIdx.x] = s1;
-    red[1][threadIdx.x] = s2;
+    k_ghost_lists(LevelView C, const uint8_t* __restrict__ host, const int* __restrict__ run_counts, LevelView F,
+                  int* __restrict__ list, int* __restrict__ hosts, int* __restrict__ status) {
+    __shared__ int red[256];
+    __shared__ int wc[8];
+    int s1 = 0;
+    for (int r = threadIdx.x; r < (int)blockIdx.x; r += 256) s1 += run_counts[r];
+    red[threadIdx.x] = s1;
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + h];
-            red[1][threadIdx.x] += red[1][threadIdx.x + h];
-        }
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
         __syncthreads();
     }
     const int b = blockIdx.x >> 4;
     const int c = ((blockIdx.x & 15) << 8) + threadIdx.x;
-    const int kind = host[(size_t)b * B3 + c];
-    const unsigned b1 = __ballot_sync(0xffffffffu, kind == 1), b2 = __ballot_sync(0xffffffffu, kind == 2);
+    const bool is_host = host[(size_t)b * B3 + c] == 1;
+    const unsigned b1 = __ballot_sync(0xffffffffu, is_host);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        wc[0][warp] = __popc(b1);
-        wc[1][warp] = __popc(b2);
-    }
+    if (lane == 0) wc[warp] = __popc(b1);
     __syncthreads();
-    if (kind == 0) return;
-    int pos = red[kind - 1][0];
-    for (int w = 0; w < warp; ++w) pos += wc[kind - 1][w];
-    pos += __popc((kind == 1 ? b1 : b2) & ((1u << lane) - 1u));
-    int* out = list + 8 * (kind == 1 ? pos : n1 + pos);
+    if (!is_host) return;
+    int pos = red[0];
+    for (int w = 0; w < warp; ++w) pos += wc[w];
+    pos += __popc(b1 & ((1u << lane) - 1u));
+    hosts[pos] = (b << 12) | c;
+    int* out = list + 8 * pos;
     const int p[3] = {C.bpos[3 * b] * BS + (c & 15), C.bpos[3 * b + 1] * BS + ((c >> 4) & 15), C.bpos[3 * b + 2] * BS + (c >> 8)};
     for (int sub = 0; sub < 8; ++sub) {
         const int g[3] = {2 * p[0] + (sub & 1), 2 * p[1] + ((sub >> 1) & 1), 2 * p[2] + (sub >> 2)};
         int gc;
         const int gb = locate(F, g, &gc);
-        if (gb < F.nreal) {   // by construction every sub-cell of a host or second-ring cell is a ghost cell
+        if (gb < F.nreal) {   // by construction every sub-cell of a host is a ghost cell
             atomicOr(status, STATUS_AMR_MISSING);
             out[sub] = 0;
             continue;
         }
         out[sub] = (gb << 12) | gc;
     }
+}
+
+// Static-neighbour masks of the active ghost cells of level F (list and
+// hosts of k_ghost_lists, n entries): bit q is set when the upwind
+// neighbour x - c_q lies in a ghost block and its coarse cell (P + o, see
+// GhostPull) is a second-ring cell of level C (host flag 2).  A ghost
+// neighbour whose coarse cell is neither a host nor in the second ring is
+// an error of the layout.
+__global__ void __launch_bounds__(256)
+    k_ghost_smask(LevelView C, LevelView F, const int* __restrict__ list, const int* __restrict__ hosts, int n,
+                  uint32_t* __restrict__ smask, int* __restrict__ status) {
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const int e = list[i], hp = hosts[i >> 3];
+    const int b = e >> 12, c = e & 4095, hb = hp >> 12, hc = hp & 4095, sub = i & 7;
+    const int s[3] = {sub & 1, (sub >> 1) & 1, sub >> 2};
+    uint32_t m = 0;
+    for (int q = 1; q < 19; ++q) {
+        const int cq[3] = {cx(q), cy(q), cz(q)};
+        int nc;
+        const int nbk = nbr_cell(F, b, c & 15, (c >> 4) & 15, c >> 8, -cq[0], -cq[1], -cq[2], &nc);
+        if (nbk < F.nreal) continue;   // a real cell, a wall or no block: the ordinary pull
+        int o[3];
+        for (int a = 0; a < 3; ++a) o[a] = cq[a] == 1 ? s[a] - 1 : (cq[a] == -1 ? s[a] : 0);
+        int pc;
+        const int pb = nbr_cell(C, hb, hc & 15, (hc >> 4) & 15, hc >> 8, o[0], o[1], o[2], &pc);
+        const int kind = (pb >= 0 && pb < C.nreal) ? C.host[(size_t)pb * B3 + pc] : 0;
+        if (kind == 2) m |= 1u << q;
+        else if (kind != 1) atomicOr(status, STATUS_AMR_MISSING);
+    }
+    smask[i] = m;
 }
 
 __global__ void k_amr_flags_full(LevelView D, uint8_t* __restrict__ f0, uint8_t* __restrict__ f1,
@@ -973,8 +1011,9 @@ struct Level {
     uint8_t* d_refined = nullptr;
     uint8_t* d_host = nullptr;
     int nglist = 0;              // active ghost cells (host sub-cells)
-    int* d_xlist = nullptr;      // every ghost cell in use, pool block << 12 | cell: the active ones, then the static ones
-    int nxlist = 0;
+    int* d_glist = nullptr;      // the active ghost cells, pool block << 12 | cell, eight per host
+    int* d_ghost_host = nullptr; // per eight: the host, real block << 12 | cell of the coarser level
+    uint32_t* d_smask = nullptr; // per active ghost cell: populations with a static ghost cell upwind
     void* d_pops[2] = {nullptr, nullptr};
     int cur = 0;
     void* d_coal = nullptr;      // levels with a finer level: coalesced host values, arithmetic type, pops layout
@@ -1234,7 +1273,9 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_nbr);
     handle_free(h, V.d_refined);
     handle_free(h, V.d_host);
-    handle_free(h, V.d_xlist);
+    handle_free(h, V.d_glist);
+    handle_free(h, V.d_ghost_host);
+    handle_free(h, V.d_smask);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
     handle_free(h, V.d_coal);
@@ -1384,36 +1425,38 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         Level& C = E->lv[l];
         if (C.nreal == 0) continue;
         const size_t nr = (size_t)C.nreal * 16;
-        d_runs[l] = (int*)handle_alloc(h, sizeof(int) * 2 * nr);
+        d_runs[l] = (int*)handle_alloc(h, sizeof(int) * nr);
         if (!d_runs[l]) {
             ok = false;
             break;
         }
-        runs[l].resize(2 * nr);
+        runs[l].resize(nr);
         k_host_flags<<<(unsigned)nr, 256, 0, h->stream>>>(view(E, C), C.d_host, d_runs[l]);
-        if (cudaMemcpyAsync(runs[l].data(), d_runs[l], sizeof(int) * 2 * nr, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        if (cudaMemcpyAsync(runs[l].data(), d_runs[l], sizeof(int) * nr, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
             ok = false;
-        h->d2h += (long long)(sizeof(int) * 2 * nr);
+        h->d2h += (long long)(sizeof(int) * nr);
     }
     if (ok && cudaStreamSynchronize(h->stream) != cudaSuccess) ok = false;
     for (int l = 0; l + 1 < L && ok; ++l) {
         Level& C = E->lv[l];
         Level& F = E->lv[l + 1];
-        long long n1 = 0, n2 = 0;
-        for (size_t r = 0; r < runs[l].size(); r += 2) {
-            n1 += runs[l][r];
-            n2 += runs[l][r + 1];
-        }
+        long long n1 = 0;
+        for (size_t r = 0; r < runs[l].size(); ++r) n1 += runs[l][r];
         F.nglist = (int)(8 * n1);
-        F.nxlist = (int)(8 * (n1 + n2));
-        F.d_xlist = (int*)handle_alloc(h, sizeof(int) * std::max<size_t>((size_t)F.nxlist, 1));
-        if (!F.d_xlist) {
+        const size_t ng = std::max<size_t>((size_t)F.nglist, 8);
+        F.d_glist = (int*)handle_alloc(h, sizeof(int) * ng);
+        F.d_ghost_host = (int*)handle_alloc(h, sizeof(int) * (ng / 8));
+        F.d_smask = (uint32_t*)handle_alloc(h, sizeof(uint32_t) * ng);
+        if (!F.d_glist || !F.d_ghost_host || !F.d_smask) {
             ok = false;
             break;
         }
-        if (F.nxlist > 0)
-            k_ghost_lists<<<(unsigned)C.nreal * 16, 256, 0, h->stream>>>(view(E, C), C.d_host, d_runs[l], (int)n1,
-                                                                           view(E, F), F.d_xlist, h->status);
+        if (F.nglist > 0) {
+            k_ghost_lists<<<(unsigned)C.nreal * 16, 256, 0, h->stream>>>(view(E, C), C.d_host, d_runs[l], view(E, F),
+                                                                           F.d_glist, F.d_ghost_host, h->status);
+            k_ghost_smask<<<(unsigned)((F.nglist + 255) / 256), 256, 0, h->stream>>>(
+                view(E, C), view(E, F), F.d_glist, F.d_ghost_host, F.nglist, F.d_smask, h->status);
+        }
     }
     if (ok && cudaStreamSynchronize(h->stream) != cudaSuccess) ok = false;
     for (int l = 0; l < L; ++l) handle_free(h, d_runs[l]);
@@ -1525,8 +1568,8 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     const CollideParams<A> P = level_params<S>(h, V);
     if (l + 1 < L) {
         Level& F = E->lv[l + 1];
-        if (F.nxlist > 0) {
-            const unsigned grid = (unsigned)((F.nxlist + UPD_THREADS - 1) / UPD_THREADS);
+        if (F.nglist > 0) {
+            const unsigned grid = (unsigned)((F.nglist + UPD_THREADS - 1) / UPD_THREADS);
             // Only level l+1's own update reads the exploded ghost cells.  When level l+1 has a finer
             // level, that level's sub-steps come first and touch neither level l+1's ghost cells nor
             // level l's populations, so the explosion runs beside them on aux.
@@ -1537,8 +1580,8 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
                 cudaStreamWaitEvent(E->aux, E->ev_aux_fork, 0);
                 xs = E->aux;
             }
-            k_explode<S><<<grid, UPD_THREADS, 0, xs>>>(view(E, V), (const S*)V.d_pops[V.cur], view(E, F),
-                                                       (S*)F.d_pops[F.cur], F.d_xlist, F.nxlist, h->status);
+            k_explode<S><<<grid, UPD_THREADS, 0, xs>>>((const S*)V.d_pops[V.cur], (S*)F.d_pops[F.cur], F.d_glist,
+                                                       F.d_ghost_host, F.nglist);
             if (beside) {
                 cudaEventRecord(E->ev_x[l + 1], E->aux);
                 E->x_pending[l + 1] = true;
@@ -1555,16 +1598,22 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     U.P = P;
     U.coal_in = nullptr;
     U.C = U.D;
+    U.csrc = nullptr;
+    U.ghost_host = nullptr;
+    U.smask = nullptr;
     U.coal_out = nullptr;
     U.solid = nullptr;
     U.status = h->status;
     const bool has_fine = l + 1 < L, has_coarse = l > 0;
     if (has_fine) U.coal_in = (const A*)V.d_coal;   // coalescence: the finer level's eight-cell means
     const int coalesce = (has_coarse && sub == 1) ? 1 : 0;   // this sub-step ends the coarser level's step
-    if (coalesce) {
+    if (has_coarse) {
         Level& C = E->lv[l - 1];
         U.C = view(E, C);
-        U.coal_out = (A*)C.d_coal;
+        U.csrc = (const S*)C.d_pops[C.cur];   // the coarser level updates after both sub-steps
+        U.ghost_host = V.d_ghost_host;
+        U.smask = V.d_smask;
+        if (coalesce) U.coal_out = (A*)C.d_coal;
     }
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) {
@@ -1595,20 +1644,19 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         E->x_pending[l] = false;
     }
     const long long ev0 = profile_mark(h);
-    // ghost cells streamed: the active ones, and at the first sub-step also
-    // the static ones (xlist holds both, active first)
-    const int ng = has_coarse ? (sub == 0 ? V.nxlist : V.nglist) : 0;
+    // the active ghost cells streamed (static ones are read from the coarser level)
+    const int ng = has_coarse ? V.nglist : 0;
     const int gblocks = (ng + UPD_THREADS - 1) / UPD_THREADS;
     if (V.nreal > 0 || gblocks > 0) {
         const unsigned grid = (unsigned)(V.nreal * (B3 / UPD_THREADS) + gblocks);
-        const int* gl = V.d_xlist;
+        const int* gl = V.d_glist;
         cudaStream_t st = h->stream;
-        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
-        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, V.nglist, gblocks, coalesce);
+        if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
+        else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
+        else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
+        else if (has_coarse) k_update<S, false, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
+        else if (coupled) k_update<S, false, false, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
+        else k_update<S, false, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
         h->launches += 1;
     }
     profile_kernel(h, ev0, profile_mark(h), 38.0 * sizeof(S) * (double)V.nreal * B3, (double)V.nreal * B3);
@@ -2153,7 +2201,7 @@ int amr_launches_per_coarse_step(const lbmp_handle* h) {
     const AmrEngine* E = h->amr;
     int per = 0;
     for (int l = E->L - 1; l >= 0; --l) {
-        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nxlist > 0) ? 1 : 0) +
+        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nglist > 0) ? 1 : 0) +
                   ((l == E->L - 1 && h->has_particle) ? 2 : 0);
         per = own + 2 * per;
     }
