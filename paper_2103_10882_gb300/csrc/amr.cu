@@ -165,20 +165,18 @@ struct UpdateArgs {
     const S* src;
     S* dst;
     CollideParams<A> P;
-    // coalescence: a host cell takes the mean of its eight ghost sub-cells,
-    // which the next finer level's last sub-step left in coal_in (this
-    // level's layout)
-    const A* coal_in;
     // levels with a coarser level C: its post-collision populations of the
     // current coarse step (csrc, read for static ghost neighbours), per group
     // of eight active ghost cells their host (real block << 12 | cell of C),
     // per active ghost cell the mask of populations whose upwind neighbour is
-    // a static ghost cell; at the last sub-step also C's coal_in
+    // a static ghost cell; at the last sub-step also C's destination buffer
+    // and collision parameters, for the hosts (coalescence)
     LevelView C;
     const S* csrc;
     const int* ghost_host;
     const uint32_t* smask;
-    A* coal_out;
+    S* cdst;
+    CollideParams<A> Pc;
     const uint8_t* solid;     // finest level with a sphere: solid flags of real cells
     int* status;
 };
@@ -248,19 +246,16 @@ __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, 
     if (missing) atomicOr(U.status, STATUS_AMR_MISSING);
 }
 
-// Update of one cell of pool block b: real cells pull (or, for hosts, take
-// the coalesced mean) and collide; ghost cells pull only.
-template <typename S, bool HAS_FINE, bool HAS_COARSE, bool REAL>
+// Update of the real cell c of pool block b: pull and collide.  Hosts (the
+// cells next to the finer region) are left to the finer level's last
+// sub-step, which forms their coalesced populations.
+template <typename S, bool HAS_FINE>
 __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27) {
     using A = typename Store<S>::A;
+    if (HAS_FINE && U.D.host[(size_t)b * B3 + c] == 1) return;
     A g[19];
-    if (HAS_FINE && REAL && U.D.host[(size_t)b * B3 + c] == 1) {
-#pragma unroll
-        for (int q = 0; q < 19; ++q) g[q] = U.coal_in[paddr(b, q, c)];
-    } else {
-        pull_cell<S>(U, b, c, nb27, g);
-    }
-    if (REAL) trt_collide<A, false, sizeof(S) == 2>(g, U.P, U.status);
+    pull_cell<S>(U, b, c, nb27, g);
+    trt_collide<A, false, sizeof(S) == 2>(g, U.P, U.status);
 #pragma unroll
     for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
 }
@@ -270,11 +265,13 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 // entries per host cell of the coarser level), no collision.  At the first
 // sub-step they store them into dst.  At the last sub-step they sum each
 // host's eight in a fixed shuffle tree instead, and the first lane of each
-// eight writes the mean into the coarser level's coal_in (coalescence).
-// The other CTAs update the real blocks, B3 / UPD_THREADS CTAs per block,
-// each a run of UPD_THREADS cells in block order (full warps).  All read
-// src (and the ghost lanes the coarser level's csrc); the real-block CTAs
-// write dst only.
+// eight takes the mean as the host's populations (coalescence), collides
+// them with the coarser level's parameters and writes the host into the
+// coarser level's destination buffer, the step of the coarser level that
+// its own update (which skips hosts) is taking beside.  The other CTAs
+// update the real blocks, B3 / UPD_THREADS CTAs per block, each a run of
+// UPD_THREADS cells in block order (full warps).  All read src (and the
+// ghost lanes the coarser level's csrc); the real-block CTAs write dst only.
 template <typename S, bool HAS_FINE, bool HAS_COARSE, bool COUPLED>
 __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS)
     k_update(UpdateArgs<S> U, const int* __restrict__ glist, int nglist, int gblocks, int coalesce) {
@@ -312,7 +309,10 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         if (valid && (i & 7) == 0) {
             const int hb = hp >> 12, hc = hp & 4095;
 #pragma unroll
-            for (int q = 0; q < 19; ++q) U.coal_out[paddr(hb, q, hc)] = g[q] * A(0.125);
+            for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
+            trt_collide<A, false, sizeof(S) == 2>(g, U.Pc, U.status);
+#pragma unroll
+            for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.cdst + paddr(hb, q, hc), g[q]);
         }
         return;
     }
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         }
         if (f == FLAG_BOUNDARY) return;
     }
-    update_cell<S, HAS_FINE, HAS_COARSE, true>(U, b, c, nb27);
+    update_cell<S, HAS_FINE>(U, b, c, nb27);
 }
 
 // ---------------------------------------------------------------- coupling
@@ -1016,7 +1016,6 @@ struct Level {
     uint32_t* d_smask = nullptr; // per active ghost cell: populations with a static ghost cell upwind
     void* d_pops[2] = {nullptr, nullptr};
     int cur = 0;
-    void* d_coal = nullptr;      // levels with a finer level: coalesced host values, arithmetic type, pops layout
     uint8_t* d_flags[2] = {nullptr, nullptr};   // finest level only
     int fcur = 0;
     double taup = 0, taum = 0;
@@ -1045,12 +1044,15 @@ struct AmrEngine {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_remap = nullptr;   // a finest remap left on the side stream (remap_pending) ends here
     bool remap_pending = false;
-    // explosions into a level that has a finer level of its own run on aux, beside that finer
-    // level's sub-steps; the level's first update waits for ev_x[level]
-    cudaStream_t aux = nullptr;
-    cudaEvent_t ev_aux_fork = nullptr;
-    cudaEvent_t ev_x[MAXL] = {};
-    bool x_pending[MAXL] = {};
+    // Levels below the finest each update on a stream of their own, beside the finer levels'
+    // sub-steps (the finest level runs on the caller's stream).  ev_state[l]: level l's last
+    // update ended; ev_xdone[l]: the explosion into level l+1 ended, and with it every earlier
+    // sub-step of level l+1 (which wrote level l's hosts and read its other buffer).
+    cudaStream_t lstream[MAXL] = {};
+    cudaEvent_t ev_state[MAXL] = {};
+    cudaEvent_t ev_xdone[MAXL] = {};
+    cudaEvent_t ev_begin = nullptr;
+    int prio_high = 0;   // the greatest stream priority
     double sensor_sigma = 0.0, sensor_c = 0.0;   // flow sensor (sigma_c = 0: off)
     double* d_sensor = nullptr;                   // per real block of all levels
     size_t sensor_cap = 0;
@@ -1278,7 +1280,6 @@ void free_level(lbmp_handle* h, Level& V) {
     handle_free(h, V.d_smask);
     handle_free(h, V.d_pops[0]);
     handle_free(h, V.d_pops[1]);
-    handle_free(h, V.d_coal);
     handle_free(h, V.d_flags[0]);
     handle_free(h, V.d_flags[1]);
     V = Level();
@@ -1397,11 +1398,6 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         V.d_host = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
         if (!V.d_map || !V.d_refined || !V.d_bpos || !V.d_nbr || !V.d_pops[0] || !V.d_pops[1] || !V.d_host)
             return LBMP_ERR_OOM;
-        if (l + 1 < L) {
-            const size_t as = h->cfg.precision == LBMP_FP64 ? 8 : 4;
-            V.d_coal = handle_alloc(h, as * 19 * B3 * (size_t)std::max(V.nreal, 1));
-            if (!V.d_coal) return LBMP_ERR_OOM;
-        }
         if (l == L - 1) {
             V.d_flags[0] = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
             V.d_flags[1] = (uint8_t*)handle_alloc(h, (size_t)B3 * std::max(V.nreal, 1));
@@ -1559,6 +1555,27 @@ CollideParams<typename Store<S>::A> level_params(const lbmp_handle* h, const Lev
     return p;
 }
 
+// Stream of level l's launches: the caller's for the finest level (and for
+// every level while per-kernel events are taken), a stream of its own for
+// each coarser level.
+cudaStream_t level_stream(const lbmp_handle* h, int l) {
+    const AmrEngine* E = h->amr;
+    return (h->profiling || l == E->L - 1) ? h->stream : E->lstream[l];
+}
+
+// One step of level l (sub: which of its parent's two sub-steps, 0 for
+// level 0).  Work order and dependencies:
+//   - the explosion into level l+1 (on l+1's stream) waits for level l's
+//     last update (ev_state[l]); level l's hosts of that state were written
+//     by level l+1's previous sub-step, earlier on the same stream;
+//   - level l+1 takes its two sub-steps, the second writing level l's hosts
+//     of the new state;
+//   - level l's update (on its own stream) waits only for that explosion
+//     (ev_xdone[l]), after which no earlier sub-step of level l+1 still
+//     reads the buffer it writes; it runs beside level l+1's sub-steps and
+//     writes every real cell of level l but the hosts.
+// The finest level runs on the caller's stream, so the critical path is the
+// chain of finest sub-steps, with the coarser updates beside it.
 template <typename S>
 void enqueue_advance(lbmp_handle* h, int l, int sub) {
     using A = typename Store<S>::A;
@@ -1566,54 +1583,47 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     const int L = E->L;
     Level& V = E->lv[l];
     const CollideParams<A> P = level_params<S>(h, V);
+    const cudaStream_t st = level_stream(h, l);
     if (l + 1 < L) {
         Level& F = E->lv[l + 1];
+        const cudaStream_t fs = level_stream(h, l + 1);
+        if (fs != st) cudaStreamWaitEvent(fs, E->ev_state[l], 0);
         if (F.nglist > 0) {
             const unsigned grid = (unsigned)((F.nglist + UPD_THREADS - 1) / UPD_THREADS);
-            // Only level l+1's own update reads the exploded ghost cells.  When level l+1 has a finer
-            // level, that level's sub-steps come first and touch neither level l+1's ghost cells nor
-            // level l's populations, so the explosion runs beside them on aux.
-            const bool beside = l + 2 < L;
-            cudaStream_t xs = h->stream;
-            if (beside) {
-                cudaEventRecord(E->ev_aux_fork, h->stream);
-                cudaStreamWaitEvent(E->aux, E->ev_aux_fork, 0);
-                xs = E->aux;
-            }
-            k_explode<S><<<grid, UPD_THREADS, 0, xs>>>((const S*)V.d_pops[V.cur], (S*)F.d_pops[F.cur], F.d_glist,
+            k_explode<S><<<grid, UPD_THREADS, 0, fs>>>((const S*)V.d_pops[V.cur], (S*)F.d_pops[F.cur], F.d_glist,
                                                        F.d_ghost_host, F.nglist);
-            if (beside) {
-                cudaEventRecord(E->ev_x[l + 1], E->aux);
-                E->x_pending[l + 1] = true;
-            }
             h->launches += 1;
         }
+        if (fs != st) cudaEventRecord(E->ev_xdone[l], fs);
         enqueue_advance<S>(h, l + 1, 0);
         enqueue_advance<S>(h, l + 1, 1);
+        if (fs != st) cudaStreamWaitEvent(st, E->ev_xdone[l], 0);
     }
     UpdateArgs<S> U;
     U.D = view(E, V);
     U.src = (const S*)V.d_pops[V.cur];
     U.dst = (S*)V.d_pops[1 - V.cur];
     U.P = P;
-    U.coal_in = nullptr;
     U.C = U.D;
     U.csrc = nullptr;
     U.ghost_host = nullptr;
     U.smask = nullptr;
-    U.coal_out = nullptr;
+    U.cdst = nullptr;
+    U.Pc = P;
     U.solid = nullptr;
     U.status = h->status;
     const bool has_fine = l + 1 < L, has_coarse = l > 0;
-    if (has_fine) U.coal_in = (const A*)V.d_coal;   // coalescence: the finer level's eight-cell means
     const int coalesce = (has_coarse && sub == 1) ? 1 : 0;   // this sub-step ends the coarser level's step
     if (has_coarse) {
         Level& C = E->lv[l - 1];
         U.C = view(E, C);
-        U.csrc = (const S*)C.d_pops[C.cur];   // the coarser level updates after both sub-steps
+        U.csrc = (const S*)C.d_pops[C.cur];   // the coarser level's step flips cur after both sub-steps
         U.ghost_host = V.d_ghost_host;
         U.smask = V.d_smask;
-        if (coalesce) U.coal_out = (A*)C.d_coal;
+        if (coalesce) {
+            U.cdst = (S*)C.d_pops[1 - C.cur];
+            U.Pc = level_params<S>(h, C);
+        }
     }
     const bool coupled = (l == L - 1) && h->has_particle;
     if (coupled) {
@@ -1627,10 +1637,10 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         for (int a = 0; a < 3; ++a) G.periodic[a] = E->periodic[a];
         G.n = (long long)V.n[0] * V.n[1] * V.n[2];
         if (E->remap_pending) {   // the previous remap (side stream) before this update
-            cudaStreamWaitEvent(h->stream, E->ev_remap, 0);
+            cudaStreamWaitEvent(st, E->ev_remap, 0);
             E->remap_pending = false;
         }
-        cudaEventRecord(E->ev_fork, h->stream);
+        cudaEventRecord(E->ev_fork, st);
         cudaStreamWaitEvent(E->side, E->ev_fork, 0);
         const size_t pre_bytes = sizeof(int) * (size_t)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS + 1);
         k_amr_boundary<S><<<E->boundary_blocks, BNDW_THREADS, pre_bytes, E->side>>>(
@@ -1639,10 +1649,6 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         cudaEventRecord(E->ev_join, E->side);
         h->launches += 1;
     }
-    if (E->x_pending[l]) {   // this level's ghost cells, exploded on aux
-        cudaStreamWaitEvent(h->stream, E->ev_x[l], 0);
-        E->x_pending[l] = false;
-    }
     const long long ev0 = profile_mark(h);
     // the active ghost cells streamed (static ones are read from the coarser level)
     const int ng = has_coarse ? V.nglist : 0;
@@ -1650,7 +1656,6 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     if (V.nreal > 0 || gblocks > 0) {
         const unsigned grid = (unsigned)(V.nreal * (B3 / UPD_THREADS) + gblocks);
         const int* gl = V.d_glist;
-        cudaStream_t st = h->stream;
         if (has_fine && has_coarse) k_update<S, true, true, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
         else if (has_fine) k_update<S, true, false, false><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
         else if (has_coarse && coupled) k_update<S, false, true, true><<<grid, UPD_THREADS, 0, st>>>(U, gl, ng, gblocks, coalesce);
@@ -1665,19 +1670,19 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         const LevelView D = view(E, V);
         uint8_t* fnext = V.d_flags[1 - V.fcur];
         const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
-        // After the second sub-step the coarser levels' update and explosion come next; they touch
-        // neither the finest real cells, their flags nor the particle, so the remap runs beside them
-        // on the side stream (after the boundary kernel there) and the next finest update, or the end
-        // of the level-0 step, waits for it.  After the first sub-step the next finest update follows
-        // at once.
+        // After the second sub-step the next work on this stream is the next explosion into this
+        // level, which touches neither the finest real cells, their flags nor the particle, so the
+        // remap runs beside it on the side stream (after the boundary kernel there) and the next
+        // finest update, or the end of the level-0 step, waits for it.  After the first sub-step the
+        // next finest update follows at once.
         const bool beside = has_coarse && sub == 1;
-        cudaStream_t rs = h->stream;
+        cudaStream_t rs = st;
         if (beside) {
-            cudaEventRecord(E->ev_fork, h->stream);
+            cudaEventRecord(E->ev_fork, st);
             cudaStreamWaitEvent(E->side, E->ev_fork, 0);
             rs = E->side;
         } else {
-            cudaStreamWaitEvent(h->stream, E->ev_join, 0);
+            cudaStreamWaitEvent(st, E->ev_join, 0);
         }
         k_amr_remap<S><<<nl, LINK_THREADS, 0, rs>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
                                                     P.inv_scale, h->link_mask, h->link_blocks, h->status,
@@ -1689,6 +1694,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         V.fcur = 1 - V.fcur;
         h->launches += 1;
     }
+    if (st != h->stream) cudaEventRecord(E->ev_state[l], st);
     V.cur = 1 - V.cur;
 }
 
@@ -1712,15 +1718,22 @@ lbmp_status amr_create(lbmp_handle* h) {
     h->amr = E;
     E->d_done = (int*)handle_alloc(h, sizeof(int));
     if (!E->d_done) return LBMP_ERR_OOM;
-    if (cudaStreamCreateWithFlags(&E->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // Priorities: the finest level's chain (the captured step's own stream and the side stream of
+    // the boundary kernel and remap) is the critical path; the coarser levels' streams, at the
+    // lowest priority, fill the SMs it leaves.  A graph keeps them with UseNodePriority.
+    int prio_least = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &E->prio_high) != cudaSuccess) return LBMP_ERR_CUDA;
+    if (cudaStreamCreateWithPriority(&E->side, cudaStreamNonBlocking, E->prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_remap, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&E->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&E->ev_aux_fork, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&E->ev_begin, cudaEventDisableTiming) != cudaSuccess)
         return LBMP_ERR_CUDA;
-    for (int l = 0; l < MAXL; ++l)
-        if (cudaEventCreateWithFlags(&E->ev_x[l], cudaEventDisableTiming) != cudaSuccess) return LBMP_ERR_CUDA;
+    for (int l = 0; l + 1 < E->L; ++l)
+        if (cudaStreamCreateWithPriority(&E->lstream[l], cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+            cudaEventCreateWithFlags(&E->ev_state[l], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&E->ev_xdone[l], cudaEventDisableTiming) != cudaSuccess)
+            return LBMP_ERR_CUDA;
 
     if (cudaMemsetAsync(E->d_done, 0, sizeof(int), h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
     return regrid_now(h);
@@ -1734,10 +1747,12 @@ void amr_destroy(lbmp_handle* h) {
     if (h->amr->ev_fork) cudaEventDestroy(h->amr->ev_fork);
     if (h->amr->ev_join) cudaEventDestroy(h->amr->ev_join);
     if (h->amr->ev_remap) cudaEventDestroy(h->amr->ev_remap);
-    if (h->amr->aux) cudaStreamDestroy(h->amr->aux);
-    if (h->amr->ev_aux_fork) cudaEventDestroy(h->amr->ev_aux_fork);
-    for (int l = 0; l < MAXL; ++l)
-        if (h->amr->ev_x[l]) cudaEventDestroy(h->amr->ev_x[l]);
+    if (h->amr->ev_begin) cudaEventDestroy(h->amr->ev_begin);
+    for (int l = 0; l < MAXL; ++l) {
+        if (h->amr->lstream[l]) cudaStreamDestroy(h->amr->lstream[l]);
+        if (h->amr->ev_state[l]) cudaEventDestroy(h->amr->ev_state[l]);
+        if (h->amr->ev_xdone[l]) cudaEventDestroy(h->amr->ev_xdone[l]);
+    }
 
     for (auto& V : h->amr->lv) free_level(h, V);
     handle_free(h, h->amr->d_sensor);
@@ -1920,6 +1935,15 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
         E->graph_tau = h->tau;
     }
     auto enqueue = [&]() {
+        // the coarser levels' streams join the step here and rejoin the caller's stream at its end
+        const bool fork = !h->profiling && E->L > 1;
+        if (fork) {
+            cudaEventRecord(E->ev_begin, h->stream);
+            for (int l = 0; l + 1 < E->L; ++l) {
+                cudaStreamWaitEvent(E->lstream[l], E->ev_begin, 0);
+                cudaEventRecord(E->ev_state[l], E->lstream[l]);
+            }
+        }
         with_storage_amr(h->cfg.precision, [&](auto tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
             enqueue_advance<S>(h, 0, 0);
@@ -1928,11 +1952,8 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
             cudaStreamWaitEvent(h->stream, E->ev_remap, 0);
             E->remap_pending = false;
         }
-        for (int l = 0; l < E->L; ++l)
-            if (E->x_pending[l]) {
-                cudaStreamWaitEvent(h->stream, E->ev_x[l], 0);
-                E->x_pending[l] = false;
-            }
+        if (fork)
+            for (int l = 0; l + 1 < E->L; ++l) cudaStreamWaitEvent(h->stream, E->ev_state[l], 0);
     };
     for (int i = 0; i < n; ++i) {
         if (h->profiling) {   // per-kernel events: plain launches
@@ -1947,7 +1968,7 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
                 // captured); enqueue() advances the host-side buffer indices
                 // exactly as the replayed graph will
                 if (!E->capture_stream &&
-                    cudaStreamCreateWithFlags(&E->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+                    cudaStreamCreateWithPriority(&E->capture_stream, cudaStreamNonBlocking, E->prio_high) != cudaSuccess)
                     return amr_cuda_error(h, "cudaStreamCreate");
                 const long long l0 = h->launches, u0 = h->updates;
                 cudaStream_t user = h->stream;
@@ -1963,7 +1984,7 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
                 h->stream = user;
                 if (e != cudaSuccess) return amr_cuda_error(h, "cudaStreamEndCapture");
                 cudaGraphExec_t ge = nullptr;
-                e = cudaGraphInstantiate(&ge, g, 0);
+                e = cudaGraphInstantiateWithFlags(&ge, g, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) return amr_cuda_error(h, "cudaGraphInstantiate");
                 E->graph[par] = ge;
