@@ -343,7 +343,8 @@ constexpr int BND_CHUNK = 128;     // box cells per boundary CTA (sizes the grid
 // instead of 1,024.
 template <typename S>
 constexpr int BND_MAXREG = sizeof(S) == 8 ? 128 : (sizeof(S) == 4 ? 56 : 64);
-constexpr int LINK_THREADS = 64;   // remap blocks: small, so the box spreads over the SMs; one count per block
+constexpr int LINK_THREADS = 64;   // box cells per run of the boundary mask (one count per run)
+constexpr int REMAP_THREADS = 256;   // remap blocks: their uncovered cells are spread over the eight warps
 
 // Exclusive prefix of n counts into pre[0..n] (pre[n] = total), computed by
 // the whole CTA (NT threads, two consecutive counts per thread and pass);
@@ -553,27 +554,33 @@ __device__ __forceinline__ void refill_cell_warp(const LevelView& D, S* __restri
 
 // Remap of Sec. 2.3 after the particle moved, over the box of finest cells
 // around the sphere, in one pass: the new solid flag of every cell (the
-// exact ball predicate); covered cells drop their populations; uncovered
-// cells are refilled afterwards, one at a time by their whole warp
-// (refill_cell_warp); fluid cells with a solid neighbour are marked for the
-// boundary list (counts per block for the ordered compaction).
-// Neighbour flags are evaluated from the same predicate instead of being
-// read back, so no second pass is needed.
+// exact ball predicate); newly covered cells drop their populations (the
+// update already zeroed the cells that were solid before); uncovered cells
+// are listed in shared memory and refilled afterwards, each by one warp of
+// the block in turn (refill_cell_warp: it reads only cells that are fluid
+// before and after the move, which nothing here writes); fluid cells with a
+// solid neighbour are marked for the boundary list (counts per run of
+// LINK_THREADS box cells for the ordered compaction).  Neighbour flags are
+// evaluated from the same predicate instead of being read back, so no
+// second pass is needed.
 template <typename S>
-__global__ void __launch_bounds__(LINK_THREADS)
+__global__ void __launch_bounds__(REMAP_THREADS)
     k_amr_remap(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
                 BoxDesc B, const ParticleState* __restrict__ ps, typename Store<S>::A scale,
                 typename Store<S>::A inv_scale, uint8_t* __restrict__ mask, int* __restrict__ block_count,
                 int* __restrict__ status, typename Store<S>::A gcoef) {
     using A = typename Store<S>::A;
     __shared__ BoxFrame F;
-    if (threadIdx.x == 0) box_frame_init(F, D.n, D.periodic, B, *ps);
+    __shared__ int s_n;
+    __shared__ int s_cell[2][REMAP_THREADS], s_g[3][REMAP_THREADS];   // uncovered cells: pool block, cell, position
+    if (threadIdx.x == 0) {
+        box_frame_init(F, D.n, D.periodic, B, *ps);
+        s_n = 0;
+    }
     __syncthreads();
     const ParticleState& P = *ps;
-    const int t = blockIdx.x * LINK_THREADS + threadIdx.x;
+    const int t = blockIdx.x * REMAP_THREADS + threadIdx.x;
     int is_b = 0;
-    bool uncovered = false;   // fluid after the move, solid before: refilled below by the warp
-    int ub = 0, uc = 0, ug[3] = {0, 0, 0};
     if (t < B.cells) {
         int g[3];
         if (box_cell(t, D.n, D.periodic, B, F, g)) {
@@ -585,39 +592,46 @@ __global__ void __launch_bounds__(LINK_THREADS)
                 const size_t x = (size_t)b * B3 + c;
                 bool any_nb = false;
                 const bool solid = ball_flag_and_neighbours(g, D.n, D.periodic, F, P, &any_nb);
+                const bool was_solid = fcur[x] == FLAG_SOLID;
                 if (solid) {
                     fnext[x] = FLAG_SOLID;
+                    if (!was_solid)
 #pragma unroll
-                    for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
+                        for (int q = 0; q < 19; ++q) Store<S>::store(pops + paddr(b, q, c), A(0), scale);
                 } else {
-                    uncovered = fcur[x] == FLAG_SOLID;
                     is_b = any_nb ? 1 : 0;
                     fnext[x] = is_b ? FLAG_BOUNDARY : FLAG_FLUID;
-                    ub = b;
-                    uc = c;
-                    ug[0] = g[0];
-                    ug[1] = g[1];
-                    ug[2] = g[2];
+                    if (was_solid) {   // uncovered: fluid after the move, solid before
+                        const int k = atomicAdd(&s_n, 1);
+                        s_cell[0][k] = b;
+                        s_cell[1][k] = c;
+                        s_g[0][k] = g[0];
+                        s_g[1][k] = g[1];
+                        s_g[2][k] = g[2];
+                    }
                 }
             }
         }
         mask[t] = (uint8_t)is_b;
     }
-    for (unsigned todo = __ballot_sync(0xffffffffu, uncovered); todo != 0u; todo &= todo - 1u) {
-        const int src = __ffs((int)todo) - 1;
-        const int g3[3] = {__shfl_sync(0xffffffffu, ug[0], src), __shfl_sync(0xffffffffu, ug[1], src),
-                           __shfl_sync(0xffffffffu, ug[2], src)};
-        refill_cell_warp<S>(D, pops, fcur, F, P, __shfl_sync(0xffffffffu, ub, src),
-                            __shfl_sync(0xffffffffu, uc, src), g3, scale, inv_scale, gcoef);
+    __syncthreads();
+    const int wid = threadIdx.x >> 5;
+    for (int k = wid; k < s_n; k += REMAP_THREADS / 32) {
+        const int g3[3] = {s_g[0][k], s_g[1][k], s_g[2][k]};
+        refill_cell_warp<S>(D, pops, fcur, F, P, s_cell[0][k], s_cell[1][k], g3, scale, inv_scale, gcoef);
     }
     const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
-    __shared__ int wsum[LINK_THREADS / 32];
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(ballot);
+    __shared__ int wsum[REMAP_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wsum[wid] = __popc(ballot);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < LINK_THREADS / 32; ++w) s += wsum[w];
-        block_count[blockIdx.x] = s;
+    constexpr int RUNS = REMAP_THREADS / LINK_THREADS, WPR = LINK_THREADS / 32;
+    if ((int)threadIdx.x < RUNS) {
+        const long long run = (long long)blockIdx.x * RUNS + threadIdx.x;
+        if (run * LINK_THREADS < B.cells) {
+            int s = 0;
+            for (int w = 0; w < WPR; ++w) s += wsum[threadIdx.x * WPR + w];
+            block_count[run] = s;
+        }
     }
 }
 
@@ -1500,11 +1514,11 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
         Ff.fcur = 0;
         // boundary cells of the current position (both flag buffers already hold its flags,
         // so the remap pass only marks: nothing is covered or uncovered)
-        const unsigned nb = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
+        const unsigned nb = (unsigned)((h->box.cells + REMAP_THREADS - 1) / REMAP_THREADS);
         with_storage_amr(h->cfg.precision, [&](auto tag) {
             using S = std::remove_pointer_t<decltype(tag)>;
             using A = typename Store<S>::A;
-            k_amr_remap<S><<<nb, LINK_THREADS, 0, h->stream>>>(view(E, Ff), (S*)Ff.d_pops[Ff.cur], Ff.d_flags[1],
+            k_amr_remap<S><<<nb, REMAP_THREADS, 0, h->stream>>>(view(E, Ff), (S*)Ff.d_pops[Ff.cur], Ff.d_flags[1],
                                                                Ff.d_flags[0], h->box, h->d_ps, (A)1, (A)1,
                                                                h->link_mask, h->link_blocks, h->status, (A)0);
         });
@@ -1669,7 +1683,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
     if (coupled) {
         const LevelView D = view(E, V);
         uint8_t* fnext = V.d_flags[1 - V.fcur];
-        const unsigned nl = (unsigned)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS);
+        const unsigned nl = (unsigned)((h->box.cells + REMAP_THREADS - 1) / REMAP_THREADS);
         // After the second sub-step the next work on this stream is the next explosion into this
         // level, which touches neither the finest real cells, their flags nor the particle, so the
         // remap runs beside it on the side stream (after the boundary kernel there) and the next
@@ -1684,7 +1698,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         } else {
             cudaStreamWaitEvent(st, E->ev_join, 0);
         }
-        k_amr_remap<S><<<nl, LINK_THREADS, 0, rs>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
+        k_amr_remap<S><<<nl, REMAP_THREADS, 0, rs>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
                                                     P.inv_scale, h->link_mask, h->link_blocks, h->status,
                                                     (A)grad_refill_coef(h->cfg.refill, V.taup));
         if (beside) {
@@ -1719,8 +1733,8 @@ lbmp_status amr_create(lbmp_handle* h) {
     E->d_done = (int*)handle_alloc(h, sizeof(int));
     if (!E->d_done) return LBMP_ERR_OOM;
     // Priorities: the finest level's chain (the captured step's own stream and the side stream of
-    // the boundary kernel and remap) is the critical path; the coarser levels' streams, at the
-    // lowest priority, fill the SMs it leaves.  A graph keeps them with UseNodePriority.
+    // the boundary kernel and remap) is the critical path; the coarser levels' streams, each below
+    // the next finer one, fill the SMs it leaves.  A graph keeps them with UseNodePriority.
     int prio_least = 0;
     if (cudaDeviceGetStreamPriorityRange(&prio_least, &E->prio_high) != cudaSuccess) return LBMP_ERR_CUDA;
     if (cudaStreamCreateWithPriority(&E->side, cudaStreamNonBlocking, E->prio_high) != cudaSuccess ||
@@ -1729,8 +1743,9 @@ lbmp_status amr_create(lbmp_handle* h) {
         cudaEventCreateWithFlags(&E->ev_remap, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_begin, cudaEventDisableTiming) != cudaSuccess)
         return LBMP_ERR_CUDA;
-    for (int l = 0; l + 1 < E->L; ++l)
-        if (cudaStreamCreateWithPriority(&E->lstream[l], cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+    for (int l = 0; l + 1 < E->L; ++l)   // finer levels first: a level's update gates the next explosion from it
+        if (cudaStreamCreateWithPriority(&E->lstream[l], cudaStreamNonBlocking,
+                                         std::min(prio_least, E->prio_high + (E->L - 1 - l))) != cudaSuccess ||
             cudaEventCreateWithFlags(&E->ev_state[l], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&E->ev_xdone[l], cudaEventDisableTiming) != cudaSuccess)
             return LBMP_ERR_CUDA;
