@@ -264,11 +264,13 @@ __device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c
 // cells of the level (glist: pool block << 12 | cell, eight consecutive
 // entries per host cell of the coarser level), no collision.  At the first
 // sub-step they store them into dst.  At the last sub-step they sum each
-// host's eight in a fixed shuffle tree instead, and the first lane of each
-// eight takes the mean as the host's populations (coalescence), collides
-// them with the coarser level's parameters and writes the host into the
-// coarser level's destination buffer, the step of the coarser level that
-// its own update (which skips hosts) is taking beside.  The other CTAs
+// host's eight in a fixed shuffle tree instead; all eight lanes take the
+// mean as the host's populations (coalescence) and collide them with the
+// coarser level's parameters; the first writes the host into the coarser
+// level's destination buffer (the step of the coarser level that its own
+// update, which skips hosts, is taking beside), and each writes the result
+// into its own ghost cell of dst, the source of the level's next first
+// sub-step: the explosion of the host's new post-collision state.  The other CTAs
 // update the real blocks, B3 / UPD_THREADS CTAs per block, each a run of
 // UPD_THREADS cells in block order (full warps).  All read src (and the
 // ghost lanes the coarser level's csrc); the real-block CTAs write dst only.
@@ -282,10 +284,11 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         const bool valid = i < nglist;
         if (!coalesce && !valid) return;
         A g[19];
-        int hp = 0;
+        int hp = 0, b = 0, c = 0;
         if (valid) {
             const int e = glist[i];
-            const int b = e >> 12, c = e & 4095;
+            b = e >> 12;
+            c = e & 4095;
             hp = U.ghost_host[i >> 3];
             const GhostPull gp{U.smask[i], hp >> 12, hp & 4095, i & 7, coalesce != 0};
             pull_cell<S, true>(U, b, c, U.D.nbr + (size_t)b * 27, g, gp);
@@ -306,13 +309,20 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
             v += __shfl_xor_sync(0xffffffffu, v, 4);
             g[q] = v;
         }
-        if (valid && (i & 7) == 0) {
-            const int hb = hp >> 12, hc = hp & 4095;
+        if (valid) {
+            // each of the eight lanes holds the sum and forms the host's collided populations
 #pragma unroll
             for (int q = 0; q < 19; ++q) g[q] *= A(0.125);
             trt_collide<A, false, sizeof(S) == 2>(g, U.Pc, U.status);
+            if ((i & 7) == 0) {   // the host, into the coarser level's new state
+                const int hb = hp >> 12, hc = hp & 4095;
 #pragma unroll
-            for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.cdst + paddr(hb, q, hc), g[q]);
+                for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.cdst + paddr(hb, q, hc), g[q]);
+            }
+            // and the explosion of that new state: this ghost cell, in the buffer the level's next
+            // pair of sub-steps starts from
+#pragma unroll
+            for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
         }
         return;
     }
@@ -1025,6 +1035,7 @@ struct Level {
     uint8_t* d_refined = nullptr;
     uint8_t* d_host = nullptr;
     int nglist = 0;              // active ghost cells (host sub-cells)
+    bool ghosts_valid = false;   // the active ghost cells of the current buffer hold the coarser level's hosts
     int* d_glist = nullptr;      // the active ghost cells, pool block << 12 | cell, eight per host
     int* d_ghost_host = nullptr; // per eight: the host, real block << 12 | cell of the coarser level
     uint32_t* d_smask = nullptr; // per active ghost cell: populations with a static ghost cell upwind
@@ -1066,7 +1077,7 @@ struct AmrEngine {
     cudaEvent_t ev_state[MAXL] = {};
     cudaEvent_t ev_xdone[MAXL] = {};
     cudaEvent_t ev_begin = nullptr;
-    int prio_high = 0;   // the greatest stream priority
+    int prio_high = 0, prio_low = 0;   // the greatest and the least stream priority
     double sensor_sigma = 0.0, sensor_c = 0.0;   // flow sensor (sigma_c = 0: off)
     double* d_sensor = nullptr;                   // per real block of all levels
     size_t sensor_cap = 0;
@@ -1075,6 +1086,18 @@ struct AmrEngine {
     bool broken = false;
 
 };
+
+// Populations changed outside a step: every level's active ghost cells are
+// exploded again by the next step.
+void amr_invalidate_ghosts(AmrEngine* E) {
+    for (auto& V : E->lv) V.ghosts_valid = false;
+}
+
+bool amr_ghosts_valid(const AmrEngine* E) {
+    for (size_t l = 1; l < E->lv.size(); ++l)
+        if (E->lv[l].nglist > 0 && !E->lv[l].ghosts_valid) return false;
+    return true;
+}
 
 void amr_drop_graphs(AmrEngine* E) {
     for (int p = 0; p < 2; ++p)
@@ -1579,15 +1602,18 @@ cudaStream_t level_stream(const lbmp_handle* h, int l) {
 
 // One step of level l (sub: which of its parent's two sub-steps, 0 for
 // level 0).  Work order and dependencies:
-//   - the explosion into level l+1 (on l+1's stream) waits for level l's
-//     last update (ev_state[l]); level l's hosts of that state were written
-//     by level l+1's previous sub-step, earlier on the same stream;
+//   - level l+1's stream waits for level l's last update (ev_state[l]):
+//     level l+1's sub-steps read level l's current state for their static
+//     ghost cells; level l's hosts of that state, and their explosion into
+//     level l+1's active ghost cells, were written by level l+1's previous
+//     last sub-step, earlier on the same stream (an explicit explosion
+//     replaces it after a change outside a step);
 //   - level l+1 takes its two sub-steps, the second writing level l's hosts
-//     of the new state;
-//   - level l's update (on its own stream) waits only for that explosion
-//     (ev_xdone[l]), after which no earlier sub-step of level l+1 still
-//     reads the buffer it writes; it runs beside level l+1's sub-steps and
-//     writes every real cell of level l but the hosts.
+//     of the new state and their explosion;
+//   - level l's update (on its own stream) waits only for the start of
+//     level l+1's two sub-steps (ev_xdone[l]), after which no earlier
+//     sub-step of level l+1 still reads the buffer it writes; it runs beside
+//     them and writes every real cell of level l but the hosts.
 // The finest level runs on the caller's stream, so the critical path is the
 // chain of finest sub-steps, with the coarser updates beside it.
 template <typename S>
@@ -1602,7 +1628,10 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         Level& F = E->lv[l + 1];
         const cudaStream_t fs = level_stream(h, l + 1);
         if (fs != st) cudaStreamWaitEvent(fs, E->ev_state[l], 0);
-        if (F.nglist > 0) {
+        // the active ghost cells of level l+1 normally hold the hosts' current state already (the
+        // previous last sub-step of level l+1 wrote it); after a change of layout or populations
+        // outside a step they are exploded here
+        if (F.nglist > 0 && !F.ghosts_valid) {
             const unsigned grid = (unsigned)((F.nglist + UPD_THREADS - 1) / UPD_THREADS);
             k_explode<S><<<grid, UPD_THREADS, 0, fs>>>((const S*)V.d_pops[V.cur], (S*)F.d_pops[F.cur], F.d_glist,
                                                        F.d_ghost_host, F.nglist);
@@ -1611,6 +1640,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         if (fs != st) cudaEventRecord(E->ev_xdone[l], fs);
         enqueue_advance<S>(h, l + 1, 0);
         enqueue_advance<S>(h, l + 1, 1);
+        F.ghosts_valid = true;
         if (fs != st) cudaStreamWaitEvent(st, E->ev_xdone[l], 0);
     }
     UpdateArgs<S> U;
@@ -1732,11 +1762,12 @@ lbmp_status amr_create(lbmp_handle* h) {
     h->amr = E;
     E->d_done = (int*)handle_alloc(h, sizeof(int));
     if (!E->d_done) return LBMP_ERR_OOM;
-    // Priorities: the finest level's chain (the captured step's own stream and the side stream of
-    // the boundary kernel and remap) is the critical path; the coarser levels' streams, each below
-    // the next finer one, fill the SMs it leaves.  A graph keeps them with UseNodePriority.
-    int prio_least = 0;
-    if (cudaDeviceGetStreamPriorityRange(&prio_least, &E->prio_high) != cudaSuccess) return LBMP_ERR_CUDA;
+    // Priorities: the finest level's chain is the critical path.  Its side stream (the boundary
+    // kernel and remap) has the highest: a boundary CTA needs the registers of three update CTAs,
+    // and without it the finest update's CTAs take every slot that frees.  Then the captured
+    // step's own stream (the finest update), then the coarser levels' streams, each below the next
+    // finer one, which fill the SMs the chain leaves.  A graph keeps them with UseNodePriority.
+    if (cudaDeviceGetStreamPriorityRange(&E->prio_low, &E->prio_high) != cudaSuccess) return LBMP_ERR_CUDA;
     if (cudaStreamCreateWithPriority(&E->side, cudaStreamNonBlocking, E->prio_high) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&E->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -1745,7 +1776,7 @@ lbmp_status amr_create(lbmp_handle* h) {
         return LBMP_ERR_CUDA;
     for (int l = 0; l + 1 < E->L; ++l)   // finer levels first: a level's update gates the next explosion from it
         if (cudaStreamCreateWithPriority(&E->lstream[l], cudaStreamNonBlocking,
-                                         std::min(prio_least, E->prio_high + (E->L - 1 - l))) != cudaSuccess ||
+                                         std::min(E->prio_low, E->prio_high + 1 + (E->L - 1 - l))) != cudaSuccess ||
             cudaEventCreateWithFlags(&E->ev_state[l], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&E->ev_xdone[l], cudaEventDisableTiming) != cudaSuccess)
             return LBMP_ERR_CUDA;
@@ -1811,6 +1842,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
         return LBMP_ERR_CUDA;
     h->h2d += sizeof(ParticleState);
     h->has_particle = true;
+    amr_invalidate_ghosts(E);
     return regrid_now(h);
 }
 
@@ -1924,6 +1956,7 @@ lbmp_status amr_block_sensor(lbmp_handle* h, int level, double* out, size_t cap,
 lbmp_status amr_init_fluid(lbmp_handle* h, double rho, const double u[3], double amp, int dir, int axis) {
     if (h->amr->broken) return LBMP_ERR_OOM;   // an earlier rebuild of the hierarchy failed
     AmrEngine* E = h->amr;
+    amr_invalidate_ghosts(E);
     const double Lax = (double)E->lv[E->L - 1].n[axis];
     with_storage_amr(h->cfg.precision, [&](auto tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
@@ -1975,6 +2008,8 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
             const long long ev_step = profile_mark(h);
             enqueue();
             profile_step(h, ev_step, profile_mark(h));
+        } else if (!amr_ghosts_valid(E)) {   // a step that explodes ghost cells is not the one a graph repeats
+            enqueue();
         } else {
             const int par = E->lv[0].cur;
             if (!E->graph[par]) {
@@ -1983,7 +2018,8 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
                 // captured); enqueue() advances the host-side buffer indices
                 // exactly as the replayed graph will
                 if (!E->capture_stream &&
-                    cudaStreamCreateWithPriority(&E->capture_stream, cudaStreamNonBlocking, E->prio_high) != cudaSuccess)
+                    cudaStreamCreateWithPriority(&E->capture_stream, cudaStreamNonBlocking,
+                                                 std::min(E->prio_high + 1, E->prio_low)) != cudaSuccess)
                     return amr_cuda_error(h, "cudaStreamCreate");
                 const long long l0 = h->launches, u0 = h->updates;
                 cudaStream_t user = h->stream;
@@ -2237,8 +2273,8 @@ int amr_launches_per_coarse_step(const lbmp_handle* h) {
     const AmrEngine* E = h->amr;
     int per = 0;
     for (int l = E->L - 1; l >= 0; --l) {
-        int own = 1 + ((l + 1 < E->L && E->lv[l + 1].nglist > 0) ? 1 : 0) +
-                  ((l == E->L - 1 && h->has_particle) ? 2 : 0);
+        // the update (the explosions into finer levels happen only after a change outside a step)
+        int own = 1 + ((l == E->L - 1 && h->has_particle) ? 2 : 0);
         per = own + 2 * per;
     }
     return per;
