@@ -417,7 +417,8 @@ __global__ void __maxnreg__(BND_MAXREG<S>)
     k_amr_boundary(LevelView D, const S* __restrict__ src, S* __restrict__ dst, const uint8_t* __restrict__ solid,
                    const uint8_t* __restrict__ mask, const int* __restrict__ run_count, BoxDesc B,
                    CollideParams<typename Store<S>::A> P, ParticleState* ps, int cli, double* partials, int* done,
-                   GridDesc G, double* __restrict__ history, int hist_cap, int* __restrict__ status) {
+                   GridDesc G, double* __restrict__ history, int hist_cap, int* __restrict__ status,
+                   PFrames* __restrict__ frames) {
     using A = typename Store<S>::A;
     extern __shared__ int pre[];   // [runs + 1]
     __shared__ LinkFrame<A> Fr;
@@ -425,8 +426,8 @@ __global__ void __maxnreg__(BND_MAXREG<S>)
     const int runs = (int)((B.cells + LINK_THREADS - 1) / LINK_THREADS);
     const int i2 = 2 * (int)threadIdx.x;   // this thread's first two counts, in flight during the set-up
     const int first0 = i2 < runs ? run_count[i2] : 0, first1 = i2 + 1 < runs ? run_count[i2 + 1] : 0;
-    if (threadIdx.x == 0) Fr.init(*ps);   // the two FP64 set-ups on two warps
-    if (threadIdx.x == 32) box_frame_init(Bf, D.n, D.periodic, B, *ps);
+    if (threadIdx.x == 0) Fr = pframe_link<A>(*frames);   // formed by the last particle update
+    if (threadIdx.x == 32) Bf = frames->bf;
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int total = block_prefix<BNDW_THREADS>(run_count, runs, pre, first0, first1);
@@ -489,7 +490,11 @@ __global__ void __maxnreg__(BND_MAXREG<S>)
         if (lane < 19) Store<S>::store(dst + paddr(b, lane, c), gq, P.scale);
     }
     block_link_sums<BNDW_THREADS>(acc, ps->x, partials + (size_t)blockIdx.x * 6);
-    if (last_block_done(done, (int)gridDim.x)) particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status);
+    if (last_block_done(done, (int)gridDim.x)) {   // every other block is past its use of the frames
+        particle_block_update<BNDW_THREADS>(ps, partials, gridDim.x, G, history, hist_cap, status, frames->inv);
+        __syncthreads();
+        if (threadIdx.x < 3) pframes_axis(frames, *ps, D.n, B, threadIdx.x);   // of the moved sphere
+    }
 }
 
 
@@ -501,12 +506,15 @@ __global__ void __maxnreg__(BND_MAXREG<S>)
 // neighbours and the rigid-body velocity u_p + omega_p x (x - x_p) give the
 // equilibrium, plus Grad's non-equilibrium term when gcoef != 0; lane
 // q < 19 writes population q.  Every lane calls it with the same cell.
+// With lf (the FP32 link frame of the moved sphere) an FP32 path forms the
+// offset (g + 1/2 - X = (g - Xi) + Xh, minimum image on periodic axes) and
+// the rigid-body velocity in FP32 instead of FP64, which is slow here.
 template <typename S>
 __device__ __forceinline__ void refill_cell_warp(const LevelView& D, S* __restrict__ pops,
                                                  const uint8_t* __restrict__ fcur, const BoxFrame& F,
                                                  const ParticleState& P, int b, int c, const int g[3],
                                                  typename Store<S>::A scale, typename Store<S>::A inv_scale,
-                                                 typename Store<S>::A gcoef) {
+                                                 typename Store<S>::A gcoef, const LinkFrame<float>* lf) {
     using A = typename Store<S>::A;
     const int lane = threadIdx.x & 31;
     bool ok = false;
@@ -539,11 +547,29 @@ __device__ __forceinline__ void refill_cell_warp(const LevelView& D, S* __restri
     for (int off = 16; off > 0; off >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, off);
     const int cnt = __popc(okm);
     const A rho = cnt > 0 ? rs / A(cnt) : A(1);
-    const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
-                         wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
-                         wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
-    const A u[3] = {A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1])), A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2])),
-                    A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]))};
+    A u[3];
+    if (sizeof(A) == 4 && lf) {
+        float d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int v = g[a] - lf->Xi[a];
+            if (D.periodic[a]) {
+                const float t = (float)v + lf->Xh[a], half = 0.5f * (float)D.n[a];
+                v += t > half ? -D.n[a] : (t < -half ? D.n[a] : 0);
+            }
+            d[a] = (float)v + lf->Xh[a];
+        }
+        u[0] = A(lf->u[0] + (lf->w[1] * d[2] - lf->w[2] * d[1]));
+        u[1] = A(lf->u[1] + (lf->w[2] * d[0] - lf->w[0] * d[2]));
+        u[2] = A(lf->u[2] + (lf->w[0] * d[1] - lf->w[1] * d[0]));
+    } else {
+        const double d[3] = {wrap_diff((g[0] + 0.5) - P.x[0], D.n[0], D.periodic[0]),
+                             wrap_diff((g[1] + 0.5) - P.x[1], D.n[1], D.periodic[1]),
+                             wrap_diff((g[2] + 0.5) - P.x[2], D.n[2], D.periodic[2])};
+        u[0] = A(P.u[0] + (P.w[1] * d[2] - P.w[2] * d[1]));
+        u[1] = A(P.u[1] + (P.w[2] * d[0] - P.w[0] * d[2]));
+        u[2] = A(P.u[2] + (P.w[0] * d[1] - P.w[1] * d[0]));
+    }
     const A uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     A Sr[6] = {A(0), A(0), A(0), A(0), A(0), A(0)};
     if (gcoef != A(0)) {   // Grad refill: face neighbour q = 1 + 2 a (+1 for -e_a), fluid before and after
@@ -562,6 +588,11 @@ __device__ __forceinline__ void refill_cell_warp(const LevelView& D, S* __restri
     }
 }
 
+// Frames of the current record, after the host changed it (one block of 128 threads).
+__global__ void k_pframes(const ParticleState* __restrict__ ps, PFrames* __restrict__ frames, LevelView D, BoxDesc B) {
+    pframes_form(frames, *ps, D.n, D.periodic, B);
+}
+
 // Remap of Sec. 2.3 after the particle moved, over the box of finest cells
 // around the sphere, in one pass: the new solid flag of every cell (the
 // exact ball predicate); newly covered cells drop their populations (the
@@ -578,13 +609,14 @@ __global__ void __launch_bounds__(REMAP_THREADS)
     k_amr_remap(LevelView D, S* __restrict__ pops, const uint8_t* __restrict__ fcur, uint8_t* __restrict__ fnext,
                 BoxDesc B, const ParticleState* __restrict__ ps, typename Store<S>::A scale,
                 typename Store<S>::A inv_scale, uint8_t* __restrict__ mask, int* __restrict__ block_count,
-                int* __restrict__ status, typename Store<S>::A gcoef) {
+                int* __restrict__ status, typename Store<S>::A gcoef, const PFrames* __restrict__ frames) {
     using A = typename Store<S>::A;
     __shared__ BoxFrame F;
     __shared__ int s_n;
     __shared__ int s_cell[2][REMAP_THREADS], s_g[3][REMAP_THREADS];   // uncovered cells: pool block, cell, position
     if (threadIdx.x == 0) {
-        box_frame_init(F, D.n, D.periodic, B, *ps);
+        if (frames) F = frames->bf;   // formed by the particle update that moved the sphere
+        else box_frame_init(F, D.n, D.periodic, B, *ps);
         s_n = 0;
     }
     __syncthreads();
@@ -628,7 +660,8 @@ __global__ void __launch_bounds__(REMAP_THREADS)
     const int wid = threadIdx.x >> 5;
     for (int k = wid; k < s_n; k += REMAP_THREADS / 32) {
         const int g3[3] = {s_g[0][k], s_g[1][k], s_g[2][k]};
-        refill_cell_warp<S>(D, pops, fcur, F, P, s_cell[0][k], s_cell[1][k], g3, scale, inv_scale, gcoef);
+        refill_cell_warp<S>(D, pops, fcur, F, P, s_cell[0][k], s_cell[1][k], g3, scale, inv_scale, gcoef,
+                            frames ? &frames->lf : nullptr);
     }
     const unsigned ballot = __ballot_sync(0xffffffffu, is_b);
     __shared__ int wsum[REMAP_THREADS / 32];
@@ -1064,6 +1097,7 @@ struct AmrEngine {
     double graph_tau = 0.0;
     cudaStream_t capture_stream = nullptr;   // private stream used only for capturing
     int* d_done = nullptr;   // last-block-done counter of the boundary kernel (zero between launches)
+    PFrames* d_frames = nullptr;   // frames of the sphere's current state (written by the particle update)
     std::vector<std::vector<uint8_t>> cover;      // block coverage per level of the current layout
     cudaStream_t side = nullptr;                  // k_amr_boundary runs here, beside the finest update
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -1543,7 +1577,7 @@ lbmp_status build_layout(lbmp_handle* h, const std::vector<Mask>& R) {
             using A = typename Store<S>::A;
             k_amr_remap<S><<<nb, REMAP_THREADS, 0, h->stream>>>(view(E, Ff), (S*)Ff.d_pops[Ff.cur], Ff.d_flags[1],
                                                                Ff.d_flags[0], h->box, h->d_ps, (A)1, (A)1,
-                                                               h->link_mask, h->link_blocks, h->status, (A)0);
+                                                               h->link_mask, h->link_blocks, h->status, (A)0, nullptr);
         });
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(h->stream) != cudaSuccess) return LBMP_ERR_CUDA;
@@ -1689,7 +1723,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         const size_t pre_bytes = sizeof(int) * (size_t)((h->box.cells + LINK_THREADS - 1) / LINK_THREADS + 1);
         k_amr_boundary<S><<<E->boundary_blocks, BNDW_THREADS, pre_bytes, E->side>>>(
             D, U.src, U.dst, U.solid, h->link_mask, h->link_blocks, h->box, P, h->d_ps, h->cfg.boundary == LBMP_CLI ? 1 : 0,
-            h->partials, E->d_done, G, h->history, h->cfg.history_capacity, h->status);
+            h->partials, E->d_done, G, h->history, h->cfg.history_capacity, h->status, E->d_frames);
         cudaEventRecord(E->ev_join, E->side);
         h->launches += 1;
     }
@@ -1730,7 +1764,7 @@ void enqueue_advance(lbmp_handle* h, int l, int sub) {
         }
         k_amr_remap<S><<<nl, REMAP_THREADS, 0, rs>>>(D, U.dst, V.d_flags[V.fcur], fnext, h->box, h->d_ps, P.scale,
                                                     P.inv_scale, h->link_mask, h->link_blocks, h->status,
-                                                    (A)grad_refill_coef(h->cfg.refill, V.taup));
+                                                    (A)grad_refill_coef(h->cfg.refill, V.taup), E->d_frames);
         if (beside) {
             cudaEventRecord(E->ev_remap, E->side);
             E->remap_pending = true;
@@ -1826,6 +1860,8 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
     h->list = (int*)handle_alloc(h, sizeof(int) * (size_t)h->list_cap);
     E->boundary_blocks = (int)((B.cells + BND_CHUNK - 1) / BND_CHUNK);
     h->partials = (double*)handle_alloc(h, sizeof(double) * 6 * (size_t)E->boundary_blocks);
+    if (!E->d_frames) E->d_frames = (PFrames*)handle_alloc(h, sizeof(PFrames));
+    if (!E->d_frames) return LBMP_ERR_OOM;
     h->link_mask = (uint8_t*)handle_alloc(h, (size_t)B.cells);
     h->link_blocks = (int*)handle_alloc(h, sizeof(int) * (size_t)((B.cells + LINK_THREADS - 1) / LINK_THREADS));
     if (!h->list || !h->partials || !h->link_mask || !h->link_blocks) return LBMP_ERR_OOM;
@@ -1842,6 +1878,7 @@ lbmp_status amr_add_sphere(lbmp_handle* h) {
         return LBMP_ERR_CUDA;
     h->h2d += sizeof(ParticleState);
     h->has_particle = true;
+    h->frames_stale = true;
     amr_invalidate_ghosts(E);
     return regrid_now(h);
 }
@@ -1981,6 +2018,11 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
     if (E->graph_tau != h->tau) {
         amr_drop_graphs(E);
         E->graph_tau = h->tau;
+    }
+    if (h->has_particle && h->frames_stale) {   // the host changed the record: its frames first
+        k_pframes<<<1, 128, 0, h->stream>>>(h->d_ps, E->d_frames, view(E, E->lv[E->L - 1]), h->box);
+        h->launches += 1;
+        h->frames_stale = false;
     }
     auto enqueue = [&]() {
         // the coarser levels' streams join the step here and rejoin the caller's stream at its end

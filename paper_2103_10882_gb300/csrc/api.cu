@@ -149,6 +149,7 @@ lbmp_status read_status(lbmp_handle* h) {
 }
 
 lbmp_status upload_particle(lbmp_handle* h) {
+    h->frames_stale = true;
     LBMP_CK(h, cudaMemcpyAsync(h->d_ps, &h->h_ps, sizeof(ParticleState), cudaMemcpyHostToDevice, h->stream));
     LBMP_CK(h, cudaStreamSynchronize(h->stream));
     h->h2d += sizeof(ParticleState);

@@ -490,6 +490,64 @@ __device__ __forceinline__ void box_frame_init(BoxFrame& F, const int n[3], cons
     F.hi = wide ? 3.0e38f : (float)(rr + m);
 }
 
+// Both frames of the sphere's current state (the link frame in FP32 and in
+// FP64, and the box frame), formed once per step by the particle update, or
+// after the host changed the record, and read by the box kernels of the
+// refined step instead of each of their blocks forming them from the FP64
+// record (FP64 is slow on this part, and every block waited for it).
+__device__ __forceinline__ double particle_mass(const ParticleState& P);
+__device__ __forceinline__ double particle_inertia(const ParticleState& P);
+
+struct PFrames {
+    LinkFrame<float> lf;
+    LinkFrame<double> ld;
+    BoxFrame bf;
+    double inv[2];   // 1/m and 1/I (particle_mass, particle_inertia): fixed between changes by the host
+};
+
+template <typename A>
+__device__ __forceinline__ const LinkFrame<A>& pframe_link(const PFrames& F) {
+    if constexpr (sizeof(A) == 8) return F.ld;
+    else return F.lf;
+}
+
+// Forms F from the record P: the three frames by lane 0 of warps 0, 1 and 2
+// of the calling block (each is one FP64 sequence), the inverses by lanes 0
+// and 1 of warp 3; every thread of a block of at least 128 calls it.
+__device__ __forceinline__ void pframes_form(PFrames* __restrict__ F, const ParticleState& P, const int n[3],
+                                             const int periodic[3], const BoxDesc& B) {
+    if (threadIdx.x == 0) F->lf.init(P);
+    else if (threadIdx.x == 32) F->ld.init(P);
+    else if (threadIdx.x == 64) box_frame_init(F->bf, n, periodic, B, P);
+    else if (threadIdx.x == 96) F->inv[0] = 1.0 / particle_mass(P);
+    else if (threadIdx.x == 97) F->inv[1] = 1.0 / particle_inertia(P);
+}
+
+// The parts of F that follow the sphere along axis a (a = 0, 1, 2 by lanes
+// 0, 1, 2 of one warp) after the particle update: the same values as
+// pframes_form, from a shorter FP64 sequence (floor by one conversion, the
+// box origin from the fraction); the radius and the FP32 pre-test bounds do
+// not change during a run and keep the values pframes_form gave them.
+__device__ __forceinline__ void pframes_axis(PFrames* __restrict__ F, const ParticleState& P, const int n[3],
+                                             const BoxDesc& B, int a) {
+    const double xr = P.x[a];
+    const double x = fabs(xr) < 1e9 ? xr : 0.0;   // as box_frame_init: keep the box arithmetic in range
+    const int xi = __double2int_rd(xr), bi = __double2int_rd(x);
+    const double frac = xr - (double)xi, bfrac = x - (double)bi;
+    F->lf.Xi[a] = xi;
+    F->ld.Xi[a] = xi;
+    F->ld.Xh[a] = 0.5 - frac;
+    F->lf.Xh[a] = (float)(0.5 - frac);
+    F->lf.u[a] = (float)P.u[a];
+    F->lf.w[a] = (float)P.w[a];
+    F->ld.u[a] = P.u[a];
+    F->ld.w[a] = P.w[a];
+    F->bf.Xi[a] = bi;
+    F->bf.Xh[a] = (float)(0.5 - bfrac);
+    // floor(x - 1/2): x - 1/2 and x - floor(x) are exact
+    F->bf.o[a] = (B.E[a] >= n[a]) ? 0 : (bfrac < 0.5 ? bi - 1 : bi) - B.R;
+}
+
 // Box cell t (x fastest) -> cell p; false where the box leaves a wall-bounded axis.
 __device__ __forceinline__ bool box_cell(int t, const int n[3], const int periodic[3], const BoxDesc& B,
                                          const BoxFrame& F, int p[3]) {
@@ -659,26 +717,36 @@ __device__ __forceinline__ void particle_advance_axis(ParticleState& P, int a, d
 template <int NT>
 __device__ __forceinline__ void particle_block_update(ParticleState* __restrict__ ps, const double* partials,
                                                       int nblocks, const GridDesc& G, double* __restrict__ history,
-                                                      int hist_cap, int* __restrict__ status) {
+                                                      int hist_cap, int* __restrict__ status,
+                                                      const double* __restrict__ inv = nullptr) {
     static_assert(NT % 32 == 0 && NT >= 256, "eight warps share the work");
     constexpr int words = (int)(sizeof(ParticleState) / sizeof(int));
     __shared__ double sFT[6], sinv[2];
     __shared__ ParticleState sP;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (wid < 6) {
+        // lane l sums partials l, l + 64, ... into s0 and l + 32, l + 96, ... into s1, in that
+        // order; eight loads at a time are issued before their sums
         double s0 = 0.0, s1 = 0.0;
-        int b = lane;
-        for (; b + 32 < nblocks; b += 64) {
-            s0 += __ldcg(partials + (size_t)b * 6 + wid);
-            s1 += __ldcg(partials + (size_t)(b + 32) * 6 + wid);
+        for (int base = 0; base < nblocks; base += 256) {
+            double v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int b = base + lane + 32 * k;
+                v[k] = b < nblocks ? __ldcg(partials + (size_t)b * 6 + wid) : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+                if (base + lane + 32 * k < nblocks) s0 += v[k];
+                if (base + lane + 32 * (k + 1) < nblocks) s1 += v[k + 1];
+            }
         }
-        if (b < nblocks) s0 += __ldcg(partials + (size_t)b * 6 + wid);
         double t = s0 + s1;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
         if (lane == 0) sFT[wid] = t;
     } else if (wid == 6) {
-        if (lane < 2) sinv[lane] = 1.0 / (lane == 0 ? particle_mass(*ps) : particle_inertia(*ps));
+        if (lane < 2) sinv[lane] = inv ? inv[lane] : 1.0 / (lane == 0 ? particle_mass(*ps) : particle_inertia(*ps));
     } else if (wid == 7) {
         const int* srcw = reinterpret_cast<const int*>(ps);
         int* dstw = reinterpret_cast<int*>(&sP);
