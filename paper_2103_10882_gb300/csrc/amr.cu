@@ -202,8 +202,9 @@ struct GhostPull {
 // scaled values g * 2^s, which the collision takes in its SCALED form).  nb27 lists the pool
 // ids of block b's 26 neighbours (and itself at index 13).  GHOST: (b, c) is
 // an active ghost cell and gp says where static ghost cells lie upwind.
+// Returns whether a source was missing (no block), which the caller reports.
 template <typename S, bool GHOST = false>
-__device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
+__device__ __forceinline__ bool pull_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27,
                                           typename Store<S>::A g[19], GhostPull gp = GhostPull{}) {
     using A = typename Store<S>::A;
     const int lx = c & 15, ly = (c >> 4) & 15, lz = c >> 8;
@@ -243,22 +244,9 @@ __device__ __forceinline__ void pull_cell(const UpdateArgs<S>& U, int b, int c, 
         missing |= lost;
         g[q] = lost ? A(0) : v;
     }
-    if (missing) atomicOr(U.status, STATUS_AMR_MISSING);
+    return missing;
 }
 
-// Update of the real cell c of pool block b: pull and collide.  Hosts (the
-// cells next to the finer region) are left to the finer level's last
-// sub-step, which forms their coalesced populations.
-template <typename S, bool HAS_FINE>
-__device__ __forceinline__ void update_cell(const UpdateArgs<S>& U, int b, int c, const int* nb27) {
-    using A = typename Store<S>::A;
-    if (HAS_FINE && U.D.host[(size_t)b * B3 + c] == 1) return;
-    A g[19];
-    pull_cell<S>(U, b, c, nb27, g);
-    trt_collide<A, false, sizeof(S) == 2>(g, U.P, U.status);
-#pragma unroll
-    for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
-}
 
 // One launch per level step: the first gblocks CTAs stream the active ghost
 // cells of the level (glist: pool block << 12 | cell, eight consecutive
@@ -291,7 +279,7 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
             c = e & 4095;
             hp = U.ghost_host[i >> 3];
             const GhostPull gp{U.smask[i], hp >> 12, hp & 4095, i & 7, coalesce != 0};
-            pull_cell<S, true>(U, b, c, U.D.nbr + (size_t)b * 27, g, gp);
+            if (pull_cell<S, true>(U, b, c, U.D.nbr + (size_t)b * 27, g, gp)) atomicOr(U.status, STATUS_AMR_MISSING);
             if (!coalesce) {
 #pragma unroll
                 for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
@@ -326,22 +314,35 @@ __global__ void __launch_bounds__(UPD_THREADS, sizeof(S) == 8 ? 1 : UPD_MIN_CTAS
         }
         return;
     }
+    // Real cells: pull and collide.  The cell's mark is loaded beside the pulls rather than before
+    // them (a branch on it would hold the pulls back by one memory round trip); the pulls of a
+    // cell it then excludes are dropped.  The finest level's flags: 1 solid (stored as zero), 2
+    // fluid next to the sphere (k_amr_boundary's cells).  Hosts (levels with a finer level, mark 1)
+    // are left to the finer level's last sub-step, which forms their coalesced populations.
     __shared__ int nb27[27];
     constexpr int SPB = B3 / UPD_THREADS;   // CTAs per block
     const int b = (blockIdx.x - gblocks) / SPB;
+    const int c = ((blockIdx.x - gblocks) % SPB) * UPD_THREADS + threadIdx.x;
+    uint8_t mark = 0;
+    if (COUPLED) mark = U.solid[(size_t)b * B3 + c];
+    else if (HAS_FINE) mark = U.D.host[(size_t)b * B3 + c];
     if (threadIdx.x < 27) nb27[threadIdx.x] = U.D.nbr[b * 27 + threadIdx.x];
     __syncthreads();
-    const int c = ((blockIdx.x - gblocks) % SPB) * UPD_THREADS + threadIdx.x;
-    if (COUPLED) {   // finest level flags: 1 solid, 2 fluid next to the sphere (k_amr_boundary's cells)
-        const uint8_t f = U.solid[(size_t)b * B3 + c];
-        if (f == FLAG_SOLID) {
+    A g[19];
+    const bool missing = pull_cell<S>(U, b, c, nb27, g);
+    if (COUPLED) {
+        if (mark == FLAG_SOLID) {
 #pragma unroll
             for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), A(0));
             return;
         }
-        if (f == FLAG_BOUNDARY) return;
+        if (mark == FLAG_BOUNDARY) return;
     }
-    update_cell<S, HAS_FINE>(U, b, c, nb27);
+    if (HAS_FINE && mark == 1) return;
+    if (missing) atomicOr(U.status, STATUS_AMR_MISSING);
+    trt_collide<A, false, sizeof(S) == 2>(g, U.P, U.status);
+#pragma unroll
+    for (int q = 0; q < 19; ++q) Store<S>::store_raw(U.dst + paddr(b, q, c), g[q]);
 }
 
 // ---------------------------------------------------------------- coupling
@@ -524,11 +525,12 @@ __device__ __forceinline__ void refill_cell_warp(const LevelView& D, S* __restri
         if (wrap3(v, D) && !ball_flag(v, D.n, D.periodic, F, P)) {
             int vc;
             const int vb = locate(D, v, &vc);
-            if (vb >= 0 && vb < D.nreal && fcur[(size_t)vb * B3 + vc] != FLAG_SOLID) {
-                ok = true;
+            if (vb >= 0 && vb < D.nreal) {
+                // the populations are loaded beside the flag (not after it): a solid neighbour's are dropped
                 A gp[19];
 #pragma unroll
                 for (int p = 0; p < 19; ++p) gp[p] = Store<S>::load(pops + paddr(vb, p, vc), inv_scale);
+                ok = fcur[(size_t)vb * B3 + vc] != FLAG_SOLID;
                 r = A(1);
 #pragma unroll
                 for (int p = 0; p < 19; ++p) r += gp[p];
