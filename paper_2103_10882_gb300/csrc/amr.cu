@@ -43,10 +43,12 @@ namespace {
 constexpr int BS = 16;
 constexpr int B3 = BS * BS * BS;
 constexpr int MAXL = 6;
-// Level update CTAs: half a z-slice of a block each (128 cells); at 12 resident CTAs per SM (40
-// registers) the short launches of the finer levels end in smaller waves than with whole slices.
+// Level update CTAs: half a z-slice of a block each (128 cells); the short launches of the finer
+// levels end in smaller waves than with whole slices.  10 resident CTAs per SM asked of the
+// compiler (48 registers): 3% shorter launches than 12 (40 registers, spills in the ghost lanes),
+// the same step time; 16 was 10% slower.
 constexpr int UPD_THREADS = 128;
-constexpr int UPD_MIN_CTAS = 12;     // resident level-update CTAs per SM asked of the compiler (FP32/FP16 arithmetic)
+constexpr int UPD_MIN_CTAS = 10;     // FP32/FP16 arithmetic
 constexpr int STATUS_AMR_MISSING = 8;    // a pull found no source cell
 // Finest-level cell flags: fluid, solid (centre inside the sphere), and
 // fluid with a solid D3Q19 neighbour (updated by k_amr_boundary).
