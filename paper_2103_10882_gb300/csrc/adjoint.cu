@@ -141,22 +141,32 @@ __device__ __forceinline__ void trt_adjoint(const A (&h)[19], A (&lam)[19], cons
 }
 
 // Block sum of the per-thread parameter parts, added to this block's FP64
-// accumulator (one slot per block, so the order of additions is fixed).
+// accumulator (one slot per block, so the order of additions is fixed).  In
+// FP32 the warps' sums are added as a double-float pair (TwoSum, exact to
+// far below FP32 resolution) and converted once: FP64 arithmetic is slow on
+// this part and every block ends with it.
 template <typename A>
 __device__ __forceinline__ void accumulate_parts(const A part[5], double* __restrict__ acc) {
-    __shared__ double red[5][AT / 32];
+    __shared__ A red[5][AT / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
         A v = part[c];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) red[c][wid] = (double)v;
+        if (lane == 0) red[c][wid] = v;
     }
     __syncthreads();
     if (threadIdx.x < 5) {
-        double s = 0.0;
-        for (int w = 0; w < AT / 32; ++w) s += red[threadIdx.x][w];
+        double s;
+        if constexpr (sizeof(A) == 4) {
+            float h = 0.0f, l = 0.0f;
+            for (int w = 0; w < AT / 32; ++w) df_add(h, l, red[threadIdx.x][w], 0.0f);
+            s = (double)h + (double)l;
+        } else {
+            s = 0.0;
+            for (int w = 0; w < AT / 32; ++w) s += red[threadIdx.x][w];
+        }
         acc[(size_t)blockIdx.x * 5 + threadIdx.x] += s;
     }
 }
@@ -238,24 +248,26 @@ __global__ void __launch_bounds__(AT, sizeof(S) == 8 ? 1 : ADJ_MIN_CTAS)
     const size_t n = (size_t)G.n;
     A part[5] = {A(0), A(0), A(0), A(0), A(0)};
     if (x < G.n) {
+        // the cell's kind is loaded beside the 38 loads of the plain case (a branch on it would
+        // hold them back by one memory round trip); a cell of another kind drops them
         const uint8_t kd = kind[x];
+        const int i = (int)(x % G.nx), j = (int)((x / G.nx) % G.ny), k = (int)(x / ((long long)G.nx * G.ny));
+        // xs[1 + d] = i - d: the pull source x - c_q at index 1 + c, x + c_q at 1 - c
+        const int xs[3] = {wrapc(i + 1, G.nx), i, wrapc(i - 1, G.nx)};
+        const int ys[3] = {wrapc(j + 1, G.ny), j, wrapc(j - 1, G.ny)};
+        const int zs[3] = {wrapc(k + 1, G.nz), k, wrapc(k - 1, G.nz)};
+        A h[19], lam[19];
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            const size_t src = (size_t)xs[1 + cx(q)] + (size_t)G.nx * ((size_t)ys[1 + cy(q)] + (size_t)G.ny * zs[1 + cz(q)]);
+            const size_t dn = (size_t)xs[1 - cx(q)] + (size_t)G.nx * ((size_t)ys[1 - cy(q)] + (size_t)G.ny * zs[1 - cz(q)]);
+            h[q] = Store<S>::load(gprev + (size_t)q * n + src, A(1));
+            lam[q] = nu_next[(size_t)q * n + dn];
+        }
         if (kd == KIND_SOLID) {
 #pragma unroll
             for (int q = 0; q < 19; ++q) nu_out[(size_t)q * n + x] = A(0);
         } else if (kd == KIND_PLAIN) {
-            const int i = (int)(x % G.nx), j = (int)((x / G.nx) % G.ny), k = (int)(x / ((long long)G.nx * G.ny));
-            // xs[1 + d] = i - d: the pull source x - c_q at index 1 + c, x + c_q at 1 - c
-            const int xs[3] = {wrapc(i + 1, G.nx), i, wrapc(i - 1, G.nx)};
-            const int ys[3] = {wrapc(j + 1, G.ny), j, wrapc(j - 1, G.ny)};
-            const int zs[3] = {wrapc(k + 1, G.nz), k, wrapc(k - 1, G.nz)};
-            A h[19], lam[19];
-#pragma unroll
-            for (int q = 0; q < 19; ++q) {
-                const size_t src = (size_t)xs[1 + cx(q)] + (size_t)G.nx * ((size_t)ys[1 + cy(q)] + (size_t)G.ny * zs[1 + cz(q)]);
-                const size_t dn = (size_t)xs[1 - cx(q)] + (size_t)G.nx * ((size_t)ys[1 - cy(q)] + (size_t)G.ny * zs[1 - cz(q)]);
-                h[q] = Store<S>::load(gprev + (size_t)q * n + src, A(1));
-                lam[q] = nu_next[(size_t)q * n + dn];
-            }
             trt_adjoint<A>(h, lam, P, part);
 #pragma unroll
             for (int q = 0; q < 19; ++q) nu_out[(size_t)q * n + x] = lam[q];
