@@ -174,6 +174,37 @@ def test_refined_sphere_fp64(orc, lib):
     assert len(g.links()[0]) > 0
 
 
+def test_host_changes_between_steps_fp64(orc, lib):
+    """The host changes the particle record between steps (a new sphere
+    velocity) and then the fluid (re-initialised): the next steps re-form the
+    sphere's frames and explode the active ghost cells again, and stay
+    within 1e-10 of the oracle doing the same on three levels."""
+    pos = (30.7, 33.2, 31.6)
+    o, g = pair(orc, lib, (16, 16, 16), 3, tau=0.7, sphere=(pos, 10.0, 0.3, 0.5), gravity=(0, 0, -2e-4))
+    o.init_equilibrium()
+    g.init_fluid()
+    o.step(2)
+    g.step(2)
+    u, w = (0.012, -0.02, 0.015), (0.001, 0.0, -0.002)
+    o.set_particle_velocity(u, w)
+    g.set_particle_velocity(u, w)
+    o.step(2)
+    g.step(2)
+    cells_close(o, g, 3, 1e-10)
+    same_integer_work(o, g, 3)
+    o.init_equilibrium()
+    g.init_fluid()
+    o.step(2)
+    g.step(2)
+    cells_close(o, g, 3, 1e-10)
+    same_integer_work(o, g, 3)
+    ho, hg = o.history(), g.history()
+    assert ho.shape == hg.shape == (24, 15)
+    Fs = 0.7 * 2e-4 * math.pi * 1000 / 6
+    np.testing.assert_allclose(hg[:, 0:6], ho[:, 0:6], rtol=0, atol=1e-10 * Fs)
+    np.testing.assert_allclose(hg[:, 6:15], ho[:, 6:15], rtol=1e-10, atol=1e-10)
+
+
 def test_moving_sphere_with_regrids(orc, lib):
     """A fast light sphere crosses block boundaries; both sides regrid every
     coarse step: block maps stay bit-exact and populations within 1e-10."""
