@@ -1094,10 +1094,11 @@ struct AmrEngine {
     double box_lo[3] = {0, 0, 0}, box_hi[3] = {0, 0, 0};
     int boundary_blocks = 1;
     long long coarse_steps = 0;
-    // one captured level-0 step per parity of the level-0 buffers; dropped
-    // whenever the layout or a kernel parameter changes
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    long long graph_launches = 0, graph_updates = 0;
+    // captured runs of one and of two level-0 steps ([steps - 1]) per parity
+    // of the level-0 buffers; dropped whenever the layout or a kernel
+    // parameter changes
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    long long graph_launches[2] = {0, 0}, graph_updates[2] = {0, 0};
     double graph_tau = 0.0;
     cudaStream_t capture_stream = nullptr;   // private stream used only for capturing
     int* d_done = nullptr;   // last-block-done counter of the boundary kernel (zero between launches)
@@ -1138,11 +1139,12 @@ bool amr_ghosts_valid(const AmrEngine* E) {
 }
 
 void amr_drop_graphs(AmrEngine* E) {
-    for (int p = 0; p < 2; ++p)
-        if (E->graph[p]) {
-            cudaGraphExecDestroy(E->graph[p]);
-            E->graph[p] = nullptr;
-        }
+    for (int k = 0; k < 2; ++k)
+        for (int p = 0; p < 2; ++p)
+            if (E->graph[k][p]) {
+                cudaGraphExecDestroy(E->graph[k][p]);
+                E->graph[k][p] = nullptr;
+            }
 }
 
 namespace {
@@ -2028,8 +2030,10 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
         h->launches += 1;
         h->frames_stale = false;
     }
-    auto enqueue = [&]() {
-        // the coarser levels' streams join the step here and rejoin the caller's stream at its end
+    // k consecutive level-0 steps.  The coarser levels' streams join here and rejoin the caller's
+    // stream at the end; between two steps of one call the stream events alone order the work, so
+    // the second step's coarser updates can start beside the first step's last finest sub-steps.
+    auto enqueue = [&](int k) {
         const bool fork = !h->profiling && E->L > 1;
         if (fork) {
             cudaEventRecord(E->ev_begin, h->stream);
@@ -2038,29 +2042,37 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
                 cudaEventRecord(E->ev_state[l], E->lstream[l]);
             }
         }
-        with_storage_amr(h->cfg.precision, [&](auto tag) {
-            using S = std::remove_pointer_t<decltype(tag)>;
-            enqueue_advance<S>(h, 0, 0);
-        });
-        if (E->remap_pending) {   // the step ends with everything on the caller's stream
+        for (int j = 0; j < k; ++j)
+            with_storage_amr(h->cfg.precision, [&](auto tag) {
+                using S = std::remove_pointer_t<decltype(tag)>;
+                enqueue_advance<S>(h, 0, 0);
+            });
+        if (E->remap_pending) {   // the steps end with everything on the caller's stream
             cudaStreamWaitEvent(h->stream, E->ev_remap, 0);
             E->remap_pending = false;
         }
         if (fork)
             for (int l = 0; l + 1 < E->L; ++l) cudaStreamWaitEvent(h->stream, E->ev_state[l], 0);
     };
-    for (int i = 0; i < n; ++i) {
+    auto regrid_due = [&](long long steps) {
+        return h->cfg.regrid_interval > 0 && (h->has_particle || E->sensor_sigma > 0.0) &&
+               steps % h->cfg.regrid_interval == 0;
+    };
+    for (int i = 0; i < n;) {
+        // two steps per graph where no regrid falls between them (one per profiled step)
+        const int k = (!h->profiling && n - i >= 2 && !regrid_due(E->coarse_steps + 1)) ? 2 : 1;
         if (h->profiling) {   // per-kernel events: plain launches
             const long long ev_step = profile_mark(h);
-            enqueue();
+            enqueue(k);
             profile_step(h, ev_step, profile_mark(h));
         } else if (!amr_ghosts_valid(E)) {   // a step that explodes ghost cells is not the one a graph repeats
-            enqueue();
+            enqueue(k);
         } else {
             const int par = E->lv[0].cur;
-            if (!E->graph[par]) {
-                // capture one level-0 step on a private stream (the caller's
-                // stream may be the legacy default stream, which cannot be
+            cudaGraphExec_t& gx = E->graph[k - 1][par];
+            if (!gx) {
+                // capture the steps on a private stream (the caller's stream
+                // may be the legacy default stream, which cannot be
                 // captured); enqueue() advances the host-side buffer indices
                 // exactly as the replayed graph will
                 if (!E->capture_stream &&
@@ -2075,7 +2087,7 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
                     h->stream = user;
                     return amr_cuda_error(h, "cudaStreamBeginCapture");
                 }
-                enqueue();
+                enqueue(k);
                 cudaGraph_t g = nullptr;
                 e = cudaStreamEndCapture(h->stream, &g);
                 h->stream = user;
@@ -2084,25 +2096,23 @@ lbmp_status amr_step(lbmp_handle* h, int n) {
                 e = cudaGraphInstantiateWithFlags(&ge, g, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) return amr_cuda_error(h, "cudaGraphInstantiate");
-                E->graph[par] = ge;
-                E->graph_launches = h->launches - l0;
-                E->graph_updates = h->updates - u0;
+                gx = ge;
+                E->graph_launches[k - 1] = h->launches - l0;
+                E->graph_updates[k - 1] = h->updates - u0;
                 if (cudaGraphLaunch(ge, h->stream) != cudaSuccess) return amr_cuda_error(h, "cudaGraphLaunch");
             } else {
-                if (cudaGraphLaunch(E->graph[par], h->stream) != cudaSuccess)
-                    return amr_cuda_error(h, "cudaGraphLaunch");
-                // the same buffer flips as the captured enqueue
-                for (int l = 0; l < E->L; ++l)
-                    if ((1LL << l) & 1) E->lv[l].cur = 1 - E->lv[l].cur;
-                h->launches += E->graph_launches;
-                h->updates += E->graph_updates;
+                if (cudaGraphLaunch(gx, h->stream) != cudaSuccess) return amr_cuda_error(h, "cudaGraphLaunch");
+                // the same buffer flips as the captured enqueue: level l flips k 2^l times
+                if (k & 1) E->lv[0].cur = 1 - E->lv[0].cur;
+                h->launches += E->graph_launches[k - 1];
+                h->updates += E->graph_updates[k - 1];
             }
         }
-        E->coarse_steps += 1;
-        h->steps += 1;
+        E->coarse_steps += k;
+        h->steps += k;
+        i += k;
         if (cudaGetLastError() != cudaSuccess) return amr_cuda_error(h, "kernel launch");
-        if (h->cfg.regrid_interval > 0 && (h->has_particle || E->sensor_sigma > 0.0) &&
-            E->coarse_steps % h->cfg.regrid_interval == 0) {
+        if (regrid_due(E->coarse_steps)) {
             const lbmp_status s = amr_regrid(h);
             if (s != LBMP_OK) return s;
         }
