@@ -122,8 +122,13 @@ void enqueue_step(lbmp_handle* h) {
 lbmp_status read_status(lbmp_handle* h) {
     int st = 0;
     LBMP_CK(h, cudaMemcpyAsync(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    // the particle record comes back with the status word (one synchronisation), so that reading
+    // it right after a step costs no second one
+    const bool with_ps = h->has_particle && !h->batch;
+    if (with_ps) LBMP_CK(h, cudaMemcpyAsync(&h->h_ps, h->d_ps, sizeof(ParticleState), cudaMemcpyDeviceToHost, h->stream));
     LBMP_CK(h, cudaStreamSynchronize(h->stream));
-    h->d2h += sizeof(int);
+    h->d2h += sizeof(int) + (with_ps ? sizeof(ParticleState) : 0);
+    h->ps_current = with_ps;
     if (st != 0) {
         int zero = 0;
         LBMP_CK(h, cudaMemcpyAsync(h->status, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
@@ -617,6 +622,7 @@ lbmp_status lbmp_gather_populations(lbmp_handle* h, const int64_t* cells, size_t
 
 lbmp_status lbmp_step_async(lbmp_handle* h, int n) {
     if (!h || n < 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_step: bad argument");
+    h->ps_current = false;
     if (h->amr) {
         const lbmp_status st = amr_step(h, n);
         if (st != LBMP_OK) return fail(h, st, "lbmp_step: " + h->err);
@@ -657,8 +663,10 @@ lbmp_status lbmp_get_particle(lbmp_handle* h, int id, double out[24]) {
         if (batch_get_particle(h, id, &tmp) != LBMP_OK) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: no such simulation");
     } else {
         if (!h->has_particle || id != 0) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_get_particle: no such sphere");
-        lbmp_status s = download_particle(h);
-        if (s != LBMP_OK) return s;
+        if (!h->ps_current) {
+            lbmp_status s = download_particle(h);
+            if (s != LBMP_OK) return s;
+        }
         tmp = h->h_ps;
     }
     const ParticleState& P = tmp;
@@ -1103,6 +1111,7 @@ lbmp_status lbmp_load(lbmp_handle* h, const char* path) {
 lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int checkpoint_interval, int axis,
                               double* J, double* forces) {
     if (!h) return LBMP_ERR_INVALID_ARG;
+    h->ps_current = false;
     if (!u0 || !J) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_forward: NULL argument");
     if (nsteps < 1 || checkpoint_interval < 1 || axis < 0 || axis > 2)
         return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_forward: need nsteps >= 1, checkpoint_interval >= 1, axis 0..2");
@@ -1120,6 +1129,7 @@ lbmp_status lbmp_drag_forward(lbmp_handle* h, const double* u0, int nsteps, int 
 lbmp_status lbmp_drag_backward(lbmp_handle* h, const double* dJ, double* grad_tau, double* grad_force,
                                double* grad_u0) {
     if (!h) return LBMP_ERR_INVALID_ARG;
+    h->ps_current = false;
     if (!dJ) return fail(h, LBMP_ERR_INVALID_ARG, "lbmp_drag_backward: NULL dJ");
     std::string why;
     lbmp_status s = adjoint_check(h, &why);

@@ -152,6 +152,7 @@ struct lbmp_handle {
     lbmp::BoxDesc box;
     bool has_particle = false;
     bool frames_stale = true;            // the host changed the particle record since the refined step formed its frames
+    bool ps_current = false;             // h_ps equals the device record (read with the status after a step)
     double tau = 0.6, magic = 3.0 / 16.0;
     double body_force[3] = {0, 0, 0};
     long long steps = 0, updates = 0, launches = 0, h2d = 0, d2h = 0;
