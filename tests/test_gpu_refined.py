@@ -339,3 +339,37 @@ def test_sensor_regrids_walls_100_finest_steps_fp64(orc, lib):
     Fs = (1 - pi) * gz * math.pi * D ** 3 / 6
     np.testing.assert_allclose(hg[:, 0:6], ho[:, 0:6], rtol=0, atol=1e-10 * Fs)
     np.testing.assert_allclose(hg[:, 6:9], ho[:, 6:9], rtol=1e-10, atol=1e-10)
+
+
+def test_headline_size_fp64(orc, lib):
+    """The bench's refined workload at its full size (level-0 64x64x256 in
+    16^3 blocks, three levels, d = 20 finest cells, pi_p = 0.5, Ga = 200,
+    walls on x and y, curl sensor on), built by the bench's own helper and
+    stepped in the launch configuration the bench times (CUDA graphs of two
+    level-0 steps, the coarser levels on their own streams), in the FP64
+    path: after three level-0 steps (twelve coupled finest sub-steps) the
+    block maps, finest flags and links are bit-exact with the oracle on the
+    host cores and every population of every level is within 1e-10."""
+    import os
+    import bench
+    w = bench.REFINED
+    tau, gm = bench.ga_tau_g(w["ga"], w["u_g"], w["diameter"], w["density_ratio"])
+    orc.set_threads(os.cpu_count() or 1)
+    o = orc.RefinedSim(w["shape"], w["levels"], tau=tau, periodic=(0, 0, 1))
+    o.add_sphere(bench.refined_start(w["shape"], w["levels"], w["diameter"]), w["diameter"], w["density_ratio"],
+                 cv=w["cv"])
+    o.set_gravity((0, 0, -gm))
+    o.set_sensor(*w["sensor"])
+    o.init_equilibrium()
+    g = bench.refined_sim(lib, "fp64")
+    o.step(3)
+    g.step(3)
+    same_integer_work(o, g, w["levels"])
+    cells_close(o, g, w["levels"], 1e-10)
+    ho, hg = o.history(), g.history()
+    assert ho.shape == hg.shape == (12, 15)
+    Fg = abs(w["density_ratio"] - 1) * gm * math.pi * w["diameter"] ** 3 / 6
+    np.testing.assert_allclose(hg[:, 0:6], ho[:, 0:6], rtol=0, atol=1e-10 * Fg)
+    np.testing.assert_allclose(hg[:, 6:15], ho[:, 6:15], rtol=1e-10, atol=1e-12)
+    o.close()
+    g.close()
