@@ -37,20 +37,45 @@ __device__ __forceinline__ double link_delta(const double d[3], int q, double r)
 // quadratic terms, which then take one factor 2^-s (P.inv_scale).
 // MRT_MODE: -1 decides TRT or MRT from P.db at run time, 0 is TRT only, 1
 // MRT only (kernels that know which one runs carry no code of the other).
-template <typename A, bool FORCED, bool SCALED = false, int MRT_MODE = -1>
+template <typename A, bool FORCED, bool SCALED = false, int MRT_MODE = -1, bool PAIRS = false>
 __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& P, int* status) {
     static_assert(!(FORCED && SCALED), "the scaled form is for the unforced collision");
     const A q2 = SCALED ? P.inv_scale : A(1);
-    A drho = A(0), jx = A(0), jy = A(0), jz = A(0);
+    // PAIRS: the moments from the sums and differences of the opposite pairs (q, q + 1), q odd,
+    // which the relaxation below uses again (c_{q+1} = -c_q: a pair adds its sum to the density and
+    // its difference times c_q to the momentum).  Fewer instructions, for the issue-bound FP16 bulk
+    // update; 18 more live values, which the register-capped level update pays for in spills.
+    A ps[9], pd[9];
+    A drho = g[0], jx = A(0), jy = A(0), jz = A(0);
+    if (PAIRS) {
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        drho += g[q];
-        if (cx(q) == 1) jx += g[q];
-        if (cx(q) == -1) jx -= g[q];
-        if (cy(q) == 1) jy += g[q];
-        if (cy(q) == -1) jy -= g[q];
-        if (cz(q) == 1) jz += g[q];
-        if (cz(q) == -1) jz -= g[q];
+        for (int k = 0; k < 9; ++k) {
+            ps[k] = g[2 * k + 1] + g[2 * k + 2];
+            pd[k] = g[2 * k + 1] - g[2 * k + 2];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int q = 2 * k + 1;
+            drho += ps[k];
+            if (cx(q) == 1) jx += pd[k];
+            if (cx(q) == -1) jx -= pd[k];
+            if (cy(q) == 1) jy += pd[k];
+            if (cy(q) == -1) jy -= pd[k];
+            if (cz(q) == 1) jz += pd[k];
+            if (cz(q) == -1) jz -= pd[k];
+        }
+    } else {
+        drho = A(0);
+#pragma unroll
+        for (int q = 0; q < 19; ++q) {
+            drho += g[q];
+            if (cx(q) == 1) jx += g[q];
+            if (cx(q) == -1) jx -= g[q];
+            if (cy(q) == 1) jy += g[q];
+            if (cy(q) == -1) jy -= g[q];
+            if (cz(q) == 1) jz += g[q];
+            if (cz(q) == -1) jz -= g[q];
+        }
     }
     A ux = jx, uy = jy, uz = jz;
     if (FORCED) {
@@ -82,8 +107,8 @@ __device__ __forceinline__ void trt_collide(A (&g)[19], const CollideParams<A>& 
         const A w = wgt<A>(q);
         const A ep = w * (drho + A(4.5) * q2 * cu * cu - A(1.5) * uu);
         const A em = w * (A(3) * cu);
-        const A gp = A(0.5) * (g[q] + g[q + 1]);
-        const A gm = A(0.5) * (g[q] - g[q + 1]);
+        const A gp = A(0.5) * (PAIRS ? ps[q >> 1] : g[q] + g[q + 1]);
+        const A gm = A(0.5) * (PAIRS ? pd[q >> 1] : g[q] - g[q + 1]);
         const A dp = sp * (gp - ep);
         const A dm = sm * (gm - em);
         if (mrt) {

@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(BULK2_THREADS)
         g1[q] = b;
     }
     if (!valid) return;
-    trt_collide<float, false, true, MRT ? 1 : 0>(g0, P, status);
-    trt_collide<float, false, true, MRT ? 1 : 0>(g1, P, status);
+    trt_collide<float, false, true, MRT ? 1 : 0, true>(g0, P, status);
+    trt_collide<float, false, true, MRT ? 1 : 0, true>(g1, P, status);
 #pragma unroll
     for (int q = 0; q < 19; ++q)
         __stcs(reinterpret_cast<__half2*>(dst + (size_t)q * n + cell), __floats2half2_rn(g0[q], g1[q]));
