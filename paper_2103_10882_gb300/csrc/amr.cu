@@ -8,15 +8,19 @@
 // resolution) in one pool, real blocks first, both in block-position order.
 // One level-l step (recursive, finer levels sub-cycled twice, Rohde's scheme
 // named in Sec. 4.1):
-//   k_explode   active ghost cells of level l+1 <- post-collision level-l
-//               cell containing them (into the buffer of the first sub-step)
+//   explosion   active ghost cells of level l+1 <- post-collision level-l
+//               cell containing them (into the buffer of the first sub-step):
+//               written by level l+1's previous last sub-step, which forms
+//               those values; k_explode only after a change outside a step
 //   (two level-(l+1) steps)
-//   k_update    real level-l cells: pull from real/ghost neighbours, or, for
-//               hosts (neighbours of the finer region), the mean of their
-//               eight ghost sub-cells (coalescence); then TRT collide.  Active
-//               ghost cells stream without colliding; the static ghost cells
-//               beyond them stand for coarse content translating rigidly and
-//               are read from the coarse level, not stored.
+//   k_update    real level-l cells but the hosts: pull from real/ghost
+//               neighbours, then TRT collide.  Active ghost cells stream
+//               without colliding; at level l+1's last sub-step they form
+//               the hosts' populations (the mean of their eight sub-cells,
+//               coalescence) and collide them.  The static ghost cells beyond
+//               them stand for coarse content translating rigidly and are read
+//               from the coarse level, not stored.  Level l's update runs on
+//               its own stream beside level l+1's sub-steps.
 //   finest level: k_amr_boundary (CLI links + momentum-exchange partials),
 //               particle update, remap (flags, refill, boundary cells).
 // The layout (which blocks exist at which level) is integer work done on the
