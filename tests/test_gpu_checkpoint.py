@@ -41,17 +41,21 @@ def test_uniform_resume_is_exact(lib, tmp_path):
     b.close()
 
 
-def test_refined_resume_is_exact(lib, tmp_path):
+@pytest.mark.parametrize("levels,shape,pos,gz", [(2, (32, 32, 48), (30.3, 31.6, 40.6), -1e-2),
+                                                 (3, (16, 16, 32), (30.7, 33.2, 60.6), -2e-3)])
+def test_refined_resume_is_exact(lib, tmp_path, levels, shape, pos, gz):
+    """Two and three levels: the loaded handle explodes its ghost cells and
+    forms the sphere's frames again before its first step."""
     path = str(tmp_path / "r.ckpt")
 
     def make():
-        s = lib.Simulation((32, 32, 48), precision="fp32", tau=0.6, levels=2, regrid_interval=3)
+        s = lib.Simulation(shape, precision="fp32", tau=0.6, levels=levels, regrid_interval=3)
         s.set_refinement_sensor(1e-3, 0.2)
         return s
 
     a = make()
-    a.add_sphere((30.3, 31.6, 40.6), 8.0, 0.2, cv=0.5)
-    a.set_gravity((0, 0, -1e-2))
+    a.add_sphere(pos, 8.0, 0.2, cv=0.5)
+    a.set_gravity((0, 0, gz))
     a.init_fluid()
     a.step(7)
     a.save(path)
@@ -59,7 +63,7 @@ def test_refined_resume_is_exact(lib, tmp_path):
     b = make()
     b.load(path)
     b.step(8)
-    for l in range(2):
+    for l in range(levels):
         assert np.array_equal(a.block_map(l), b.block_map(l))
         xa, ga = a.level_cells(l)
         xb, gb = b.level_cells(l)
