@@ -154,7 +154,10 @@ lbmp_status lbmp_gather_populations(lbmp_handle* h, const int64_t* cells, size_t
 /* Advances n coupled steps (Algorithm 1): stream + collide with CLI and
  * momentum-exchange forces, force averaging, gravity, virtual force and
  * Velocity Verlet, then the remap with equilibrium refill.  Asynchronous on
- * the handle's stream except for a status check every call. */
+ * the handle's stream except for a status check every call, which also
+ * brings the particle record back (a following lbmp_get_particle then needs
+ * no second synchronisation).  Refined grids replay level-0 steps from CUDA
+ * graphs of one or two steps. */
 lbmp_status lbmp_step(lbmp_handle* h, int n);
 /* Same as lbmp_step but does not read the device status word (fully
  * asynchronous); lbmp_check_status reads it later. */
